@@ -133,15 +133,19 @@ def hf_direction(n) -> int:
 
 
 # --- steps of the method --------------------------------------------------------
-def advect(g, alpha, u, v, w, dt: float, step_index: int):
+def advect(g, alpha, u, v, w, dt: float, step_index: int, fluxes: bool = False):
+    """Returns (alpha_new, report) or, with fluxes=True, (alpha_new, (fx, fy, fz), report)."""
     a = _f64(alpha).copy()
+    _, us, vs, ws = shapes(g)
+    fx, fy, fz = np.zeros(us), np.zeros(vs), np.zeros(ws)
     rep = Report()
     G = _grid(g)
     st = lib().or_advect(ctypes.byref(G), _ptr(a), _ptr(_f64(u)), _ptr(_f64(v)), _ptr(_f64(w)),
-                         ctypes.c_double(dt), ctypes.c_long(step_index), ctypes.byref(rep))
+                         ctypes.c_double(dt), ctypes.c_long(step_index), _ptr(fx), _ptr(fy),
+                         _ptr(fz), ctypes.byref(rep))
     if st != 0:
         raise RuntimeError(f"or_advect failed ({st})")
-    return a, rep.as_dict()
+    return (a, (fx, fy, fz), rep.as_dict()) if fluxes else (a, rep.as_dict())
 
 
 def curvature(g, alpha):
@@ -198,31 +202,30 @@ def solve(g, bx, by, bz, b, P0=None, rtol: float = 1e-12, max_iter: int = 200000
     return P, rep.as_dict(), st
 
 
-def momentum(g, p, alpha_n, u, v, w, dt: float):
+def predict(g, p, alpha_n, alpha_np1, uc, vc, wc, u, v, w, fx, fy, fz, dt: float):
+    """Cell-centred intermediate velocity (steps 8-9)."""
+    cs = shapes(g)[0]
+    out = [np.zeros(cs) for _ in range(3)]
+    G, Ph = _grid(g), _phys(p)
+    st = lib().or_predict(ctypes.byref(G), ctypes.byref(Ph), _ptr(_f64(alpha_n)),
+                          _ptr(_f64(alpha_np1)), _ptr(_f64(uc)), _ptr(_f64(vc)), _ptr(_f64(wc)),
+                          _ptr(_f64(u)), _ptr(_f64(v)), _ptr(_f64(w)), _ptr(_f64(fx)),
+                          _ptr(_f64(fy)), _ptr(_f64(fz)), ctypes.c_double(dt), *map(_ptr, out))
+    if st != 0:
+        raise RuntimeError(f"or_predict failed ({st})")
+    return tuple(out)
+
+
+def cell_to_face(g, uc, vc, wc):
+    """Face velocities as the linear average of the two cells (step 10)."""
     _, us, vs, ws = shapes(g)
-    Mu, Mv, Mw = np.zeros(us), np.zeros(vs), np.zeros(ws)
-    G, Ph = _grid(g), _phys(p)
-    st = lib().or_momentum(ctypes.byref(G), ctypes.byref(Ph), _ptr(_f64(alpha_n)), _ptr(_f64(u)),
-                           _ptr(_f64(v)), _ptr(_f64(w)), ctypes.c_double(dt), _ptr(Mu), _ptr(Mv),
-                           _ptr(Mw))
+    u, v, w = np.zeros(us), np.zeros(vs), np.zeros(ws)
+    G = _grid(g)
+    st = lib().or_cell_to_face(ctypes.byref(G), _ptr(_f64(uc)), _ptr(_f64(vc)), _ptr(_f64(wc)),
+                               _ptr(u), _ptr(v), _ptr(w))
     if st != 0:
-        raise RuntimeError(f"or_momentum failed ({st})")
-    return Mu, Mv, Mw
-
-
-def divide_rho(g, p, alpha_np1, Mu, Mv, Mw):
-    u, v, w = _f64(Mu).copy(), _f64(Mv).copy(), _f64(Mw).copy()
-    G, Ph = _grid(g), _phys(p)
-    st = lib().or_divide_rho(ctypes.byref(G), ctypes.byref(Ph), _ptr(_f64(alpha_np1)), _ptr(u),
-                             _ptr(v), _ptr(w))
-    if st != 0:
-        raise RuntimeError(f"or_divide_rho failed ({st})")
+        raise RuntimeError(f"or_cell_to_face failed ({st})")
     return u, v, w
-
-
-def predict(g, p, alpha_n, alpha_np1, u, v, w, dt: float):
-    """Intermediate face velocities u_hat (steps 8-10)."""
-    return divide_rho(g, p, alpha_np1, *momentum(g, p, alpha_n, u, v, w, dt))
 
 
 def rhs(g, bx, by, bz, u, v, w, sx, sy, sz, dt: float):
@@ -236,37 +239,40 @@ def rhs(g, bx, by, bz, u, v, w, sx, sy, sz, dt: float):
     return b
 
 
-def correct(g, bx, by, bz, P, sx, sy, sz, dt: float, u, v, w):
-    u, v, w = _f64(u).copy(), _f64(v).copy(), _f64(w).copy()
+def correct(g, bx, by, bz, P, sx, sy, sz, dt: float, uc, vc, wc, u, v, w):
+    uc, vc, wc, u, v, w = (_f64(x).copy() for x in (uc, vc, wc, u, v, w))
     rep = Report()
     G = _grid(g)
     st = lib().or_correct(ctypes.byref(G), _ptr(_f64(bx)), _ptr(_f64(by)), _ptr(_f64(bz)),
                           _ptr(_f64(P)), _ptr(_f64(sx)), _ptr(_f64(sy)), _ptr(_f64(sz)),
-                          ctypes.c_double(dt), _ptr(u), _ptr(v), _ptr(w), ctypes.byref(rep))
+                          ctypes.c_double(dt), _ptr(uc), _ptr(vc), _ptr(wc), _ptr(u), _ptr(v),
+                          _ptr(w), ctypes.byref(rep))
     if st != 0:
         raise RuntimeError(f"or_correct failed ({st})")
-    return u, v, w, rep.as_dict()
+    return uc, vc, wc, u, v, w, rep.as_dict()
 
 
-def project(g, p, alpha_np1, u_hat, v_hat, w_hat, P0, sx, sy, sz, dt: float, rtol=1e-12,
+def project(g, p, alpha_np1, uhc, vhc, whc, uh, vh, wh, P0, sx, sy, sz, dt: float, rtol=1e-12,
             max_iter=200000):
-    """Steps 11-12: assemble b, solve for P, correct the face velocities."""
+    """Steps 11-12: assemble b from the face velocities, solve for P, correct
+    faces and cells. Returns (uc, vc, wc, u, v, w, P, report, status)."""
     bx, by, bz = beta(g, p, alpha_np1)
-    b = rhs(g, bx, by, bz, u_hat, v_hat, w_hat, sx, sy, sz, dt)
+    b = rhs(g, bx, by, bz, uh, vh, wh, sx, sy, sz, dt)
     P, srep, st = solve(g, bx, by, bz, b, P0, rtol, max_iter)
-    u, v, w, crep = correct(g, bx, by, bz, P, sx, sy, sz, dt, u_hat, v_hat, w_hat)
+    uc, vc, wc, u, v, w, crep = correct(g, bx, by, bz, P, sx, sy, sz, dt, uhc, vhc, whc, uh, vh, wh)
     srep.update({k: crep[k] for k in ("max_div", "max_u")})
-    return u, v, w, P, srep, st
+    return uc, vc, wc, u, v, w, P, srep, st
 
 
-def step(g, p, alpha, u, v, w, P, dt: float, step_index: int, rtol: float = 1e-12,
+def step(g, p, alpha, uc, vc, wc, u, v, w, P, dt: float, step_index: int, rtol: float = 1e-12,
          max_iter: int = 200000):
-    a, u, v, w, P = (_f64(x).copy() for x in (alpha, u, v, w, P))
+    """One time step; returns (alpha, uc, vc, wc, u, v, w, P, report, status)."""
+    arrs = [_f64(x).copy() for x in (alpha, uc, vc, wc, u, v, w, P)]
     rep = Report()
     G, Ph = _grid(g), _phys(p)
-    st = lib().or_step(ctypes.byref(G), ctypes.byref(Ph), _ptr(a), _ptr(u), _ptr(v), _ptr(w),
-                       _ptr(P), ctypes.c_double(dt), ctypes.c_long(step_index),
-                       ctypes.c_double(rtol), ctypes.c_int(max_iter), ctypes.byref(rep))
+    st = lib().or_step(ctypes.byref(G), ctypes.byref(Ph), *map(_ptr, arrs), ctypes.c_double(dt),
+                       ctypes.c_long(step_index), ctypes.c_double(rtol), ctypes.c_int(max_iter),
+                       ctypes.byref(rep))
     if st < 0:
         raise RuntimeError(f"or_step failed ({st})")
-    return a, u, v, w, P, rep.as_dict(), st
+    return (*arrs, rep.as_dict(), st)

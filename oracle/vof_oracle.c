@@ -10,7 +10,14 @@
  *
  * Readings of the paper that this file implements (the paper is silent or
  * garbled on them; the CUDA library follows the same readings):
- *  - velocities live on cell faces (staggered), Section 2.2 steps 10-12;
+ *  - velocities live at cell centres (the momentum variable, Section 2:
+ *    a collocated grid) and on cell faces (the divergence-free field that
+ *    advects alpha); face values are the linear average of the two cells
+ *    (step 10) corrected by the face pressure gradient (steps 11-12), and the
+ *    cells are corrected by the average of their two face corrections;
+ *  - momentum is convected with the mass fluxes of the geometric VOF sweep
+ *    (step 9: sum over phases of rho_k times the phase volume flux), with
+ *    the donor cell's velocity (upwind) or the two-cell mean (central);
  *  - the interface normal is minus the central gradient of alpha smoothed
  *    with the separable [1,2,1]^3/64 kernel (Section 2, Rudman smoothing);
  *  - geometric donor-slab fluxes with direction splitting, x-y-z on even
@@ -285,7 +292,8 @@ static int face_of(const or_grid* g, const double* u, const double* v, const dou
 }
 
 int or_advect(const or_grid* g, double* alpha, const double* u, const double* v,
-              const double* w, double dt, long step_index, or_report* rep) {
+              const double* w, double dt, long step_index, double* fx, double* fy, double* fz,
+              or_report* rep) {
     long N = ncells(g);
     double h3 = g->h * g->h * g->h;
     unsigned char* cm = (unsigned char*)malloc((size_t)N);
@@ -310,6 +318,10 @@ int or_advect(const or_grid* g, double* alpha, const double* u, const double* v,
     }
     double vol_before = ordered_sum(part, g->nz) * h3;
 
+    double* fl[3] = {fx, fy, fz};
+    const long nface[3] = {(long)(g->nx + 1) * g->ny * g->nz, (long)g->nx * (g->ny + 1) * g->nz, N};
+    for (int d = 0; d < 3; ++d)
+        if (fl[d]) memset(fl[d], 0, sizeof(double) * (size_t)nface[d]);
     for (int s = 0; s < 3; ++s) {
         int dir = (step_index % 2 == 0) ? s : 2 - s;
         reconstruct(g, alpha, &P);
@@ -323,6 +335,12 @@ int or_advect(const or_grid* g, double* alpha, const double* u, const double* v,
                     double vm, vp, fm = 0.0, fp = 0.0;
                     if (face_of(g, u, v, w, dir, 0, i, j, k, &L, &R, &vm))
                         fm = face_flux(g, alpha, &P, dir, L, R, vm, dt);
+                    /* record the flux of this face (each face is the minus face of one cell) */
+                    if (fl[dir]) {
+                        if (dir == 0) fl[0][U_(g, i, j, k)] = fm;
+                        else if (dir == 1) fl[1][V_(g, i, j, k)] = fm;
+                        else fl[2][W_(g, i, j, k)] = fm;
+                    }
                     if (face_of(g, u, v, w, dir, 1, i, j, k, &L, &R, &vp))
                         fp = face_flux(g, alpha, &P, dir, L, R, vp, dt);
                     double an = alpha[c] - (fp - fm) + (cm[c] ? 1.0 : 0.0) * (vp - vm) * dt / g->h;
@@ -657,228 +675,150 @@ int or_solve(const or_grid* g, const double* bx, const double* by, const double*
 }
 
 /* ------------------------------------------------------------------------ */
-/* Momentum predictor: conservative convection, explicit full-stress viscous */
-/* term and body force on the staggered faces (steps 8-9, Eq. 2)             */
+/* Momentum predictor (steps 8-10). Velocities are cell-centred (the         */
+/* momentum variable) and on faces (the divergence-free advecting field).    */
+/* Momentum is convected with the mass fluxes of the geometric VOF sweep,    */
+/* sum_k rho_k (phase volume flux), so rho^{n+1} from alpha^{n+1} is exactly */
+/* the density these fluxes produce when div u_f = 0 (step 9).               */
 /* ------------------------------------------------------------------------ */
-typedef struct {
-    const or_grid* g;
-    const or_phys* p;
-    const double *a, *u, *v, *w;
-} mom_t;
-
-static inline double RHO(const mom_t* M, int i, int j, int k) { return rho_of(M->p, M->a[C_(M->g, i, j, k)]); }
-/* viscosity with mirrored ghosts across the walls */
-static inline double MU(const mom_t* M, int i, int j, int k) {
-    const or_grid* g = M->g;
+/* cell velocity component with no-slip ghosts: every component changes sign
+ * across a wall (zero velocity on the wall face) */
+static double VC(const or_grid* g, const double* q, int i, int j, int k) {
+    double s = 1.0;
+    if (i < 0) { i = 0; s = -s; } else if (i >= g->nx) { i = g->nx - 1; s = -s; }
+    if (j < 0) { j = 0; s = -s; } else if (j >= g->ny) { j = g->ny - 1; s = -s; }
+    return s * q[C_(g, i, j, k)];
+}
+static double MUC(const or_grid* g, const or_phys* p, const double* a, int i, int j, int k) {
     if (i < 0) i = 0;
     if (i >= g->nx) i = g->nx - 1;
     if (j < 0) j = 0;
     if (j >= g->ny) j = g->ny - 1;
-    return mu_of(M->p, M->a[C_(g, i, j, k)]);
-}
-/* velocities with no-slip ghosts for the tangential components; the wall
- * normal component is zero on the wall faces themselves */
-static double UU(const mom_t* M, int i, int j, int k) {
-    const or_grid* g = M->g;
-    if (i <= 0 || i >= g->nx) return 0.0;
-    if (j < 0) return -M->u[U_(g, i, 0, k)];
-    if (j >= g->ny) return -M->u[U_(g, i, g->ny - 1, k)];
-    return M->u[U_(g, i, j, k)];
-}
-static double VV(const mom_t* M, int i, int j, int k) {
-    const or_grid* g = M->g;
-    if (j <= 0 || j >= g->ny) return 0.0;
-    if (i < 0) return -M->v[V_(g, 0, j, k)];
-    if (i >= g->nx) return -M->v[V_(g, g->nx - 1, j, k)];
-    return M->v[V_(g, i, j, k)];
-}
-static double WW(const mom_t* M, int i, int j, int k) {
-    const or_grid* g = M->g;
-    if (i < 0) return -WW(M, 0, j, k);
-    if (i >= g->nx) return -WW(M, g->nx - 1, j, k);
-    if (j < 0) return -WW(M, i, 0, k);
-    if (j >= g->ny) return -WW(M, i, g->ny - 1, k);
-    return M->w[W_(g, i, j, k)];
-}
-static inline double transported(const or_phys* p, double m, double qlo, double qhi) {
-    if (p->conv_scheme == 1) return m >= 0.0 ? qlo : qhi;
-    return 0.5 * (qlo + qhi);
+    return mu_of(p, a[C_(g, i, j, k)]);
 }
 
-/* u-momentum on x-face (i,j,k), 1 <= i <= nx-1 */
-static double mom_u(const mom_t* M, int i, int j, int k, double dt) {
-    const or_grid* g = M->g;
+/* Viscous force (component comp) on cell (i,j,k): (1/h) sum over the six
+ * faces of the outward traction mu_f (d q_comp/d x_d + d q_d/d x_comp),
+ * mu_f the linear face average of the cell viscosities (step 10), normal
+ * derivatives from the two cells, tangential ones averaged from the central
+ * differences in the two cells. */
+static double viscous(const or_grid* g, const or_phys* p, const double* a, const double* const U[3],
+                      int comp, int i, int j, int k) {
     const double h = g->h;
-    /* x-direction fluxes at the cell centres i-1 and i */
-    double Fx[2], Sx[2];
-    for (int s = 0; s < 2; ++s) {
-        int ic = i - 1 + s;
-        double ulo = UU(M, ic, j, k), uhi = UU(M, ic + 1, j, k);
-        double m = RHO(M, ic, j, k) * 0.5 * (ulo + uhi);
-        Fx[s] = m * transported(M->p, m, ulo, uhi);
-        Sx[s] = 2.0 * MU(M, ic, j, k) * (uhi - ulo) / h;
-    }
-    /* y-direction fluxes at the edges y = j*h and y = (j+1)*h */
-    double Fy[2], Sy[2];
-    for (int s = 0; s < 2; ++s) {
-        int je = j + s;
-        double m = 0.0, q = 0.0;
-        if (je > 0 && je < g->ny) {
-            double re = 0.25 * (RHO(M, i - 1, je - 1, k) + RHO(M, i, je - 1, k) + RHO(M, i - 1, je, k) + RHO(M, i, je, k));
-            m = re * 0.5 * (VV(M, i - 1, je, k) + VV(M, i, je, k));
-            q = transported(M->p, m, UU(M, i, je - 1, k), UU(M, i, je, k));
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side) {
+            const double sg = side ? 1.0 : -1.0;
+            int o[3] = {0, 0, 0};
+            o[d] = side ? 1 : -1;
+            const int ni = i + o[0], nj = j + o[1], nk = k + o[2];
+            const double muf = 0.5 * (MUC(g, p, a, i, j, k) + MUC(g, p, a, ni, nj, nk));
+            const double dq = sg * (VC(g, U[comp], ni, nj, nk) - VC(g, U[comp], i, j, k)) / h;
+            double dt_ = dq; /* d == comp: the two terms coincide */
+            if (d != comp) {
+                int e[3] = {0, 0, 0};
+                e[comp] = 1;
+                const double g1 = (VC(g, U[d], i + e[0], j + e[1], k + e[2]) -
+                                   VC(g, U[d], i - e[0], j - e[1], k - e[2])) / (2.0 * h);
+                const double g2 = (VC(g, U[d], ni + e[0], nj + e[1], nk + e[2]) -
+                                   VC(g, U[d], ni - e[0], nj - e[1], nk - e[2])) / (2.0 * h);
+                dt_ = 0.5 * (g1 + g2);
+            }
+            s += sg * muf * (dq + dt_);
         }
-        Fy[s] = m * q;
-        double mue = 0.25 * (MU(M, i - 1, je - 1, k) + MU(M, i, je - 1, k) + MU(M, i - 1, je, k) + MU(M, i, je, k));
-        Sy[s] = mue * ((UU(M, i, je, k) - UU(M, i, je - 1, k)) / h + (VV(M, i, je, k) - VV(M, i - 1, je, k)) / h);
-    }
-    /* z-direction fluxes at the edges z = k*h and z = (k+1)*h */
-    double Fz[2], Sz[2];
-    for (int s = 0; s < 2; ++s) {
-        int ke = k + s;
-        double re = 0.25 * (RHO(M, i - 1, j, ke - 1) + RHO(M, i, j, ke - 1) + RHO(M, i - 1, j, ke) + RHO(M, i, j, ke));
-        double m = re * 0.5 * (WW(M, i - 1, j, ke) + WW(M, i, j, ke));
-        Fz[s] = m * transported(M->p, m, UU(M, i, j, ke - 1), UU(M, i, j, ke));
-        double mue = 0.25 * (MU(M, i - 1, j, ke - 1) + MU(M, i, j, ke - 1) + MU(M, i - 1, j, ke) + MU(M, i, j, ke));
-        Sz[s] = mue * ((UU(M, i, j, ke) - UU(M, i, j, ke - 1)) / h + (WW(M, i, j, ke) - WW(M, i - 1, j, ke)) / h);
-    }
-    double Cf = (Fx[1] - Fx[0] + Fy[1] - Fy[0] + Fz[1] - Fz[0]) / h;
-    double Vf = (Sx[1] - Sx[0] + Sy[1] - Sy[0] + Sz[1] - Sz[0]) / h;
-    double rho_f = 0.5 * (RHO(M, i - 1, j, k) + RHO(M, i, j, k));
-    return rho_f * UU(M, i, j, k) + dt * (-Cf + Vf);
+    return s / h;
 }
 
-/* v-momentum on y-face (i,j,k), 1 <= j <= ny-1 */
-static double mom_v(const mom_t* M, int i, int j, int k, double dt) {
-    const or_grid* g = M->g;
-    const double h = g->h;
-    double Fy[2], Sy[2];
-    for (int s = 0; s < 2; ++s) {
-        int jc = j - 1 + s;
-        double vlo = VV(M, i, jc, k), vhi = VV(M, i, jc + 1, k);
-        double m = RHO(M, i, jc, k) * 0.5 * (vlo + vhi);
-        Fy[s] = m * transported(M->p, m, vlo, vhi);
-        Sy[s] = 2.0 * MU(M, i, jc, k) * (vhi - vlo) / h;
-    }
-    double Fx[2], Sx[2];
-    for (int s = 0; s < 2; ++s) {
-        int ie = i + s;
-        double m = 0.0, q = 0.0;
-        if (ie > 0 && ie < g->nx) {
-            double re = 0.25 * (RHO(M, ie - 1, j - 1, k) + RHO(M, ie, j - 1, k) + RHO(M, ie - 1, j, k) + RHO(M, ie, j, k));
-            m = re * 0.5 * (UU(M, ie, j - 1, k) + UU(M, ie, j, k));
-            q = transported(M->p, m, VV(M, ie - 1, j, k), VV(M, ie, j, k));
+/* Convective momentum change of component q over the step on cell (i,j,k):
+ * sum over faces of (outward) M_f q*_f, M_f = rho_l F_f + rho_g (u_f dt/h -
+ * F_f) with F_f the liquid volume flux of the VOF sweep (cell volumes);
+ * q*_f the donor cell's value (upwind) or the two-cell mean (central). */
+static double convection(const or_grid* g, const or_phys* p, const double* q, const double* u,
+                         const double* v, const double* w, const double* fx, const double* fy,
+                         const double* fz, double dt, int i, int j, int k) {
+    double c = 0.0;
+    for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side) {
+            int li = i, lj = j, lk = k; /* left cell of the face */
+            long f;
+            double uf, F;
+            if (d == 0) {
+                const int fi = i + side;
+                if (fi == 0 || fi == g->nx) continue; /* wall: no mass flux */
+                li = fi - 1;
+                f = U_(g, fi, j, k);
+                uf = u[f];
+                F = fx[f];
+            } else if (d == 1) {
+                const int fj = j + side;
+                if (fj == 0 || fj == g->ny) continue;
+                lj = fj - 1;
+                f = V_(g, i, fj, k);
+                uf = v[f];
+                F = fy[f];
+            } else {
+                const int fk = k + side;
+                lk = fk - 1;
+                f = W_(g, i, j, fk);
+                uf = w[f];
+                F = fz[f];
+            }
+            int ri = li, rj = lj, rk = lk;
+            if (d == 0) ri++; else if (d == 1) rj++; else rk++;
+            const double M = p->rho_l * F + p->rho_g * (uf * dt / g->h - F);
+            const double qL = q[C_(g, li, lj, lk)], qR = q[C_(g, ri, rj, rk)];
+            const double qs = p->conv_scheme == 1 ? (uf > 0.0 ? qL : qR) : 0.5 * (qL + qR);
+            c += (side ? 1.0 : -1.0) * M * qs;
         }
-        Fx[s] = m * q;
-        double mue = 0.25 * (MU(M, ie - 1, j - 1, k) + MU(M, ie, j - 1, k) + MU(M, ie - 1, j, k) + MU(M, ie, j, k));
-        Sx[s] = mue * ((VV(M, ie, j, k) - VV(M, ie - 1, j, k)) / h + (UU(M, ie, j, k) - UU(M, ie, j - 1, k)) / h);
-    }
-    double Fz[2], Sz[2];
-    for (int s = 0; s < 2; ++s) {
-        int ke = k + s;
-        double re = 0.25 * (RHO(M, i, j - 1, ke - 1) + RHO(M, i, j, ke - 1) + RHO(M, i, j - 1, ke) + RHO(M, i, j, ke));
-        double m = re * 0.5 * (WW(M, i, j - 1, ke) + WW(M, i, j, ke));
-        Fz[s] = m * transported(M->p, m, VV(M, i, j, ke - 1), VV(M, i, j, ke));
-        double mue = 0.25 * (MU(M, i, j - 1, ke - 1) + MU(M, i, j, ke - 1) + MU(M, i, j - 1, ke) + MU(M, i, j, ke));
-        Sz[s] = mue * ((VV(M, i, j, ke) - VV(M, i, j, ke - 1)) / h + (WW(M, i, j, ke) - WW(M, i, j - 1, ke)) / h);
-    }
-    double Cf = (Fx[1] - Fx[0] + Fy[1] - Fy[0] + Fz[1] - Fz[0]) / h;
-    double Vf = (Sx[1] - Sx[0] + Sy[1] - Sy[0] + Sz[1] - Sz[0]) / h;
-    double rho_f = 0.5 * (RHO(M, i, j - 1, k) + RHO(M, i, j, k));
-    return rho_f * VV(M, i, j, k) + dt * (-Cf + Vf);
+    return c;
 }
 
-/* w-momentum on z-face (i,j,k), every k (periodic) */
-static double mom_w(const mom_t* M, int i, int j, int k, double dt) {
-    const or_grid* g = M->g;
-    const double h = g->h;
-    double Fz[2], Sz[2];
-    for (int s = 0; s < 2; ++s) {
-        int kc = k - 1 + s;
-        double wlo = WW(M, i, j, kc), whi = WW(M, i, j, kc + 1);
-        double m = RHO(M, i, j, kc) * 0.5 * (wlo + whi);
-        Fz[s] = m * transported(M->p, m, wlo, whi);
-        Sz[s] = 2.0 * MU(M, i, j, kc) * (whi - wlo) / h;
-    }
-    double Fx[2], Sx[2];
-    for (int s = 0; s < 2; ++s) {
-        int ie = i + s;
-        double m = 0.0, q = 0.0;
-        if (ie > 0 && ie < g->nx) {
-            double re = 0.25 * (RHO(M, ie - 1, j, k - 1) + RHO(M, ie, j, k - 1) + RHO(M, ie - 1, j, k) + RHO(M, ie, j, k));
-            m = re * 0.5 * (UU(M, ie, j, k - 1) + UU(M, ie, j, k));
-            q = transported(M->p, m, WW(M, ie - 1, j, k), WW(M, ie, j, k));
-        }
-        Fx[s] = m * q;
-        double mue = 0.25 * (MU(M, ie - 1, j, k - 1) + MU(M, ie, j, k - 1) + MU(M, ie - 1, j, k) + MU(M, ie, j, k));
-        Sx[s] = mue * ((WW(M, ie, j, k) - WW(M, ie - 1, j, k)) / h + (UU(M, ie, j, k) - UU(M, ie, j, k - 1)) / h);
-    }
-    double Fy[2], Sy[2];
-    for (int s = 0; s < 2; ++s) {
-        int je = j + s;
-        double m = 0.0, q = 0.0;
-        if (je > 0 && je < g->ny) {
-            double re = 0.25 * (RHO(M, i, je - 1, k - 1) + RHO(M, i, je, k - 1) + RHO(M, i, je - 1, k) + RHO(M, i, je, k));
-            m = re * 0.5 * (VV(M, i, je, k - 1) + VV(M, i, je, k));
-            q = transported(M->p, m, WW(M, i, je - 1, k), WW(M, i, je, k));
-        }
-        Fy[s] = m * q;
-        double mue = 0.25 * (MU(M, i, je - 1, k - 1) + MU(M, i, je, k - 1) + MU(M, i, je - 1, k) + MU(M, i, je, k));
-        Sy[s] = mue * ((WW(M, i, je, k) - WW(M, i, je - 1, k)) / h + (VV(M, i, je, k) - VV(M, i, je, k - 1)) / h);
-    }
-    double Cf = (Fx[1] - Fx[0] + Fy[1] - Fy[0] + Fz[1] - Fz[0]) / h;
-    double Vf = (Sx[1] - Sx[0] + Sy[1] - Sy[0] + Sz[1] - Sz[0]) / h;
-    double rho_f = 0.5 * (RHO(M, i, j, k - 1) + RHO(M, i, j, k));
-    double Bf = (rho_f - M->p->rho0) * M->p->g_z + M->p->dpdz;
-    return rho_f * WW(M, i, j, k) + dt * (-Cf + Vf + Bf);
-}
-
-int or_momentum(const or_grid* g, const or_phys* p, const double* alpha_n, const double* u,
-                const double* v, const double* w, double dt, double* mu_, double* mv, double* mw) {
+int or_predict(const or_grid* g, const or_phys* p, const double* alpha_n, const double* alpha_np1,
+               const double* uc, const double* vc, const double* wc, const double* u,
+               const double* v, const double* w, const double* fx, const double* fy,
+               const double* fz, double dt, double* uhc, double* vhc, double* whc) {
     if (g->per_x || g->per_y) return -1;
-    mom_t M = {g, p, alpha_n, u, v, w};
+    const double* const U[3] = {uc, vc, wc};
+    double* const OUT[3] = {uhc, vhc, whc};
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                const long c = C_(g, i, j, k);
+                const double rn = rho_of(p, alpha_n[c]), rn1 = rho_of(p, alpha_np1[c]);
+                for (int comp = 0; comp < 3; ++comp) {
+                    const double C = convection(g, p, U[comp], u, v, w, fx, fy, fz, dt, i, j, k);
+                    const double V = viscous(g, p, alpha_n, U, comp, i, j, k);
+                    const double B = comp == 2 ? (rn - p->rho0) * p->g_z + p->dpdz : 0.0;
+                    OUT[comp][c] = (rn * U[comp][c] - C + dt * (V + B)) / rn1;
+                }
+            }
+    return 0;
+}
+
+/* step 10: face velocities as the linear average of the two cell values */
+int or_cell_to_face(const or_grid* g, const double* uc, const double* vc, const double* wc,
+                    double* u, double* v, double* w) {
+    if (g->per_x || g->per_y) return -1;
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < g->nz; ++k) {
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i <= g->nx; ++i)
-                mu_[U_(g, i, j, k)] = (i == 0 || i == g->nx) ? 0.0 : mom_u(&M, i, j, k, dt);
+                u[U_(g, i, j, k)] = (i == 0 || i == g->nx) ? 0.0
+                    : 0.5 * (uc[C_(g, i - 1, j, k)] + uc[C_(g, i, j, k)]);
         for (int j = 0; j <= g->ny; ++j)
             for (int i = 0; i < g->nx; ++i)
-                mv[V_(g, i, j, k)] = (j == 0 || j == g->ny) ? 0.0 : mom_v(&M, i, j, k, dt);
+                v[V_(g, i, j, k)] = (j == 0 || j == g->ny) ? 0.0
+                    : 0.5 * (vc[C_(g, i, j - 1, k)] + vc[C_(g, i, j, k)]);
         for (int j = 0; j < g->ny; ++j)
-            for (int i = 0; i < g->nx; ++i) mw[W_(g, i, j, k)] = mom_w(&M, i, j, k, dt);
-    }
-    return 0;
-}
-
-int or_divide_rho(const or_grid* g, const or_phys* p, const double* a, double* u, double* v,
-                  double* w) {
-    if (g->per_x || g->per_y) return -1;
-#pragma omp parallel for schedule(static)
-    for (int k = 0; k < g->nz; ++k) {
-        for (int j = 0; j < g->ny; ++j)
-            for (int i = 0; i <= g->nx; ++i) {
-                long f = U_(g, i, j, k);
-                u[f] = (i == 0 || i == g->nx) ? 0.0
-                     : u[f] / (0.5 * (rho_of(p, a[C_(g, i - 1, j, k)]) + rho_of(p, a[C_(g, i, j, k)])));
-            }
-        for (int j = 0; j <= g->ny; ++j)
-            for (int i = 0; i < g->nx; ++i) {
-                long f = V_(g, i, j, k);
-                v[f] = (j == 0 || j == g->ny) ? 0.0
-                     : v[f] / (0.5 * (rho_of(p, a[C_(g, i, j - 1, k)]) + rho_of(p, a[C_(g, i, j, k)])));
-            }
-        for (int j = 0; j < g->ny; ++j)
-            for (int i = 0; i < g->nx; ++i) {
-                long f = W_(g, i, j, k);
-                w[f] = w[f] / (0.5 * (rho_of(p, a[C_(g, i, j, k - 1)]) + rho_of(p, a[C_(g, i, j, k)])));
-            }
+            for (int i = 0; i < g->nx; ++i)
+                w[W_(g, i, j, k)] = 0.5 * (wc[C_(g, i, j, k - 1)] + wc[C_(g, i, j, k)]);
     }
     return 0;
 }
 
 /* ------------------------------------------------------------------------ */
-/* Projection                                                                */
+/* Projection (steps 11-12)                                                  */
 /* ------------------------------------------------------------------------ */
 int or_rhs(const or_grid* g, const double* bx, const double* by, const double* bz,
            const double* u, const double* v, const double* w, const double* sx,
@@ -904,38 +844,67 @@ int or_rhs(const or_grid* g, const double* bx, const double* by, const double* b
     return 0;
 }
 
+/* Face acceleration a_f = beta_f ((P_R - P_L)/h - s_f) (zero on walls);
+ * u_f -= dt a_f, and each cell component -= dt times the mean of the
+ * accelerations on its two faces in that direction (f -> c averaging of
+ * step 12). Reports max|div u_f| and max|u_f|. */
 int or_correct(const or_grid* g, const double* bx, const double* by, const double* bz,
                const double* P, const double* sx, const double* sy, const double* sz, double dt,
-               double* u, double* v, double* w, or_report* rep) {
+               double* uc, double* vc, double* wc, double* u, double* v, double* w,
+               or_report* rep) {
     if (g->per_x || g->per_y) return -1;
     const double h = g->h;
+    const long nu = (long)(g->nx + 1) * g->ny * g->nz, nv = (long)g->nx * (g->ny + 1) * g->nz,
+               nw = ncells(g);
+    double* ax = (double*)calloc((size_t)nu, sizeof(double));
+    double* ay = (double*)calloc((size_t)nv, sizeof(double));
+    double* az = (double*)calloc((size_t)nw, sizeof(double));
     double* dpart = (double*)calloc((size_t)g->nz, sizeof(double));
     double* upart = (double*)calloc((size_t)g->nz, sizeof(double));
-    if (!dpart || !upart) return -2;
+    if (!ax || !ay || !az || !dpart || !upart) return -2;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->nz; ++k) {
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 1; i < g->nx; ++i) {
+                long f = U_(g, i, j, k);
+                ax[f] = bx[f] * ((P[C_(g, i, j, k)] - P[C_(g, i - 1, j, k)]) / h - sx[f]);
+            }
+        for (int j = 1; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long f = V_(g, i, j, k);
+                ay[f] = by[f] * ((P[C_(g, i, j, k)] - P[C_(g, i, j - 1, k)]) / h - sy[f]);
+            }
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long f = W_(g, i, j, k);
+                az[f] = bz[f] * ((P[C_(g, i, j, k)] - P[C_(g, i, j, k - 1)]) / h - sz[f]);
+            }
+    }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < g->nz; ++k) {
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i <= g->nx; ++i) {
                 long f = U_(g, i, j, k);
-                if (i == 0 || i == g->nx) { u[f] = 0.0; continue; }
-                double G = (P[C_(g, i, j, k)] - P[C_(g, i - 1, j, k)]) / h;
-                u[f] = u[f] - dt * bx[f] * (G - sx[f]);
+                u[f] = (i == 0 || i == g->nx) ? 0.0 : u[f] - dt * ax[f];
             }
         for (int j = 0; j <= g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
                 long f = V_(g, i, j, k);
-                if (j == 0 || j == g->ny) { v[f] = 0.0; continue; }
-                double G = (P[C_(g, i, j, k)] - P[C_(g, i, j - 1, k)]) / h;
-                v[f] = v[f] - dt * by[f] * (G - sy[f]);
+                v[f] = (j == 0 || j == g->ny) ? 0.0 : v[f] - dt * ay[f];
             }
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
                 long f = W_(g, i, j, k);
-                double G = (P[C_(g, i, j, k)] - P[C_(g, i, j, k - 1)]) / h;
-                w[f] = w[f] - dt * bz[f] * (G - sz[f]);
+                w[f] = w[f] - dt * az[f];
+            }
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long c = C_(g, i, j, k);
+                uc[c] -= dt * 0.5 * (ax[U_(g, i, j, k)] + ax[U_(g, i + 1, j, k)]);
+                vc[c] -= dt * 0.5 * (ay[V_(g, i, j, k)] + ay[V_(g, i, j + 1, k)]);
+                wc[c] -= dt * 0.5 * (az[W_(g, i, j, k)] + az[W_(g, i, j, k + 1)]);
             }
     }
-    /* report max|div u| and max|u| (after every plane is corrected) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < g->nz; ++k) {
         double md = 0.0, mu = 0.0;
@@ -961,56 +930,61 @@ int or_correct(const or_grid* g, const double* bx, const double* by, const doubl
         rep->max_div = md;
         rep->max_u = mu;
     }
-    free(dpart); free(upart);
+    free(ax); free(ay); free(az); free(dpart); free(upart);
     return 0;
 }
 
 /* ------------------------------------------------------------------------ */
 /* One time step, Section 2.2 steps 1-12 (with the readings listed above)    */
 /* ------------------------------------------------------------------------ */
-int or_step(const or_grid* g, const or_phys* p, double* alpha, double* u, double* v, double* w,
-            double* P, double dt, long step_index, double rtol, int max_iter, or_report* rep) {
+int or_step(const or_grid* g, const or_phys* p, double* alpha, double* uc, double* vc, double* wc,
+            double* u, double* v, double* w, double* P, double dt, long step_index, double rtol,
+            int max_iter, or_report* rep) {
     if (g->per_x || g->per_y) return -1;
     long N = ncells(g);
     size_t nu = (size_t)(g->nx + 1) * g->ny * g->nz, nv = (size_t)g->nx * (g->ny + 1) * g->nz,
            nw = (size_t)N;
-    double* Mu = (double*)malloc(sizeof(double) * nu);
-    double* Mv = (double*)malloc(sizeof(double) * nv);
-    double* Mw = (double*)malloc(sizeof(double) * nw);
+    double* an = (double*)malloc(sizeof(double) * (size_t)N);
+    double* fx = (double*)malloc(sizeof(double) * nu);
+    double* fy = (double*)malloc(sizeof(double) * nv);
+    double* fz = (double*)malloc(sizeof(double) * nw);
     double* bx = (double*)malloc(sizeof(double) * nu);
     double* by = (double*)malloc(sizeof(double) * nv);
     double* bz = (double*)malloc(sizeof(double) * nw);
     double* sx = (double*)malloc(sizeof(double) * nu);
     double* sy = (double*)malloc(sizeof(double) * nv);
     double* sz = (double*)malloc(sizeof(double) * nw);
+    double* hc[3];
+    for (int d = 0; d < 3; ++d) hc[d] = (double*)malloc(sizeof(double) * (size_t)N);
     double* kap = (double*)malloc(sizeof(double) * (size_t)N);
     double* b = (double*)malloc(sizeof(double) * (size_t)N);
-    if (!Mu || !Mv || !Mw || !bx || !by || !bz || !sx || !sy || !sz || !kap || !b) return -2;
+    if (!an || !fx || !fy || !fz || !bx || !by || !bz || !sx || !sy || !sz || !hc[0] || !hc[1] ||
+        !hc[2] || !kap || !b)
+        return -2;
     or_report local;
     memset(&local, 0, sizeof(local));
 
-    /* steps 2, 8, 9: rho^n, mu^n and the explicit momentum terms, all at
-     * time level n (computed before alpha is advanced; they only read
-     * level-n data) */
-    or_momentum(g, p, alpha, u, v, w, dt, Mu, Mv, Mw);
-    /* step 3: advance alpha with u^n */
-    or_advect(g, alpha, u, v, w, dt, step_index, &local);
-    /* step 4: rho^{n+1}, beta_f = 1 / rho_f^{n+1} */
+    /* steps 1-2: the level-n state (rho^n, mu^n follow from alpha^n) */
+    memcpy(an, alpha, sizeof(double) * (size_t)N);
+    /* step 3: advance alpha with the face velocities u_f^n, keeping the
+     * liquid volume fluxes for the momentum transport */
+    or_advect(g, alpha, u, v, w, dt, step_index, fx, fy, fz, &local);
+    /* steps 8-9: cell-centred intermediate velocity (rho^{n+1} from alpha^{n+1}) */
+    or_predict(g, p, an, alpha, uc, vc, wc, u, v, w, fx, fy, fz, dt, hc[0], hc[1], hc[2]);
+    memcpy(uc, hc[0], sizeof(double) * (size_t)N);
+    memcpy(vc, hc[1], sizeof(double) * (size_t)N);
+    memcpy(wc, hc[2], sizeof(double) * (size_t)N);
+    /* step 10: intermediate face velocities by linear averaging */
+    or_cell_to_face(g, uc, vc, wc, u, v, w);
+    /* step 4 (beta from rho^{n+1}) and steps 5-7 (curvature, face force) */
     or_beta(g, p, alpha, bx, by, bz);
-    /* steps 5-7: curvature and the sharp surface force on faces */
     or_ssf(g, p, alpha, kap, sx, sy, sz, &local);
-    /* step 10: intermediate face velocities u_hat = M / rho_f^{n+1} */
-    memcpy(u, Mu, sizeof(double) * nu);
-    memcpy(v, Mv, sizeof(double) * nv);
-    memcpy(w, Mw, sizeof(double) * nw);
-    or_divide_rho(g, p, alpha, u, v, w);
-    /* step 11: pressure (with the surface-tension jump) */
+    /* step 11: pressure with the surface-tension jump; step 12: correction */
     or_rhs(g, bx, by, bz, u, v, w, sx, sy, sz, dt, b);
     int st = or_solve(g, bx, by, bz, b, P, rtol, max_iter, &local);
-    /* step 12: divergence-free correction */
-    or_correct(g, bx, by, bz, P, sx, sy, sz, dt, u, v, w, &local);
+    or_correct(g, bx, by, bz, P, sx, sy, sz, dt, uc, vc, wc, u, v, w, &local);
     if (rep) *rep = local;
-    free(Mu); free(Mv); free(Mw); free(bx); free(by); free(bz);
-    free(sx); free(sy); free(sz); free(kap); free(b);
+    free(an); free(fx); free(fy); free(fz); free(bx); free(by); free(bz);
+    free(sx); free(sy); free(sz); free(hc[0]); free(hc[1]); free(hc[2]); free(kap); free(b);
     return st;
 }

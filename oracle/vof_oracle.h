@@ -67,8 +67,11 @@ void or_normal(const or_grid* g, const double* alpha, int i, int j, int k, doubl
 int or_hf_direction(const double n[3]);
 
 /* --- VOF advection (Eq. 3; geometric split fluxes) ----------------------- */
+/* fx, fy, fz (optional, may be NULL): signed liquid volume crossing each
+ * face during its sweep, in cell volumes, face layouts as u, v, w. */
 int or_advect(const or_grid* g, double* alpha, const double* u, const double* v,
-              const double* w, double dt, long step_index, or_report* rep);
+              const double* w, double dt, long step_index, double* fx, double* fy, double* fz,
+              or_report* rep);
 
 /* --- curvature and sharp surface force (Eqs. 6-7; steps 5-7) ------------ */
 /* kappa per cell (0 where not computed), valid flag per cell (may be NULL). */
@@ -92,29 +95,35 @@ int or_solve(const or_grid* g, const double* bx, const double* by,
              int max_iter, or_report* rep);
 
 /* --- momentum predictor (steps 8-10) ------------------------------------- */
-/* M_f = rho_f^n u_f^n + dt (-C_f + V_f + B_f) written into mu_, mv, mw. */
-int or_momentum(const or_grid* g, const or_phys* p, const double* alpha_n,
-                const double* u, const double* v, const double* w, double dt,
-                double* mu_, double* mv, double* mw);
-/* u_hat = M / rho_f^{n+1}, in place on (u,v,w) holding M; walls zeroed. */
-int or_divide_rho(const or_grid* g, const or_phys* p, const double* alpha_np1,
-                  double* u, double* v, double* w);
+/* Cell-centred u_hat = [rho^n u^n - C + dt (V + B)] / rho^{n+1}, C the
+ * convective momentum change with the VOF mass fluxes (fluxes from
+ * or_advect with the face velocities u, v, w). */
+int or_predict(const or_grid* g, const or_phys* p, const double* alpha_n,
+               const double* alpha_np1, const double* uc, const double* vc,
+               const double* wc, const double* u, const double* v, const double* w,
+               const double* fx, const double* fy, const double* fz, double dt,
+               double* uhc, double* vhc, double* whc);
+/* Face values as the mean of the two cells (zero on walls). */
+int or_cell_to_face(const or_grid* g, const double* uc, const double* vc,
+                    const double* wc, double* u, double* v, double* w);
 
 /* --- projection (steps 11-12) -------------------------------------------- */
-/* b = -div(u_hat)/dt - div(beta s). */
+/* b = -div(u_hat_f)/dt - div(beta s). */
 int or_rhs(const or_grid* g, const double* bx, const double* by, const double* bz,
            const double* u, const double* v, const double* w, const double* sx,
            const double* sy, const double* sz, double dt, double* b);
-/* u = u_hat - dt beta ((P_R - P_L)/h - s); reports max|div u|, max|u|. */
+/* a_f = beta_f ((P_R - P_L)/h - s_f); u_f -= dt a_f; cells -= dt times the
+ * mean of their two face accelerations. Reports max|div u_f|, max|u_f|. */
 int or_correct(const or_grid* g, const double* bx, const double* by,
                const double* bz, const double* P, const double* sx,
-               const double* sy, const double* sz, double dt, double* u,
-               double* v, double* w, or_report* rep);
+               const double* sy, const double* sz, double dt, double* uc,
+               double* vc, double* wc, double* u, double* v, double* w,
+               or_report* rep);
 
 /* --- one whole time step (steps 1-12) ------------------------------------ */
-int or_step(const or_grid* g, const or_phys* p, double* alpha, double* u,
-            double* v, double* w, double* P, double dt, long step_index,
-            double rtol, int max_iter, or_report* rep);
+int or_step(const or_grid* g, const or_phys* p, double* alpha, double* uc, double* vc,
+            double* wc, double* u, double* v, double* w, double* P, double dt,
+            long step_index, double rtol, int max_iter, or_report* rep);
 
 /* Threads used by the OpenMP loops (for the CPU-baseline report). */
 int or_num_threads(void);

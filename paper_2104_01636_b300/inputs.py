@@ -64,7 +64,9 @@ class Phys:
 
 @dataclass
 class Case:
-    """One workload: grid, constants and the initial state."""
+    """One workload: grid, constants and the initial state. Velocities are
+    given at cell centres (uc, vc, wc) and on faces (u, v, w); the face field
+    is discretely divergence-free and the cell field is its face average."""
     name: str
     grid: Grid
     phys: Phys
@@ -78,6 +80,17 @@ class Case:
     centres: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     radius: float = 0.0
     notes: str = ""
+    uc: np.ndarray = None
+    vc: np.ndarray = None
+    wc: np.ndarray = None
+
+    def __post_init__(self):
+        if self.uc is None:
+            self.uc, self.vc, self.wc = face_to_cell(self.u, self.v, self.w)
+
+    def state(self):
+        """(alpha, uc, vc, wc, u, v, w, P) in the order the step functions take."""
+        return (self.alpha, self.uc, self.vc, self.wc, self.u, self.v, self.w, self.P)
 
 
 # ----------------------------------------------------------------------------
@@ -265,6 +278,12 @@ def curl_noise(grid: Grid, rms: float, seed: int, kmax: int = 4):
     return u * s, v * s, w * s
 
 
+def face_to_cell(u, v, w):
+    """Cell-centred velocity components as the mean of the two faces."""
+    return (0.5 * (u[:, :, 1:] + u[:, :, :-1]), 0.5 * (v[:, 1:, :] + v[:, :-1, :]),
+            0.5 * (w + np.roll(w, -1, axis=0)))
+
+
 def divergence(grid: Grid, u, v, w):
     """Discrete divergence per cell (input sanity checks only)."""
     h = grid.h
@@ -274,11 +293,16 @@ def divergence(grid: Grid, u, v, w):
 
 def stable_dt(grid: Grid, phys: Phys, umax: float, cfl: float = 0.25, safety: float = 0.5):
     """Fixed time step: the smallest of the advective (CFL), capillary and
-    explicit-viscous limits, times a safety factor."""
+    explicit-viscous limits, times a safety factor. The viscous limit uses
+    the largest viscosity over the smallest density, since cells at the
+    interface mix the liquid's viscosity with the gas's density."""
     h = grid.h
-    lims = [math.sqrt((phys.rho_l + phys.rho_g) * h ** 3 / (4 * math.pi * phys.sigma))]
-    nu = max(phys.mu_l / phys.rho_l, phys.mu_g / phys.rho_g)
-    lims.append(h * h / (6 * nu))
+    lims = []
+    if phys.sigma > 0:
+        lims.append(math.sqrt((phys.rho_l + phys.rho_g) * h ** 3 / (4 * math.pi * phys.sigma)))
+    nu = max(phys.mu_l, phys.mu_g) / min(phys.rho_l, phys.rho_g)
+    if nu > 0:
+        lims.append(h * h / (6 * nu))
     if umax > 0:
         lims.append(cfl * h / umax)
     return safety * min(lims)
