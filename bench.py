@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of one projection time step on the paper-shaped bubbly duct.
+
+Workload: 224 x 224 x 640 cells (32.1M; the paper's "32 million control
+volumes", Section 4 / abstract), 864 gas spheres of diameter 12h placed by
+seeded rejection sampling, 1/7-power mean profile at Re_b = 5300 plus 8%
+divergence-free perturbations, gravity along -z; synthetic inputs only.
+
+A step is one call of the library's `step` (predictor terms, VOF advection,
+curvature and surface force, pressure solve to rtol, projection). Timed with
+CUDA events on the library's stream between barriers; the inputs (257 MB per
+field) are larger than the 126 MB L2, so no flush is needed between steps.
+
+Output: one JSON line (rank 0). With --impl reference the same metric is
+measured for the FP64 CPU oracle on a bounded sample of the workload.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/s & Poisson cell-updates/s at 32M cells; served p50/p99 vs FP64"
+UNIT = "time-steps/s"
+WORKLOAD = "paper-shaped duct 224x224x640 (32.1M cells), 864 spheres d=12h, Re_b=5300 1/7 profile + 8% noise"
+
+# Algorithmic bytes per fine-grid cell for one launch of each kernel class
+# (FP64): what the kernel must read and write at minimum.
+#  smooth_l0   one red-black colour: other-colour x (4), all face betas (24),
+#              own-colour right side (4), own-colour x written (4)
+#  residual_l0 q = A p with p.q: p (8), betas (24), q written (8)
+#  restrict_l0 residual of 8 children averaged: x, f (16), betas (24),
+#              coarse f written (1)
+#  prolong_l0  fine x read and written (16), coarse x (1)
+ALGO_BYTES_PER_CELL = {"smooth_l0": 36.0, "residual_l0": 40.0, "restrict_l0": 41.0,
+                       "prolong_l0": 17.0}
+KERNEL_SOURCE = {"smooth_l0": "k_poisson.cu", "residual_l0": "k_poisson.cu",
+                 "restrict_l0": "k_poisson.cu", "prolong_l0": "k_poisson.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--nz", type=int, default=640, help="z cells (smaller for quick runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(cls: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(cls)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2104_01636_b300", "csrc", KERNEL_SOURCE[cls])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d["dram_bytes_per_launch"] if d.get("source_sha256") == h else None
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline(args, steps=1, label="bounded sample"):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the same generator with 16 z-planes (224x224x16, ~0.8M cells). Its
+    steps/s is scaled to the 32.1M-cell metric by the cell ratio."""
+    import oracle
+    from paper_2104_01636_b300 import inputs as I
+    full = 224 * 224 * 640
+    nz_s = 16
+    case = I.paper_shaped(224, 224, nz_s, nbub=round(864 * nz_s / 640), seed=2106)
+    g, ph = case.grid, case.phys
+    state = case.state()
+    t_tot, iters = 0.0, 0
+    for s in range(steps):
+        t0 = time.perf_counter()
+        *state, rep, st = oracle.step(g, ph, *state, case.dt, s, rtol=args.rtol)
+        t_tot += time.perf_counter() - t0
+        iters += rep["iters"]
+    sps_sample = steps / t_tot
+    return {
+        "value": sps_sample * g.ncells / full,
+        "unit": UNIT,
+        "cores": oracle.num_threads(),
+        "kind": "oracle",
+        "sample": (f"{steps} oracle step(s) of the same generator on 224x224x{nz_s} "
+                   f"({g.ncells} cells, {round(864 * nz_s / 640)} spheres), rtol {args.rtol:g}, "
+                   f"scaled to 32.1M cells by the cell ratio ({label})"),
+        "sample_s_per_step": t_tot / steps,
+        "poisson_cell_updates_per_s": g.ncells * iters / t_tot,
+        "jacobi_cg_iters_per_step": iters / steps,
+    }
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(args, steps=1)
+    cb = cpu_baseline(args, steps=max(1, args.steps), label="reference arm")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "poisson_cell_updates_per_s": cb["poisson_cell_updates_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2104_01636_b300 as vd
+    from paper_2104_01636_b300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    nbub = round(864 * args.nz / 640)
+    case = I.paper_shaped(224, 224, args.nz, nbub=nbub, seed=2106 + rank)
+    g = case.grid
+    N = g.ncells
+    prec = vd.PREC_FP64 if args.precision == "fp64" else vd.PREC_MIXED_FP32
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = vd.VofContext(g, case.phys, vd.c_solver(prec, rtol=args.rtol, max_iter=500),
+                            stream=stream)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        T = [dev(x) for x in case.state()]
+        torch.cuda.synchronize()
+        for s in range(args.warmup):
+            ctx.step(*T, case.dt, s)
+        barrier()
+
+        # ---- timed region: device-resident inputs --------------------------
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        n0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = 0
+        barrier()
+        e0.record(stream)
+        for s in range(args.warmup, args.warmup + args.steps):
+            rep = ctx.step(*T, case.dt, s)
+            iters += rep["iters"]
+        e1.record(stream)
+        barrier()
+        launches = ctx.launch_count() - n0
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        ms_max = float(t_local.item())
+        ms_per_step = ms_max / args.steps
+        value = world * args.steps / (ms_max / 1e3)
+
+        # ---- roofline: per-kernel CUDA events on the library stream --------
+        ctx.set_timing(True)
+        ctx.kernel_times()
+        k_steps = max(2, min(args.steps, 5))
+        solve_ms, it2 = 0.0, 0
+        for s in range(k_steps):
+            rep = ctx.step(*T, case.dt, args.warmup + args.steps + s)
+            solve_ms += rep["ms"][4]
+            it2 += rep["iters"]
+        kt = ctx.kernel_times()
+        ctx.set_timing(False)
+        cls = max(ALGO_BYTES_PER_CELL, key=lambda k: kt.get(k, (0.0, 0))[0])
+        kms, kn = kt[cls]
+        avg_ms = kms / max(kn, 1)
+        algo = ALGO_BYTES_PER_CELL[cls] * N
+        peak, peak_kind = peaks()
+        achieved = algo / (avg_ms / 1e3) / 1e9
+        step_ms_timed = sum(v[0] for v in kt.values()) / k_steps
+        roofline = {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic_for(cls), "algorithmic_bytes": algo,
+                    "avg_launch_ms": avg_ms, "launches_per_step": kn / k_steps,
+                    "share_of_step": kms / k_steps / step_ms_timed if step_ms_timed else None,
+                    "classes_ms_per_step": {k: round(v[0] / k_steps, 4) for k, v in kt.items()}}
+        poisson = N * it2 / (solve_ms / 1e3) if solve_ms > 0 else None
+
+        # ---- end to end: pinned host buffers copied in and out every step --
+        H = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in T]
+        for h, t in zip(H, T):
+            h.copy_(t)
+        torch.cuda.synchronize()
+        h2d = sum(t.numel() * t.element_size() for t in T)
+        barrier()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        base = args.warmup + args.steps + k_steps
+        for s in range(args.steps):
+            for t, h in zip(T, H):
+                t.copy_(h, non_blocking=True)
+            ctx.step(*T, case.dt, base + s, report=False)
+            for t, h in zip(T, H):
+                h.copy_(t, non_blocking=True)
+        e3.record(stream)
+        barrier()
+        ms_e2e = e2.elapsed_time(e3)
+        te = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value = world * args.steps / (float(te.item()) / 1e3)
+        ctx.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args, steps=1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.nz == 640 else WORKLOAD.replace("640", str(args.nz)),
+                   "cells": N, "spheres": nbub, "rtol": args.rtol,
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (257 MB per cell field), no flush",
+                   "dt": case.dt},
+        "poisson_cell_updates_per_s": poisson,
+        "pcg_iters_per_step": iters / args.steps,
+        "roofline": roofline,
+        "cpu_baseline": (None if cb is None else
+                         {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": h2d},
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

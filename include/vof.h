@@ -1,0 +1,206 @@
+/*
+ * vof.h -- C ABI of a single-GPU (sm_103a) projection time step for
+ * incompressible air-water flow with a volume-of-fluid interface and the
+ * sharp-surface-force (SSF) pressure jump, after Kumar & Vanka, "Large Scale
+ * GPU Based Simulations of Turbulent Bubbly Flow in a Square Duct",
+ * Section 2 (Eqs. 1-7, solution procedure steps 1-12) and Section 4.
+ *
+ * Grid and layout (all fields FP64, x fastest, caller-owned DEVICE memory,
+ * contiguous, no padding):
+ *   cells    nx*ny*nz                     index i + nx*(j + ny*k)
+ *   u        (nx+1)*ny*nz  x-faces       index i + (nx+1)*(j + ny*k); face i
+ *                                        lies between cells i-1 and i
+ *   v        nx*(ny+1)*nz  y-faces       index i + nx*(j + (ny+1)*k)
+ *   w        nx*ny*nz      z-faces       index i + nx*(j + ny*k); face k lies
+ *                                        between cells k-1 and k (periodic)
+ * The duct has no-slip walls at x = 0, nx*h and y = 0, ny*h (the wall faces
+ * i = 0, nx of u and j = 0, ny of v carry zero velocity and are written as
+ * zero by project/step) and is periodic in z (Section 4). alpha is the
+ * liquid volume fraction (1 liquid, 0 gas). Pressure P is cell-centred and
+ * is the total pressure p + p_tilde of steps 6 and 11 (the surface-tension
+ * pressure and the dynamic pressure, obtained from one solve because both
+ * elliptic problems share the operator and are linear in their sources).
+ *
+ * Velocity lives in two places, as in the paper's collocated solver
+ * (Section 2, steps 8-12): cell-centred (uc, vc, wc; cell layout), the
+ * momentum variable, and on faces (u, v, w), the divergence-free field that
+ * advects alpha and carries the mass fluxes.
+ *
+ * Calls are asynchronous on the context's stream except where a report is
+ * requested: then the call synchronises the stream before returning so the
+ * report is complete. Errors are return codes; vof_last_error() gives a
+ * message. A context is not thread-safe; use one per host thread/stream.
+ * There is no CPU fallback: every arithmetic step runs in CUDA kernels.
+ */
+#ifndef VOF_H
+#define VOF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VOF_OK = 0,
+    VOF_ERR_ARG = 1,            /* bad size, pointer, flag or value           */
+    VOF_ERR_OOM = 2,            /* device allocation failed                   */
+    VOF_ERR_CUDA = 3,           /* a CUDA runtime call failed                 */
+    VOF_ERR_NOT_CONVERGED = 4,  /* pressure solve hit max_iter (p = last iterate) */
+    VOF_ERR_NONFINITE = 5,      /* NaN/Inf in a residual norm                 */
+    VOF_ERR_CFL = 6,            /* |u| dt / h > 1 on some face                */
+    VOF_ERR_TIMEOUT = 7,        /* a bounded device wait ran out              */
+    VOF_ERR_ADMISSION = 8,      /* workspace exceeds the memory budget        */
+    VOF_ERR_UNSUPPORTED = 9     /* valid request this build does not support  */
+} vof_status;
+
+typedef struct {
+    int nx, ny, nz;       /* cells; nx, ny >= 2; nz >= 4 and even            */
+    double h;             /* uniform spacing (m)                              */
+    int periodic_x;       /* 1: x periodic instead of walls (vof_advect only) */
+    int periodic_y;       /* 1: y periodic instead of walls (vof_advect only) */
+} vof_grid;
+
+enum { VOF_CONV_CENTRAL = 0, VOF_CONV_UPWIND = 1 };
+enum { VOF_KAPPA_HEIGHT_FUNCTION = 0, VOF_KAPPA_EXACT = 1 };
+
+typedef struct {
+    double rho_l, rho_g;  /* densities (Eq. 4)                                 */
+    double mu_l, mu_g;    /* viscosities (Eq. 5)                               */
+    double sigma;         /* surface tension coefficient (Eq. 2)               */
+    double g_z;           /* gravity along z (negative: downward, Section 4)   */
+    double rho0;          /* density whose weight is removed (Section 4)       */
+    double dpdz;          /* imposed mean driving force per volume along +z    */
+    int conv_scheme;      /* VOF_CONV_*                                        */
+    int kappa_mode;       /* VOF_KAPPA_*                                       */
+    double kappa_exact;   /* curvature used when kappa_mode == EXACT (1/m)     */
+} vof_phys;
+
+enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED_FP32 = 1 };
+
+typedef struct {
+    int precision;        /* VOF_PREC_*: multigrid preconditioner precision   */
+    double rtol;          /* stop when ||b - A P||_2 <= rtol ||b||_2          */
+    int max_iter;         /* Krylov iteration cap                             */
+    int nu_pre, nu_post;  /* red-black Gauss-Seidel sweeps per level          */
+} vof_solver;
+
+typedef struct {
+    int iters;                    /* Krylov iterations of the last solve        */
+    double res0, res;             /* initial / final relative residual          */
+    double b_mean;                /* mean removed from the right side           */
+    double vol_before, vol_after; /* liquid volume sum(alpha) h^3 (m^3)         */
+    double vol_clipped;           /* volume added by clipping alpha to [0,1]    */
+    double max_div;               /* max |div u| after the projection (1/s)     */
+    double max_u;                 /* max |face velocity| after projection (m/s) */
+    long long hf_fallbacks;       /* faces whose curvature needed the fallback  */
+    float ms[8];                  /* advect, ssf, predict, rhs, solve, project,
+                                     other, total (ms; filled when timing is on) */
+} vof_report;
+
+typedef struct vof_ctx vof_ctx;
+
+/* Device memory a context for this grid/solver needs (bytes), without
+ * allocating anything. Returns VOF_ERR_ARG for an invalid grid. */
+vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, size_t* bytes);
+
+/* Create a context on the current CUDA device: validates the grid, physics
+ * and solver settings and allocates the whole workspace once (multigrid
+ * hierarchy, Krylov vectors, scratch). budget_bytes > 0 caps that workspace
+ * (VOF_ERR_ADMISSION if exceeded); 0 means no cap. stream is a cudaStream_t
+ * (NULL = legacy default stream). On failure *out is NULL. */
+vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solver* solver,
+                      size_t budget_bytes, void* stream, vof_ctx** out);
+vof_status vof_destroy(vof_ctx* ctx);
+const char* vof_last_error(const vof_ctx* ctx);
+
+/* Advance alpha in place by one time step of dt with the face velocities
+ * (u, v, w) (Eq. 3): PLIC reconstruction with the normal from the smoothed
+ * volume fraction (Section 2, Rudman), plane constants in FP64, and
+ * geometric donor-slab fluxes in three direction-split sweeps (x, y, z when
+ * step_index is even, z, y, x when odd; the "second-order operator split"
+ * of Section 2.1), the divergence term weighted by [alpha^n > 1/2] so the
+ * liquid volume is conserved to round-off when div u = 0 (abstract:
+ * absolute mass conservation). Wall-face values of u, v are ignored.
+ * fx, fy, fz (optional, NULL to skip; face layouts as u, v, w): the signed
+ * liquid volume that crossed each face in its sweep, in cell volumes -- the
+ * mass fluxes vof_predict needs. VOF_ERR_CFL if some |u| dt/h > 1. report
+ * (optional) gets the volumes. */
+vof_status vof_advect(vof_ctx* ctx, double* alpha, const double* u, const double* v,
+                      const double* w, double dt, long long step_index, double* fx, double* fy,
+                      double* fz, vof_report* report);
+
+/* Interface curvature and the sharp surface force on faces (Eq. 6, steps
+ * 5-7): kappa per cell from height functions (Section 2, Cummins et al.;
+ * 0 where no valid column exists) or kappa_exact, and
+ *   s_f = sigma * kappa_f * (G_R - G_L) / h,  G = [alpha < 1/2],
+ * with kappa_f the mean of the valid neighbouring cell values. Outputs
+ * kappa (cells) and sx, sy, sz (face layouts as u, v, w; zero on walls). */
+vof_status ssf_force(vof_ctx* ctx, const double* alpha, double* kappa, double* sx, double* sy,
+                     double* sz);
+
+/* Solve the variable-coefficient pressure equation (Eq. 7, steps 6/11)
+ *   (A P)_c = (1/h^2) sum_f beta_f (P_c - P_nb) = b_c,
+ *   beta_f = 2 / (rho_L + rho_R),  rho = alpha rho_l + (1 - alpha) rho_g,
+ * with geometric-multigrid-preconditioned flexible CG. mean(b) is removed
+ * (singular operator: walls and periodic z) and reported; p is the initial
+ * guess on entry and the mean-free solution on exit. VOF_ERR_NOT_CONVERGED
+ * leaves the last iterate in p. */
+vof_status pressure_solve(vof_ctx* ctx, const double* alpha, const double* b, double* p,
+                          vof_report* report);
+
+/* y = A x with beta from alpha (the operator of pressure_solve). */
+vof_status vof_apply_operator(vof_ctx* ctx, const double* alpha, const double* x, double* y);
+
+/* Momentum predictor (Eq. 2; steps 8-10). On entry (uc, vc, wc) hold the
+ * cell velocity u^n and (u, v, w) the face velocity that advected alpha
+ * from alpha_n to alpha_np1 with liquid face fluxes (fx, fy, fz) from
+ * vof_advect. On exit (uc, vc, wc) hold the intermediate cell velocity
+ *   u_hat = [rho^n u^n - sum_f M_f q*_f + dt (V + B)] / rho^{n+1},
+ *   M_f = rho_l F_f + rho_g (u_f dt/h - F_f)   (mass moved by the sweep),
+ * q*_f the donor cell's velocity (upwind) or the two-cell mean (central),
+ * V the explicit full-stress viscous force, B = (rho^n - rho0) g_z + dpdz on
+ * the z-component (Section 4); and (u, v, w) hold u_hat_f, the mean of the
+ * two cells (step 10), zero on walls. */
+vof_status vof_predict(vof_ctx* ctx, const double* alpha_n, const double* alpha_np1, double* uc,
+                       double* vc, double* wc, double* u, double* v, double* w, const double* fx,
+                       const double* fy, const double* fz, double dt);
+
+/* Projection (steps 11-12): b = -div(u_hat_f)/dt - div(beta s), solve
+ * A P = b (p: initial guess in, solution out), then with the face
+ * acceleration a_f = beta_f ((P_R - P_L)/h - s_f):
+ *   u_f = u_hat_f - dt a_f,   u_c = u_hat_c - dt (a_f- + a_f+)/2
+ * (each cell component takes the mean of its two faces in that direction).
+ * (uc, vc, wc) and (u, v, w) are updated in place. report gets iterations,
+ * residuals, max|div u_f| and max|u_f|. */
+vof_status project(vof_ctx* ctx, const double* alpha, double* uc, double* vc, double* wc, double* u,
+                   double* v, double* w, double* p, const double* sx, const double* sy,
+                   const double* sz, double dt, vof_report* report);
+
+/* One whole time step (steps 1-12): vof_advect with the face velocities,
+ * vof_predict, ssf_force on alpha^{n+1}, project. All arguments are updated
+ * in place. */
+vof_status step(vof_ctx* ctx, double* alpha, double* uc, double* vc, double* wc, double* u,
+                double* v, double* w, double* p, double dt, long long step_index,
+                vof_report* report);
+
+/* Number of CUDA kernels this context has launched since creation. */
+vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
+
+/* Per-phase CUDA-event timing inside the calls (off by default). When on,
+ * kernel classes are bracketed by events on the context stream and the
+ * accumulated device time and launch counts are returned by
+ * vof_kernel_times (then reset). Classes: "advect", "ssf", "predict", "rhs",
+ * "smooth_l0" (fine-grid red-black half-sweeps), "smooth" (coarser levels),
+ * "residual_l0" (fine-grid operator applications in the Krylov loop),
+ * "restrict_l0", "restrict", "prolong_l0", "prolong", "coarse", "krylov"
+ * (fine-grid vector updates), "project"; n = number of classes written
+ * (<= cap). */
+vof_status vof_set_timing(vof_ctx* ctx, int on);
+vof_status vof_kernel_times(vof_ctx* ctx, const char** names, double* ms, long long* launches,
+                            int cap, int* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

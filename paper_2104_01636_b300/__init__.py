@@ -1,0 +1,265 @@
+"""Python binding of libvofduct.so, the sm_103a projection-step library.
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels behind the C ABI of include/vof.h. Fields are torch float64 CUDA
+tensors (contiguous) shaped like the arrays of `paper_2104_01636_b300.inputs`:
+cells (nz, ny, nx), x-faces (nz, ny, nx+1), y-faces (nz, ny+1, nx), z-faces
+(nz, ny, nx). Velocities come as cell-centred (uc, vc, wc) and face (u, v, w)
+fields. Calls run on the context's stream (the current torch stream at
+creation unless one is given).
+
+There is no CPU fallback: a missing library or device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libvofduct.so")
+
+STATUS = {0: "VOF_OK", 1: "VOF_ERR_ARG", 2: "VOF_ERR_OOM", 3: "VOF_ERR_CUDA",
+          4: "VOF_ERR_NOT_CONVERGED", 5: "VOF_ERR_NONFINITE", 6: "VOF_ERR_CFL",
+          7: "VOF_ERR_TIMEOUT", 8: "VOF_ERR_ADMISSION", 9: "VOF_ERR_UNSUPPORTED"}
+PREC_FP64, PREC_MIXED_FP32 = 0, 1
+
+
+class VofError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str = "", report=None):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        self.report = report
+        super().__init__(f"{where}: {self.name}{': ' + msg if msg else ''}")
+
+
+class CGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int)]
+
+
+class CPhys(ctypes.Structure):
+    _fields_ = [("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
+                ("mu_l", ctypes.c_double), ("mu_g", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("g_z", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("dpdz", ctypes.c_double),
+                ("conv_scheme", ctypes.c_int), ("kappa_mode", ctypes.c_int),
+                ("kappa_exact", ctypes.c_double)]
+
+
+class CSolver(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int)]
+
+
+class CReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("b_mean", ctypes.c_double), ("vol_before", ctypes.c_double),
+                ("vol_after", ctypes.c_double), ("vol_clipped", ctypes.c_double),
+                ("max_div", ctypes.c_double), ("max_u", ctypes.c_double),
+                ("hf_fallbacks", ctypes.c_longlong), ("ms", ctypes.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n != "ms"}
+        d["ms"] = list(self.ms)
+        return d
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_D = ctypes.c_double
+
+
+def load() -> ctypes.CDLL:
+    """Load libvofduct.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2104_01636_b300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "vof_workspace_bytes": [P(CGrid), P(CSolver), P(ctypes.c_size_t)],
+        "vof_create": [P(CGrid), P(CPhys), P(CSolver), ctypes.c_size_t, _VP, P(_VP)],
+        "vof_destroy": [_VP],
+        "vof_advect": [_VP, _VP, _VP, _VP, _VP, _D, ctypes.c_longlong, _VP, _VP, _VP,
+                       P(CReport)],
+        "ssf_force": [_VP, _VP, _VP, _VP, _VP, _VP],
+        "pressure_solve": [_VP, _VP, _VP, _VP, P(CReport)],
+        "vof_apply_operator": [_VP, _VP, _VP, _VP],
+        "vof_predict": [_VP] * 12 + [_D],
+        "project": [_VP] * 12 + [_D, P(CReport)],
+        "step": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
+        "vof_set_timing": [_VP, ctypes.c_int],
+        "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
+        "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
+                             P(ctypes.c_int)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.vof_last_error.argtypes = [_VP]
+    lib.vof_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def c_grid(g) -> CGrid:
+    return CGrid(int(g.nx), int(g.ny), int(g.nz), float(g.h), int(getattr(g, "per_x", 0)),
+                 int(getattr(g, "per_y", 0)))
+
+
+def c_phys(p) -> CPhys:
+    return CPhys(p.rho_l, p.rho_g, p.mu_l, p.mu_g, p.sigma, p.g_z, p.rho0, p.dpdz,
+                 int(p.conv_scheme), int(p.kappa_mode), float(p.kappa_exact))
+
+
+def c_solver(precision=PREC_FP64, rtol=1e-10, max_iter=200, nu_pre=2, nu_post=2) -> CSolver:
+    return CSolver(int(precision), float(rtol), int(max_iter), int(nu_pre), int(nu_post))
+
+
+def workspace_bytes(grid, solver: CSolver | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    g = c_grid(grid)
+    s = solver or c_solver()
+    st = load().vof_workspace_bytes(ctypes.byref(g), ctypes.byref(s), ctypes.byref(out))
+    if st:
+        raise VofError(st, "vof_workspace_bytes")
+    return int(out.value)
+
+
+class VofContext:
+    """One library context (workspace on the current CUDA device)."""
+
+    def __init__(self, grid, phys, solver: CSolver | None = None, budget_bytes: int = 0,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.lib = load()
+        self.grid = grid
+        self.shapes = ((grid.nz, grid.ny, grid.nx), (grid.nz, grid.ny, grid.nx + 1),
+                       (grid.nz, grid.ny + 1, grid.nx), (grid.nz, grid.ny, grid.nx))
+        self._g, self._p = c_grid(grid), c_phys(phys)
+        self._s = solver or c_solver()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._ctx = _VP()
+        st = self.lib.vof_create(ctypes.byref(self._g), ctypes.byref(self._p),
+                                 ctypes.byref(self._s), ctypes.c_size_t(budget_bytes),
+                                 _VP(stream.cuda_stream), ctypes.byref(self._ctx))
+        if st:
+            raise VofError(st, "vof_create")
+
+    # -- helpers -------------------------------------------------------------
+    def _chk(self, st: int, where: str, rep: CReport | None = None):
+        if st:
+            msg = self.lib.vof_last_error(self._ctx)
+            raise VofError(st, where, msg.decode() if msg else "",
+                           rep.as_dict() if rep is not None else None)
+
+    def _ptr(self, t, kind: int, name: str):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous()):
+            raise TypeError(f"{name}: need a contiguous float64 CUDA tensor")
+        if tuple(t.shape) != self.shapes[kind]:
+            raise ValueError(f"{name}: shape {tuple(t.shape)} != {self.shapes[kind]}")
+        return _VP(t.data_ptr())
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self.lib.vof_destroy(self._ctx)
+            self._ctx = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points (same names as the C ABI) --------------------------------
+    def vof_advect(self, alpha, u, v, w, dt: float, step_index: int, fluxes=None,
+                   report: bool = True):
+        """fluxes: optional (fx, fy, fz) face tensors receiving the liquid fluxes."""
+        rep = CReport()
+        fl = ([self._ptr(f, k + 1, n) for k, (f, n) in enumerate(zip(fluxes, ("fx", "fy", "fz")))]
+              if fluxes is not None else [None, None, None])
+        st = self.lib.vof_advect(self._ctx, self._ptr(alpha, 0, "alpha"), self._ptr(u, 1, "u"),
+                                 self._ptr(v, 2, "v"), self._ptr(w, 3, "w"), float(dt),
+                                 int(step_index), *fl, ctypes.byref(rep) if report else None)
+        self._chk(st, "vof_advect", rep)
+        return rep.as_dict() if report else None
+
+    def ssf_force(self, alpha, kappa, sx, sy, sz):
+        st = self.lib.ssf_force(self._ctx, self._ptr(alpha, 0, "alpha"), self._ptr(kappa, 0, "kappa"),
+                                self._ptr(sx, 1, "sx"), self._ptr(sy, 2, "sy"), self._ptr(sz, 3, "sz"))
+        self._chk(st, "ssf_force")
+
+    def pressure_solve(self, alpha, b, p, report: bool = True):
+        rep = CReport()
+        st = self.lib.pressure_solve(self._ctx, self._ptr(alpha, 0, "alpha"), self._ptr(b, 0, "b"),
+                                     self._ptr(p, 0, "p"), ctypes.byref(rep) if report else None)
+        self._chk(st, "pressure_solve", rep)
+        return rep.as_dict() if report else None
+
+    def vof_apply_operator(self, alpha, x, y):
+        st = self.lib.vof_apply_operator(self._ctx, self._ptr(alpha, 0, "alpha"),
+                                         self._ptr(x, 0, "x"), self._ptr(y, 0, "y"))
+        self._chk(st, "vof_apply_operator")
+
+    def vof_predict(self, alpha_n, alpha_np1, uc, vc, wc, u, v, w, fx, fy, fz, dt: float):
+        st = self.lib.vof_predict(self._ctx, self._ptr(alpha_n, 0, "alpha_n"),
+                                  self._ptr(alpha_np1, 0, "alpha_np1"), self._ptr(uc, 0, "uc"),
+                                  self._ptr(vc, 0, "vc"), self._ptr(wc, 0, "wc"),
+                                  self._ptr(u, 1, "u"), self._ptr(v, 2, "v"), self._ptr(w, 3, "w"),
+                                  self._ptr(fx, 1, "fx"), self._ptr(fy, 2, "fy"),
+                                  self._ptr(fz, 3, "fz"), float(dt))
+        self._chk(st, "vof_predict")
+
+    def project(self, alpha, uc, vc, wc, u, v, w, p, sx, sy, sz, dt: float, report: bool = True):
+        rep = CReport()
+        st = self.lib.project(self._ctx, self._ptr(alpha, 0, "alpha"), self._ptr(uc, 0, "uc"),
+                              self._ptr(vc, 0, "vc"), self._ptr(wc, 0, "wc"), self._ptr(u, 1, "u"),
+                              self._ptr(v, 2, "v"), self._ptr(w, 3, "w"), self._ptr(p, 0, "p"),
+                              self._ptr(sx, 1, "sx"), self._ptr(sy, 2, "sy"), self._ptr(sz, 3, "sz"),
+                              float(dt), ctypes.byref(rep) if report else None)
+        self._chk(st, "project", rep)
+        return rep.as_dict() if report else None
+
+    def step(self, alpha, uc, vc, wc, u, v, w, p, dt: float, step_index: int,
+             report: bool = True):
+        rep = CReport()
+        st = self.lib.step(self._ctx, self._ptr(alpha, 0, "alpha"), self._ptr(uc, 0, "uc"),
+                           self._ptr(vc, 0, "vc"), self._ptr(wc, 0, "wc"), self._ptr(u, 1, "u"),
+                           self._ptr(v, 2, "v"), self._ptr(w, 3, "w"), self._ptr(p, 0, "p"),
+                           float(dt), int(step_index), ctypes.byref(rep) if report else None)
+        self._chk(st, "step", rep)
+        return rep.as_dict() if report else None
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong(0)
+        self._chk(self.lib.vof_launch_count(self._ctx, ctypes.byref(n)), "vof_launch_count")
+        return int(n.value)
+
+    def set_timing(self, on: bool):
+        self._chk(self.lib.vof_set_timing(self._ctx, int(bool(on))), "vof_set_timing")
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        n_l = (ctypes.c_longlong * cap)()
+        n = ctypes.c_int(0)
+        self._chk(self.lib.vof_kernel_times(self._ctx, names, ms, n_l, cap, ctypes.byref(n)),
+                  "vof_kernel_times")
+        return {names[i].decode(): (ms[i], int(n_l[i])) for i in range(n.value)}

@@ -1,0 +1,557 @@
+// C ABI of the projection step (include/vof.h): context lifetime, argument
+// validation, the workspace, and the five entry points of the time step.
+#include <cmath>
+#include <cstring>
+
+#include "vof_internal.cuh"
+
+namespace {
+
+constexpr int P_A = 20, P_B = 21, P_C = 22;  // scratch partial slots
+
+struct Sizes {
+    size_t n, nu, nv, nw;
+};
+
+Sizes sizes_of(const vof_grid* g) {
+    Sizes s;
+    s.n = (size_t)g->nx * g->ny * g->nz;
+    s.nu = (size_t)(g->nx + 1) * g->ny * g->nz;
+    s.nv = (size_t)g->nx * (g->ny + 1) * g->nz;
+    s.nw = s.n;
+    return s;
+}
+
+bool grid_ok(const vof_grid* g, std::string& why) {
+    if (!g) { why = "grid is NULL"; return false; }
+    if (g->nx < 2 || g->ny < 2 || g->nz < 4) { why = "need nx, ny >= 2 and nz >= 4"; return false; }
+    if (g->nz % 2) { why = "nz must be even (red-black ordering on the periodic axis)"; return false; }
+    if (!(g->h > 0.0) || !std::isfinite(g->h)) { why = "h must be positive"; return false; }
+    if ((g->periodic_x && g->nx % 2) || (g->periodic_y && g->ny % 2)) {
+        why = "periodic x/y need an even cell count";
+        return false;
+    }
+    const double faces = (double)(g->nx + 1) * (double)(g->ny + 1) * (double)g->nz;
+    if (faces >= 2147483647.0) { why = "grid too large for 32-bit indexing"; return false; }
+    const long tiles = (long)((g->nx + TBX - 1) / TBX) * ((g->ny + TBY - 1) / TBY);
+    if (tiles > MAX_PARTIALS) { why = "cross-section too large"; return false; }
+    return true;
+}
+
+size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
+    const Sizes s = sizes_of(g);
+    const size_t faces = s.nu + s.nv + s.nw;
+    size_t b = 0;
+    b += 3 * faces * sizeof(double);                  // beta, surface force, fluxes
+    b += s.n * sizeof(double);                        // kappa
+    b += 3 * s.n;                                     // valid, cmask, has
+    b += 4 * s.n * sizeof(double);                    // planes
+    b += 3 * s.n * sizeof(double);                    // cell intermediate velocity
+    b += 3 * s.n * sizeof(double);                    // alpha scratch
+    b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
+    b += mg_workspace_bytes(g, sv, nullptr);
+    b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
+    return b;
+}
+
+vof_status alloc(vof_ctx* c, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, VOF_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(*p);
+    return VOF_OK;
+}
+
+void readback(vof_ctx* c) {
+    cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost, c->st);
+    cudaStreamSynchronize(c->st);
+}
+
+void flush_timers(vof_ctx* c) {
+    if (c->ev_marks.empty()) return;
+    cudaStreamSynchronize(c->st);
+    for (auto& m : c->ev_marks) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev_pool[m.second.first], c->ev_pool[m.second.second]);
+        c->t_ms[m.first] += ms;
+        c->t_n[m.first] += 1;
+    }
+    c->ev_marks.clear();
+}
+
+vof_status check_ctx(vof_ctx* c) {
+    if (!c) return VOF_ERR_ARG;
+    c->err.clear();
+    return VOF_OK;
+}
+
+#define REQUIRE_PTR(c, p)                                                 \
+    do {                                                                  \
+        if (!(p)) return set_err((c), VOF_ERR_ARG, #p " is NULL");        \
+    } while (0)
+
+vof_status walls_only(vof_ctx* c, const char* who) {
+    if (c->g.periodic_x || c->g.periodic_y)
+        return set_err(c, VOF_ERR_UNSUPPORTED,
+                       std::string(who) + " needs wall boundaries in x and y");
+    return VOF_OK;
+}
+
+vof_status cfl_check(vof_ctx* c, const double* u, const double* v, const double* w, double dt) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(c, VOF_ERR_ARG, "dt must be positive");
+    launch_cfl(c, u, v, w, dt, P_A);
+    readback(c);
+    const double cfl = c->hbuf[S_CFL] * dt / c->g.h;
+    if (!std::isfinite(cfl)) return set_err(c, VOF_ERR_NONFINITE, "non-finite velocity");
+    if (cfl > 1.0)
+        return set_err(c, VOF_ERR_CFL, "Courant number " + std::to_string(cfl) + " exceeds 1");
+    return VOF_OK;
+}
+
+// three direction-split sweeps; alpha in place (ping-pong through a1, a2);
+// the liquid flux of every face is left in flux[dir]
+void advect_impl(vof_ctx* c, double* alpha, const double* u, const double* v, const double* w,
+                 double dt, long long step_index, double* const flux[3]) {
+    const double h3 = c->g.h * c->g.h * c->g.h;
+    int m = timer_begin(c, T_ADVECT);
+    launch_vof_mask_volume(c, alpha, P_A);
+    timer_end(c, T_ADVECT, m);
+    finalize_sum(c, P_A, c->Lc.nblocks, S_VOL0, h3);
+    const double* vel[3] = {u, v, w};
+    const double* src = alpha;
+    for (int s = 0; s < 3; ++s) {
+        const int dir = (step_index % 2 == 0) ? s : 2 - s;
+        double* dst = s == 2 ? alpha : (s == 0 ? c->a1 : c->a2);
+        launch_reconstruct(c, src);
+        launch_face_flux(c, dir, src, vel[dir], dt, flux[dir]);
+        launch_vof_update(c, dir, src, dst, vel[dir], flux[dir], dt, P_B);
+        finalize_sum(c, P_B, c->Lc.nblocks, S_CLIP0 + s, h3);
+        src = dst;
+    }
+    launch_volume(c, alpha, P_A);
+    finalize_sum(c, P_A, c->Lc.nblocks, S_VOL1, h3);
+}
+
+void fill_vof_report(vof_ctx* c, vof_report* r) {
+    r->vol_before = c->hbuf[S_VOL0];
+    r->vol_after = c->hbuf[S_VOL1];
+    r->vol_clipped = c->hbuf[S_CLIP0] + c->hbuf[S_CLIP1] + c->hbuf[S_CLIP2];
+}
+
+void ssf_impl(vof_ctx* c, const double* alpha, double* kappa, double* sx, double* sy, double* sz) {
+    launch_curvature(c, alpha, kappa, c->valid);
+    launch_ssf_faces(c, alpha, kappa, c->valid, sx, sy, sz, P_C);
+}
+
+void report_timing_begin(vof_ctx* c, double snap[T_NCLASS]) {
+    if (!c->timing) return;
+    flush_timers(c);
+    for (int t = 0; t < T_NCLASS; ++t) snap[t] = c->t_ms[t];
+}
+
+void report_timing_end(vof_ctx* c, const double snap[T_NCLASS], vof_report* r) {
+    if (!c->timing || !r) return;
+    flush_timers(c);
+    double d[T_NCLASS];
+    for (int t = 0; t < T_NCLASS; ++t) d[t] = c->t_ms[t] - snap[t];
+    r->ms[0] = (float)d[T_ADVECT];
+    r->ms[1] = (float)d[T_SSF];
+    r->ms[2] = (float)d[T_PREDICT];
+    r->ms[3] = (float)d[T_RHS];
+    r->ms[4] = (float)(d[T_SMOOTH0] + d[T_SMOOTH] + d[T_RESIDUAL] + d[T_RESTRICT0] +
+                       d[T_RESTRICT] + d[T_PROLONG0] + d[T_PROLONG] + d[T_COARSE] + d[T_KRYLOV]);
+    r->ms[5] = (float)d[T_PROJECT];
+    r->ms[6] = 0.f;
+    double tot = 0;
+    for (int t = 0; t < T_NCLASS; ++t) tot += d[t];
+    r->ms[7] = (float)tot;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// helpers used by the other translation units
+// ---------------------------------------------------------------------------
+vof_status set_err(vof_ctx* c, vof_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+vof_status cuda_check(vof_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return VOF_OK;
+    return set_err(c, VOF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+vof_status launch_check(vof_ctx* c, const char* what) {
+    return cuda_check(c, cudaGetLastError(), what);
+}
+
+int timer_begin(vof_ctx* c, int cls) {
+    if (!c->timing) return -1;
+    if (c->ev_marks.size() >= 8192) flush_timers(c);
+    const size_t need = 2 * (c->ev_marks.size() + 1);
+    while (c->ev_pool.size() < need) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    const int a = (int)(2 * c->ev_marks.size()), b = a + 1;
+    cudaEventRecord(c->ev_pool[a], c->st);
+    c->ev_marks.push_back({cls, {a, b}});
+    return (int)c->ev_marks.size() - 1;
+}
+
+void timer_end(vof_ctx* c, int, int mark) {
+    if (mark < 0) return;
+    cudaEventRecord(c->ev_pool[c->ev_marks[mark].second.second], c->st);
+}
+
+// ---------------------------------------------------------------------------
+// the C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, size_t* bytes) {
+    std::string why;
+    if (!grid_ok(grid, why) || !bytes) return VOF_ERR_ARG;
+    vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2};
+    *bytes = workspace_bytes(grid, solver ? solver : &def);
+    return VOF_OK;
+}
+
+vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solver* solver,
+                      size_t budget_bytes, void* stream, vof_ctx** out) {
+    if (!out) return VOF_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!grid_ok(grid, why) || !phys || !solver) return VOF_ERR_ARG;
+    if (!(phys->rho_l > 0) || !(phys->rho_g > 0) || !(phys->mu_l >= 0) || !(phys->mu_g >= 0) ||
+        !(phys->sigma >= 0) || (phys->conv_scheme != VOF_CONV_CENTRAL &&
+                                phys->conv_scheme != VOF_CONV_UPWIND) ||
+        (phys->kappa_mode != VOF_KAPPA_HEIGHT_FUNCTION && phys->kappa_mode != VOF_KAPPA_EXACT))
+        return VOF_ERR_ARG;
+    if (!(solver->rtol > 0) || solver->max_iter < 1 || solver->nu_pre < 1 ||
+        solver->nu_pre != solver->nu_post ||
+        (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
+        return VOF_ERR_ARG;
+    const size_t need = workspace_bytes(grid, solver);
+    if (budget_bytes && need > budget_bytes) return VOF_ERR_ADMISSION;
+
+    vof_ctx* c = new vof_ctx();
+    c->g = *grid;
+    c->ph = *phys;
+    c->sv = *solver;
+    c->d = Dims{grid->nx, grid->ny, grid->nz};
+    c->st = (cudaStream_t)stream;
+    c->bytes = need;
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return VOF_ERR_CUDA;
+    }
+    c->Lc = launch_cells(grid->nx, grid->ny, grid->nz, c->sm_count);
+    const Sizes s = sizes_of(grid);
+    vof_status st = VOF_OK;
+    auto A = [&](void** p, size_t b) {
+        if (st == VOF_OK) st = alloc(c, p, b);
+    };
+    const size_t D = sizeof(double);
+    A((void**)&c->bx, s.nu * D);
+    A((void**)&c->by, s.nv * D);
+    A((void**)&c->bz, s.nw * D);
+    A((void**)&c->sx, s.nu * D);
+    A((void**)&c->sy, s.nv * D);
+    A((void**)&c->sz, s.nw * D);
+    A((void**)&c->fx, s.nu * D);
+    A((void**)&c->fy, s.nv * D);
+    A((void**)&c->fz, s.nw * D);
+    for (int q = 0; q < 3; ++q) A((void**)&c->uh[q], s.n * D);
+    A((void**)&c->kappa, s.n * D);
+    A((void**)&c->valid, s.n);
+    A((void**)&c->cmask, s.n);
+    A((void**)&c->has, s.n);
+    A((void**)&c->plane, 4 * s.n * D);
+    A((void**)&c->a1, s.n * D);
+    A((void**)&c->a2, s.n * D);
+    A((void**)&c->an, s.n * D);
+    A((void**)&c->b, s.n * D);
+    A((void**)&c->r, s.n * D);
+    A((void**)&c->z, s.n * D);
+    A((void**)&c->p, s.n * D);
+    A((void**)&c->q, s.n * D);
+    A((void**)&c->rhs, s.n * D);
+    A((void**)&c->part, (size_t)NSLOTS * MAX_PARTIALS * D);
+    A((void**)&c->scal, S_NSCALARS * D);
+    A((void**)&c->dflag, 64);
+    if (st == VOF_OK) st = mg_allocate(c);
+    if (st == VOF_OK && cudaMallocHost((void**)&c->hbuf, S_NSCALARS * D) != cudaSuccess) {
+        cudaGetLastError();
+        st = VOF_ERR_OOM;
+    }
+    if (st == VOF_OK) {
+        cudaMemsetAsync(c->scal, 0, S_NSCALARS * D, c->st);
+        cudaMemsetAsync(c->part, 0, (size_t)NSLOTS * MAX_PARTIALS * D, c->st);
+        st = cuda_check(c, cudaStreamSynchronize(c->st), "vof_create");
+    }
+    if (st != VOF_OK) {
+        vof_destroy(c);
+        return st;
+    }
+    *out = c;
+    return VOF_OK;
+}
+
+vof_status vof_destroy(vof_ctx* c) {
+    if (!c) return VOF_ERR_ARG;
+    cudaStreamSynchronize(c->st);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->hbuf) cudaFreeHost(c->hbuf);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+    return VOF_OK;
+}
+
+const char* vof_last_error(const vof_ctx* c) {
+    if (!c) return "NULL context";
+    return c->err.c_str();
+}
+
+vof_status vof_advect(vof_ctx* c, double* alpha, const double* u, const double* v,
+                      const double* w, double dt, long long step_index, double* fx, double* fy,
+                      double* fz, vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
+    if ((st = cfl_check(c, u, v, w, dt))) return st;
+    double snap[T_NCLASS];
+    report_timing_begin(c, snap);
+    double* const flux[3] = {fx ? fx : c->fx, fy ? fy : c->fy, fz ? fz : c->fz};
+    advect_impl(c, alpha, u, v, w, dt, step_index, flux);
+    if ((st = launch_check(c, "vof_advect"))) return st;
+    if (report) {
+        readback(c);
+        fill_vof_report(c, report);
+        report_timing_end(c, snap, report);
+        if ((st = launch_check(c, "vof_advect"))) return st;
+    }
+    return VOF_OK;
+}
+
+vof_status ssf_force(vof_ctx* c, const double* alpha, double* kappa, double* sx, double* sy,
+                     double* sz) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, kappa);
+    REQUIRE_PTR(c, sx);
+    REQUIRE_PTR(c, sy);
+    REQUIRE_PTR(c, sz);
+    if ((st = walls_only(c, "ssf_force"))) return st;
+    ssf_impl(c, alpha, kappa, sx, sy, sz);
+    return launch_check(c, "ssf_force");
+}
+
+vof_status pressure_solve(vof_ctx* c, const double* alpha, const double* b, double* p,
+                          vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, b);
+    REQUIRE_PTR(c, p);
+    if ((st = walls_only(c, "pressure_solve"))) return st;
+    double snap[T_NCLASS];
+    report_timing_begin(c, snap);
+    launch_beta(c, alpha);
+    vof_report r;
+    std::memset(&r, 0, sizeof(r));
+    st = solve_pressure(c, b, p, &r);
+    if (report) {
+        *report = r;
+        report_timing_end(c, snap, report);
+    }
+    return st;
+}
+
+vof_status vof_apply_operator(vof_ctx* c, const double* alpha, const double* x, double* y) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, x);
+    REQUIRE_PTR(c, y);
+    if ((st = walls_only(c, "vof_apply_operator"))) return st;
+    launch_beta(c, alpha);
+    launch_apply_A(c, c->lv[0], x, y);
+    return launch_check(c, "vof_apply_operator");
+}
+
+vof_status vof_predict(vof_ctx* c, const double* alpha_n, const double* alpha_np1, double* uc,
+                       double* vc, double* wc, double* u, double* v, double* w, const double* fx,
+                       const double* fy, const double* fz, double dt) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha_n);
+    REQUIRE_PTR(c, alpha_np1);
+    REQUIRE_PTR(c, uc);
+    REQUIRE_PTR(c, vc);
+    REQUIRE_PTR(c, wc);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    REQUIRE_PTR(c, fx);
+    REQUIRE_PTR(c, fy);
+    REQUIRE_PTR(c, fz);
+    if ((st = walls_only(c, "vof_predict"))) return st;
+    if (!(dt > 0.0)) return set_err(c, VOF_ERR_ARG, "dt must be positive");
+    const double* const U[3] = {uc, vc, wc};
+    launch_predict(c, alpha_n, alpha_np1, U, u, v, w, fx, fy, fz, dt, c->uh);
+    launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], u, v, w);
+    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
+    cudaMemcpyAsync(uc, c->uh[0], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(vc, c->uh[1], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(wc, c->uh[2], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    return launch_check(c, "vof_predict");
+}
+
+// steps 11-12 on (u_hat_c in Uh, u_hat_f in u, v, w): right side, solve,
+// correction of faces (in place) and cells (written to Uc)
+static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* const Uc[3],
+                               double* u, double* v, double* w, double* p, const double* sx,
+                               const double* sy, const double* sz, double dt, vof_report* r) {
+    launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, -1);
+    vof_status st = solve_pressure(c, c->rhs, p, r);
+    if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
+    launch_correct(c, p, sx, sy, sz, dt, Uh, Uc, u, v, w, P_A, P_B);
+    readback(c);
+    r->max_div = c->hbuf[S_MAXDIV];
+    r->max_u = c->hbuf[S_MAXU];
+    vof_status st2 = launch_check(c, "project");
+    return st2 ? st2 : st;
+}
+
+vof_status project(vof_ctx* c, const double* alpha, double* uc, double* vc, double* wc, double* u,
+                   double* v, double* w, double* p, const double* sx, const double* sy,
+                   const double* sz, double dt, vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, uc);
+    REQUIRE_PTR(c, vc);
+    REQUIRE_PTR(c, wc);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    REQUIRE_PTR(c, p);
+    REQUIRE_PTR(c, sx);
+    REQUIRE_PTR(c, sy);
+    REQUIRE_PTR(c, sz);
+    if ((st = walls_only(c, "project"))) return st;
+    if (!(dt > 0.0)) return set_err(c, VOF_ERR_ARG, "dt must be positive");
+    double snap[T_NCLASS];
+    report_timing_begin(c, snap);
+    launch_beta(c, alpha);
+    vof_report r;
+    std::memset(&r, 0, sizeof(r));
+    // the cell correction reads u_hat_c and writes u_c: keep a copy of u_hat_c
+    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
+    cudaMemcpyAsync(c->uh[0], uc, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->uh[1], vc, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->uh[2], wc, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
+    double* const Uc[3] = {uc, vc, wc};
+    st = project_impl(c, Uh, Uc, u, v, w, p, sx, sy, sz, dt, &r);
+    if (report) {
+        *report = r;
+        report_timing_end(c, snap, report);
+    }
+    return st;
+}
+
+vof_status step(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
+                double* v, double* w, double* p, double dt, long long step_index,
+                vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, uc);
+    REQUIRE_PTR(c, vc);
+    REQUIRE_PTR(c, wc);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    REQUIRE_PTR(c, p);
+    if ((st = walls_only(c, "step"))) return st;
+    if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
+    if ((st = cfl_check(c, u, v, w, dt))) return st;
+    double snap[T_NCLASS];
+    report_timing_begin(c, snap);
+    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
+    // steps 1-2: keep alpha^n (rho^n, mu^n) for the predictor
+    cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    // step 3: advect alpha with u_f^n, keeping the liquid face fluxes
+    double* const flux[3] = {c->fx, c->fy, c->fz};
+    advect_impl(c, alpha, u, v, w, dt, step_index, flux);
+    // steps 8-9: cell-centred intermediate velocity
+    const double* const U[3] = {uc, vc, wc};
+    launch_predict(c, c->an, alpha, U, u, v, w, c->fx, c->fy, c->fz, dt, c->uh);
+    // step 10: face intermediate velocity
+    launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], u, v, w);
+    // step 4 (beta from alpha^{n+1}) and steps 5-7 (curvature, face force)
+    launch_beta(c, alpha);
+    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
+    // steps 11-12
+    vof_report r;
+    std::memset(&r, 0, sizeof(r));
+    const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
+    double* const Uc[3] = {uc, vc, wc};
+    st = project_impl(c, Uh, Uc, u, v, w, p, c->sx, c->sy, c->sz, dt, &r);
+    if (report) {
+        readback(c);
+        fill_vof_report(c, &r);
+        r.hf_fallbacks = (long long)llround(c->hbuf[S_FALLBACK]);
+        *report = r;
+        report_timing_end(c, snap, report);
+    }
+    return st;
+}
+
+vof_status vof_launch_count(const vof_ctx* c, long long* n) {
+    if (!c || !n) return VOF_ERR_ARG;
+    *n = c->nlaunch;
+    return VOF_OK;
+}
+
+vof_status vof_set_timing(vof_ctx* c, int on) {
+    if (!c) return VOF_ERR_ARG;
+    if (!on) flush_timers(c);
+    c->timing = on ? 1 : 0;
+    return VOF_OK;
+}
+
+vof_status vof_kernel_times(vof_ctx* c, const char** names, double* ms, long long* launches,
+                            int cap, int* n) {
+    static const char* kNames[T_NCLASS] = {
+        "advect",   "ssf",         "predict",         "rhs",        "smooth_l0",
+        "smooth",   "residual_l0", "restrict_l0",     "restrict",   "prolong_l0",
+        "prolong",  "coarse",      "krylov",          "project"};
+    if (!c || !n) return VOF_ERR_ARG;
+    flush_timers(c);
+    int k = 0;
+    for (int t = 0; t < T_NCLASS && k < cap; ++t, ++k) {
+        if (names) names[k] = kNames[t];
+        if (ms) ms[k] = c->t_ms[t];
+        if (launches) launches[k] = c->t_n[t];
+        c->t_ms[t] = 0;
+        c->t_n[t] = 0;
+    }
+    *n = k;
+    return VOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Geometric multigrid preconditioner of the pressure solve (the paper's
+// multigrid-accelerated red-black relaxation, Section 2.1, used here as one
+// symmetric V-cycle per Krylov iteration), templated on the scalar type:
+// T = double for the FP64 path, T = float for the mixed-precision path
+// (FP32 V-cycle inside the FP64 flexible-CG iteration).
+//
+// Level l has spacing 2^l h and halves every dimension. A coarse face
+// coefficient is the mean of the four fine faces it covers (walls stay 0),
+// restriction averages the fine residual over the eight children and
+// prolongation adds the coarse value to its eight children; the smoother is
+// red-black Gauss-Seidel, x_c = (h^2 f_c + sum beta x_nb) / sum beta. The
+// coarsest level is solved by Jacobi-preconditioned CG in one thread block
+// (FP64 reductions in both modes).
+#include "vof_internal.cuh"
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ T stencil_t(const Dims& d, const T* __restrict__ bx,
+                                       const T* __restrict__ by, const T* __restrict__ bz,
+                                       const T* __restrict__ x, int i, int j, int k) {
+    const int c = cid(d, i, j, k);
+    const T xc = x[c];
+    const int cw = i > 0 ? c - 1 : c;
+    const int ce = i < d.nx - 1 ? c + 1 : c;
+    const int cs = j > 0 ? c - d.nx : c;
+    const int cn = j < d.ny - 1 ? c + d.nx : c;
+    const int kp = wrapk(k + 1, d.nz);
+    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, kp);
+    T s = bx[uid(d, i, j, k)] * (xc - x[cw]);
+    s += bx[uid(d, i + 1, j, k)] * (xc - x[ce]);
+    s += by[vid(d, i, j, k)] * (xc - x[cs]);
+    s += by[vid(d, i, j + 1, k)] * (xc - x[cn]);
+    s += bz[wid(d, i, j, k)] * (xc - x[cb]);
+    s += bz[wid(d, i, j, kp)] * (xc - x[ct]);
+    return s;
+}
+
+template <class T>
+__global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __restrict__ by,
+                         const T* __restrict__ bz, T* __restrict__ x, const T* __restrict__ f,
+                         int color, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= d.nx || j >= d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    for (int k = k0; k < k1; ++k) {
+        if (((i + j + k) & 1) != color) continue;
+        const int c = cid(d, i, j, k);
+        const int cw = i > 0 ? c - 1 : c;
+        const int ce = i < d.nx - 1 ? c + 1 : c;
+        const int cs = j > 0 ? c - d.nx : c;
+        const int cn = j < d.ny - 1 ? c + d.nx : c;
+        const int kp = wrapk(k + 1, d.nz);
+        const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, kp);
+        const T b0 = bx[uid(d, i, j, k)], b1 = bx[uid(d, i + 1, j, k)];
+        const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
+        const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
+        const T num = h2 * f[c] + b0 * x[cw] + b1 * x[ce] + b2 * x[cs] + b3 * x[cn] + b4 * x[cb] +
+                      b5 * x[ct];
+        const T den = b0 + b1 + b2 + b3 + b4 + b5;
+        x[c] = den > T(0) ? num / den : T(0);
+    }
+}
+
+template <class T>
+__global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T* __restrict__ by,
+                             const T* __restrict__ bz, const T* __restrict__ xf,
+                             const T* __restrict__ ff, Dims dc, T* __restrict__ fc, int kchunk) {
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    for (int K = k0; K < k1; ++K) {
+        T s = T(0);
+        for (int c3 = 0; c3 < 8; ++c3) {
+            const int i = 2 * I + (c3 & 1), j = 2 * J + ((c3 >> 1) & 1), k = 2 * K + (c3 >> 2);
+            s += ff[cid(df, i, j, k)] - stencil_t(df, bx, by, bz, xf, i, j, k) * ih2f;
+        }
+        fc[cid(dc, I, J, K)] = T(0.125) * s;
+    }
+}
+
+template <class T>
+__global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __restrict__ xf,
+                            int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= df.nx || j >= df.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
+    for (int k = k0; k < k1; ++k) xf[cid(df, i, j, k)] += xc[cid(dc, i >> 1, j >> 1, k >> 1)];
+}
+
+template <class T>
+__global__ void k_coarsen_beta_t(Dims df, const T* __restrict__ bxf, const T* __restrict__ byf,
+                                 const T* __restrict__ bzf, Dims dc, T* __restrict__ bxc,
+                                 T* __restrict__ byc, T* __restrict__ bzc, int kchunk) {
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    for (int K = k0; K < k1; ++K) {
+        const int i = 2 * I, j = 2 * J, k = 2 * K;
+        bxc[uid(dc, I, J, K)] = T(0.25) * (bxf[uid(df, i, j, k)] + bxf[uid(df, i, j + 1, k)] +
+                                           bxf[uid(df, i, j, k + 1)] + bxf[uid(df, i, j + 1, k + 1)]);
+        if (I == dc.nx - 1) bxc[uid(dc, dc.nx, J, K)] = T(0);
+        byc[vid(dc, I, J, K)] = T(0.25) * (byf[vid(df, i, j, k)] + byf[vid(df, i + 1, j, k)] +
+                                           byf[vid(df, i, j, k + 1)] + byf[vid(df, i + 1, j, k + 1)]);
+        if (J == dc.ny - 1) byc[vid(dc, I, dc.ny, K)] = T(0);
+        bzc[wid(dc, I, J, K)] = T(0.25) * (bzf[wid(df, i, j, k)] + bzf[wid(df, i + 1, j, k)] +
+                                           bzf[wid(df, i, j + 1, k)] + bzf[wid(df, i + 1, j + 1, k)]);
+    }
+}
+
+// Jacobi-preconditioned CG on the coarsest level, one thread block; vectors
+// in T, reductions in FP64. Bounded iteration count; the result is made
+// mean-free (the operator's null space is the constants).
+template <class T>
+__global__ void k_coarse_cg_t(Dims d, T ih2, const T* __restrict__ bx, const T* __restrict__ by,
+                              const T* __restrict__ bz, const T* __restrict__ f,
+                              T* __restrict__ x, T* __restrict__ scratch, int maxit, double tol) {
+    __shared__ double bc[2];
+    const int n = d.nx * d.ny * d.nz;
+    T* rr = scratch;
+    T* pp = scratch + n;
+    T* qq = scratch + 2 * n;
+    T* dinv = scratch + 3 * n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double s = 0.0;
+    for (int c = tid; c < n; c += nt) {
+        const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / (d.nx * d.ny);
+        const T dg = bx[uid(d, i, j, k)] + bx[uid(d, i + 1, j, k)] + by[vid(d, i, j, k)] +
+                     by[vid(d, i, j + 1, k)] + bz[wid(d, i, j, k)] +
+                     bz[wid(d, i, j, wrapk(k + 1, d.nz))];
+        dinv[c] = dg > T(0) ? T(1) / (dg * ih2) : T(0);
+        x[c] = T(0);
+        rr[c] = f[c];
+        s += (double)f[c];
+    }
+    s = block_sum(s);
+    if (tid == 0) bc[0] = s / n;
+    __syncthreads();
+    const T fm = (T)bc[0];
+    double rz = 0.0, r2 = 0.0;
+    for (int c = tid; c < n; c += nt) {
+        rr[c] -= fm;
+        pp[c] = dinv[c] * rr[c];
+        rz += (double)rr[c] * (double)pp[c];
+        r2 += (double)rr[c] * (double)rr[c];
+    }
+    rz = block_sum(rz);
+    r2 = block_sum(r2);
+    if (tid == 0) { bc[0] = rz; bc[1] = r2; }
+    __syncthreads();
+    rz = bc[0];
+    const double r20 = bc[1];
+    if (r20 > 0.0) {
+        for (int it = 0; it < maxit; ++it) {
+            double pq = 0.0;
+            for (int c = tid; c < n; c += nt) {
+                const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / (d.nx * d.ny);
+                const T v = stencil_t(d, bx, by, bz, pp, i, j, k) * ih2;
+                qq[c] = v;
+                pq += (double)pp[c] * (double)v;
+            }
+            pq = block_sum(pq);
+            if (tid == 0) bc[0] = pq;
+            __syncthreads();
+            pq = bc[0];
+            if (!(pq > 0.0)) break;
+            const T al = (T)(rz / pq);
+            double r2n = 0.0, rzn = 0.0;
+            for (int c = tid; c < n; c += nt) {
+                x[c] += al * pp[c];
+                rr[c] -= al * qq[c];
+                r2n += (double)rr[c] * (double)rr[c];
+                rzn += (double)rr[c] * (double)dinv[c] * (double)rr[c];
+            }
+            r2n = block_sum(r2n);
+            rzn = block_sum(rzn);
+            if (tid == 0) { bc[0] = r2n; bc[1] = rzn; }
+            __syncthreads();
+            r2n = bc[0];
+            rzn = bc[1];
+            if (r2n <= tol * tol * r20) break;
+            const T be = (T)(rzn / rz);
+            rz = rzn;
+            for (int c = tid; c < n; c += nt) pp[c] = dinv[c] * rr[c] + be * pp[c];
+            __syncthreads();
+        }
+    }
+    s = 0.0;
+    for (int c = tid; c < n; c += nt) s += (double)x[c];
+    s = block_sum(s);
+    if (tid == 0) bc[0] = s / n;
+    __syncthreads();
+    const T xm = (T)bc[0];
+    for (int c = tid; c < n; c += nt) x[c] -= xm;
+}
+
+template <class T>
+__global__ void k_zero_t(int n, T* __restrict__ x) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        x[c] = T(0);
+}
+
+__global__ void k_to_f32(int n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        b[c] = (float)a[c];
+}
+
+__global__ void k_to_f64(int n, const float* __restrict__ a, double* __restrict__ b) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        b[c] = (double)a[c];
+}
+
+inline int flat_blocks(int n) {
+    int b = (n + 255) / 256;
+    return b < 1 ? 1 : (b > 1184 ? 1184 : b);
+}
+
+template <class T>
+struct LA {
+    T *bx, *by, *bz, *x, *f;
+};
+template <class T>
+LA<T> arrays(const Level& L);
+template <>
+LA<double> arrays<double>(const Level& L) {
+    return {L.bx, L.by, L.bz, L.x, L.f};
+}
+template <>
+LA<float> arrays<float>(const Level& L) {
+    return {L.bxf, L.byf, L.bzf, L.xf, L.ff};
+}
+
+}  // namespace
+
+template <class T>
+void mg_rbgs(vof_ctx* c, const Level& L, int color) {
+    const LA<T> a = arrays<T>(L);
+    const int cls = L.idx == 0 ? T_SMOOTH0 : T_SMOOTH;
+    int m = timer_begin(c, cls);
+    VOF_LAUNCH(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, a.x,
+               a.f, color, L.L.kchunk);
+    timer_end(c, cls, m);
+}
+
+template <class T>
+void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
+    const LA<T> a = arrays<T>(F), b = arrays<T>(C);
+    const int cls = F.idx == 0 ? T_RESTRICT0 : T_RESTRICT;
+    int m = timer_begin(c, cls);
+    VOF_LAUNCH(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx, a.by,
+               a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
+    timer_end(c, cls, m);
+}
+
+template <class T>
+void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
+    const LA<T> a = arrays<T>(C), b = arrays<T>(F);
+    const int cls = F.idx == 0 ? T_PROLONG0 : T_PROLONG;
+    int m = timer_begin(c, cls);
+    VOF_LAUNCH(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, F.L.kchunk);
+    timer_end(c, cls, m);
+}
+
+template <class T>
+void mg_coarsen_beta(vof_ctx* c, const Level& F, const Level& C) {
+    const LA<T> a = arrays<T>(F), b = arrays<T>(C);
+    VOF_LAUNCH(c, k_coarsen_beta_t<T>, C.L.grid, C.L.block, F.d, a.bx, a.by, a.bz, C.d, b.bx, b.by,
+               b.bz, C.L.kchunk);
+}
+
+template <class T>
+void mg_coarse(vof_ctx* c, const Level& L) {
+    const LA<T> a = arrays<T>(L);
+    int m = timer_begin(c, T_COARSE);
+    // FP64: tight; FP32: to what single precision can hold
+    const double tol = sizeof(T) == 8 ? 1e-8 : 1e-5;
+    VOF_LAUNCH(c, k_coarse_cg_t<T>, 1, 1024, L.d, (T)(1.0 / (L.h * L.h)), a.bx, a.by, a.bz, a.f,
+               a.x, (T*)c->coarse_scratch, 400, tol);
+    timer_end(c, T_COARSE, m);
+}
+
+template <class T>
+void mg_zero(vof_ctx* c, const Level& L) {
+    const LA<T> a = arrays<T>(L);
+    VOF_LAUNCH(c, k_zero_t<T>, flat_blocks(L.ncells), 256, L.ncells, a.x);
+}
+
+void mg_to_f32(vof_ctx* c, const double* a, float* b, int n) {
+    VOF_LAUNCH(c, k_to_f32, flat_blocks(n), 256, n, a, b);
+}
+
+void mg_to_f64(vof_ctx* c, const float* a, double* b, int n) {
+    VOF_LAUNCH(c, k_to_f64, flat_blocks(n), 256, n, a, b);
+}
+
+template void mg_rbgs<double>(vof_ctx*, const Level&, int);
+template void mg_rbgs<float>(vof_ctx*, const Level&, int);
+template void mg_restrict<double>(vof_ctx*, const Level&, const Level&);
+template void mg_restrict<float>(vof_ctx*, const Level&, const Level&);
+template void mg_prolong<double>(vof_ctx*, const Level&, const Level&);
+template void mg_prolong<float>(vof_ctx*, const Level&, const Level&);
+template void mg_coarsen_beta<double>(vof_ctx*, const Level&, const Level&);
+template void mg_coarsen_beta<float>(vof_ctx*, const Level&, const Level&);
+template void mg_coarse<double>(vof_ctx*, const Level&);
+template void mg_coarse<float>(vof_ctx*, const Level&);
+template void mg_zero<double>(vof_ctx*, const Level&);
+template void mg_zero<float>(vof_ctx*, const Level&);

@@ -1,0 +1,301 @@
+// Variable-coefficient pressure operator (Eq. 7, steps 6/11) and the FP64
+// kernels of the outer flexible-CG iteration (the multigrid preconditioner
+// lives in k_mg.cu).
+//
+//   (A x)_c = (1/h^2) sum_f beta_f (x_c - x_nb),  beta_f = 1 / rho_f,
+//   rho_f = (rho_L + rho_R)/2 (linear face averaging, step 10).
+//
+// Walls carry beta = 0, so the stencil reads a clamped neighbour there and
+// multiplies it by zero; z is periodic. The residual, the operator and the
+// Krylov updates are FP64 in every precision mode.
+#include "vof_internal.cuh"
+
+namespace {
+
+struct CellIdx {
+    int i, j, k0, k1;
+    bool act;
+};
+
+__device__ __forceinline__ CellIdx cell_range(const Dims& d, int kchunk) {
+    CellIdx r;
+    r.i = blockIdx.x * TBX + threadIdx.x;
+    r.j = blockIdx.y * TBY + threadIdx.y;
+    r.act = r.i < d.nx && r.j < d.ny;
+    r.k0 = blockIdx.z * kchunk;
+    r.k1 = min(r.k0 + kchunk, d.nz);
+    return r;
+}
+
+// (A x)_c * h^2 without the 1/h^2 factor
+__device__ __forceinline__ double stencil(const Dims& d, const double* __restrict__ bx,
+                                          const double* __restrict__ by,
+                                          const double* __restrict__ bz,
+                                          const double* __restrict__ x, int i, int j, int k) {
+    const int c = cid(d, i, j, k);
+    const double xc = x[c];
+    const int cw = i > 0 ? c - 1 : c;
+    const int ce = i < d.nx - 1 ? c + 1 : c;
+    const int cs = j > 0 ? c - d.nx : c;
+    const int cn = j < d.ny - 1 ? c + d.nx : c;
+    const int kp = wrapk(k + 1, d.nz);
+    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, kp);
+    double s = bx[uid(d, i, j, k)] * (xc - x[cw]);
+    s += bx[uid(d, i + 1, j, k)] * (xc - x[ce]);
+    s += by[vid(d, i, j, k)] * (xc - x[cs]);
+    s += by[vid(d, i, j + 1, k)] * (xc - x[cn]);
+    s += bz[wid(d, i, j, k)] * (xc - x[cb]);
+    s += bz[wid(d, i, j, kp)] * (xc - x[ct]);
+    return s;
+}
+
+__global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double rg,
+                       double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
+                       int kchunk) {
+    CellIdx r = cell_range(d, kchunk);
+    if (!r.act) return;
+    const int i = r.i, j = r.j;
+    for (int k = r.k0; k < r.k1; ++k) {
+        const int c = cid(d, i, j, k);
+        const double rc = a[c] * rl + (1.0 - a[c]) * rg;
+        // x-face i (between i-1 and i); the last thread also writes the wall face nx
+        if (i == 0) {
+            bx[uid(d, 0, j, k)] = 0.0;
+        } else {
+            const double rw = a[c - 1] * rl + (1.0 - a[c - 1]) * rg;
+            bx[uid(d, i, j, k)] = 1.0 / (0.5 * (rw + rc));
+        }
+        if (i == d.nx - 1) bx[uid(d, d.nx, j, k)] = 0.0;
+        if (j == 0) {
+            by[vid(d, i, 0, k)] = 0.0;
+        } else {
+            const double rs = a[c - d.nx] * rl + (1.0 - a[c - d.nx]) * rg;
+            by[vid(d, i, j, k)] = 1.0 / (0.5 * (rs + rc));
+        }
+        if (j == d.ny - 1) by[vid(d, i, d.ny, k)] = 0.0;
+        const int cb = cid(d, i, j, wrapk(k - 1, d.nz));
+        const double rb = a[cb] * rl + (1.0 - a[cb]) * rg;
+        bz[wid(d, i, j, k)] = 1.0 / (0.5 * (rb + rc));
+    }
+}
+
+__global__ void k_apply_A(Dims d, double ih2, const double* __restrict__ bx,
+                          const double* __restrict__ by, const double* __restrict__ bz,
+                          const double* __restrict__ x, double* __restrict__ y, int kchunk) {
+    CellIdx r = cell_range(d, kchunk);
+    if (!r.act) return;
+    for (int k = r.k0; k < r.k1; ++k)
+        y[cid(d, r.i, r.j, k)] = stencil(d, bx, by, bz, x, r.i, r.j, k) * ih2;
+}
+
+// y = A x and the block partials of x.y
+__global__ void k_apply_A_dot(Dims d, double ih2, const double* __restrict__ bx,
+                              const double* __restrict__ by, const double* __restrict__ bz,
+                              const double* __restrict__ x, double* __restrict__ y,
+                              double* __restrict__ part, int kchunk) {
+    CellIdx r = cell_range(d, kchunk);
+    double acc = 0.0;
+    if (r.act)
+        for (int k = r.k0; k < r.k1; ++k) {
+            const int c = cid(d, r.i, r.j, k);
+            const double v = stencil(d, bx, by, bz, x, r.i, r.j, k) * ih2;
+            y[c] = v;
+            acc += x[c] * v;
+        }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
+// r = f - A x and the block partials of r.r
+__global__ void k_residual(Dims d, double ih2, const double* __restrict__ bx,
+                           const double* __restrict__ by, const double* __restrict__ bz,
+                           const double* __restrict__ x, const double* __restrict__ f,
+                           double* __restrict__ res, double* __restrict__ part, int kchunk) {
+    CellIdx r = cell_range(d, kchunk);
+    double acc = 0.0;
+    if (r.act)
+        for (int k = r.k0; k < r.k1; ++k) {
+            const int c = cid(d, r.i, r.j, k);
+            const double v = f[c] - stencil(d, bx, by, bz, x, r.i, r.j, k) * ih2;
+            res[c] = v;
+            acc += v * v;
+        }
+    acc = block_sum(acc);
+    if (part && threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
+// ---- flat vector kernels (fixed grid => deterministic partials) ----------
+__global__ void k_dot(int n, const double* __restrict__ x, const double* __restrict__ y,
+                      double* __restrict__ part) {
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        acc += x[c] * y[c];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sum(int n, const double* __restrict__ x, double* __restrict__ part) {
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        acc += x[c];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sub_scalar(int n, double* __restrict__ x, const double* __restrict__ s) {
+    const double m = *s;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        x[c] -= m;
+}
+
+__global__ void k_copy(int n, double* __restrict__ dst, const double* __restrict__ src) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        dst[c] = src[c];
+}
+
+__global__ void k_zero(int n, double* __restrict__ x) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        x[c] = 0.0;
+}
+
+__global__ void k_cg_update(int n, double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q,
+                            const double* __restrict__ scal, double* __restrict__ part) {
+    const double al = scal[S_ALPHA];
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        x[c] += al * p[c];
+        const double rv = r[c] - al * q[c];
+        r[c] = rv;
+        acc += rv * rv;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_dot2(int n, const double* __restrict__ z, const double* __restrict__ r,
+                       const double* __restrict__ q, double* __restrict__ pa,
+                       double* __restrict__ pb) {
+    double a = 0.0, b = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        a += z[c] * r[c];
+        b += z[c] * q[c];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_p_update(int n, double* __restrict__ p, const double* __restrict__ z,
+                           const double* __restrict__ scal) {
+    const double be = scal[S_BETA];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        p[c] = z[c] + be * p[c];
+}
+
+__global__ void k_scalar_alpha(double* scal) {
+    const double pq = scal[S_PQ];
+    scal[S_ALPHA] = pq > 0.0 ? scal[S_RZ] / pq : 0.0;
+}
+
+__global__ void k_scalar_beta(double* scal) {
+    const double pq = scal[S_PQ];
+    scal[S_BETA] = pq > 0.0 ? -scal[S_ZQ] / pq : 0.0;
+}
+
+constexpr int FLAT_THREADS = 256;
+inline int flat_blocks(int n) {
+    int b = (n + FLAT_THREADS - 1) / FLAT_THREADS;
+    if (b > 1184) b = 1184;
+    if (b < 1) b = 1;
+    return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+void launch_beta(vof_ctx* c, const double* alpha) {
+    const Launch& L = c->Lc;
+    VOF_LAUNCH(c, k_beta, L.grid, L.block, c->d, alpha, c->ph.rho_l, c->ph.rho_g, c->bx, c->by,
+                                          c->bz, L.kchunk);
+}
+
+void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y) {
+    VOF_LAUNCH(c, k_apply_A, l.L.grid, l.L.block, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz, x, y,
+                                                  l.L.kchunk);
+}
+
+void launch_apply_A_dot(vof_ctx* c, const Level& l, const double* p, double* q, int slot) {
+    int m = timer_begin(c, T_RESIDUAL);
+    VOF_LAUNCH(c, k_apply_A_dot, l.L.grid, l.L.block, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz, p,
+                                                      q, c->part + (size_t)slot * MAX_PARTIALS,
+                                                      l.L.kchunk);
+    timer_end(c, T_RESIDUAL, m);
+    finalize_sum(c, slot, l.L.nblocks, slot, 1.0);
+}
+
+void launch_residual(vof_ctx* c, const Level& l, const double* x, const double* f, double* r,
+                     int slot) {
+    int m = timer_begin(c, T_RESIDUAL);
+    VOF_LAUNCH(c, k_residual, l.L.grid, l.L.block, 
+        l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz, x, f, r,
+        slot >= 0 ? c->part + (size_t)slot * MAX_PARTIALS : nullptr, l.L.kchunk);
+    timer_end(c, T_RESIDUAL, m);
+    if (slot >= 0) finalize_sum(c, slot, l.L.nblocks, slot, 1.0);
+}
+
+void launch_dot(vof_ctx* c, const double* x, const double* y, int n, int slot) {
+    const int nb = flat_blocks(n);
+    VOF_LAUNCH(c, k_dot, nb, FLAT_THREADS, n, x, y, c->part + (size_t)slot * MAX_PARTIALS);
+    finalize_sum(c, slot, nb, slot, 1.0);
+}
+
+void launch_sub_mean(vof_ctx* c, double* x, int n, int slot_mean) {
+    const int nb = flat_blocks(n);
+    VOF_LAUNCH(c, k_sum, nb, FLAT_THREADS, n, x, c->part + (size_t)slot_mean * MAX_PARTIALS);
+    finalize_sum(c, slot_mean, nb, slot_mean, 1.0 / (double)n);
+    VOF_LAUNCH(c, k_sub_scalar, nb, FLAT_THREADS, n, x, c->scal + slot_mean);
+}
+
+void launch_copy(vof_ctx* c, double* dst, const double* src, int n) {
+    VOF_LAUNCH(c, k_copy, flat_blocks(n), FLAT_THREADS, n, dst, src);
+}
+
+void launch_zero(vof_ctx* c, double* x, int n) {
+    VOF_LAUNCH(c, k_zero, flat_blocks(n), FLAT_THREADS, n, x);
+}
+
+void launch_cg_update(vof_ctx* c, int n, double* x, double* r, const double* p, const double* q,
+                      int slot) {
+    const int nb = flat_blocks(n);
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_cg_update, nb, FLAT_THREADS, n, x, r, p, q, c->scal,
+                                                c->part + (size_t)slot * MAX_PARTIALS);
+    timer_end(c, T_KRYLOV, m);
+    finalize_sum(c, slot, nb, slot, 1.0);
+}
+
+void launch_dot2(vof_ctx* c, int n, const double* z, const double* r, const double* q, int sa,
+                 int sb) {
+    const int nb = flat_blocks(n);
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_dot2, nb, FLAT_THREADS, n, z, r, q, c->part + (size_t)sa * MAX_PARTIALS,
+                                           c->part + (size_t)sb * MAX_PARTIALS);
+    timer_end(c, T_KRYLOV, m);
+    finalize_sum(c, sa, nb, sa, 1.0);
+    finalize_sum(c, sb, nb, sb, 1.0);
+}
+
+void launch_p_update(vof_ctx* c, int n, double* p, const double* z) {
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_p_update, flat_blocks(n), FLAT_THREADS, n, p, z, c->scal);
+    timer_end(c, T_KRYLOV, m);
+}
+
+void launch_scalar_alpha(vof_ctx* c) { VOF_LAUNCH(c, k_scalar_alpha, 1, 1, c->scal); }
+void launch_scalar_beta(vof_ctx* c) { VOF_LAUNCH(c, k_scalar_beta, 1, 1, c->scal); }

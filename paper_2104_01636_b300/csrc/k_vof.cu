@@ -1,0 +1,214 @@
+// Geometric VOF advection (Eq. 3; the geometric construction with a
+// direction-split update, Section 2.1):
+//   reconstruct: per interface cell the normal n = -grad(alpha smoothed by
+//                [1,2,1]^3/64) and the FP64 plane constant d;
+//   face flux:   signed liquid volume in the donor slab of width |u| dt;
+//   update:      alpha <- alpha - (F+ - F-) + c (u+ - u-) dt/h, clipped,
+//                with c = [alpha^n > 1/2] frozen over the three sweeps so
+//                the volume is conserved to round-off when div u = 0.
+// Each face flux is computed once and stored, so the update telescopes
+// exactly.
+#include "plic.cuh"
+#include "vof_geom.cuh"
+#include "vof_internal.cuh"
+
+namespace {
+
+// PLIC plane of one cell: normal (cell units) and plane constant
+struct __align__(32) Plane {
+    double n0, n1, n2, d;
+};
+
+__global__ void k_reconstruct(Geo g, const double* __restrict__ a, unsigned char* __restrict__ has,
+                              Plane* __restrict__ plane, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= g.d.nx || j >= g.d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.d.nz);
+    for (int k = k0; k < k1; ++k) {
+        const int c = cid(g.d, i, j, k);
+        const double ac = a[c];
+        unsigned char h = 0;
+        if (ac > EPS_IF && ac < 1.0 - EPS_IF) {
+            double n[3];
+            smoothed_normal(g, a, i, j, k, n);
+            if (n[0] != 0.0 || n[1] != 0.0 || n[2] != 0.0) {
+                h = 1;
+                plane[c] = Plane{n[0], n[1], n[2], plic::plane_constant(n[0], n[1], n[2], ac)};
+            }
+        }
+        has[c] = h;
+    }
+}
+
+// flux through the minus face of every cell in direction dir (face index =
+// cell index along dir); wall faces get zero
+__global__ void k_face_flux(Geo g, int dir, const double* __restrict__ a,
+                            const unsigned char* __restrict__ has,
+                            const Plane* __restrict__ plane, const double* __restrict__ vel,
+                            double* __restrict__ flux, double dt_h, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= g.d.nx || j >= g.d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.d.nz);
+    const Dims& d = g.d;
+    for (int k = k0; k < k1; ++k) {
+        int f, cL;
+        const int cR = cid(d, i, j, k);
+        bool wall = false;
+        if (dir == 0) {
+            f = uid(d, i, j, k);
+            wall = (i == 0 && !g.per_x);
+            cL = cid(d, i == 0 ? d.nx - 1 : i - 1, j, k);
+        } else if (dir == 1) {
+            f = vid(d, i, j, k);
+            wall = (j == 0 && !g.per_y);
+            cL = cid(d, i, j == 0 ? d.ny - 1 : j - 1, k);
+        } else {
+            f = wid(d, i, j, k);
+            cL = cid(d, i, j, wrapk(k - 1, d.nz));
+        }
+        double F = 0.0;
+        const double u = wall ? 0.0 : vel[f];
+        if (u != 0.0) {
+            const double cfl = fabs(u) * dt_h;
+            const int dn = u > 0.0 ? cL : cR;
+            double V;
+            if (!has[dn]) {
+                V = cfl * a[dn];
+            } else {
+                const Plane pl = plane[dn];
+                V = plic::slab_fraction(pl.n0, pl.n1, pl.n2, pl.d, dir, cfl, u > 0.0);
+            }
+            F = u > 0.0 ? V : -V;
+        }
+        flux[f] = F;
+        // the far wall (or periodic duplicate) face is never a minus face
+        if (dir == 0 && i == d.nx - 1) flux[uid(d, d.nx, j, k)] = 0.0;
+        if (dir == 1 && j == d.ny - 1) flux[vid(d, i, d.ny, k)] = 0.0;
+    }
+}
+
+__global__ void k_vof_update(Geo g, int dir, const double* __restrict__ ain,
+                             double* __restrict__ aout, const double* __restrict__ flux,
+                             const double* __restrict__ vel, const unsigned char* __restrict__ cm,
+                             double dt_h, double* __restrict__ part, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const Dims& d = g.d;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    double clip = 0.0;
+    if (act)
+        for (int k = k0; k < k1; ++k) {
+            const int c = cid(d, i, j, k);
+            int fm, fp;
+            bool wm = false, wp = false;
+            if (dir == 0) {
+                fm = uid(d, i, j, k);
+                fp = uid(d, i + 1 == d.nx && g.per_x ? 0 : i + 1, j, k);
+                wm = i == 0 && !g.per_x;
+                wp = i == d.nx - 1 && !g.per_x;
+            } else if (dir == 1) {
+                fm = vid(d, i, j, k);
+                fp = vid(d, i, j + 1 == d.ny && g.per_y ? 0 : j + 1, k);
+                wm = j == 0 && !g.per_y;
+                wp = j == d.ny - 1 && !g.per_y;
+            } else {
+                fm = wid(d, i, j, k);
+                fp = wid(d, i, j, wrapk(k + 1, d.nz));
+            }
+            const double Fm = wm ? 0.0 : flux[fm], Fp = wp ? 0.0 : flux[fp];
+            const double vm = wm ? 0.0 : vel[fm], vp = wp ? 0.0 : vel[fp];
+            const double an = ain[c] - (Fp - Fm) + (cm[c] ? 1.0 : 0.0) * (vp - vm) * dt_h;
+            const double ac = fmin(fmax(an, 0.0), 1.0);
+            clip += an - ac;
+            aout[c] = ac;
+        }
+    clip = block_sum(clip);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = clip;
+}
+
+__global__ void k_mask_volume(Dims d, const double* __restrict__ a, unsigned char* __restrict__ cm,
+                              double* __restrict__ part, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    double s = 0.0;
+    if (act)
+        for (int k = k0; k < k1; ++k) {
+            const int c = cid(d, i, j, k);
+            s += a[c];
+            if (cm) cm[c] = a[c] > 0.5;
+        }
+    s = block_sum(s);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = s;
+}
+
+// max |vel| over non-wall faces only (the CFL check ignores wall-face values)
+__global__ void k_cfl(Geo g, const double* __restrict__ u, const double* __restrict__ v,
+                      const double* __restrict__ w, double* __restrict__ part, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const Dims& d = g.d;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    double m = 0.0;
+    if (act)
+        for (int k = k0; k < k1; ++k) {
+            if (i > 0 || g.per_x) m = fmax(m, fabs(u[uid(d, i, j, k)]));
+            if (j > 0 || g.per_y) m = fmax(m, fabs(v[vid(d, i, j, k)]));
+            m = fmax(m, fabs(w[wid(d, i, j, k)]));
+        }
+    m = block_max(m);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = m;
+}
+
+inline Geo geo(const vof_ctx* c) { return Geo{c->d, c->g.periodic_x, c->g.periodic_y}; }
+
+}  // namespace
+
+void launch_vof_mask_volume(vof_ctx* c, const double* alpha, int slot) {
+    const Launch& L = c->Lc;
+    VOF_LAUNCH(c, k_mask_volume, L.grid, L.block, c->d, alpha, c->cmask,
+                                                 c->part + (size_t)slot * MAX_PARTIALS, L.kchunk);
+}
+
+void launch_volume(vof_ctx* c, const double* alpha, int slot) {
+    const Launch& L = c->Lc;
+    VOF_LAUNCH(c, k_mask_volume, L.grid, L.block, c->d, alpha, nullptr,
+                                                 c->part + (size_t)slot * MAX_PARTIALS, L.kchunk);
+}
+
+void launch_reconstruct(vof_ctx* c, const double* alpha) {
+    const Launch& L = c->Lc;
+    int m = timer_begin(c, T_ADVECT);
+    VOF_LAUNCH(c, k_reconstruct, L.grid, L.block, geo(c), alpha, c->has, (Plane*)c->plane,
+                                                 L.kchunk);
+    timer_end(c, T_ADVECT, m);
+}
+
+void launch_face_flux(vof_ctx* c, int dir, const double* alpha, const double* vel, double dt,
+                      double* flux) {
+    const Launch& L = c->Lc;
+    int m = timer_begin(c, T_ADVECT);
+    VOF_LAUNCH(c, k_face_flux, L.grid, L.block, geo(c), dir, alpha, c->has,
+                                               (const Plane*)c->plane, vel, flux,
+                                               dt / c->g.h, L.kchunk);
+    timer_end(c, T_ADVECT, m);
+}
+
+void launch_vof_update(vof_ctx* c, int dir, const double* ain, double* aout, const double* vel,
+                       const double* flux, double dt, int slot) {
+    const Launch& L = c->Lc;
+    int m = timer_begin(c, T_ADVECT);
+    VOF_LAUNCH(c, k_vof_update, L.grid, L.block, geo(c), dir, ain, aout, flux, vel, c->cmask,
+                                                dt / c->g.h, c->part + (size_t)slot * MAX_PARTIALS,
+                                                L.kchunk);
+    timer_end(c, T_ADVECT, m);
+}
+
+void launch_cfl(vof_ctx* c, const double* u, const double* v, const double* w, double dt,
+                int slot) {
+    const Launch& L = c->Lc;
+    VOF_LAUNCH(c, k_cfl, L.grid, L.block, geo(c), u, v, w, c->part + (size_t)slot * MAX_PARTIALS,
+                                         L.kchunk);
+    finalize_max(c, slot, L.nblocks, S_CFL);
+    (void)dt;
+}

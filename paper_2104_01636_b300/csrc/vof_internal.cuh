@@ -1,0 +1,253 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Layout conventions are those of include/vof.h (x fastest, staggered faces,
+// walls in x and y, periodic z).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vof.h"
+
+// ---------------------------------------------------------------------------
+// launch geometry: 2-D thread tiles in (x, y) marching over a chunk of z
+// planes, so every cell kernel has a bounded, SM-count-sized grid and
+// per-block partial sums stay few enough for a one-block finalise.
+// ---------------------------------------------------------------------------
+constexpr int TBX = 32;
+constexpr int TBY = 8;
+constexpr int TB = TBX * TBY;
+constexpr int MAX_PARTIALS = 4096;  // per reduction slot
+constexpr int NSLOTS = 24;          // reduction slots in the partials buffer
+
+struct Dims {
+    int nx, ny, nz;
+};
+
+struct Launch {
+    dim3 grid, block;
+    int kchunk;
+    int nblocks;
+};
+
+Launch launch_cells(int nx, int ny, int nz, int sm_count);
+
+// every kernel launch of the library goes through this macro so the context
+// can report how many of its kernels ran
+#define VOF_LAUNCH(c, kernel, grid, block, ...)                \
+    do {                                                       \
+        ++(c)->nlaunch;                                        \
+        kernel<<<(grid), (block), 0, (c)->st>>>(__VA_ARGS__);  \
+    } while (0)
+
+// index helpers (int32: vof_create rejects grids whose face counts overflow)
+__host__ __device__ __forceinline__ int wrapk(int k, int nz) {
+    return k < 0 ? k + nz : (k >= nz ? k - nz : k);
+}
+__host__ __device__ __forceinline__ int cid(const Dims& d, int i, int j, int k) {
+    return i + d.nx * (j + d.ny * k);
+}
+__host__ __device__ __forceinline__ int uid(const Dims& d, int i, int j, int k) {
+    return i + (d.nx + 1) * (j + d.ny * k);
+}
+__host__ __device__ __forceinline__ int vid(const Dims& d, int i, int j, int k) {
+    return i + d.nx * (j + (d.ny + 1) * k);
+}
+__host__ __device__ __forceinline__ int wid(const Dims& d, int i, int j, int k) {
+    return i + d.nx * (j + d.ny * k);
+}
+
+// Deterministic block sum (fixed shuffle tree, then fixed warp order).
+// Every thread of the block must call it; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh_bs[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) sh_bs[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        v = tid < (nthreads + 31) / 32 ? sh_bs[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double sh_bm[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) sh_bm[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        v = tid < (nthreads + 31) / 32 ? sh_bm[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+__device__ __forceinline__ int block_linear() {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// timing classes (CUDA events on the context stream, when enabled)
+// ---------------------------------------------------------------------------
+enum TimerClass {
+    T_ADVECT = 0, T_SSF, T_PREDICT, T_RHS, T_SMOOTH0, T_SMOOTH, T_RESIDUAL, T_RESTRICT0,
+    T_RESTRICT, T_PROLONG0, T_PROLONG, T_COARSE, T_KRYLOV, T_PROJECT, T_NCLASS
+};
+
+// ---------------------------------------------------------------------------
+// multigrid level
+// ---------------------------------------------------------------------------
+struct Level {
+    int idx = 0;  // 0 = fine grid
+    Dims d;
+    double h;
+    int ncells;
+    double *bx = nullptr, *by = nullptr, *bz = nullptr;  // face coefficients
+    double *x = nullptr, *f = nullptr;                    // correction / right side
+    float *bxf = nullptr, *byf = nullptr, *bzf = nullptr;  // FP32 copies (mixed)
+    float *xf = nullptr, *ff = nullptr;
+    Launch L;
+};
+
+struct vof_ctx {
+    vof_grid g;
+    vof_phys ph;
+    vof_solver sv;
+    Dims d;
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    int sm_count = 148;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    Launch Lc;  // fine-grid cell launch
+
+    // fine-grid workspace
+    double *bx = nullptr, *by = nullptr, *bz = nullptr;    // beta on faces
+    double *sx = nullptr, *sy = nullptr, *sz = nullptr;    // surface force (step)
+    double *kappa = nullptr;                               // curvature (step)
+    unsigned char *valid = nullptr, *cmask = nullptr, *has = nullptr;
+    double *plane = nullptr;  // 4 per cell: n[3], d
+    double *fx = nullptr, *fy = nullptr, *fz = nullptr;  // liquid fluxes / face accelerations
+    double *uh[3] = {nullptr, nullptr, nullptr};          // cell intermediate velocity
+    double *a1 = nullptr, *a2 = nullptr, *an = nullptr;  // alpha scratch
+    double *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double* rhs = nullptr;  // assembled right side of the projection
+    std::vector<Level> lv;
+    double* coarse_scratch = nullptr;
+
+    double* part = nullptr;  // NSLOTS x MAX_PARTIALS block partials
+    double* scal = nullptr;  // device scalars
+    double* hbuf = nullptr;  // pinned host mirror of scal
+    int* dflag = nullptr;    // device error flags
+
+    // timing
+    int timing = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<int, int>>> ev_marks;  // class, (start, stop)
+    double t_ms[T_NCLASS] = {0};
+    long long t_n[T_NCLASS] = {0};
+
+    long long nlaunch = 0;  // kernels launched by this context
+    std::string err;
+};
+
+// scalar slots in ctx->scal
+enum ScalarSlot {
+    S_RR = 0,     // ||r||^2
+    S_BB,         // ||b||^2
+    S_PQ,         // p.q
+    S_RZ,         // r.z
+    S_ZQ,         // z.q
+    S_ALPHA,      // CG step length
+    S_BETA,       // CG direction update
+    S_MEAN,       // mean removed
+    S_VOL0, S_VOL1, S_CLIP0, S_CLIP1, S_CLIP2, S_MAXDIV, S_MAXU, S_FALLBACK, S_CFL, S_SUM,
+    S_NSCALARS
+};
+
+// ---------------------------------------------------------------------------
+// helpers implemented in capi.cu
+// ---------------------------------------------------------------------------
+vof_status set_err(vof_ctx* c, vof_status s, const std::string& msg);
+vof_status cuda_check(vof_ctx* c, cudaError_t e, const char* what);
+vof_status launch_check(vof_ctx* c, const char* what);
+int timer_begin(vof_ctx* c, int cls);
+void timer_end(vof_ctx* c, int cls, int mark);
+
+// reductions (k_common.cu): sum / max of the block partials of slot into scal[dst]
+void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale);
+void finalize_max(vof_ctx* c, int slot, int nparts, int dst);
+
+// ---------------------------------------------------------------------------
+// kernel launch wrappers
+// ---------------------------------------------------------------------------
+// poisson (k_poisson.cu)
+void launch_beta(vof_ctx* c, const double* alpha);
+void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y);
+void launch_residual(vof_ctx* c, const Level& l, const double* x, const double* f, double* r,
+                     int slot);
+void launch_dot(vof_ctx* c, const double* x, const double* y, int n, int slot);
+void launch_sub_mean(vof_ctx* c, double* x, int n, int slot_mean);
+void launch_copy(vof_ctx* c, double* dst, const double* src, int n);
+void launch_zero(vof_ctx* c, double* x, int n);
+void launch_apply_A_dot(vof_ctx* c, const Level& l, const double* p, double* q, int slot);
+void launch_cg_update(vof_ctx* c, int n, double* x, double* r, const double* p, const double* q,
+                      int slot);
+void launch_dot2(vof_ctx* c, int n, const double* z, const double* r, const double* q, int slot_a,
+                 int slot_b);
+void launch_p_update(vof_ctx* c, int n, double* p, const double* z);
+void launch_scalar_alpha(vof_ctx* c);
+void launch_scalar_beta(vof_ctx* c);
+
+// multigrid (k_mg.cu), T = double (FP64 path) or float (mixed path)
+template <class T> void mg_rbgs(vof_ctx* c, const Level& L, int color);
+template <class T> void mg_restrict(vof_ctx* c, const Level& fine, const Level& coarse);
+template <class T> void mg_prolong(vof_ctx* c, const Level& coarse, const Level& fine);
+template <class T> void mg_coarsen_beta(vof_ctx* c, const Level& fine, const Level& coarse);
+template <class T> void mg_coarse(vof_ctx* c, const Level& L);
+template <class T> void mg_zero(vof_ctx* c, const Level& L);
+void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
+void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
+
+// vof (k_vof.cu)
+void launch_vof_mask_volume(vof_ctx* c, const double* alpha, int slot);
+void launch_reconstruct(vof_ctx* c, const double* alpha);
+void launch_face_flux(vof_ctx* c, int dir, const double* alpha, const double* vel, double dt,
+                      double* flux);
+void launch_vof_update(vof_ctx* c, int dir, const double* ain, double* aout, const double* vel,
+                       const double* flux, double dt, int slot);
+void launch_cfl(vof_ctx* c, const double* u, const double* v, const double* w, double dt, int slot);
+void launch_volume(vof_ctx* c, const double* alpha, int slot);
+
+// curvature and surface force (k_ssf.cu)
+void launch_curvature(vof_ctx* c, const double* alpha, double* kappa, unsigned char* valid);
+void launch_ssf_faces(vof_ctx* c, const double* alpha, const double* kappa,
+                      const unsigned char* valid, double* sx, double* sy, double* sz, int slot);
+
+// momentum (k_momentum.cu)
+void launch_predict(vof_ctx* c, const double* alpha_n, const double* alpha_np1,
+                    const double* const U[3], const double* u, const double* v, const double* w,
+                    const double* fx, const double* fy, const double* fz, double dt,
+                    double* const out[3]);
+void launch_cell_to_face(vof_ctx* c, const double* uc, const double* vc, const double* wc,
+                         double* u, double* v, double* w);
+
+// projection (k_project.cu)
+void launch_rhs(vof_ctx* c, const double* u, const double* v, const double* w, const double* sx,
+                const double* sy, const double* sz, double dt, double* b, int slot);
+void launch_correct(vof_ctx* c, const double* P, const double* sx, const double* sy,
+                    const double* sz, double dt, const double* const Uh[3], double* const Uc[3],
+                    double* u, double* v, double* w, int slot_div, int slot_u);
+
+// solver driver (solver.cu)
+vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report* rep);
+size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels);
+vof_status mg_allocate(vof_ctx* c);
+void mg_build_coefficients(vof_ctx* c);

@@ -13,10 +13,10 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def ctx(case_or_grid, phys=None, rtol=1e-12, max_iter=400, **kw):
+def ctx(case_or_grid, phys=None, rtol=1e-12, max_iter=400, precision=0, **kw):
     g = case_or_grid.grid if phys is None else case_or_grid
     p = case_or_grid.phys if phys is None else phys
-    return vd.VofContext(g, p, vd.c_solver(rtol=rtol, max_iter=max_iter, **kw))
+    return vd.VofContext(g, p, vd.c_solver(precision, rtol=rtol, max_iter=max_iter, **kw))
 
 
 def rel_l2(a, b):

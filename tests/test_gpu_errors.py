@@ -21,6 +21,7 @@ def test_cfl_violation_is_rejected_before_launch():
             C.vof_advect(a, dev(np.zeros(us)), dev(np.zeros(vs)), dev(np.full(ws, 1.0)),
                          2.0 * g.h, 0)
         assert e.value.name == "VOF_ERR_CFL"
+        assert "Courant" in str(e.value)
 
 
 def test_null_pointer_and_bad_args():
@@ -31,8 +32,9 @@ def test_null_pointer_and_bad_args():
         assert b"NULL" in lib.vof_last_error(C._ctx)
         cs, us, vs, ws = g.shapes()
         with pytest.raises(vd.VofError) as e:
-            C.step(dev(np.ones(cs)), dev(np.zeros(us)), dev(np.zeros(vs)), dev(np.zeros(ws)),
-                   dev(np.zeros(cs)), -1.0, 0)
+            C.step(dev(np.ones(cs)), dev(np.zeros(cs)), dev(np.zeros(cs)), dev(np.zeros(cs)),
+                   dev(np.zeros(us)), dev(np.zeros(vs)), dev(np.zeros(ws)), dev(np.zeros(cs)),
+                   -1.0, 0)
         assert e.value.name == "VOF_ERR_ARG"
 
 

@@ -10,7 +10,11 @@ oracle):
   * pressure solves at rtol 1e-12 on both sides: 1e-8 relative L2 (the
     residual tolerance times the operator's conditioning);
   * whole steps: |dp_gpu - dp_oracle| / dp_Laplace <= 1e-6 and velocity
-    relative L2 <= 1e-8 after the stated number of steps.
+    relative L2 <= 1e-8 after the stated number of steps. The Laplace jump
+    is a difference of two region means of P and inherits the solve's
+    residual times the operator's conditioning (~1e5 here): the oracle
+    against itself at rtol 1e-12 vs 1e-14 already differs by 9e-6 dp_L, so
+    the static-bubble runs use rtol 1e-13 on both sides (2e-7 dp_L).
 """
 import numpy as np
 import pytest
@@ -43,8 +47,11 @@ def test_operator_parity(dims):
         assert rel_max(host(y), ref) < 1e-12
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(37, 21, 30), (48, 40, 64)])
-def test_pressure_solve_parity(dims):
+def test_pressure_solve_parity(dims, prec):
+    """FP64 and mixed (FP32 V-cycle, FP64 residual/updates) solves both reach
+    rtol 1e-12 and agree with the oracle to the conditioning bound."""
     g = I.Grid(*dims)
     ph = I.Phys()
     _, a = _spheres(g, 3, 4)
@@ -55,7 +62,7 @@ def test_pressure_solve_parity(dims):
     b = oracle.apply_A(g, bx, by, bz, Pstar) + 3.0  # non-zero mean is removed
     Po, orep, st = oracle.solve(g, bx, by, bz, b, rtol=1e-12)
     assert st == 0
-    with ctx(g, ph, rtol=1e-12) as C:
+    with ctx(g, ph, rtol=1e-12, precision=prec) as C:
         p = dev(np.zeros_like(b))
         rep = C.pressure_solve(dev(a), dev(b), p)
         P = host(p)
@@ -74,13 +81,17 @@ def test_advect_parity(dims, per):
     w = w + 0.04
     dt = 0.45 * g.h / max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
     a_o = a0.copy()
+    cs, us, vs, ws = g.shapes()
     with ctx(g, I.Phys()) as C:
         a_d = dev(a0)
         U, Vv, W = dev(u), dev(v), dev(w)
+        fl = [dev(np.zeros(s_)) for s_ in (us, vs, ws)]
         for s in range(4):
-            rep = C.vof_advect(a_d, U, Vv, W, dt, s)
-            a_o, orep = oracle.advect(g, a_o, u, v, w, dt, s)
+            rep = C.vof_advect(a_d, U, Vv, W, dt, s, fluxes=fl)
+            a_o, flo, orep = oracle.advect(g, a_o, u, v, w, dt, s, fluxes=True)
             assert np.max(np.abs(host(a_d) - a_o)) < 1e-12
+            for x, y in zip(fl, flo):
+                assert np.max(np.abs(host(x) - y)) < 1e-13
             assert rep["vol_after"] == pytest.approx(orep["vol_after"], rel=1e-13)
             assert rep["vol_after"] == pytest.approx(rep["vol_before"], rel=1e-13)
 
@@ -119,13 +130,15 @@ def test_predict_parity(conv):
     case = I.rising_swarm(36, 28, 40, nbub=3, seed=8, steps=1)
     g = case.grid
     ph = I.Phys(**{**case.phys.__dict__, "conv_scheme": conv})
-    a1, _ = oracle.advect(g, case.alpha, case.u, case.v, case.w, case.dt, 0)
-    ref = oracle.predict(g, ph, case.alpha, a1, case.u, case.v, case.w, case.dt)
+    a1, fl, _ = oracle.advect(g, case.alpha, case.u, case.v, case.w, case.dt, 0, fluxes=True)
+    ref_c = oracle.predict(g, ph, case.alpha, a1, case.uc, case.vc, case.wc, case.u, case.v,
+                           case.w, *fl, case.dt)
+    ref_f = oracle.cell_to_face(g, *ref_c)
     with ctx(g, ph) as C:
-        U, Vv, W = dev(case.u), dev(case.v), dev(case.w)
-        C.vof_predict(dev(case.alpha), dev(a1), U, Vv, W, case.dt)
-        got = [host(U), host(Vv), host(W)]
-    for x, y in zip(got, ref):
+        T = [dev(x) for x in (case.uc, case.vc, case.wc, case.u, case.v, case.w)]
+        C.vof_predict(dev(case.alpha), dev(a1), *T, *(dev(f) for f in fl), case.dt)
+        got = [host(t) for t in T]
+    for x, y in zip(got, list(ref_c) + list(ref_f)):
         assert rel_max(x, y) < 1e-12
 
 
@@ -134,16 +147,16 @@ def test_project_parity():
     g, ph = case.grid, case.phys
     kap, sx, sy, sz, _ = oracle.ssf(g, ph, case.alpha)
     rng = np.random.default_rng(10)
-    uh = case.u + 0.01 * rng.normal(size=case.u.shape)
-    vh = case.v + 0.01 * rng.normal(size=case.v.shape)
-    wh = case.w + 0.01 * rng.normal(size=case.w.shape)
-    uo, vo, wo, Po, orep, st = oracle.project(g, ph, case.alpha, uh, vh, wh, case.P, sx, sy, sz,
-                                              case.dt, rtol=1e-12)
+    uhc, vhc, whc = (x + 0.01 * rng.normal(size=x.shape) for x in (case.uc, case.vc, case.wc))
+    uh, vh, wh = oracle.cell_to_face(g, uhc, vhc, whc)
+    *ref, Po, orep, st = oracle.project(g, ph, case.alpha, uhc, vhc, whc, uh, vh, wh, case.P,
+                                        sx, sy, sz, case.dt, rtol=1e-12)
     assert st == 0
     with ctx(case, rtol=1e-12) as C:
-        U, Vv, W, P = dev(uh), dev(vh), dev(wh), dev(case.P)
-        rep = C.project(dev(case.alpha), U, Vv, W, P, dev(sx), dev(sy), dev(sz), case.dt)
-        assert rel_l2([host(U), host(Vv), host(W)], [uo, vo, wo]) < 1e-10
+        T = [dev(x) for x in (uhc, vhc, whc, uh, vh, wh)]
+        P = dev(case.P)
+        rep = C.project(dev(case.alpha), *T, P, dev(sx), dev(sy), dev(sz), case.dt)
+        assert rel_l2([host(t) for t in T], ref) < 1e-10
         assert rel_l2(host(P), Po) < 1e-8
         assert rep["max_div"] * case.dt < 1e-10
 
@@ -156,44 +169,43 @@ def _laplace_jump(case, a, P):
     return P[(a < 1e-9) & (r < R - 2 * g.h)].mean() - P[(a > 1 - 1e-9) & (r > R + 2 * g.h)].mean()
 
 
+def _run_both(case, steps, rtol, precision=0):
+    g, ph = case.grid, case.phys
+    ref = case.state()
+    reps, oreps = [], []
+    with ctx(case, rtol=rtol, precision=precision) as C:
+        T = [dev(x) for x in case.state()]
+        for s in range(steps):
+            reps.append(C.step(*T, case.dt, s))
+            *ref, orep, st = oracle.step(g, ph, *ref, case.dt, s, rtol=rtol)
+            assert st == 0
+            oreps.append(orep)
+        got = [host(t) for t in T]
+    return got, ref, reps, oreps
+
+
 @pytest.mark.parametrize("kappa_mode", [1, 0])
 def test_step_static_bubble_20_steps(kappa_mode):
     case = I.static_bubble(kappa_mode=kappa_mode)
-    g, ph = case.grid, case.phys
-    ao, uo, vo, wo, Po = case.alpha, case.u, case.v, case.w, case.P
-    with ctx(case, rtol=1e-12) as C:
-        T = [dev(x) for x in (case.alpha, case.u, case.v, case.w, case.P)]
-        for s in range(20):
-            rep = C.step(*T, case.dt, s)
-            ao, uo, vo, wo, Po, orep, st = oracle.step(g, ph, ao, uo, vo, wo, Po, case.dt, s,
-                                                      rtol=1e-12)
-            assert st == 0
-        a, u, v, w, P = (host(t) for t in T)
-    dp_l = 2 * ph.sigma / case.radius
-    dp, dpo = _laplace_jump(case, a, P), _laplace_jump(case, ao, Po)
+    got, ref, reps, oreps = _run_both(case, 20, rtol=1e-13)
+    dp_l = 2 * case.phys.sigma / case.radius
+    dp, dpo = _laplace_jump(case, got[0], got[7]), _laplace_jump(case, ref[0], ref[7])
     assert abs(dp - dpo) / dp_l <= 1e-6
     if kappa_mode == 1:
         assert dp == pytest.approx(dp_l, rel=1e-9)
-        assert rep["max_u"] < 1e-11
+        assert reps[-1]["max_u"] < 1e-11
     else:
-        assert rel_l2([u, v, w], [uo, vo, wo]) <= 1e-8
-        assert rep["max_u"] == pytest.approx(orep["max_u"], rel=1e-6)
-    assert np.max(np.abs(a - ao)) < 1e-12
+        assert rel_l2(got[1:7], ref[1:7]) <= 1e-8
+        assert reps[-1]["max_u"] == pytest.approx(oreps[-1]["max_u"], rel=1e-6)
+    assert np.max(np.abs(got[0] - ref[0])) < 1e-12
 
 
-def test_step_rising_swarm_parity():
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_rising_swarm_parity(prec):
     case = I.rising_swarm(32, 32, 48, nbub=3, seed=11, steps=6)
-    g, ph = case.grid, case.phys
-    ao, uo, vo, wo, Po = case.alpha, case.u, case.v, case.w, case.P
-    with ctx(case, rtol=1e-12) as C:
-        T = [dev(x) for x in (case.alpha, case.u, case.v, case.w, case.P)]
-        for s in range(case.steps):
-            rep = C.step(*T, case.dt, s)
-            ao, uo, vo, wo, Po, orep, st = oracle.step(g, ph, ao, uo, vo, wo, Po, case.dt, s,
-                                                      rtol=1e-12)
-            assert st == 0
-            assert rep["vol_after"] == pytest.approx(orep["vol_after"], rel=1e-13)
-        a, u, v, w, P = (host(t) for t in T)
-    assert rel_l2([u, v, w], [uo, vo, wo]) <= 1e-8
-    assert np.max(np.abs(a - ao)) < 1e-10
-    assert rel_l2(P, Po) < 1e-7
+    got, ref, reps, oreps = _run_both(case, case.steps, rtol=1e-12, precision=prec)
+    for r, o in zip(reps, oreps):
+        assert r["vol_after"] == pytest.approx(o["vol_after"], rel=1e-13)
+    assert rel_l2(got[1:7], ref[1:7]) <= 1e-8
+    assert np.max(np.abs(got[0] - ref[0])) < 1e-10
+    assert rel_l2(got[7], ref[7]) < 1e-7
