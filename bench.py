@@ -33,18 +33,22 @@ METRIC = "time-steps/s & Poisson cell-updates/s at 32M cells; served p50/p99 vs 
 UNIT = "time-steps/s"
 WORKLOAD = "paper-shaped duct 224x224x640 (32.1M cells), 864 spheres d=12h, Re_b=5300 1/7 profile + 8% noise"
 
-# Algorithmic bytes per fine-grid cell for one launch of each kernel class
-# (FP64): what the kernel must read and write at minimum.
-#  smooth_l0   one red-black colour: other-colour x (4), all face betas (24),
-#              own-colour right side (4), own-colour x written (4)
-#  residual_l0 q = A p with p.q: p (8), betas (24), q written (8)
-#  restrict_l0 residual of 8 children averaged: x, f (16), betas (24),
-#              coarse f written (1)
-#  prolong_l0  fine x read and written (16), coarse x (1)
-ALGO_BYTES_PER_CELL = {"smooth_l0": 36.0, "residual_l0": 40.0, "restrict_l0": 41.0,
-                       "prolong_l0": 17.0}
-KERNEL_SOURCE = {"smooth_l0": "k_poisson.cu", "residual_l0": "k_poisson.cu",
-                 "restrict_l0": "k_poisson.cu", "prolong_l0": "k_poisson.cu"}
+# Algorithmic bytes per fine-grid cell for one launch of each kernel class:
+# what the kernel must read and write at minimum, with E the byte size of the
+# multigrid scalar (8 for the FP64 path, 4 for the mixed path's FP32 V-cycle).
+#  smooth_l0   one red-black colour: other-colour x (E/2), all face betas
+#              (3E), own-colour right side (E/2), own-colour x written (E/2)
+#  restrict_l0 residual of 8 children averaged: x, f (2E), betas (3E),
+#              coarse f written (E/8)
+#  prolong_l0  fine x read and written (2E), coarse x (E/8)
+#  residual_l0 q = A p with p.q, always FP64: p (8), betas (24), q (8)
+def algo_bytes_per_cell(cls: str, E: int) -> float:
+    return {"smooth_l0": 4.5 * E, "restrict_l0": 5.125 * E, "prolong_l0": 2.125 * E,
+            "residual_l0": 40.0}[cls]
+
+
+KERNEL_SOURCE = {"smooth_l0": "k_mg.cu", "residual_l0": "k_poisson.cu",
+                 "restrict_l0": "k_mg.cu", "prolong_l0": "k_mg.cu"}
 
 
 def parse():
@@ -257,10 +261,10 @@ def main():
             it2 += rep["iters"]
         kt = ctx.kernel_times()
         ctx.set_timing(False)
-        cls = max(ALGO_BYTES_PER_CELL, key=lambda k: kt.get(k, (0.0, 0))[0])
+        cls = max(KERNEL_SOURCE, key=lambda k: kt.get(k, (0.0, 0))[0])
         kms, kn = kt[cls]
         avg_ms = kms / max(kn, 1)
-        algo = ALGO_BYTES_PER_CELL[cls] * N
+        algo = algo_bytes_per_cell(cls, 8 if args.precision == "fp64" else 4) * N
         peak, peak_kind = peaks()
         achieved = algo / (avg_ms / 1e3) / 1e9
         step_ms_timed = sum(v[0] for v in kt.values()) / k_steps
