@@ -152,6 +152,34 @@ vof_status pressure_solve(vof_ctx* ctx, const double* alpha, const double* b, do
 /* y = A x with beta from alpha (the operator of pressure_solve). */
 vof_status vof_apply_operator(vof_ctx* ctx, const double* alpha, const double* x, double* y);
 
+/* Largest total face count (x + y + z faces) vof_apply_operator_noalloc
+ * accepts: its fixed scratch holds this many doubles (24 MiB). */
+#define VOF_NOALLOC_MAX_FACES (3u << 20)
+
+/* y = A x as vof_apply_operator computes it, but with no context and no
+ * device allocation at all. The paper has no counterpart: it exists for
+ * callers that cannot call cudaMalloc -- code running while its stream is
+ * being captured into a CUDA graph, hosts that reserve all device memory up
+ * front in their own arena, latency-critical loops where an allocation
+ * could synchronise the device. The face coefficients beta it builds from
+ * alpha go into one fixed device array inside the library (24 MiB, held by
+ * every GPU that loads the library until the process exits), so
+ *  - grids with more than VOF_NOALLOC_MAX_FACES faces in total are
+ *    rejected with VOF_ERR_ADMISSION before anything is launched;
+ *  - every call shares that array and overwrites all of it that it reads,
+ *    so nothing needs clearing between calls, but calls whose kernels
+ *    overlap on the GPU (different streams, or different host threads on
+ *    one device) race on it: serialise them;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, which may load the library's module), so make
+ *    that first call before any stream capture on that device.
+ * alpha, x, y: device arrays in the cell layout; stream: cudaStream_t (NULL
+ * = legacy default stream); the call is asynchronous on it. Walls only
+ * (VOF_ERR_UNSUPPORTED for periodic x or y). */
+vof_status vof_apply_operator_noalloc(const vof_grid* grid, const vof_phys* phys,
+                                      const double* alpha, const double* x, double* y,
+                                      void* stream);
+
 /* Momentum predictor (Eq. 2; steps 8-10). On entry (uc, vc, wc) hold the
  * cell velocity u^n and (u, v, w) the face velocity that advected alpha
  * from alpha_n to alpha_np1 with liquid face fluxes (fx, fy, fz) from
