@@ -82,8 +82,16 @@ typedef struct {
     int precision;        /* VOF_PREC_*: multigrid preconditioner precision   */
     double rtol;          /* stop when ||b - A P||_2 <= rtol ||b||_2          */
     int max_iter;         /* Krylov iteration cap                             */
-    int nu_pre, nu_post;  /* red-black Gauss-Seidel sweeps per level          */
+    int nu_pre, nu_post;  /* red-black Gauss-Seidel sweeps per level (equal)  */
+    double mg_omega;      /* scale of the coarse-grid correction, (0, 2];
+                             0 selects the default 1                          */
+    int coarse_iters;     /* CG iterations cap on the coarsest level; 0 = 400 */
+    double coarse_tol;    /* relative residual target there; 0 = default      */
+    int mg_interp;        /* VOF_MG_CONSTANT or VOF_MG_TRILINEAR prolongation
+                             (restriction is its transpose / 8 in both)       */
 } vof_solver;
+
+enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 
 typedef struct {
     int iters;                    /* Krylov iterations of the last solve        */

@@ -45,6 +45,7 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     b += 3 * faces * sizeof(double);                  // beta, surface force, fluxes
     b += s.n * sizeof(double);                        // kappa
     b += 3 * s.n;                                     // valid, cmask, has
+    b += s.n * sizeof(int) + 64;                      // interface list
     b += 4 * s.n * sizeof(double);                    // planes
     b += 3 * s.n * sizeof(double);                    // cell intermediate velocity
     b += 3 * s.n * sizeof(double);                    // alpha scratch
@@ -215,7 +216,7 @@ extern "C" {
 vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, size_t* bytes) {
     std::string why;
     if (!grid_ok(grid, why) || !bytes) return VOF_ERR_ARG;
-    vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2};
+    vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2, 0.0, 0, 0.0, VOF_MG_CONSTANT};
     *bytes = workspace_bytes(grid, solver ? solver : &def);
     return VOF_OK;
 }
@@ -232,7 +233,9 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
         (phys->kappa_mode != VOF_KAPPA_HEIGHT_FUNCTION && phys->kappa_mode != VOF_KAPPA_EXACT))
         return VOF_ERR_ARG;
     if (!(solver->rtol > 0) || solver->max_iter < 1 || solver->nu_pre < 1 ||
-        solver->nu_pre != solver->nu_post ||
+        solver->nu_pre != solver->nu_post || !(solver->mg_omega >= 0.0) ||
+        solver->mg_omega > 2.0 || solver->coarse_iters < 0 || !(solver->coarse_tol >= 0.0) ||
+        (solver->mg_interp != VOF_MG_CONSTANT && solver->mg_interp != VOF_MG_TRILINEAR) ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
         return VOF_ERR_ARG;
     const size_t need = workspace_bytes(grid, solver);
@@ -273,6 +276,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     A((void**)&c->valid, s.n);
     A((void**)&c->cmask, s.n);
     A((void**)&c->has, s.n);
+    A((void**)&c->if_list, s.n * sizeof(int));
+    A((void**)&c->if_count, 64);
     A((void**)&c->plane, 4 * s.n * D);
     A((void**)&c->a1, s.n * D);
     A((void**)&c->a2, s.n * D);

@@ -9,8 +9,11 @@
 // restriction averages the fine residual over the eight children and
 // prolongation adds the coarse value to its eight children; the smoother is
 // red-black Gauss-Seidel, x_c = (h^2 f_c + sum beta x_nb) / sum beta. The
-// coarsest level is solved by Jacobi-preconditioned CG in one thread block
-// (FP64 reductions in both modes).
+// coarsest level (up to DENSE_MAX cells) is solved exactly with an explicit
+// inverse formed once per solve by FP64 Gauss-Jordan elimination; larger
+// coarsest levels fall back to Jacobi-preconditioned CG in one thread block.
+#include <algorithm>
+
 #include "vof_internal.cuh"
 
 namespace {
@@ -81,11 +84,114 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
 
 template <class T>
 __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __restrict__ xf,
-                            int kchunk) {
+                            T omega, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= df.nx || j >= df.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
-    for (int k = k0; k < k1; ++k) xf[cid(df, i, j, k)] += xc[cid(dc, i >> 1, j >> 1, k >> 1)];
+    for (int k = k0; k < k1; ++k)
+        xf[cid(df, i, j, k)] += omega * xc[cid(dc, i >> 1, j >> 1, k >> 1)];
+}
+
+// Cell-centred trilinear prolongation along one axis: the fine cell 2I
+// takes 3/4 of coarse I and 1/4 of I-1, the fine cell 2I+1 3/4 of I and 1/4
+// of I+1; across a wall the outside share goes to the parent (constant
+// extension), on the periodic axis it wraps.
+struct Tri {
+    int lo, hi;   // the two coarse indices
+    float wlo, whi;
+};
+__device__ __forceinline__ Tri tri1(int i, int N, bool periodic) {
+    const int I = i >> 1;
+    int nb = (i & 1) ? I + 1 : I - 1;
+    Tri t;
+    if (nb < 0 || nb >= N) {
+        if (periodic) {
+            nb = nb < 0 ? nb + N : nb - N;
+        } else {
+            t.lo = I; t.hi = I; t.wlo = 1.f; t.whi = 0.f;
+            return t;
+        }
+    }
+    t.lo = I; t.hi = nb; t.wlo = 0.75f; t.whi = 0.25f;
+    return t;
+}
+
+template <class T>
+__global__ void k_prolong_tri_t(Dims dc, const T* __restrict__ xc, Dims df, T* __restrict__ xf,
+                                T omega, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= df.nx || j >= df.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
+    const Tri tx = tri1(i, dc.nx, false), ty = tri1(j, dc.ny, false);
+    for (int k = k0; k < k1; ++k) {
+        const Tri tz = tri1(k, dc.nz, true);
+        const int xs[2] = {tx.lo, tx.hi}, ys[2] = {ty.lo, ty.hi}, zs[2] = {tz.lo, tz.hi};
+        const T wx[2] = {(T)tx.wlo, (T)tx.whi}, wy[2] = {(T)ty.wlo, (T)ty.whi},
+                wz[2] = {(T)tz.wlo, (T)tz.whi};
+        T s = T(0);
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a)
+                    s += wx[a] * wy[b] * wz[c] * xc[cid(dc, xs[a], ys[b], zs[c])];
+        xf[cid(df, i, j, k)] += omega * s;
+    }
+}
+
+// r = f - A x on one level (the MG residual before full-weighting restriction)
+template <class T>
+__global__ void k_mg_residual_t(Dims d, T ih2, const T* __restrict__ bx, const T* __restrict__ by,
+                                const T* __restrict__ bz, const T* __restrict__ x,
+                                const T* __restrict__ f, T* __restrict__ r, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= d.nx || j >= d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    for (int k = k0; k < k1; ++k) {
+        const int c = cid(d, i, j, k);
+        r[c] = f[c] - stencil_t(d, bx, by, bz, x, i, j, k) * ih2;
+    }
+}
+
+// weight that fine index i gives coarse index C along an axis
+__device__ __forceinline__ float w1(int i, int C, int N, bool periodic) {
+    const Tri t = tri1(i, N, periodic);
+    float w = 0.f;
+    if (t.lo == C) w += t.wlo;
+    if (t.hi == C) w += t.whi;
+    return w;
+}
+
+// Restriction as the transpose of the trilinear prolongation, divided by 8:
+// coarse I gathers fine cells 2I-1 .. 2I+2 along each axis with the weights
+// those fine cells give I when prolongating.
+template <class T>
+__global__ void k_restrict_fw_t(Dims df, const T* __restrict__ rf, Dims dc, T* __restrict__ fc,
+                                int kchunk) {
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    for (int K = k0; K < k1; ++K) {
+        T s = T(0);
+        for (int c = -1; c <= 2; ++c) {
+            int k = 2 * K + c;
+            k = k < 0 ? k + df.nz : (k >= df.nz ? k - df.nz : k);
+            const float wz = w1(k, K, dc.nz, true);
+            if (wz == 0.f) continue;
+            for (int b = -1; b <= 2; ++b) {
+                const int j = 2 * J + b;
+                if (j < 0 || j >= df.ny) continue;
+                const float wy = w1(j, J, dc.ny, false);
+                if (wy == 0.f) continue;
+                for (int a = -1; a <= 2; ++a) {
+                    const int i = 2 * I + a;
+                    if (i < 0 || i >= df.nx) continue;
+                    const float wx = w1(i, I, dc.nx, false);
+                    if (wx == 0.f) continue;
+                    s += (T)(wx * wy * wz) * rf[cid(df, i, j, k)];
+                }
+            }
+        }
+        fc[cid(dc, I, J, K)] = T(0.125) * s;
+    }
 }
 
 template <class T>
@@ -194,6 +300,75 @@ __global__ void k_coarse_cg_t(Dims d, T ih2, const T* __restrict__ bx, const T* 
     for (int c = tid; c < n; c += nt) x[c] -= xm;
 }
 
+// ---- dense coarsest-level solve --------------------------------------------
+// M = A_c + s 1 1^T (SPD; on mean-free right sides M^{-1} f is the mean-free
+// solution of A_c x = f, since the constants are an eigenvector of M with
+// eigenvalue s n and the range of A_c is orthogonal to them).
+template <class T>
+__global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
+                                 const T* __restrict__ by, const T* __restrict__ bz, double s,
+                                 double* __restrict__ M) {
+    const int n = d.nx * d.ny * d.nz;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n;
+         e += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), col = (int)(e % n);
+        const int i = r % d.nx, j = (r / d.nx) % d.ny, k = r / (d.nx * d.ny);
+        double v = s;
+        if (col == r) {
+            v += ((double)bx[uid(d, i, j, k)] + bx[uid(d, i + 1, j, k)] + by[vid(d, i, j, k)] +
+                  by[vid(d, i, j + 1, k)] + bz[wid(d, i, j, k)] +
+                  bz[wid(d, i, j, wrapk(k + 1, d.nz))]) * ih2;
+        } else {
+            // the six neighbours (walls carry beta = 0; on a periodic axis of
+            // length 2 both neighbours are the same cell and both faces count)
+            if (i > 0 && col == r - 1) v -= (double)bx[uid(d, i, j, k)] * ih2;
+            if (i < d.nx - 1 && col == r + 1) v -= (double)bx[uid(d, i + 1, j, k)] * ih2;
+            if (j > 0 && col == r - d.nx) v -= (double)by[vid(d, i, j, k)] * ih2;
+            if (j < d.ny - 1 && col == r + d.nx) v -= (double)by[vid(d, i, j + 1, k)] * ih2;
+            if (col == cid(d, i, j, wrapk(k - 1, d.nz))) v -= (double)bz[wid(d, i, j, k)] * ih2;
+            if (col == cid(d, i, j, wrapk(k + 1, d.nz)))
+                v -= (double)bz[wid(d, i, j, wrapk(k + 1, d.nz))] * ih2;
+        }
+        M[e] = v;
+    }
+}
+
+// One Gauss-Jordan pivot step of the in-place inversion of an SPD matrix
+// (no pivoting needed), reading A and writing B.
+__global__ void k_gauss_jordan(int n, int kp, const double* __restrict__ A, double* __restrict__ B) {
+    __shared__ double rp;
+    if (threadIdx.x == 0) rp = 1.0 / A[(long)kp * n + kp];
+    __syncthreads();
+    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    const int i = (int)(e / n), j = (int)(e % n);
+    double v;
+    if (i == kp && j == kp) v = rp;
+    else if (i == kp) v = A[e] * rp;
+    else if (j == kp) v = -A[e] * rp;
+    else v = A[e] - A[(long)i * n + kp] * (A[(long)kp * n + j] * rp);
+    B[e] = v;
+}
+
+__global__ void k_dense_to_f32(long n2, const double* __restrict__ a, float* __restrict__ b) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n2;
+         e += (long)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+// x = Minv f: one warp per row, FP64 accumulation
+template <class T>
+__global__ void k_dense_apply(int n, const T* __restrict__ Minv, const T* __restrict__ f,
+                              T* __restrict__ x) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const T* row = Minv + (long)warp * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += (double)row[j] * (double)f[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[warp] = (T)acc;
+}
+
 template <class T>
 __global__ void k_zero_t(int n, T* __restrict__ x) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
@@ -247,8 +422,16 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
     const LA<T> a = arrays<T>(F), b = arrays<T>(C);
     const int cls = F.idx == 0 ? T_RESTRICT0 : T_RESTRICT;
     int m = timer_begin(c, cls);
-    VOF_LAUNCH(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx, a.by,
-               a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
+    if (c->sv.mg_interp == VOF_MG_TRILINEAR) {
+        T* r = (T*)F.rs;
+        VOF_LAUNCH(c, k_mg_residual_t<T>, F.L.grid, F.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx,
+                   a.by, a.bz, a.x, a.f, r, F.L.kchunk);
+        VOF_LAUNCH(c, k_restrict_fw_t<T>, C.L.grid, C.L.block, F.d, (const T*)r, C.d, b.f,
+                   C.L.kchunk);
+    } else {
+        VOF_LAUNCH(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx,
+                   a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
+    }
     timer_end(c, cls, m);
 }
 
@@ -257,7 +440,12 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
     const LA<T> a = arrays<T>(C), b = arrays<T>(F);
     const int cls = F.idx == 0 ? T_PROLONG0 : T_PROLONG;
     int m = timer_begin(c, cls);
-    VOF_LAUNCH(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, F.L.kchunk);
+    const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
+    if (c->sv.mg_interp == VOF_MG_TRILINEAR)
+        VOF_LAUNCH(c, k_prolong_tri_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega,
+                   F.L.kchunk);
+    else
+        VOF_LAUNCH(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
     timer_end(c, cls, m);
 }
 
@@ -268,14 +456,48 @@ void mg_coarsen_beta(vof_ctx* c, const Level& F, const Level& C) {
                b.bz, C.L.kchunk);
 }
 
+// Factor the coarsest level once per solve: explicit inverse of A_c + s 11^T
+// in FP64 (and an FP32 copy for the mixed V-cycle).
+template <class T>
+void mg_dense_setup(vof_ctx* c, const Level& L) {
+    const LA<T> a = arrays<T>(L);
+    const int n = L.ncells;
+    const long n2 = (long)n * n;
+    const double ih2 = 1.0 / (L.h * L.h);
+    // s n ~ the typical diagonal entry: the largest face coefficient is not
+    // known on the host, so use the liquid value scale of the fine operator
+    const double s = c->dense_shift * ih2 / n;
+    const int nb = (int)std::min<long>((n2 + 255) / 256, 65535L * 8);
+    int m = timer_begin(c, T_COARSE);
+    VOF_LAUNCH(c, k_dense_assemble<T>, nb, 256, L.d, ih2, a.bx, a.by, a.bz, s, c->dense_a);
+    double* A = c->dense_a;
+    double* B = c->dense_b;
+    const int gj_blocks = (int)((n2 + 255) / 256);
+    for (int kp = 0; kp < n; ++kp) {
+        VOF_LAUNCH(c, k_gauss_jordan, gj_blocks, 256, n, kp, A, B);
+        std::swap(A, B);
+    }
+    c->dense_inv = A;
+    if (sizeof(T) == 4) VOF_LAUNCH(c, k_dense_to_f32, nb, 256, n2, A, c->dense_inv_f);
+    timer_end(c, T_COARSE, m);
+}
+
 template <class T>
 void mg_coarse(vof_ctx* c, const Level& L) {
     const LA<T> a = arrays<T>(L);
     int m = timer_begin(c, T_COARSE);
-    // FP64: tight; FP32: to what single precision can hold
-    const double tol = sizeof(T) == 8 ? 1e-8 : 1e-5;
+    if (c->dense_n > 0) {
+        const int n = L.ncells;
+        const T* Minv = sizeof(T) == 4 ? (const T*)c->dense_inv_f : (const T*)c->dense_inv;
+        VOF_LAUNCH(c, k_dense_apply<T>, (n * 32 + 255) / 256, 256, n, Minv, a.f, a.x);
+        timer_end(c, T_COARSE, m);
+        return;
+    }
+    // default targets: FP64 tight, FP32 what single precision can hold
+    const double tol = c->sv.coarse_tol > 0.0 ? c->sv.coarse_tol : (sizeof(T) == 8 ? 1e-8 : 1e-5);
+    const int maxit = c->sv.coarse_iters > 0 ? c->sv.coarse_iters : 400;
     VOF_LAUNCH(c, k_coarse_cg_t<T>, 1, 1024, L.d, (T)(1.0 / (L.h * L.h)), a.bx, a.by, a.bz, a.f,
-               a.x, (T*)c->coarse_scratch, 400, tol);
+               a.x, (T*)c->coarse_scratch, maxit, tol);
     timer_end(c, T_COARSE, m);
 }
 
@@ -304,4 +526,6 @@ template void mg_coarsen_beta<float>(vof_ctx*, const Level&, const Level&);
 template void mg_coarse<double>(vof_ctx*, const Level&);
 template void mg_coarse<float>(vof_ctx*, const Level&);
 template void mg_zero<double>(vof_ctx*, const Level&);
+template void mg_dense_setup<double>(vof_ctx*, const Level&);
+template void mg_dense_setup<float>(vof_ctx*, const Level&);
 template void mg_zero<float>(vof_ctx*, const Level&);

@@ -26,18 +26,14 @@ struct Pred {
     int upwind;
 };
 
+// velocity component with no-slip ghosts: every component changes sign
+// across a wall (the sign is applied as a negation, not a multiply)
 __device__ __forceinline__ double vcell(const Pred& P, int comp, int i, int j, int k) {
-    double s = 1.0;
-    if (i < 0) { i = 0; s = -s; } else if (i >= P.d.nx) { i = P.d.nx - 1; s = -s; }
-    if (j < 0) { j = 0; s = -s; } else if (j >= P.d.ny) { j = P.d.ny - 1; s = -s; }
-    return s * P.U[comp][cid(P.d, i, j, wrapk(k, P.d.nz))];
-}
-
-__device__ __forceinline__ double mucell(const Pred& P, int i, int j, int k) {
-    i = min(max(i, 0), P.d.nx - 1);
-    j = min(max(j, 0), P.d.ny - 1);
-    const double al = P.an[cid(P.d, i, j, wrapk(k, P.d.nz))];
-    return al * P.ml + (1.0 - al) * P.mg;
+    bool flip = false;
+    if (i < 0) { i = 0; flip = !flip; } else if (i >= P.d.nx) { i = P.d.nx - 1; flip = !flip; }
+    if (j < 0) { j = 0; flip = !flip; } else if (j >= P.d.ny) { j = P.d.ny - 1; flip = !flip; }
+    const double q = P.U[comp][cid(P.d, i, j, wrapk(k, P.d.nz))];
+    return flip ? -q : q;
 }
 
 __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ o1,
@@ -46,78 +42,88 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
     const Dims& d = P.d;
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
-    const double dt_h = P.dt / P.h;
+    const double inv_h = 1.0 / P.h;
+    const double inv_h2 = inv_h * inv_h;
+    const double drho = P.rl - P.rg, dmu = P.ml - P.mg;
+    const double rg_dth = P.rg * (P.dt * inv_h);
     for (int k = k0; k < k1; ++k) {
         const int c = cid(d, i, j, k);
-        const double rn = P.an[c] * P.rl + (1.0 - P.an[c]) * P.rg;
-        const double rn1 = P.a1[c] * P.rl + (1.0 - P.a1[c]) * P.rg;
-        const double muc = mucell(P, i, j, k);
-        // mass flux and neighbour of each of the six faces (walls: M = 0)
-        double M[6];
+        const double an = P.an[c];
+        const double rn = fma(an, drho, P.rg);
+        const double rn1 = fma(P.a1[c], drho, P.rg);
+        const double muc = fma(an, dmu, P.mg);
+        // per face f (0,1: -x,+x; 2,3: -y,+y; 4,5: -z,+z): neighbour cell
+        // (clamped at walls), face viscosity, mass flux (0 on walls), donor side
         int nbc[6];
-        double upwL[6];  // 1 if the face's left cell is the donor
-        double sgn[6];
+        double muf[6], M[6];
+        bool left_donor[6];
+        #pragma unroll
         for (int f = 0; f < 6; ++f) {
             const int dd = f >> 1, side = f & 1;
-            sgn[f] = side ? 1.0 : -1.0;
-            int fi = i, fj = j, fk = k;  // face index in its direction's layout
+            int ni = i, nj = j, nk = k;
             bool wall = false;
             double uf = 0.0, F = 0.0;
             if (dd == 0) {
-                fi = i + side;
+                ni = side ? i + 1 : i - 1;
+                const int fi = i + side;
                 wall = fi == 0 || fi == d.nx;
                 if (!wall) { uf = P.u[uid(d, fi, j, k)]; F = P.fx[uid(d, fi, j, k)]; }
-                nbc[f] = side ? (i + 1 < d.nx ? c + 1 : c) : (i > 0 ? c - 1 : c);
             } else if (dd == 1) {
-                fj = j + side;
+                nj = side ? j + 1 : j - 1;
+                const int fj = j + side;
                 wall = fj == 0 || fj == d.ny;
                 if (!wall) { uf = P.v[vid(d, i, fj, k)]; F = P.fy[vid(d, i, fj, k)]; }
-                nbc[f] = side ? (j + 1 < d.ny ? c + d.nx : c) : (j > 0 ? c - d.nx : c);
             } else {
-                fk = wrapk(k + side, d.nz);
+                nk = side ? k + 1 : k - 1;
+                const int fk = wrapk(k + side, d.nz);
                 uf = P.w[wid(d, i, j, fk)];
                 F = P.fz[wid(d, i, j, fk)];
-                nbc[f] = cid(d, i, j, wrapk(k + (side ? 1 : -1), d.nz));
             }
-            M[f] = wall ? 0.0 : P.rl * F + P.rg * (uf * dt_h - F);
-            upwL[f] = uf > 0.0 ? 1.0 : 0.0;
+            const int ci = min(max(ni, 0), d.nx - 1), cj = min(max(nj, 0), d.ny - 1);
+            nbc[f] = cid(d, ci, cj, wrapk(nk, d.nz));
+            muf[f] = 0.5 * (muc + fma(P.an[nbc[f]], dmu, P.mg));
+            M[f] = wall ? 0.0 : fma(drho, F, rg_dth * uf);
+            left_donor[f] = uf > 0.0;
         }
+        const double r_rn1 = 1.0 / rn1;
         double out[3];
+        #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
             const double qc = P.U[comp][c];
-            // convection
+            // convection: outward mass flux times the transported velocity
             double C = 0.0;
+            #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                if (M[f] == 0.0) continue;
                 const double qn = P.U[comp][nbc[f]];
                 const double qL = (f & 1) ? qc : qn, qR = (f & 1) ? qn : qc;
-                const double qs = P.upwind ? (upwL[f] > 0.0 ? qL : qR) : 0.5 * (qL + qR);
-                C += sgn[f] * M[f] * qs;
+                const double qs = P.upwind ? (left_donor[f] ? qL : qR) : 0.5 * (qL + qR);
+                C = (f & 1) ? fma(M[f], qs, C) : fma(-M[f], qs, C);
             }
-            // viscous traction over the six faces
+            // viscous: (1/h^2) sum_f mu_f [(q_nb - q_c) + s_f (tangential difference)/4]
             double V = 0.0;
+            #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 const int dd = f >> 1;
                 int o[3] = {0, 0, 0};
                 o[dd] = (f & 1) ? 1 : -1;
                 const int ni = i + o[0], nj = j + o[1], nk = k + o[2];
-                const double muf = 0.5 * (muc + mucell(P, ni, nj, nk));
-                const double dq = sgn[f] * (vcell(P, comp, ni, nj, nk) - qc) / P.h;
-                double tr = dq;
-                if (dd != comp) {
+                const double diff = vcell(P, comp, ni, nj, nk) - qc;
+                double t;
+                if (dd == comp) {
+                    t = diff + diff;
+                } else {
                     int e[3] = {0, 0, 0};
                     e[comp] = 1;
                     const double g1 = vcell(P, dd, i + e[0], j + e[1], k + e[2]) -
                                       vcell(P, dd, i - e[0], j - e[1], k - e[2]);
                     const double g2 = vcell(P, dd, ni + e[0], nj + e[1], nk + e[2]) -
                                       vcell(P, dd, ni - e[0], nj - e[1], nk - e[2]);
-                    tr = 0.25 * (g1 + g2) / P.h;
+                    t = fma((f & 1) ? 0.25 : -0.25, g1 + g2, diff);
                 }
-                V += sgn[f] * muf * (dq + tr);
+                V = fma(muf[f], t, V);
             }
-            V /= P.h;
             const double B = comp == 2 ? (rn - P.rho0) * P.gz + P.dpdz : 0.0;
-            out[comp] = (rn * qc - C + P.dt * (V + B)) / rn1;
+            out[comp] = (fma(rn, qc, -C) + P.dt * fma(V, inv_h2, B)) * r_rn1;
         }
         o0[c] = out[0];
         o1[c] = out[1];

@@ -3,6 +3,8 @@
 //   reconstruct: per interface cell the normal n = -grad(alpha smoothed by
 //                [1,2,1]^3/64) and the FP64 plane constant d;
 //   face flux:   signed liquid volume in the donor slab of width |u| dt;
+// The FP64 geometry runs only for the interface cells, compacted into a list
+// each sweep so that warps are not held up by the few cut cells among them.
 //   update:      alpha <- alpha - (F+ - F-) + c (u+ - u-) dt/h, clipped,
 //                with c = [alpha^n > 1/2] frozen over the three sweeps so
 //                the volume is conserved to round-off when div u = 0.
@@ -19,33 +21,59 @@ struct __align__(32) Plane {
     double n0, n1, n2, d;
 };
 
-__global__ void k_reconstruct(Geo g, const double* __restrict__ a, unsigned char* __restrict__ has,
-                              Plane* __restrict__ plane, int kchunk) {
+// Pass 1: clear the plane flags and append the interface cells to a list
+// (warp-aggregated atomic; the list order never changes any value).
+__global__ void k_if_list(Dims d, const double* __restrict__ a, unsigned char* __restrict__ has,
+                          int* __restrict__ list, int* __restrict__ count, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
-    if (i >= g.d.nx || j >= g.d.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.d.nz);
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    const unsigned lane = (threadIdx.x + TBX * threadIdx.y) & 31;
     for (int k = k0; k < k1; ++k) {
-        const int c = cid(g.d, i, j, k);
-        const double ac = a[c];
-        unsigned char h = 0;
-        if (ac > EPS_IF && ac < 1.0 - EPS_IF) {
-            double n[3];
-            smoothed_normal(g, a, i, j, k, n);
-            if (n[0] != 0.0 || n[1] != 0.0 || n[2] != 0.0) {
-                h = 1;
-                plane[c] = Plane{n[0], n[1], n[2], plic::plane_constant(n[0], n[1], n[2], ac)};
-            }
+        int c = 0;
+        bool itf = false;
+        if (act) {
+            c = cid(d, i, j, k);
+            const double ac = a[c];
+            itf = ac > EPS_IF && ac < 1.0 - EPS_IF;
+            has[c] = 0;
         }
-        has[c] = h;
+        const unsigned m = __ballot_sync(0xffffffffu, itf);
+        if (m) {
+            int base = 0;
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = atomicAdd(count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (itf) list[base + __popc(m & ((1u << lane) - 1u))] = c;
+        }
     }
 }
 
-// flux through the minus face of every cell in direction dir (face index =
-// cell index along dir); wall faces get zero
-__global__ void k_face_flux(Geo g, int dir, const double* __restrict__ a,
-                            const unsigned char* __restrict__ has,
-                            const Plane* __restrict__ plane, const double* __restrict__ vel,
-                            double* __restrict__ flux, double dt_h, int kchunk) {
+// Pass 2: normal and FP64 plane constant of every listed interface cell.
+__global__ void k_reconstruct_list(Geo g, const double* __restrict__ a,
+                                   const int* __restrict__ list, const int* __restrict__ count,
+                                   unsigned char* __restrict__ has, Plane* __restrict__ plane) {
+    const int n = *count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int c = list[t];
+        const int i = c % g.d.nx, j = (c / g.d.nx) % g.d.ny, k = c / (g.d.nx * g.d.ny);
+        double nrm[3];
+        smoothed_normal(g, a, i, j, k, nrm);
+        if (nrm[0] != 0.0 || nrm[1] != 0.0 || nrm[2] != 0.0) {
+            plane[c] = Plane{nrm[0], nrm[1], nrm[2],
+                             plic::plane_constant(nrm[0], nrm[1], nrm[2], a[c])};
+            has[c] = 1;
+        }
+    }
+}
+
+// Pass 3: every face of direction dir whose donor carries no plane moves
+// the donor's uniform content, F = |u| dt/h * alpha (signed); wall faces 0.
+// Faces whose donor carries a plane are left to pass 4.
+__global__ void k_face_flux_simple(Geo g, int dir, const double* __restrict__ a,
+                                   const unsigned char* __restrict__ has,
+                                   const double* __restrict__ vel, double* __restrict__ flux,
+                                   double dt_h, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= g.d.nx || j >= g.d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.d.nz);
@@ -66,24 +94,61 @@ __global__ void k_face_flux(Geo g, int dir, const double* __restrict__ a,
             f = wid(d, i, j, k);
             cL = cid(d, i, j, wrapk(k - 1, d.nz));
         }
-        double F = 0.0;
         const double u = wall ? 0.0 : vel[f];
-        if (u != 0.0) {
-            const double cfl = fabs(u) * dt_h;
-            const int dn = u > 0.0 ? cL : cR;
-            double V;
-            if (!has[dn]) {
-                V = cfl * a[dn];
-            } else {
-                const Plane pl = plane[dn];
-                V = plic::slab_fraction(pl.n0, pl.n1, pl.n2, pl.d, dir, cfl, u > 0.0);
-            }
-            F = u > 0.0 ? V : -V;
+        const int dn = u > 0.0 ? cL : cR;
+        if (u == 0.0) {
+            flux[f] = 0.0;
+        } else if (!has[dn]) {
+            const double V = fabs(u) * dt_h * a[dn];
+            flux[f] = u > 0.0 ? V : -V;
         }
-        flux[f] = F;
         // the far wall (or periodic duplicate) face is never a minus face
         if (dir == 0 && i == d.nx - 1) flux[uid(d, d.nx, j, k)] = 0.0;
         if (dir == 1 && j == d.ny - 1) flux[vid(d, i, d.ny, k)] = 0.0;
+    }
+}
+
+// Pass 4: the donor-slab volume through each face whose donor is a listed
+// cell with a plane: its plus face when that face's velocity is positive,
+// its minus face when negative.
+__global__ void k_face_flux_list(Geo g, int dir, const int* __restrict__ list,
+                                 const int* __restrict__ count,
+                                 const unsigned char* __restrict__ has,
+                                 const Plane* __restrict__ plane, const double* __restrict__ vel,
+                                 double* __restrict__ flux, double dt_h) {
+    const Dims& d = g.d;
+    const int n = *count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int c = list[t];
+        if (!has[c]) continue;
+        const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / (d.nx * d.ny);
+        int fm, fp;
+        bool wm = false, wp = false;
+        if (dir == 0) {
+            fm = uid(d, i, j, k);
+            fp = uid(d, i + 1 == d.nx && g.per_x ? 0 : i + 1, j, k);
+            wm = i == 0 && !g.per_x;
+            wp = i == d.nx - 1 && !g.per_x;
+        } else if (dir == 1) {
+            fm = vid(d, i, j, k);
+            fp = vid(d, i, j + 1 == d.ny && g.per_y ? 0 : j + 1, k);
+            wm = j == 0 && !g.per_y;
+            wp = j == d.ny - 1 && !g.per_y;
+        } else {
+            fm = wid(d, i, j, k);
+            fp = wid(d, i, j, wrapk(k + 1, d.nz));
+        }
+        const Plane pl = plane[c];
+        if (!wp) {
+            const double u = vel[fp];
+            if (u > 0.0)
+                flux[fp] = plic::slab_fraction(pl.n0, pl.n1, pl.n2, pl.d, dir, u * dt_h, true);
+        }
+        if (!wm) {
+            const double u = vel[fm];
+            if (u < 0.0)
+                flux[fm] = -plic::slab_fraction(pl.n0, pl.n1, pl.n2, pl.d, dir, -u * dt_h, false);
+        }
     }
 }
 
@@ -179,8 +244,11 @@ void launch_volume(vof_ctx* c, const double* alpha, int slot) {
 void launch_reconstruct(vof_ctx* c, const double* alpha) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_ADVECT);
-    VOF_LAUNCH(c, k_reconstruct, L.grid, L.block, geo(c), alpha, c->has, (Plane*)c->plane,
-                                                 L.kchunk);
+    cudaMemsetAsync(c->if_count, 0, sizeof(int), c->st);
+    VOF_LAUNCH(c, k_if_list, L.grid, L.block, c->d, alpha, c->has, c->if_list, c->if_count,
+               L.kchunk);
+    VOF_LAUNCH(c, k_reconstruct_list, c->sm_count * 4, 128, geo(c), alpha, c->if_list,
+               c->if_count, c->has, (Plane*)c->plane);
     timer_end(c, T_ADVECT, m);
 }
 
@@ -188,9 +256,10 @@ void launch_face_flux(vof_ctx* c, int dir, const double* alpha, const double* ve
                       double* flux) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_ADVECT);
-    VOF_LAUNCH(c, k_face_flux, L.grid, L.block, geo(c), dir, alpha, c->has,
-                                               (const Plane*)c->plane, vel, flux,
-                                               dt / c->g.h, L.kchunk);
+    VOF_LAUNCH(c, k_face_flux_simple, L.grid, L.block, geo(c), dir, alpha, c->has, vel, flux,
+               dt / c->g.h, L.kchunk);
+    VOF_LAUNCH(c, k_face_flux_list, c->sm_count * 4, 128, geo(c), dir, c->if_list, c->if_count,
+               c->has, (const Plane*)c->plane, vel, flux, dt / c->g.h);
     timer_end(c, T_ADVECT, m);
 }
 

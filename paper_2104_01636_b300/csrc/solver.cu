@@ -91,8 +91,13 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
         const size_t n = (size_t)dims[l].nx * dims[l].ny * dims[l].nz;
         b += faces_bytes(dims[l], elt) + 2 * n * elt;
     }
+    if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
+        for (size_t l = 0; l + 1 < dims.size(); ++l)
+            b += (size_t)dims[l].nx * dims[l].ny * dims[l].nz * elt;
     const Dims& dc = dims.back();
-    b += 4 * (size_t)dc.nx * dc.ny * dc.nz * sizeof(double);
+    const size_t nc = (size_t)dc.nx * dc.ny * dc.nz;
+    b += 4 * nc * sizeof(double);
+    if (nc <= (size_t)DENSE_MAX) b += nc * nc * (2 * sizeof(double) + (mixed ? sizeof(float) : 0));
     return b;
 }
 
@@ -141,18 +146,52 @@ vof_status mg_allocate(vof_ctx* c) {
             L.f = q + nu + nv + 2 * n;
         }
     }
+    if (c->sv.mg_interp == VOF_MG_TRILINEAR) {
+        const size_t elt = mixed ? sizeof(float) : sizeof(double);
+        for (size_t l = 0; l + 1 < c->lv.size(); ++l) {
+            void* q = nullptr;
+            if (cudaMalloc(&q, elt * (size_t)c->lv[l].ncells) != cudaSuccess) {
+                cudaGetLastError();
+                return set_err(c, VOF_ERR_OOM, "cudaMalloc multigrid residual");
+            }
+            c->allocs.push_back(q);
+            c->lv[l].rs = q;
+        }
+    }
     const Level& Lc = c->lv.back();
     void* p = nullptr;
     if (cudaMalloc(&p, 4 * sizeof(double) * (size_t)Lc.ncells) != cudaSuccess)
         return set_err(c, VOF_ERR_OOM, "cudaMalloc coarse scratch");
     c->allocs.push_back(p);
     c->coarse_scratch = (double*)p;
+    if (Lc.ncells <= DENSE_MAX) {
+        const size_t n2 = (size_t)Lc.ncells * Lc.ncells;
+        void *a = nullptr, *b = nullptr, *f = nullptr;
+        if (cudaMalloc(&a, n2 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&b, n2 * sizeof(double)) != cudaSuccess ||
+            (mixed && cudaMalloc(&f, n2 * sizeof(float)) != cudaSuccess)) {
+            cudaGetLastError();
+            if (a) cudaFree(a);
+            if (b) cudaFree(b);
+            return set_err(c, VOF_ERR_OOM, "cudaMalloc dense coarse inverse");
+        }
+        c->allocs.push_back(a);
+        c->allocs.push_back(b);
+        if (f) c->allocs.push_back(f);
+        c->dense_a = (double*)a;
+        c->dense_b = (double*)b;
+        c->dense_inv_f = (float*)f;
+        c->dense_n = Lc.ncells;
+        // shift: the liquid face coefficient (the smallest physical one) per face
+        c->dense_shift = 1.0 / c->ph.rho_l;
+    }
     return VOF_OK;
 }
 
 void mg_build_coefficients(vof_ctx* c) {
     if (c->sv.precision == VOF_PREC_FP64) {
         for (size_t l = 1; l < c->lv.size(); ++l) mg_coarsen_beta<double>(c, c->lv[l - 1], c->lv[l]);
+        if (c->dense_n > 0) mg_dense_setup<double>(c, c->lv.back());
         return;
     }
     const Level& L0 = c->lv[0];
@@ -161,6 +200,7 @@ void mg_build_coefficients(vof_ctx* c) {
     mg_to_f32(c, c->by, L0.byf, nv);
     mg_to_f32(c, c->bz, L0.bzf, L0.ncells);
     for (size_t l = 1; l < c->lv.size(); ++l) mg_coarsen_beta<float>(c, c->lv[l - 1], c->lv[l]);
+    if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
 }
 
 // Solves A P = b_in - mean(b_in) with the fine-level beta already built.

@@ -113,6 +113,7 @@ struct Level {
     double *x = nullptr, *f = nullptr;                    // correction / right side
     float *bxf = nullptr, *byf = nullptr, *bzf = nullptr;  // FP32 copies (mixed)
     float *xf = nullptr, *ff = nullptr;
+    void* rs = nullptr;  // residual scratch for full-weighting restriction (T per cell)
     Launch L;
 };
 
@@ -133,6 +134,8 @@ struct vof_ctx {
     double *sx = nullptr, *sy = nullptr, *sz = nullptr;    // surface force (step)
     double *kappa = nullptr;                               // curvature (step)
     unsigned char *valid = nullptr, *cmask = nullptr, *has = nullptr;
+    int* if_list = nullptr;   // interface cells of the current sweep
+    int* if_count = nullptr;  // their number (device)
     double *plane = nullptr;  // 4 per cell: n[3], d
     double *fx = nullptr, *fy = nullptr, *fz = nullptr;  // liquid fluxes / face accelerations
     double *uh[3] = {nullptr, nullptr, nullptr};          // cell intermediate velocity
@@ -141,6 +144,11 @@ struct vof_ctx {
     double* rhs = nullptr;  // assembled right side of the projection
     std::vector<Level> lv;
     double* coarse_scratch = nullptr;
+    // dense inverse of the coarsest level (when it has <= DENSE_MAX cells)
+    int dense_n = 0;
+    double dense_shift = 0.0;  // s n / (1/h^2): regularising shift of the constants
+    double *dense_a = nullptr, *dense_b = nullptr, *dense_inv = nullptr;
+    float* dense_inv_f = nullptr;
 
     double* part = nullptr;  // NSLOTS x MAX_PARTIALS block partials
     double* scal = nullptr;  // device scalars
@@ -213,6 +221,8 @@ template <class T> void mg_prolong(vof_ctx* c, const Level& coarse, const Level&
 template <class T> void mg_coarsen_beta(vof_ctx* c, const Level& fine, const Level& coarse);
 template <class T> void mg_coarse(vof_ctx* c, const Level& L);
 template <class T> void mg_zero(vof_ctx* c, const Level& L);
+template <class T> void mg_dense_setup(vof_ctx* c, const Level& L);
+constexpr int DENSE_MAX = 1536;  // largest coarsest level solved by the dense inverse
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
 void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
 
