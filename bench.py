@@ -57,10 +57,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--nz", type=int, default=640, help="z cells (smaller for quick runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests in the serving run (0 skips it)")
     return ap.parse_args()
 
 
@@ -185,6 +188,74 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------------------
+SERVE_BUDGET = 40 << 30
+SERVE_SLOTS = 8
+
+
+def serving_run(vd, reqs, precision: int, rate, seed: int = 2108, rtol: float = 1e-8):
+    """Submits the request mix to a VofServer with exponential inter-arrival
+    gaps at `rate` requests/s (None: all at once, the saturation run) and
+    returns latency percentiles (submit -> result) and throughput. Host
+    copies of the inputs are made before the arrivals start."""
+    import numpy as np
+    gaps = (np.zeros(len(reqs)) if rate is None else
+            np.random.default_rng(seed).exponential(1.0 / rate, len(reqs)))
+    bufs = []
+    for r in reqs:
+        if r.kind == "step":
+            bufs.append([np.array(a, dtype=np.float64, order="C", copy=True)
+                         for a in r.case.state()])
+        else:
+            bufs.append([r.case.alpha.copy(), r.b.copy(), np.zeros_like(r.b)])
+    sv = vd.c_solver(precision, rtol=rtol, max_iter=500)
+    with vd.VofServer(SERVE_BUDGET, SERVE_SLOTS) as S:
+        ids = []
+        t0 = time.perf_counter()
+        t_next = 0.0
+        for r, gap, b in zip(reqs, gaps, bufs):
+            t_next += gap
+            delay = t0 + t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            c = r.case
+            if r.kind == "step":
+                ids.append(S.submit_step(c.grid, c.phys, sv, b, r.n_steps, c.dt))
+            else:
+                ids.append(S.submit_solve(c.grid, c.phys, sv, *b))
+        res = [S.wait(i) for i in ids]
+    bad = [x["status"] for x in res if x["status"] != "VOF_OK"]
+    lat = np.array([x["t_finish"] - x["t_submit"] for x in res])
+    span = max(x["t_finish"] for x in res) - min(x["t_submit"] for x in res)
+    busy = sum(x["t_finish"] - x["t_admit"] for x in res)
+    cell_steps = sum(r.case.grid.ncells * max(r.n_steps, 1) for r in reqs)
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3),
+            "requests_per_s": len(reqs) / span, "cell_steps_per_s": cell_steps / span,
+            "mean_concurrency": busy / span, "failed": bad,
+            "offered_rate": rate}
+
+
+def serving(vd, I, n_req: int, do_fp64: bool):
+    """Continuous-batching serving of a seeded ensemble mix: per precision a
+    saturation run (all requests at once) gives the throughput, then Poisson
+    arrivals at 70% of that throughput give p50/p99 latency."""
+    reqs = I.serving_mix(n_req, seed=2108)
+    serving_run(vd, reqs[:4], vd.PREC_MIXED_FP32, None)  # warm-up: modules, memory pool
+    out = {"requests": n_req, "budget_bytes": SERVE_BUDGET, "slots": SERVE_SLOTS,
+           "mix": ("grids {32^3, 64x64x128, 96x96x192, 128x128x256}, 1-64 spheres "
+                   "d in [8,14]h, 50% STEP(1-10 steps) / 50% SOLVE, rtol 1e-8, seed 2108"),
+           "load": "Poisson arrivals at 0.7 x the saturation throughput"}
+    for name, prec in (("mixed", vd.PREC_MIXED_FP32), ("fp64", vd.PREC_FP64)):
+        if name == "fp64" and not do_fp64:
+            continue
+        sat = serving_run(vd, reqs, prec, None)
+        loaded = serving_run(vd, reqs, prec, 0.7 * sat["requests_per_s"])
+        out[name] = {"saturation": sat, "loaded": loaded}
+    return out
+
+
+# ----------------------------------------------------------------------------
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -301,6 +372,32 @@ def main():
         e2e_value = world * args.steps / (float(te.item()) / 1e3)
         ctx.close()
 
+        # ---- the FP64 path on the same workload, for comparison ------------
+        fp64 = None
+        if args.precision == "mixed" and not args.no_fp64_compare:
+            ctx64 = vd.VofContext(g, case.phys, vd.c_solver(vd.PREC_FP64, rtol=args.rtol,
+                                                            max_iter=500), stream=stream)
+            T64 = [dev(x) for x in case.state()]
+            for s in range(2):
+                ctx64.step(*T64, case.dt, s)
+            n64 = max(1, min(args.steps, 5))
+            it64 = 0
+            barrier()
+            e0.record(stream)
+            for s in range(2, 2 + n64):
+                it64 += ctx64.step(*T64, case.dt, s)["iters"]
+            e1.record(stream)
+            barrier()
+            ms64 = e0.elapsed_time(e1)
+            fp64 = {"value": n64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / n64,
+                    "pcg_iters_per_step": it64 / n64, "steps": n64, "rtol": args.rtol}
+            ctx64.close()
+            del T64
+
+    serve = None
+    if world == 1 and args.serve_requests > 0:
+        serve = serving(vd, I, args.serve_requests, not args.no_fp64_compare)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -328,6 +425,8 @@ def main():
                 "d2h_bytes_per_step": h2d},
         "gpu_launches": launches,
         "clocks": ck,
+        "fp64_path": fp64,
+        "serving": serve,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

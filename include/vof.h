@@ -76,6 +76,10 @@ typedef struct {
     double kappa_exact;   /* curvature used when kappa_mode == EXACT (1/m)     */
 } vof_phys;
 
+/* FP64: flexible CG in FP64 preconditioned by an FP64 V-cycle.
+ * MIXED_FP32: FP64 defect correction (residual b - A P and the update of P
+ * in FP64) around an inner flexible CG in FP32 preconditioned by an FP32
+ * V-cycle. */
 enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED_FP32 = 1 };
 
 typedef struct {
@@ -94,7 +98,9 @@ typedef struct {
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 
 typedef struct {
-    int iters;                    /* Krylov iterations of the last solve        */
+    int iters;                    /* Krylov iterations of the last solve (mixed:
+                                     inner FP32 iterations summed)              */
+    int refinements;              /* mixed: FP64 defect-correction steps        */
     double res0, res;             /* initial / final relative residual          */
     double b_mean;                /* mean removed from the right side           */
     double vol_before, vol_after; /* liquid volume sum(alpha) h^3 (m^3)         */
@@ -215,10 +221,18 @@ vof_status project(vof_ctx* ctx, const double* alpha, double* uc, double* vc, do
 
 /* One whole time step (steps 1-12): vof_advect with the face velocities,
  * vof_predict, ssf_force on alpha^{n+1}, project. All arguments are updated
- * in place. */
+ * in place.
+ * glibc also exports a symbol named step (its legacy <regexp.h> matcher).
+ * The library is linked -Bsymbolic so its own calls never reach glibc's,
+ * and a handle from dlopen finds this one; a program that links the
+ * library directly and whose link order puts libc first should call
+ * vof_step, the same function under an unambiguous name. */
 vof_status step(vof_ctx* ctx, double* alpha, double* uc, double* vc, double* wc, double* u,
                 double* v, double* w, double* p, double dt, long long step_index,
                 vof_report* report);
+vof_status vof_step(vof_ctx* ctx, double* alpha, double* uc, double* vc, double* wc, double* u,
+                    double* v, double* w, double* p, double dt, long long step_index,
+                    vof_report* report);
 
 /* Number of CUDA kernels this context has launched since creation. */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
@@ -235,6 +249,58 @@ vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
 vof_status vof_set_timing(vof_ctx* ctx, int on);
 vof_status vof_kernel_times(vof_ctx* ctx, const char** names, double* ms, long long* launches,
                             int cap, int* n);
+
+/* ---- request server: continuous batching of independent cases ----------
+ * The paper has no serving layer; this serves ensembles of independent duct
+ * cases (time steps or pressure solves on grids of their own) on one GPU.
+ * Requests queue in arrival order; the head request is admitted as soon as
+ * one of max_concurrent worker slots is free and its device memory (fields
+ * plus context workspace, see vof_workspace_bytes) fits in what is left of
+ * budget_bytes. Each admitted request runs on its worker's own CUDA stream,
+ * so requests overlap on the device; a result does not depend on what else
+ * was running. Host arrays of a request are read when it starts and
+ * overwritten with the results when it finishes; they must stay valid until
+ * vof_wait/vof_poll report it finished. */
+typedef struct vof_server vof_server;
+
+enum { VOF_REQ_STEP = 0, VOF_REQ_SOLVE = 1 };
+
+typedef struct {
+    int kind;               /* VOF_REQ_STEP: n_steps calls of step();
+                               VOF_REQ_SOLVE: one pressure_solve()           */
+    vof_grid grid;
+    vof_phys phys;
+    vof_solver solver;
+    int n_steps;            /* STEP: number of time steps (>= 1)             */
+    double dt;              /* STEP: time step                               */
+    long long step0;        /* STEP: index of the first step (split order)   */
+    double *alpha, *uc, *vc, *wc, *u, *v, *w, *p;  /* HOST arrays, layouts as
+                               in step(); SOLVE uses alpha (read), p (guess in,
+                               solution out) and b                            */
+    const double* b;        /* SOLVE: right side (host)                       */
+} vof_request;
+
+typedef struct {
+    int status;             /* vof_status of the request; -1 until finished  */
+    int state;              /* 0 queued, 1 running, 2 finished               */
+    double t_submit, t_admit, t_finish;  /* seconds since server creation    */
+    vof_report report;      /* of the solve / of the last step               */
+} vof_result;
+
+/* budget_bytes > 0: device memory the admitted requests may hold together;
+ * max_concurrent in [1, 64]: worker slots (CUDA streams). Uses the current
+ * device, and raises the release threshold of that device's default memory
+ * pool (the one cudaMallocAsync draws from) to budget_bytes so that memory
+ * freed by a finished request is reused by the next one. */
+vof_status vof_server_create(size_t budget_bytes, int max_concurrent, vof_server** out);
+/* VOF_ERR_ADMISSION if the request alone exceeds the budget; VOF_ERR_ARG for
+ * invalid requests. *id identifies the request. */
+vof_status vof_submit(vof_server* server, const vof_request* request, unsigned long long* id);
+vof_status vof_poll(vof_server* server, unsigned long long id, vof_result* result);
+/* Blocks until the request has finished. */
+vof_status vof_wait(vof_server* server, unsigned long long id, vof_result* result);
+/* Finishes every queued request, then frees the server. */
+vof_status vof_server_destroy(vof_server* server);
 
 #ifdef __cplusplus
 }

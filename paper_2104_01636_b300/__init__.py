@@ -54,7 +54,8 @@ class CSolver(ctypes.Structure):
 
 
 class CReport(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double),
                 ("b_mean", ctypes.c_double), ("vol_before", ctypes.c_double),
                 ("vol_after", ctypes.c_double), ("vol_clipped", ctypes.c_double),
                 ("max_div", ctypes.c_double), ("max_u", ctypes.c_double),
@@ -64,6 +65,27 @@ class CReport(ctypes.Structure):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n != "ms"}
         d["ms"] = list(self.ms)
         return d
+
+
+REQ_STEP, REQ_SOLVE = 0, 1
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class CRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("grid", CGrid), ("phys", CPhys), ("solver", CSolver),
+                ("n_steps", ctypes.c_int), ("dt", ctypes.c_double), ("step0", ctypes.c_longlong),
+                ("alpha", _DP), ("uc", _DP), ("vc", _DP), ("wc", _DP), ("u", _DP), ("v", _DP),
+                ("w", _DP), ("p", _DP), ("b", _DP)]
+
+
+class CResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("state", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double), ("report", CReport)]
+
+    def as_dict(self) -> dict:
+        return {"status": STATUS.get(self.status, self.status), "state": self.state,
+                "t_submit": self.t_submit, "t_admit": self.t_admit, "t_finish": self.t_finish,
+                "report": self.report.as_dict()}
 
 
 _lib = None
@@ -97,6 +119,11 @@ def load() -> ctypes.CDLL:
         "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
         "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
                              P(ctypes.c_int)],
+        "vof_server_create": [ctypes.c_size_t, ctypes.c_int, P(_VP)],
+        "vof_submit": [_VP, P(CRequest), P(ctypes.c_ulonglong)],
+        "vof_poll": [_VP, ctypes.c_ulonglong, P(CResult)],
+        "vof_wait": [_VP, ctypes.c_ulonglong, P(CResult)],
+        "vof_server_destroy": [_VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -267,3 +294,98 @@ class VofContext:
         self._chk(self.lib.vof_kernel_times(self._ctx, names, ms, n_l, cap, ctypes.byref(n)),
                   "vof_kernel_times")
         return {names[i].decode(): (ms[i], int(n_l[i])) for i in range(n.value)}
+
+
+class VofServer:
+    """Continuous-batching server of independent cases on the current device.
+
+    Requests carry numpy float64 host arrays (C order, the shapes above);
+    the server reads them when the request starts and writes the results
+    back into the same arrays when it finishes. The binding keeps each
+    request's arrays alive until its result has been collected.
+    """
+
+    def __init__(self, budget_bytes: int, max_concurrent: int = 4):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        torch.cuda.init()
+        self.lib = load()
+        self._srv = _VP()
+        st = self.lib.vof_server_create(ctypes.c_size_t(int(budget_bytes)), int(max_concurrent),
+                                        ctypes.byref(self._srv))
+        if st:
+            raise VofError(st, "vof_server_create")
+        self._keep = {}
+
+    @staticmethod
+    def _arr(a, shape, name):
+        import numpy as np
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.flags.writeable):
+            raise TypeError(f"{name}: need a writeable C-contiguous float64 numpy array")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {tuple(a.shape)} != {tuple(shape)}")
+        return a.ctypes.data_as(_DP)
+
+    def _submit(self, rq: CRequest, keep) -> int:
+        rid = ctypes.c_ulonglong(0)
+        st = self.lib.vof_submit(self._srv, ctypes.byref(rq), ctypes.byref(rid))
+        if st:
+            raise VofError(st, "vof_submit")
+        self._keep[rid.value] = (rq, keep)
+        return int(rid.value)
+
+    def submit_step(self, grid, phys, solver, state, n_steps: int, dt: float, step0: int = 0) -> int:
+        """state: the eight arrays (alpha, uc, vc, wc, u, v, w, p), advanced in place."""
+        cs = (grid.nz, grid.ny, grid.nx)
+        shapes = (cs, cs, cs, cs, (grid.nz, grid.ny, grid.nx + 1), (grid.nz, grid.ny + 1, grid.nx),
+                  cs, cs)
+        names = ("alpha", "uc", "vc", "wc", "u", "v", "w", "p")
+        ptrs = [self._arr(a, sh, n) for a, sh, n in zip(state, shapes, names)]
+        rq = CRequest(REQ_STEP, c_grid(grid), c_phys(phys), solver or c_solver(), int(n_steps),
+                      float(dt), int(step0), *ptrs, None)
+        return self._submit(rq, tuple(state))
+
+    def submit_solve(self, grid, phys, solver, alpha, b, p) -> int:
+        """One pressure solve; p holds the initial guess and receives the solution."""
+        cs = (grid.nz, grid.ny, grid.nx)
+        pa, pb, pp = self._arr(alpha, cs, "alpha"), self._arr(b, cs, "b"), self._arr(p, cs, "p")
+        rq = CRequest(REQ_SOLVE, c_grid(grid), c_phys(phys), solver or c_solver(), 0, 0.0, 0,
+                      pa, None, None, None, None, None, None, pp, pb)
+        return self._submit(rq, (alpha, b, p))
+
+    def poll(self, rid: int) -> dict:
+        res = CResult()
+        st = self.lib.vof_poll(self._srv, ctypes.c_ulonglong(rid), ctypes.byref(res))
+        if st:
+            raise VofError(st, "vof_poll")
+        if res.state == 2:
+            self._keep.pop(rid, None)
+        return res.as_dict()
+
+    def wait(self, rid: int) -> dict:
+        res = CResult()
+        st = self.lib.vof_wait(self._srv, ctypes.c_ulonglong(rid), ctypes.byref(res))
+        if st:
+            raise VofError(st, "vof_wait")
+        self._keep.pop(rid, None)
+        return res.as_dict()
+
+    def close(self):
+        if getattr(self, "_srv", None) and self._srv.value:
+            self.lib.vof_server_destroy(self._srv)
+            self._srv = _VP()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

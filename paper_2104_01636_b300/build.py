@@ -39,7 +39,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
+    # -Bsymbolic: the library's calls to its own exported functions bind to
+    # its own definitions (glibc exports a legacy function named step)
     cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+           "-Xlinker", "-Bsymbolic",
            "-I", os.path.join(ROOT, "include"), *extra, "-o", LIB, *sources()]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)

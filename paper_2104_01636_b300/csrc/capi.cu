@@ -56,11 +56,8 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
 }
 
 vof_status alloc(vof_ctx* c, void** p, size_t bytes) {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return set_err(c, VOF_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-    }
-    c->allocs.push_back(*p);
+    *p = dev_alloc(c, bytes);
+    if (!*p) return set_err(c, VOF_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes failed");
     return VOF_OK;
 }
 
@@ -174,6 +171,19 @@ void report_timing_end(vof_ctx* c, const double snap[T_NCLASS], vof_report* r) {
 // ---------------------------------------------------------------------------
 // helpers used by the other translation units
 // ---------------------------------------------------------------------------
+// Workspace comes from the stream-ordered allocator on the context's stream:
+// freeing it does not synchronise the whole device, so contexts that come
+// and go on other streams (the request server) do not stall each other.
+void* dev_alloc(vof_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    c->allocs.push_back(p);
+    return p;
+}
+
 vof_status set_err(vof_ctx* c, vof_status s, const std::string& msg) {
     if (c) c->err = msg;
     return s;
@@ -207,6 +217,73 @@ void timer_end(vof_ctx* c, int, int mark) {
     if (mark < 0) return;
     cudaEventRecord(c->ev_pool[c->ev_marks[mark].second.second], c->st);
 }
+
+// steps 11-12 on (u_hat_c in Uh, u_hat_f in u, v, w): right side, solve,
+// correction of faces (in place) and cells (written to Uc)
+static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* const Uc[3],
+                               double* u, double* v, double* w, double* p, const double* sx,
+                               const double* sy, const double* sz, double dt, vof_report* r) {
+    launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, -1);
+    vof_status st = solve_pressure(c, c->rhs, p, r);
+    if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
+    launch_correct(c, p, sx, sy, sz, dt, Uh, Uc, u, v, w, P_A, P_B);
+    readback(c);
+    r->max_div = c->hbuf[S_MAXDIV];
+    r->max_u = c->hbuf[S_MAXU];
+    vof_status st2 = launch_check(c, "project");
+    return st2 ? st2 : st;
+}
+
+// the whole time step behind step() and vof_step(); internal callers (the
+// request server) use this name, never the exported one
+vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
+                      double* v, double* w, double* p, double dt, long long step_index,
+                      vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, uc);
+    REQUIRE_PTR(c, vc);
+    REQUIRE_PTR(c, wc);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    REQUIRE_PTR(c, p);
+    if ((st = walls_only(c, "step"))) return st;
+    if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
+    if ((st = cfl_check(c, u, v, w, dt))) return st;
+    double snap[T_NCLASS];
+    report_timing_begin(c, snap);
+    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
+    // steps 1-2: keep alpha^n (rho^n, mu^n) for the predictor
+    cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    // step 3: advect alpha with u_f^n, keeping the liquid face fluxes
+    double* const flux[3] = {c->fx, c->fy, c->fz};
+    advect_impl(c, alpha, u, v, w, dt, step_index, flux);
+    // steps 8-9: cell-centred intermediate velocity
+    const double* const U[3] = {uc, vc, wc};
+    launch_predict(c, c->an, alpha, U, u, v, w, c->fx, c->fy, c->fz, dt, c->uh);
+    // step 10: face intermediate velocity
+    launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], u, v, w);
+    // step 4 (beta from alpha^{n+1}) and steps 5-7 (curvature, face force)
+    launch_beta(c, alpha);
+    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
+    // steps 11-12
+    vof_report r;
+    std::memset(&r, 0, sizeof(r));
+    const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
+    double* const Uc[3] = {uc, vc, wc};
+    st = project_impl(c, Uh, Uc, u, v, w, p, c->sx, c->sy, c->sz, dt, &r);
+    if (report) {
+        readback(c);
+        fill_vof_report(c, &r);
+        r.hf_fallbacks = (long long)llround(c->hbuf[S_FALLBACK]);
+        *report = r;
+        report_timing_end(c, snap, report);
+    }
+    return st;
+}
+
 
 // ---------------------------------------------------------------------------
 // the C ABI
@@ -292,10 +369,7 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     A((void**)&c->scal, S_NSCALARS * D);
     A((void**)&c->dflag, 64);
     if (st == VOF_OK) st = mg_allocate(c);
-    if (st == VOF_OK && cudaMallocHost((void**)&c->hbuf, S_NSCALARS * D) != cudaSuccess) {
-        cudaGetLastError();
-        st = VOF_ERR_OOM;
-    }
+    if (st == VOF_OK) c->hbuf = c->hbuf_store.data();
     if (st == VOF_OK) {
         cudaMemsetAsync(c->scal, 0, S_NSCALARS * D, c->st);
         cudaMemsetAsync(c->part, 0, (size_t)NSLOTS * MAX_PARTIALS * D, c->st);
@@ -312,8 +386,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
 vof_status vof_destroy(vof_ctx* c) {
     if (!c) return VOF_ERR_ARG;
     cudaStreamSynchronize(c->st);
-    for (void* p : c->allocs) cudaFree(p);
-    if (c->hbuf) cudaFreeHost(c->hbuf);
+    for (void* p : c->allocs) cudaFreeAsync(p, c->st);
+    cudaStreamSynchronize(c->st);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return VOF_OK;
@@ -424,22 +498,6 @@ vof_status vof_predict(vof_ctx* c, const double* alpha_n, const double* alpha_np
     return launch_check(c, "vof_predict");
 }
 
-// steps 11-12 on (u_hat_c in Uh, u_hat_f in u, v, w): right side, solve,
-// correction of faces (in place) and cells (written to Uc)
-static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* const Uc[3],
-                               double* u, double* v, double* w, double* p, const double* sx,
-                               const double* sy, const double* sz, double dt, vof_report* r) {
-    launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, -1);
-    vof_status st = solve_pressure(c, c->rhs, p, r);
-    if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
-    launch_correct(c, p, sx, sy, sz, dt, Uh, Uc, u, v, w, P_A, P_B);
-    readback(c);
-    r->max_div = c->hbuf[S_MAXDIV];
-    r->max_u = c->hbuf[S_MAXU];
-    vof_status st2 = launch_check(c, "project");
-    return st2 ? st2 : st;
-}
-
 vof_status project(vof_ctx* c, const double* alpha, double* uc, double* vc, double* wc, double* u,
                    double* v, double* w, double* p, const double* sx, const double* sy,
                    const double* sz, double dt, vof_report* report) {
@@ -481,49 +539,13 @@ vof_status project(vof_ctx* c, const double* alpha, double* uc, double* vc, doub
 vof_status step(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
                 double* v, double* w, double* p, double dt, long long step_index,
                 vof_report* report) {
-    vof_status st = check_ctx(c);
-    if (st) return st;
-    REQUIRE_PTR(c, alpha);
-    REQUIRE_PTR(c, uc);
-    REQUIRE_PTR(c, vc);
-    REQUIRE_PTR(c, wc);
-    REQUIRE_PTR(c, u);
-    REQUIRE_PTR(c, v);
-    REQUIRE_PTR(c, w);
-    REQUIRE_PTR(c, p);
-    if ((st = walls_only(c, "step"))) return st;
-    if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
-    if ((st = cfl_check(c, u, v, w, dt))) return st;
-    double snap[T_NCLASS];
-    report_timing_begin(c, snap);
-    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
-    // steps 1-2: keep alpha^n (rho^n, mu^n) for the predictor
-    cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-    // step 3: advect alpha with u_f^n, keeping the liquid face fluxes
-    double* const flux[3] = {c->fx, c->fy, c->fz};
-    advect_impl(c, alpha, u, v, w, dt, step_index, flux);
-    // steps 8-9: cell-centred intermediate velocity
-    const double* const U[3] = {uc, vc, wc};
-    launch_predict(c, c->an, alpha, U, u, v, w, c->fx, c->fy, c->fz, dt, c->uh);
-    // step 10: face intermediate velocity
-    launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], u, v, w);
-    // step 4 (beta from alpha^{n+1}) and steps 5-7 (curvature, face force)
-    launch_beta(c, alpha);
-    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
-    // steps 11-12
-    vof_report r;
-    std::memset(&r, 0, sizeof(r));
-    const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
-    double* const Uc[3] = {uc, vc, wc};
-    st = project_impl(c, Uh, Uc, u, v, w, p, c->sx, c->sy, c->sz, dt, &r);
-    if (report) {
-        readback(c);
-        fill_vof_report(c, &r);
-        r.hf_fallbacks = (long long)llround(c->hbuf[S_FALLBACK]);
-        *report = r;
-        report_timing_end(c, snap, report);
-    }
-    return st;
+    return step_entry(c, alpha, uc, vc, wc, u, v, w, p, dt, step_index, report);
+}
+
+vof_status vof_step(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
+                    double* v, double* w, double* p, double dt, long long step_index,
+                    vof_report* report) {
+    return step_entry(c, alpha, uc, vc, wc, u, v, w, p, dt, step_index, report);
 }
 
 vof_status vof_launch_count(const vof_ctx* c, long long* n) {

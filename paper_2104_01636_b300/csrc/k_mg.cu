@@ -65,6 +65,39 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
     }
 }
 
+// Same sweep with one thread per x-pair (2t, 2t+1): exactly one member has
+// the sweep's colour on every plane, so no lane idles. Within one colour the
+// cells written and the cells read (their neighbours, of the other colour)
+// are disjoint, so x is read and written through separate restrict
+// pointers to the same array, which lets loads of later planes be issued
+// early. Needs an even nx (every smoothed level has one).
+template <class T>
+__global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* __restrict__ by,
+                              const T* __restrict__ bz, const T* __restrict__ xr,
+                              T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk) {
+    const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (t >= (d.nx >> 1) || j >= d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const int i = 2 * t + ((j + k + color) & 1);
+        const int c = cid(d, i, j, k);
+        const int cw = i > 0 ? c - 1 : c;
+        const int ce = i < d.nx - 1 ? c + 1 : c;
+        const int cs = j > 0 ? c - d.nx : c;
+        const int cn = j < d.ny - 1 ? c + d.nx : c;
+        const int kp = wrapk(k + 1, d.nz);
+        const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, kp);
+        const T b0 = bx[uid(d, i, j, k)], b1 = bx[uid(d, i + 1, j, k)];
+        const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
+        const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
+        const T num = h2 * f[c] + b0 * xr[cw] + b1 * xr[ce] + b2 * xr[cs] + b3 * xr[cn] +
+                      b4 * xr[cb] + b5 * xr[ct];
+        const T den = b0 + b1 + b2 + b3 + b4 + b5;
+        xw[c] = den > T(0) ? num / den : T(0);
+    }
+}
+
 template <class T>
 __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T* __restrict__ by,
                              const T* __restrict__ bz, const T* __restrict__ xf,
@@ -307,7 +340,7 @@ __global__ void k_coarse_cg_t(Dims d, T ih2, const T* __restrict__ bx, const T* 
 template <class T>
 __global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
                                  const T* __restrict__ by, const T* __restrict__ bz, double s,
-                                 double* __restrict__ M) {
+                                 T* __restrict__ M) {
     const int n = d.nx * d.ny * d.nz;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n;
          e += (long)gridDim.x * blockDim.x) {
@@ -329,31 +362,26 @@ __global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
             if (col == cid(d, i, j, wrapk(k + 1, d.nz)))
                 v -= (double)bz[wid(d, i, j, wrapk(k + 1, d.nz))] * ih2;
         }
-        M[e] = v;
+        M[e] = (T)v;
     }
 }
 
 // One Gauss-Jordan pivot step of the in-place inversion of an SPD matrix
 // (no pivoting needed), reading A and writing B.
-__global__ void k_gauss_jordan(int n, int kp, const double* __restrict__ A, double* __restrict__ B) {
-    __shared__ double rp;
-    if (threadIdx.x == 0) rp = 1.0 / A[(long)kp * n + kp];
+template <class S>
+__global__ void k_gauss_jordan(int n, int kp, const S* __restrict__ A, S* __restrict__ B) {
+    __shared__ S rp;
+    if (threadIdx.x == 0) rp = S(1) / A[(long)kp * n + kp];
     __syncthreads();
     const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= (long)n * n) return;
     const int i = (int)(e / n), j = (int)(e % n);
-    double v;
+    S v;
     if (i == kp && j == kp) v = rp;
     else if (i == kp) v = A[e] * rp;
     else if (j == kp) v = -A[e] * rp;
     else v = A[e] - A[(long)i * n + kp] * (A[(long)kp * n + j] * rp);
     B[e] = v;
-}
-
-__global__ void k_dense_to_f32(long n2, const double* __restrict__ a, float* __restrict__ b) {
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n2;
-         e += (long)gridDim.x * blockDim.x)
-        b[e] = (float)a[e];
 }
 
 // x = Minv f: one warp per row, FP64 accumulation
@@ -373,6 +401,87 @@ template <class T>
 __global__ void k_zero_t(int n, T* __restrict__ x) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         x[c] = T(0);
+}
+
+// ---- inner FP32 Krylov kernels of the mixed-precision solve -----------------
+// Per-thread partial sums are FP32 with Kahan compensation (on B300 an FP64
+// add per element costs more than the memory traffic of these kernels); the
+// block and grid sums of the partials are FP64.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// q = A32 p and the block partials of p.q (FP64 accumulation)
+__global__ void k_apply_A_dot32(Dims d, float ih2, const float* __restrict__ bx,
+                                const float* __restrict__ by, const float* __restrict__ bz,
+                                const float* __restrict__ p, float* __restrict__ q,
+                                double* __restrict__ part, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    Kahan ks;
+    if (act)
+        for (int k = k0; k < k1; ++k) {
+            const int c = cid(d, i, j, k);
+            const float v = stencil_t(d, bx, by, bz, p, i, j, k) * ih2;
+            q[c] = v;
+            ks.add(p[c] * v);
+        }
+    const double acc = block_sum(ks.value());
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
+// e += alpha p, r -= alpha q, partials of r.r
+__global__ void k_cg_update32(int n, float* __restrict__ e, float* __restrict__ r,
+                              const float* __restrict__ p, const float* __restrict__ q,
+                              const double* __restrict__ scal, double* __restrict__ part) {
+    const float al = (float)scal[S_ALPHA];
+    Kahan ks;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        e[c] += al * p[c];
+        const float rv = r[c] - al * q[c];
+        r[c] = rv;
+        ks.add(rv * rv);
+    }
+    const double acc = block_sum(ks.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_dot2_32(int n, const float* __restrict__ z, const float* __restrict__ r,
+                          const float* __restrict__ q, double* __restrict__ pa,
+                          double* __restrict__ pb) {
+    Kahan ka, kb;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const float zc = z[c];
+        ka.add(zc * r[c]);
+        kb.add(zc * q[c]);
+    }
+    const double a = block_sum(ka.value());
+    const double b = block_sum(kb.value());
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_p_update32(int n, float* __restrict__ p, const float* __restrict__ z,
+                             const double* __restrict__ scal) {
+    const float be = (float)scal[S_BETA];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        p[c] = z[c] + be * p[c];
+}
+
+// x64 += e32 (the outer FP64 update of the defect correction)
+__global__ void k_add_f32_to_f64(int n, const float* __restrict__ e, double* __restrict__ x) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        x[c] += (double)e[c];
 }
 
 __global__ void k_to_f32(int n, const double* __restrict__ a, float* __restrict__ b) {
@@ -412,8 +521,14 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color) {
     const LA<T> a = arrays<T>(L);
     const int cls = L.idx == 0 ? T_SMOOTH0 : T_SMOOTH;
     int m = timer_begin(c, cls);
-    VOF_LAUNCH(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, a.x,
-               a.f, color, L.L.kchunk);
+    if (L.d.nx % 2 == 0) {
+        const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
+        VOF_LAUNCH(c, k_rbgs_pair_t<T>, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
+                   (const T*)a.x, a.x, a.f, color, L.L.kchunk);
+    } else {
+        VOF_LAUNCH(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
+                   a.x, a.f, color, L.L.kchunk);
+    }
     timer_end(c, cls, m);
 }
 
@@ -457,28 +572,30 @@ void mg_coarsen_beta(vof_ctx* c, const Level& F, const Level& C) {
 }
 
 // Factor the coarsest level once per solve: explicit inverse of A_c + s 11^T
-// in FP64 (and an FP32 copy for the mixed V-cycle).
+// by Gauss-Jordan in the V-cycle's precision (FP64 path: FP64; mixed path:
+// FP32, an inverse accurate to about cond * eps_32, ample for a
+// preconditioner whose outer iteration is FP64).
 template <class T>
 void mg_dense_setup(vof_ctx* c, const Level& L) {
     const LA<T> a = arrays<T>(L);
     const int n = L.ncells;
     const long n2 = (long)n * n;
     const double ih2 = 1.0 / (L.h * L.h);
-    // s n ~ the typical diagonal entry: the largest face coefficient is not
-    // known on the host, so use the liquid value scale of the fine operator
+    // s n: the liquid-coefficient scale of the diagonal, so the constants'
+    // eigenvalue of the shifted matrix sits among the operator's own
     const double s = c->dense_shift * ih2 / n;
     const int nb = (int)std::min<long>((n2 + 255) / 256, 65535L * 8);
-    int m = timer_begin(c, T_COARSE);
-    VOF_LAUNCH(c, k_dense_assemble<T>, nb, 256, L.d, ih2, a.bx, a.by, a.bz, s, c->dense_a);
-    double* A = c->dense_a;
-    double* B = c->dense_b;
     const int gj_blocks = (int)((n2 + 255) / 256);
+    int m = timer_begin(c, T_COARSE);
+    T* A = (T*)c->dense_a;
+    T* B = (T*)c->dense_b;
+    VOF_LAUNCH(c, k_dense_assemble<T>, nb, 256, L.d, ih2, a.bx, a.by, a.bz, s, A);
     for (int kp = 0; kp < n; ++kp) {
-        VOF_LAUNCH(c, k_gauss_jordan, gj_blocks, 256, n, kp, A, B);
+        VOF_LAUNCH(c, k_gauss_jordan<T>, gj_blocks, 256, n, kp, (const T*)A, B);
         std::swap(A, B);
     }
-    c->dense_inv = A;
-    if (sizeof(T) == 4) VOF_LAUNCH(c, k_dense_to_f32, nb, 256, n2, A, c->dense_inv_f);
+    if (sizeof(T) == 4) c->dense_inv_f = (float*)A;
+    else c->dense_inv = (double*)A;
     timer_end(c, T_COARSE, m);
 }
 
@@ -505,6 +622,47 @@ template <class T>
 void mg_zero(vof_ctx* c, const Level& L) {
     const LA<T> a = arrays<T>(L);
     VOF_LAUNCH(c, k_zero_t<T>, flat_blocks(L.ncells), 256, L.ncells, a.x);
+}
+
+void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
+    const Level& L = c->lv[0];
+    int m = timer_begin(c, T_RESIDUAL);
+    VOF_LAUNCH(c, k_apply_A_dot32, L.L.grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)), L.bxf,
+               L.byf, L.bzf, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
+    timer_end(c, T_RESIDUAL, m);
+    finalize_sum(c, slot, L.L.nblocks, slot, 1.0);
+}
+
+void k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q,
+                   int slot) {
+    const int nb = flat_blocks(n);
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
+               c->part + (size_t)slot * MAX_PARTIALS);
+    timer_end(c, T_KRYLOV, m);
+    finalize_sum(c, slot, nb, slot, 1.0);
+}
+
+void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q, int sa, int sb) {
+    const int nb = flat_blocks(n);
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_dot2_32, nb, 256, n, z, r, q, c->part + (size_t)sa * MAX_PARTIALS,
+               c->part + (size_t)sb * MAX_PARTIALS);
+    timer_end(c, T_KRYLOV, m);
+    finalize_sum(c, sa, nb, sa, 1.0);
+    finalize_sum(c, sb, nb, sb, 1.0);
+}
+
+void k32_p_update(vof_ctx* c, int n, float* p, const float* z) {
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_p_update32, flat_blocks(n), 256, n, p, z, c->scal);
+    timer_end(c, T_KRYLOV, m);
+}
+
+void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x) {
+    int m = timer_begin(c, T_KRYLOV);
+    VOF_LAUNCH(c, k_add_f32_to_f64, flat_blocks(n), 256, n, e, x);
+    timer_end(c, T_KRYLOV, m);
 }
 
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n) {

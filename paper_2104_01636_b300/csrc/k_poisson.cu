@@ -124,6 +124,25 @@ __global__ void k_residual(Dims d, double ih2, const double* __restrict__ bx,
     if (part && threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
 }
 
+// r = f - A x in FP64, stored as FP32 (the inner right side of the mixed
+// solve), with block partials of the FP64 r.r
+__global__ void k_residual_to32(Dims d, double ih2, const double* __restrict__ bx,
+                                const double* __restrict__ by, const double* __restrict__ bz,
+                                const double* __restrict__ x, const double* __restrict__ f,
+                                float* __restrict__ r32, double* __restrict__ part, int kchunk) {
+    CellIdx r = cell_range(d, kchunk);
+    double acc = 0.0;
+    if (r.act)
+        for (int k = r.k0; k < r.k1; ++k) {
+            const int c = cid(d, r.i, r.j, k);
+            const double v = f[c] - stencil(d, bx, by, bz, x, r.i, r.j, k) * ih2;
+            r32[c] = (float)v;
+            acc += v * v;
+        }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
 // ---- flat vector kernels (fixed grid => deterministic partials) ----------
 __global__ void k_dot(int n, const double* __restrict__ x, const double* __restrict__ y,
                       double* __restrict__ part) {
@@ -247,6 +266,15 @@ void launch_residual(vof_ctx* c, const Level& l, const double* x, const double* 
         slot >= 0 ? c->part + (size_t)slot * MAX_PARTIALS : nullptr, l.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
     if (slot >= 0) finalize_sum(c, slot, l.L.nblocks, slot, 1.0);
+}
+
+void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r32, int slot) {
+    const Level& l = c->lv[0];
+    int m = timer_begin(c, T_RESIDUAL);
+    VOF_LAUNCH(c, k_residual_to32, l.L.grid, l.L.block, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz,
+               x, f, r32, c->part + (size_t)slot * MAX_PARTIALS, l.L.kchunk);
+    timer_end(c, T_RESIDUAL, m);
+    finalize_sum(c, slot, l.L.nblocks, slot, 1.0);
 }
 
 void launch_dot(vof_ctx* c, const double* x, const double* y, int n, int slot) {

@@ -10,6 +10,7 @@
 // transpose of prolongation), so it is an SPD preconditioner; the flexible
 // (A-orthogonalising) update keeps the outer iteration robust to the
 // iteratively solved coarsest level.
+#include <algorithm>
 #include <cmath>
 
 #include "vof_internal.cuh"
@@ -91,13 +92,14 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
         const size_t n = (size_t)dims[l].nx * dims[l].ny * dims[l].nz;
         b += faces_bytes(dims[l], elt) + 2 * n * elt;
     }
+    if (mixed) b += 3 * (size_t)dims[0].nx * dims[0].ny * dims[0].nz * sizeof(float);  // e, p, q
     if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
         for (size_t l = 0; l + 1 < dims.size(); ++l)
             b += (size_t)dims[l].nx * dims[l].ny * dims[l].nz * elt;
     const Dims& dc = dims.back();
     const size_t nc = (size_t)dc.nx * dc.ny * dc.nz;
     b += 4 * nc * sizeof(double);
-    if (nc <= (size_t)DENSE_MAX) b += nc * nc * (2 * sizeof(double) + (mixed ? sizeof(float) : 0));
+    if (nc <= (size_t)DENSE_MAX) b += nc * nc * 2 * elt;
     return b;
 }
 
@@ -124,12 +126,8 @@ vof_status mg_allocate(vof_ctx* c) {
         const size_t nv = (size_t)L.d.nx * (L.d.ny + 1) * L.d.nz;
         const size_t n = L.ncells;
         const size_t elt = mixed ? sizeof(float) : sizeof(double);
-        void* p = nullptr;
-        if (cudaMalloc(&p, elt * (nu + nv + 3 * n)) != cudaSuccess) {
-            cudaGetLastError();
-            return set_err(c, VOF_ERR_OOM, "cudaMalloc multigrid level");
-        }
-        c->allocs.push_back(p);
+        void* p = dev_alloc(c, elt * (nu + nv + 3 * n));
+        if (!p) return set_err(c, VOF_ERR_OOM, "allocation of a multigrid level failed");
         if (mixed) {
             float* q = (float*)p;
             L.bxf = q;
@@ -146,41 +144,34 @@ vof_status mg_allocate(vof_ctx* c) {
             L.f = q + nu + nv + 2 * n;
         }
     }
+    if (mixed) {
+        float** inner[3] = {&c->e32, &c->p32, &c->q32};
+        for (float** v : inner) {
+            void* q = dev_alloc(c, sizeof(float) * (size_t)c->lv[0].ncells);
+            if (!q) return set_err(c, VOF_ERR_OOM, "allocation of inner Krylov vectors failed");
+            *v = (float*)q;
+        }
+    }
     if (c->sv.mg_interp == VOF_MG_TRILINEAR) {
         const size_t elt = mixed ? sizeof(float) : sizeof(double);
         for (size_t l = 0; l + 1 < c->lv.size(); ++l) {
-            void* q = nullptr;
-            if (cudaMalloc(&q, elt * (size_t)c->lv[l].ncells) != cudaSuccess) {
-                cudaGetLastError();
-                return set_err(c, VOF_ERR_OOM, "cudaMalloc multigrid residual");
-            }
-            c->allocs.push_back(q);
+            void* q = dev_alloc(c, elt * (size_t)c->lv[l].ncells);
+            if (!q) return set_err(c, VOF_ERR_OOM, "allocation of a multigrid residual failed");
             c->lv[l].rs = q;
         }
     }
     const Level& Lc = c->lv.back();
-    void* p = nullptr;
-    if (cudaMalloc(&p, 4 * sizeof(double) * (size_t)Lc.ncells) != cudaSuccess)
-        return set_err(c, VOF_ERR_OOM, "cudaMalloc coarse scratch");
-    c->allocs.push_back(p);
+    void* p = dev_alloc(c, 4 * sizeof(double) * (size_t)Lc.ncells);
+    if (!p) return set_err(c, VOF_ERR_OOM, "allocation of the coarse scratch failed");
     c->coarse_scratch = (double*)p;
     if (Lc.ncells <= DENSE_MAX) {
         const size_t n2 = (size_t)Lc.ncells * Lc.ncells;
-        void *a = nullptr, *b = nullptr, *f = nullptr;
-        if (cudaMalloc(&a, n2 * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&b, n2 * sizeof(double)) != cudaSuccess ||
-            (mixed && cudaMalloc(&f, n2 * sizeof(float)) != cudaSuccess)) {
-            cudaGetLastError();
-            if (a) cudaFree(a);
-            if (b) cudaFree(b);
-            return set_err(c, VOF_ERR_OOM, "cudaMalloc dense coarse inverse");
-        }
-        c->allocs.push_back(a);
-        c->allocs.push_back(b);
-        if (f) c->allocs.push_back(f);
+        const size_t elt = mixed ? sizeof(float) : sizeof(double);
+        void* a = dev_alloc(c, n2 * elt);
+        void* b = a ? dev_alloc(c, n2 * elt) : nullptr;
+        if (!a || !b) return set_err(c, VOF_ERR_OOM, "allocation of the dense coarse inverse failed");
         c->dense_a = (double*)a;
         c->dense_b = (double*)b;
-        c->dense_inv_f = (float*)f;
         c->dense_n = Lc.ncells;
         // shift: the liquid face coefficient (the smallest physical one) per face
         c->dense_shift = 1.0 / c->ph.rho_l;
@@ -203,11 +194,89 @@ void mg_build_coefficients(vof_ctx* c) {
     if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
 }
 
+// Mixed precision: FP64 defect correction around an inner FP32 solve.
+//   r = b - A64 P (FP64, stored also as FP32);  solve A32 e = r to a modest
+//   relative tolerance with FP32 flexible CG preconditioned by the FP32
+//   V-cycle;  P += e (FP64);  repeat until ||b - A64 P|| <= rtol ||b||.
+// The residual, the update of P and every dot product stay FP64.
+static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, vof_report* rep,
+                              double b_mean) {
+    Level& L0 = c->lv[0];
+    const int n = L0.ncells;
+    float* r32 = L0.ff;  // the inner residual is the V-cycle's fine right side
+    float* z32 = L0.xf;  // and its output is the preconditioned residual
+    double res = res0;
+    int inner_total = 0, outer = 0;
+    bool converged = res <= c->sv.rtol;
+    while (!converged && inner_total < c->sv.max_iter && outer < 50) {
+        // r32 holds the current FP64 residual rounded to FP32
+        const double rr0 = res * bnorm * res * bnorm;
+        const double tol_in = std::max(1e-5, 0.2 * c->sv.rtol / res);
+        // a stagnating FP32 inner solve must not use up the whole budget
+        const int inner_cap = inner_total + std::max(20, c->sv.max_iter / 4);
+        cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
+        vcycle<float>(c, 0);
+        k32_dot2(c, n, z32, r32, r32, S_RZ, S_ZQ);
+        cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
+        while (inner_total < c->sv.max_iter && inner_total < inner_cap) {
+            ++inner_total;
+            k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
+            launch_scalar_alpha(c);
+            k32_cg_update(c, n, c->e32, r32, c->p32, c->q32, S_RR);
+            readback(c);
+            const double rr = c->hbuf[S_RR];
+            if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
+            if (rr <= tol_in * tol_in * rr0) break;
+            vcycle<float>(c, 0);
+            k32_dot2(c, n, z32, r32, c->q32, S_RZ, S_ZQ);
+            launch_scalar_beta(c);
+            k32_p_update(c, n, c->p32, z32);
+        }
+        // FP64 update and true residual
+        k32_add_to_f64(c, n, c->e32, P);
+        launch_residual_to32(c, P, c->b, r32, S_RR);
+        readback(c);
+        res = std::sqrt(c->hbuf[S_RR]) / bnorm;
+        if (!std::isfinite(res)) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
+        ++outer;
+        converged = res <= c->sv.rtol;
+    }
+    launch_sub_mean(c, P, n, S_SUM);
+    vof_status st = cuda_check(c, cudaGetLastError(), "pressure solve");
+    if (rep) {
+        rep->iters = inner_total;
+        rep->refinements = outer;
+        rep->res0 = res0;
+        rep->res = res;
+        rep->b_mean = b_mean;
+    }
+    if (st != VOF_OK) return st;
+    if (!converged)
+        return set_err(c, VOF_ERR_NOT_CONVERGED,
+                       "pressure solve did not reach rtol within max_iter (res=" +
+                           std::to_string(res) + ")");
+    return VOF_OK;
+}
+
 // Solves A P = b_in - mean(b_in) with the fine-level beta already built.
 vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report* rep) {
     const int n = c->lv[0].ncells;
     Level& L0 = c->lv[0];
     mg_build_coefficients(c);
+    if (c->sv.precision == VOF_PREC_MIXED_FP32) {
+        launch_copy(c, c->b, b_in, n);
+        launch_sub_mean(c, c->b, n, S_MEAN);
+        launch_dot(c, c->b, c->b, n, S_BB);
+        launch_residual_to32(c, P, c->b, L0.ff, S_RR);
+        readback(c);
+        vof_status st = cuda_check(c, cudaGetLastError(), "pressure solve setup");
+        if (st != VOF_OK) return st;
+        double bnorm = std::sqrt(c->hbuf[S_BB]);
+        if (!(bnorm >= 1e-300)) bnorm = 1e-300;
+        const double res0 = std::sqrt(c->hbuf[S_RR]) / bnorm;
+        if (!std::isfinite(res0)) return set_err(c, VOF_ERR_NONFINITE, "non-finite initial residual");
+        return solve_mixed(c, P, bnorm, res0, rep, c->hbuf[S_MEAN]);
+    }
 
     launch_copy(c, c->b, b_in, n);
     launch_sub_mean(c, c->b, n, S_MEAN);
@@ -256,6 +325,7 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
     st = cuda_check(c, cudaGetLastError(), "pressure solve");
     if (rep) {
         rep->iters = it;
+        rep->refinements = 0;
         rep->res0 = res0;
         rep->res = res;
         rep->b_mean = b_mean;

@@ -142,6 +142,7 @@ struct vof_ctx {
     double *a1 = nullptr, *a2 = nullptr, *an = nullptr;  // alpha scratch
     double *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double* rhs = nullptr;  // assembled right side of the projection
+    float *e32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // inner FP32 Krylov (mixed)
     std::vector<Level> lv;
     double* coarse_scratch = nullptr;
     // dense inverse of the coarsest level (when it has <= DENSE_MAX cells)
@@ -152,7 +153,8 @@ struct vof_ctx {
 
     double* part = nullptr;  // NSLOTS x MAX_PARTIALS block partials
     double* scal = nullptr;  // device scalars
-    double* hbuf = nullptr;  // pinned host mirror of scal
+    double* hbuf = nullptr;  // host mirror of scal (points into hbuf_store)
+    std::vector<double> hbuf_store = std::vector<double>(64, 0.0);
     int* dflag = nullptr;    // device error flags
 
     // timing
@@ -184,6 +186,7 @@ enum ScalarSlot {
 // helpers implemented in capi.cu
 // ---------------------------------------------------------------------------
 vof_status set_err(vof_ctx* c, vof_status s, const std::string& msg);
+void* dev_alloc(vof_ctx* c, size_t bytes);  // stream-ordered, freed by vof_destroy
 vof_status cuda_check(vof_ctx* c, cudaError_t e, const char* what);
 vof_status launch_check(vof_ctx* c, const char* what);
 int timer_begin(vof_ctx* c, int cls);
@@ -224,6 +227,13 @@ template <class T> void mg_zero(vof_ctx* c, const Level& L);
 template <class T> void mg_dense_setup(vof_ctx* c, const Level& L);
 constexpr int DENSE_MAX = 1536;  // largest coarsest level solved by the dense inverse
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
+// inner FP32 Krylov of the mixed solve (k_mg.cu) and its FP64 residual (k_poisson.cu)
+void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
+void k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q, int slot);
+void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q, int sa, int sb);
+void k32_p_update(vof_ctx* c, int n, float* p, const float* z);
+void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x);
+void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r32, int slot);
 void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
 
 // vof (k_vof.cu)
@@ -258,6 +268,11 @@ void launch_correct(vof_ctx* c, const double* P, const double* sx, const double*
 
 // solver driver (solver.cu)
 vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report* rep);
+// the whole time step (the body of the exported step/vof_step); the
+// library's own callers use this name, which no system library exports
+vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
+                      double* v, double* w, double* p, double dt, long long step_index,
+                      vof_report* report);
 size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels);
 vof_status mg_allocate(vof_ctx* c);
 void mg_build_coefficients(vof_ctx* c);

@@ -141,9 +141,12 @@ def sphere_alpha(grid: Grid, centres, radius: float, sub: int = 8) -> np.ndarray
 
 
 def place_spheres(grid: Grid, n: int, d: float, seed: int, gap: float = None,
-                  wall_gap: float = None, max_tries: int = 2_000_000) -> np.ndarray:
+                  wall_gap: float = None, max_tries: int = 2_000_000,
+                  allow_fewer: bool = False) -> np.ndarray:
     """Seeded rejection sampling of n sphere centres (metres): centre spacing
-    >= d + gap (periodic in z), and >= d/2 + wall_gap from the x/y walls."""
+    >= d + gap (periodic in z), and >= d/2 + wall_gap from the x/y walls.
+    With allow_fewer, returns the spheres placed within max_tries instead of
+    raising."""
     h = grid.h
     gap = 2 * h if gap is None else gap
     wall_gap = h if wall_gap is None else wall_gap
@@ -155,6 +158,8 @@ def place_spheres(grid: Grid, n: int, d: float, seed: int, gap: float = None,
     while len(out) < n:
         tries += 1
         if tries > max_tries:
+            if allow_fewer and out:
+                break
             raise RuntimeError(f"could not place {n} spheres (placed {len(out)})")
         c = np.array([rng.uniform(lo, W - lo), rng.uniform(lo, Wy - lo), rng.uniform(0, L)])
         if out:
@@ -339,17 +344,10 @@ def rising_swarm(nx: int = 64, ny: int = 64, nz: int = 128, nbub: int = 8, d_cel
     g = Grid(nx, ny, nz)
     d = d_cells * g.h
     centres = place_spheres(g, nbub, d, seed)
-    alpha = sphere_alpha(g, centres, d / 2)
-    w0, G = laminar_w(g, w_b, MU_L)
-    un, vn, wn = curl_noise(g, 0.10 * w_b, seed + 1)
-    phi = gas_fraction(alpha)
-    ph = Phys(g_z=-GRAV, rho0=(1 - phi) * RHO_L + phi * RHO_G, dpdz=G)
-    u, v, w = un, vn, w0 + wn
-    umax = max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
-    cs = g.shapes()[0]
-    return Case("rising_swarm", g, ph, alpha, u, v, w, np.zeros(cs), stable_dt(g, ph, umax),
-                steps, centres, d / 2,
-                f"{nx}x{ny}x{nz}, {nbub} spheres d={d_cells}h, laminar w_b={w_b} + 10% noise")
+    c = _swarm_from(g, centres, d, seed, steps, w_b)
+    c.name = "rising_swarm"
+    c.notes = f"{nx}x{ny}x{nz}, {nbub} spheres d={d_cells}h, laminar w_b={w_b} + 10% noise"
+    return c
 
 
 def paper_shaped(nx: int = 224, ny: int = 224, nz: int = 640, nbub: int = 864,
@@ -379,3 +377,59 @@ def paper_shaped(nx: int = 224, ny: int = 224, nz: int = 640, nbub: int = 864,
 
 def with_phys(case: Case, **kw) -> Case:
     return replace(case, phys=replace(case.phys, **kw))
+
+
+# ----------------------------------------------------------------------------
+# request mix for the serving loop
+# ----------------------------------------------------------------------------
+SERVE_GRIDS = ((32, 32, 32), (64, 64, 128), (96, 96, 192), (128, 128, 256))
+
+
+@dataclass
+class Request:
+    kind: str          # "step" (n_steps time steps) or "solve" (one pressure solve)
+    case: Case
+    n_steps: int
+    b: np.ndarray = None  # right side of a solve
+
+
+def serving_mix(n_req: int, seed: int = 2108, grids=SERVE_GRIDS, p_step: float = 0.5):
+    """Seeded request mix: grid drawn uniformly from `grids`, 1-64 spheres
+    with d drawn from [8, 14]h (fewer where the grid cannot hold them), the
+    rising-swarm flow, and either 1-10 time steps or one pressure solve whose
+    right side is zero-mean Gaussian noise scaled like -div(u)/dt of the
+    case's flow. The paper has no serving workload; this stands in for an
+    ensemble of independent duct cases."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_req):
+        dims = grids[int(rng.integers(len(grids)))]
+        d_cells = float(rng.uniform(8.0, 14.0))
+        nbub = int(rng.integers(1, 65))
+        kind = "step" if rng.uniform() < p_step else "solve"
+        n_steps = int(rng.integers(1, 11)) if kind == "step" else 0
+        sub = seed * 1000 + r
+        g = Grid(*dims)
+        d = d_cells * g.h
+        centres = place_spheres(g, nbub, d, sub, max_tries=20_000, allow_fewer=True)
+        case = _swarm_from(g, centres, d, sub, max(n_steps, 1))
+        b = None
+        if kind == "solve":
+            b = np.random.default_rng(sub + 1).normal(size=g.shapes()[0])
+            b = (b - b.mean()) * (0.1 * 0.1104 / g.h / case.dt)
+        out.append(Request(kind, case, n_steps, b))
+    return out
+
+
+def _swarm_from(g: Grid, centres, d: float, seed: int, steps: int, w_b: float = 0.1104) -> Case:
+    """Rising-swarm flow (laminar duct profile of bulk velocity w_b + 10%
+    divergence-free noise, gravity along -z) around the given sphere centres."""
+    alpha = sphere_alpha(g, centres, d / 2)
+    w0, G = laminar_w(g, w_b, MU_L)
+    un, vn, wn = curl_noise(g, 0.10 * w_b, seed + 1)
+    phi = gas_fraction(alpha)
+    ph = Phys(g_z=-GRAV, rho0=(1 - phi) * RHO_L + phi * RHO_G, dpdz=G)
+    u, v, w = un, vn, w0 + wn
+    umax = max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
+    return Case("serve", g, ph, alpha, u, v, w, np.zeros(g.shapes()[0]),
+                stable_dt(g, ph, umax), steps, centres, d / 2)

@@ -52,3 +52,54 @@ def test_invalid_grids_rejected(dims):
     with pytest.raises(vd.VofError) as e:
         vd.workspace_bytes(Grid(*dims))
     assert e.value.name == "VOF_ERR_ARG"
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's sizes and offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    checks = {
+        "vof_grid": (vd.CGrid, ["nx", "h", "periodic_y"]),
+        "vof_phys": (vd.CPhys, ["rho_l", "conv_scheme", "kappa_exact"]),
+        "vof_solver": (vd.CSolver, ["precision", "rtol", "mg_omega", "coarse_tol", "mg_interp"]),
+        "vof_report": (vd.CReport, ["iters", "res0", "hf_fallbacks", "ms"]),
+        "vof_request": (vd.CRequest, ["kind", "grid", "phys", "solver", "n_steps", "dt", "step0",
+                                      "alpha", "p", "b"]),
+        "vof_result": (vd.CResult, ["status", "t_submit", "report"]),
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vof.h"', "int main(void){"]
+    for cname, (_, fields) in checks.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, f, val = line.split()
+        got[(cname, f)] = int(val)
+    for cname, (cls, fields) in checks.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f in fields:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_library_binds_its_own_symbols():
+    """glibc exports a legacy function named step; the library is linked
+    -Bsymbolic so that its internal calls reach its own definitions."""
+    import shutil
+    import subprocess
+    vbuild.build()
+    if shutil.which("readelf") is None:
+        pytest.skip("readelf not available")
+    out = subprocess.run(["readelf", "-d", vd.LIB_PATH], check=True, capture_output=True,
+                         text=True).stdout
+    assert "SYMBOLIC" in out
+    assert hasattr(vd.load(), "vof_step")
