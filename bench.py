@@ -121,17 +121,22 @@ class Clocks:
 
 
 def traffic_for(cls: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per launch from the committed ncu table (profiles/
+    ncu_traffic.txt: class, source file, its sha256, bytes per launch), or
+    None when the kernel's source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(cls)
-    if not d:
-        return None
-    src = os.path.join(ROOT, "paper_2104_01636_b300", "csrc", KERNEL_SOURCE[cls])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return d["dram_bytes_per_launch"] if d.get("source_sha256") == h else None
+    for line in open(p):
+        f = line.split()
+        if len(f) != 4 or f[0] != cls or line.startswith("#"):
+            continue
+        src = os.path.join(ROOT, "paper_2104_01636_b300", "csrc", f[1])
+        if not os.path.exists(src):
+            return None
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return float(f[3]) if h == f[2] else None
+    return None
 
 
 # ----------------------------------------------------------------------------
