@@ -34,21 +34,36 @@ UNIT = "time-steps/s"
 WORKLOAD = "paper-shaped duct 224x224x640 (32.1M cells), 864 spheres d=12h, Re_b=5300 1/7 profile + 8% noise"
 
 # Algorithmic bytes per fine-grid cell for one launch of each kernel class:
-# what the kernel must read and write at minimum, with E the byte size of the
-# multigrid scalar (8 for the FP64 path, 4 for the mixed path's FP32 V-cycle).
-#  smooth_l0   one red-black colour: other-colour x (E/2), all face betas
-#              (3E), own-colour right side (E/2), own-colour x written (E/2)
-#  restrict_l0 residual of 8 children averaged: x, f (2E), betas (3E),
-#              coarse f written (E/8)
-#  prolong_l0  fine x read and written (2E), coarse x (E/8)
-#  residual_l0 q = A p with p.q, always FP64: p (8), betas (24), q (8)
-def algo_bytes_per_cell(cls: str, E: int) -> float:
-    return {"smooth_l0": 4.5 * E, "restrict_l0": 5.125 * E, "prolong_l0": 2.125 * E,
-            "residual_l0": 40.0}[cls]
+# what the kernel must read and write at minimum.
+# FP64 path (separate red and black launches, stored FP64 face coefficients):
+#  smooth_l0   one colour: other-colour x (4), all face betas (24), own-colour
+#              right side (4), own-colour x written (4)              = 36
+#  restrict_l0 residual of 8 children averaged: x, f (16), betas (24),
+#              coarse f written (1)                                  = 41
+#  prolong_l0  fine x read and written (16), coarse x (1)            = 17
+# Mixed path (FP32 V-cycle, finest level from the FP32 cell density, one
+# launch per whole red-black sweep, x ping-ponged between two buffers):
+#  smooth_l0   full sweep: old x (4), density (4), f (4), new x (4) = 16;
+#              the first pre-smoothing sweep starts from zero (12); with
+#              nu sweeps before and after: (12 + 16 (2 nu - 1)) / (2 nu)
+#  restrict_l0 x, density, f (12), coarse f written (0.5)           = 12.5
+#  prolong_l0  fine x read and written (8), coarse x (0.5)          = 8.5
+#  residual_l0 FP64 outer residual (P 8, b 8, betas 24, FP32 r 4)   = 44
+NU = 2
 
 
-KERNEL_SOURCE = {"smooth_l0": "k_mg.cu", "residual_l0": "k_poisson.cu",
-                 "restrict_l0": "k_mg.cu", "prolong_l0": "k_mg.cu"}
+def algo_bytes_per_cell(cls: str, precision: str) -> float:
+    if precision == "fp64":
+        return {"smooth_l0": 36.0, "restrict_l0": 41.0, "prolong_l0": 17.0,
+                "residual_l0": 40.0}[cls]
+    return {"smooth_l0": (12.0 + 16.0 * (2 * NU - 1)) / (2 * NU), "restrict_l0": 12.5,
+            "prolong_l0": 8.5, "residual_l0": 44.0}[cls]
+
+
+KERNEL_SOURCE = {"fp64": {"smooth_l0": "k_mg.cu", "residual_l0": "k_poisson.cu",
+                          "restrict_l0": "k_mg.cu", "prolong_l0": "k_mg.cu"},
+                 "mixed": {"smooth_l0": "k_smooth_tma.cu", "residual_l0": "k_poisson.cu",
+                           "restrict_l0": "k_smooth_tma.cu", "prolong_l0": "k_mg.cu"}}
 
 
 def parse():
@@ -120,7 +135,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def traffic_for(cls: str):
+def traffic_for(cls: str, precision: str):
     """DRAM bytes per launch from the committed ncu table (profiles/
     ncu_traffic.txt: class, source file, its sha256, bytes per launch), or
     None when the kernel's source changed since the counters were taken."""
@@ -130,6 +145,8 @@ def traffic_for(cls: str):
     for line in open(p):
         f = line.split()
         if len(f) != 4 or f[0] != cls or line.startswith("#"):
+            continue
+        if f[1] != KERNEL_SOURCE[precision][cls]:
             continue
         src = os.path.join(ROOT, "paper_2104_01636_b300", "csrc", f[1])
         if not os.path.exists(src):
@@ -337,16 +354,16 @@ def main():
             it2 += rep["iters"]
         kt = ctx.kernel_times()
         ctx.set_timing(False)
-        cls = max(KERNEL_SOURCE, key=lambda k: kt.get(k, (0.0, 0))[0])
+        cls = max(KERNEL_SOURCE[args.precision], key=lambda k: kt.get(k, (0.0, 0))[0])
         kms, kn = kt[cls]
         avg_ms = kms / max(kn, 1)
-        algo = algo_bytes_per_cell(cls, 8 if args.precision == "fp64" else 4) * N
+        algo = algo_bytes_per_cell(cls, args.precision) * N
         peak, peak_kind = peaks()
         achieved = algo / (avg_ms / 1e3) / 1e9
         step_ms_timed = sum(v[0] for v in kt.values()) / k_steps
         roofline = {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic_for(cls), "algorithmic_bytes": algo,
+                    "traffic": traffic_for(cls, args.precision), "algorithmic_bytes": algo,
                     "avg_launch_ms": avg_ms, "launches_per_step": kn / k_steps,
                     "share_of_step": kms / k_steps / step_ms_timed if step_ms_timed else None,
                     "classes_ms_per_step": {k: round(v[0] / k_steps, 4) for k, v in kt.items()}}

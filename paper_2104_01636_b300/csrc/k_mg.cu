@@ -227,23 +227,23 @@ __global__ void k_restrict_fw_t(Dims df, const T* __restrict__ rf, Dims dc, T* _
     }
 }
 
-template <class T>
-__global__ void k_coarsen_beta_t(Dims df, const T* __restrict__ bxf, const T* __restrict__ byf,
-                                 const T* __restrict__ bzf, Dims dc, T* __restrict__ bxc,
+template <class T, class TI = T>
+__global__ void k_coarsen_beta_t(Dims df, const TI* __restrict__ bxf, const TI* __restrict__ byf,
+                                 const TI* __restrict__ bzf, Dims dc, T* __restrict__ bxc,
                                  T* __restrict__ byc, T* __restrict__ bzc, int kchunk) {
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
     for (int K = k0; K < k1; ++K) {
         const int i = 2 * I, j = 2 * J, k = 2 * K;
-        bxc[uid(dc, I, J, K)] = T(0.25) * (bxf[uid(df, i, j, k)] + bxf[uid(df, i, j + 1, k)] +
-                                           bxf[uid(df, i, j, k + 1)] + bxf[uid(df, i, j + 1, k + 1)]);
+        bxc[uid(dc, I, J, K)] = T(TI(0.25) * (bxf[uid(df, i, j, k)] + bxf[uid(df, i, j + 1, k)] +
+                                              bxf[uid(df, i, j, k + 1)] + bxf[uid(df, i, j + 1, k + 1)]));
         if (I == dc.nx - 1) bxc[uid(dc, dc.nx, J, K)] = T(0);
-        byc[vid(dc, I, J, K)] = T(0.25) * (byf[vid(df, i, j, k)] + byf[vid(df, i + 1, j, k)] +
-                                           byf[vid(df, i, j, k + 1)] + byf[vid(df, i + 1, j, k + 1)]);
+        byc[vid(dc, I, J, K)] = T(TI(0.25) * (byf[vid(df, i, j, k)] + byf[vid(df, i + 1, j, k)] +
+                                              byf[vid(df, i, j, k + 1)] + byf[vid(df, i + 1, j, k + 1)]));
         if (J == dc.ny - 1) byc[vid(dc, I, dc.ny, K)] = T(0);
-        bzc[wid(dc, I, J, K)] = T(0.25) * (bzf[wid(df, i, j, k)] + bzf[wid(df, i + 1, j, k)] +
-                                           bzf[wid(df, i, j + 1, k)] + bzf[wid(df, i + 1, j + 1, k)]);
+        bzc[wid(dc, I, J, K)] = T(TI(0.25) * (bzf[wid(df, i, j, k)] + bzf[wid(df, i + 1, j, k)] +
+                                              bzf[wid(df, i, j + 1, k)] + bzf[wid(df, i + 1, j + 1, k)]));
     }
 }
 
@@ -569,6 +569,15 @@ void mg_coarsen_beta(vof_ctx* c, const Level& F, const Level& C) {
     const LA<T> a = arrays<T>(F), b = arrays<T>(C);
     VOF_LAUNCH(c, k_coarsen_beta_t<T>, C.L.grid, C.L.block, F.d, a.bx, a.by, a.bz, C.d, b.bx, b.by,
                b.bz, C.L.kchunk);
+}
+
+// FP64 finest-level coefficients averaged straight into the FP32 level 1
+// (the mixed V-cycle's finest level keeps no FP32 face arrays)
+void mg_coarsen_beta_from64(vof_ctx* c, const Level& F, const Level& C) {
+    void (*const kern)(Dims, const double*, const double*, const double*, Dims, float*, float*,
+                       float*, int) = k_coarsen_beta_t<float, double>;
+    VOF_LAUNCH(c, kern, C.L.grid, C.L.block, F.d, F.bx, F.by, F.bz, C.d, C.bxf, C.byf, C.bzf,
+               C.L.kchunk);
 }
 
 // Factor the coarsest level once per solve: explicit inverse of A_c + s 11^T

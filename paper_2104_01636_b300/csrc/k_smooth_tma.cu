@@ -1,0 +1,478 @@
+// Finest level of the mixed-precision V-cycle (pressure equation, Eq. 7):
+// the face coefficients are formed on the fly from one FP32 density per cell,
+//   beta_f = 1 / (0.5 (rho_L + rho_R)) = 2 / (rho_L + rho_R),
+// the same face rule as the FP64 coefficients (rho the linear mix of the two
+// phases by the volume fraction), so a kernel reads one value per cell
+// instead of three face arrays. Three kernels use that operator and nothing
+// else does on this level, so the V-cycle stays a symmetric preconditioner:
+//
+//  * k_sweep_rho: one whole red-black Gauss-Seidel sweep per launch (first
+//    colour from the other colour's old values, then the other colour from
+//    the new ones). A block owns a 32 x 32 (x, y) tile and marches over a
+//    chunk of z planes; TMA (cp.async.bulk.tensor) stages the planes of x and
+//    of the density, halo included, in shared memory. The first colour is
+//    computed on the tile and on its one-cell ring (the ring redundantly with
+//    the neighbouring tiles), so a block never reads another block's result;
+//    x is read from one buffer and written to another, and the result does
+//    not depend on the order in which blocks run.
+//  * k_restrict_rho: residual f - A x averaged over the eight children.
+//  * k_apply_A_dot_rho32: q = A p with the partials of p.q (inner CG).
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "vof_internal.cuh"
+
+namespace {
+
+constexpr int STX = 32, STY = 32;           // tile of a sweep block
+constexpr int SBX = STX + 8, SBY = STY + 4;  // staged box: x from i0-4 (16-byte aligned), y from j0-2
+constexpr int RNX = STX + 2, RNY = STY + 2;  // first-colour values on the tile and its ring
+constexpr int NSLOT = 5;                     // staged planes: 3 in use, 2 in flight
+constexpr int PLANE = SBX * SBY;             // floats per staged plane
+constexpr int WAIT_LIMIT = 1 << 20;          // bounded waits on the TMA barriers
+constexpr size_t SWEEP_SMEM =
+    (size_t)(2 * NSLOT * PLANE + 3 * RNX * RNY) * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
+static_assert(sizeof(CUtensorMap) == 128, "tensor map storage in the context is 128 bytes");
+static_assert((SBX * sizeof(float)) % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
+static_assert((PLANE * sizeof(float)) % 128 == 0, "staged planes keep 128-byte alignment");
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// the face coefficient 2 / (rho_L + rho_R); the sweep uses its exact half
+__device__ __forceinline__ float beta_rho(float rc, float rn) { return 2.f * rcp_approx(rc + rn); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+struct SweepArgs {
+    int nx, ny, nz;
+    float h2half;  // h^2 / 2: the sweep works with half coefficients 1 / (rho_L + rho_R)
+    int c0;        // colour updated first: cells with (i + j + k) % 2 == c0
+    int kchunk;
+    const float* f;
+    float* xout;
+    double* err;  // set to 1 when a wait on a TMA barrier gives up
+};
+
+// 1 / (rho_L + rho_R), half the face coefficient: every finest-level kernel
+// forms its coefficients through this one expression
+__device__ __forceinline__ float half_beta(float rc, float rn) { return rcp_approx(rc + rn); }
+
+__device__ __forceinline__ float2 half_beta2(float2 rc, float2 rn) {
+    const float2 s = __fadd2_rn(rc, rn);
+    return make_float2(rcp_approx(s.x), rcp_approx(s.y));
+}
+
+// Each thread owns the x-pair (ib, ib+1) in rows jA = j0+ty and jB = jA+16.
+// On every plane one member of the pair has the first colour and the other
+// the second, at the same x in both rows, so the two rows are updated with
+// packed FP32x2 arithmetic. The z-face coefficients computed for the first
+// colour are kept in registers and reused by the second colour.
+template <bool ZERO>
+__global__ void __launch_bounds__(256, 3)
+    k_sweep_rho(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_rho,
+                SweepArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    float* sX = reinterpret_cast<float*>(smem_raw + (((raw + 127u) & ~127u) - raw));
+    float* sR = sX + NSLOT * PLANE;
+    float* sN = sR + NSLOT * PLANE;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sN + 3 * RNX * RNY);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 16 * ty;
+    const int i0 = blockIdx.x * STX, j0 = blockIdx.y * STY;
+    const int k0 = blockIdx.z * a.kchunk;
+    const int k1 = min(k0 + a.kchunk, a.nz);
+    if (k0 >= k1) return;  // whole block
+    const int pbase = k0 - 2;  // first staged plane (unwrapped index)
+    constexpr uint32_t bytes = (ZERO ? 1u : 2u) * (uint32_t)(PLANE * sizeof(float));
+
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    int issued = pbase - 1;  // last plane issued (thread 0)
+    auto issue = [&](int p) {
+        const int s = (p - pbase) % NSLOT;
+        const int z = wrapk(p, a.nz);
+        mbar_expect_tx(&bar[s], bytes);
+        if (!ZERO) tma_load_3d(sX + s * PLANE, &tm_x, &bar[s], i0 - 4, j0 - 2, z);
+        tma_load_3d(sR + s * PLANE, &tm_rho, &bar[s], i0 - 4, j0 - 2, z);
+        issued = p;
+    };
+    if (tid == 0)
+        for (int p = pbase; p <= k0 + 1; ++p) issue(p);
+
+    bool bad = false;
+    auto wait_slot = [&](int s, uint32_t par) {
+        for (int it = 0; !bad && !mbar_try_wait(&bar[s], par);)
+            if (++it > WAIT_LIMIT) bad = true;
+    };
+    wait_slot(0, 0);
+    wait_slot(1, 0);
+
+    // per-thread geometry
+    const int nx = a.nx, ny = a.ny;
+    const int ib = i0 + 2 * tx;
+    const int jA = j0 + ty, jB = jA + 16;
+    const bool inA = ib < nx && jA < ny, inB = ib < nx && jB < ny;
+    const bool ylA = jA > 0, yhA = jA < ny - 1, yhB = jB < ny - 1;  // jB > 0 always
+    const int oA = (ty + 2) * SBX + 2 * tx + 4, oB = oA + 16 * SBX;  // staged offsets of (ib, jA/jB)
+    const int nA = (ty + 1) * RNX + 2 * tx + 1, nB = nA + 16 * RNX;  // first-colour offsets
+    const size_t plane = (size_t)ny * nx;
+    const float h2h = a.h2half;
+
+    // slots of planes k, k+1, k+2 (staged) and k-1, k, k+1 (first colour)
+    int S1 = 0, S2 = 1, S3 = 2;
+    uint32_t par3 = 0;  // parity of slot S3's current fill
+    float* N0 = sN + 2 * (RNX * RNY);
+    float* N1 = sN;
+    float* N2 = sN + (RNX * RNY);
+    float2 bup1 = make_float2(0.f, 0.f), bup2 = make_float2(0.f, 0.f);  // z+ coefficients, 1 and 2 planes back
+
+    for (int k = pbase; k < k1; ++k) {
+        wait_slot(S3, par3);
+        const int q = k + 1, kq = wrapk(q, a.nz);
+        const int P = (a.c0 + jA + q) & 1;  // x offset of the first colour in the pair on plane q
+        const int i = ib + P;
+        float2 bdown = make_float2(0.f, 0.f), bup = make_float2(0.f, 0.f);
+        // ---- first colour on plane q: the thread's two cells, packed -------
+        if (!bad) {
+            const float* Rq = sR + S2 * PLANE;
+            const float* Rm = sR + S1 * PLANE;
+            const float* Rp = sR + S3 * PLANE;
+            const float* Xq = sX + S2 * PLANE;
+            const float* Xm = sX + S1 * PLANE;
+            const float* Xp = sX + S3 * PLANE;
+            const int a_ = oA + P, b_ = oB + P;
+            const float2 rc = make_float2(Rq[a_], Rq[b_]);
+            const float* fq = a.f + (size_t)kq * plane + i;
+            float2 num = make_float2(inA ? h2h * __ldg(fq + (size_t)jA * nx) : 0.f,
+                                     inB ? h2h * __ldg(fq + (size_t)jB * nx) : 0.f);
+            float2 den = make_float2(0.f, 0.f);
+            auto acc = [&](float2 b, int da, int db, const float* X) {
+                if (!ZERO) num = __ffma2_rn(b, make_float2(X[a_ + da], X[b_ + db]), num);
+                den = __fadd2_rn(den, b);
+            };
+            if (i > 0) acc(half_beta2(rc, make_float2(Rq[a_ - 1], Rq[b_ - 1])), -1, -1, Xq);
+            if (i < nx - 1) acc(half_beta2(rc, make_float2(Rq[a_ + 1], Rq[b_ + 1])), 1, 1, Xq);
+            {
+                float2 b = half_beta2(rc, make_float2(Rq[a_ - SBX], Rq[b_ - SBX]));
+                if (!ylA) b.x = 0.f;
+                acc(b, -SBX, -SBX, Xq);
+                b = half_beta2(rc, make_float2(Rq[a_ + SBX], Rq[b_ + SBX]));
+                if (!yhA) b.x = 0.f;
+                if (!yhB) b.y = 0.f;
+                acc(b, SBX, SBX, Xq);
+            }
+            bdown = half_beta2(rc, make_float2(Rm[a_], Rm[b_]));
+            acc(bdown, 0, 0, Xm);
+            bup = half_beta2(rc, make_float2(Rp[a_], Rp[b_]));
+            acc(bup, 0, 0, Xp);
+            N2[nA + P] = inA ? __fdividef(num.x, den.x) : 0.f;
+            N2[nB + P] = inB ? __fdividef(num.y, den.y) : 0.f;
+
+            if (tid < 64) {  // the ring: 16 first-colour cells per side (0 outside the domain)
+                const int side = tid >> 4, m = tid & 15;
+                int ri, rj;
+                if (side < 2) {
+                    ri = side == 0 ? i0 - 1 : i0 + STX;
+                    rj = j0 + 2 * m + ((a.c0 + ri + q) & 1);
+                } else {
+                    rj = side == 2 ? j0 - 1 : j0 + STY;
+                    ri = i0 + 2 * m + ((a.c0 + rj + q) & 1);
+                }
+                float v = 0.f;
+                if (ri >= 0 && ri < nx && rj >= 0 && rj < ny) {
+                    const int o = (rj - j0 + 2) * SBX + (ri - i0 + 4);
+                    const float r0 = Rq[o];
+                    float rn = h2h * __ldg(a.f + (size_t)kq * plane + (size_t)rj * nx + ri), rd = 0.f;
+                    float b;
+                    if (ri > 0) { b = half_beta(r0, Rq[o - 1]); if (!ZERO) rn = fmaf(b, Xq[o - 1], rn); rd += b; }
+                    if (ri < nx - 1) { b = half_beta(r0, Rq[o + 1]); if (!ZERO) rn = fmaf(b, Xq[o + 1], rn); rd += b; }
+                    if (rj > 0) { b = half_beta(r0, Rq[o - SBX]); if (!ZERO) rn = fmaf(b, Xq[o - SBX], rn); rd += b; }
+                    if (rj < ny - 1) { b = half_beta(r0, Rq[o + SBX]); if (!ZERO) rn = fmaf(b, Xq[o + SBX], rn); rd += b; }
+                    b = half_beta(r0, Rm[o]); if (!ZERO) rn = fmaf(b, Xm[o], rn); rd += b;
+                    b = half_beta(r0, Rp[o]); if (!ZERO) rn = fmaf(b, Xp[o], rn); rd += b;
+                    v = __fdividef(rn, rd);
+                }
+                N2[(rj - j0 + 1) * RNX + (ri - i0 + 1)] = v;
+            }
+        }
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) {
+                *a.err = 1.0;
+                // let the copies already issued land before the block exits
+                for (int p = k + 3; p <= issued; ++p) {
+                    const int s = (p - pbase) % NSLOT;
+                    const uint32_t par = (uint32_t)((p - pbase) / NSLOT) & 1u;
+                    for (int it = 0; !mbar_try_wait(&bar[s], par) && it < WAIT_LIMIT; ++it) {
+                    }
+                }
+            }
+            return;
+        }
+        // ---- second colour on plane k at the same x, written with the first -
+        if (k >= k0) {
+            const int kk = wrapk(k, a.nz);
+            const float* Rk = sR + S1 * PLANE;
+            const int a_ = oA + P, b_ = oB + P, na = nA + P, nb = nB + P;
+            const float2 rc = make_float2(Rk[a_], Rk[b_]);
+            const float* fk = a.f + (size_t)kk * plane + i;
+            float2 num = make_float2(inA ? h2h * __ldg(fk + (size_t)jA * nx) : 0.f,
+                                     inB ? h2h * __ldg(fk + (size_t)jB * nx) : 0.f);
+            float2 den = make_float2(0.f, 0.f);
+            auto acc = [&](float2 b, float2 xn) {
+                num = __ffma2_rn(b, xn, num);
+                den = __fadd2_rn(den, b);
+            };
+            if (i > 0)
+                acc(half_beta2(rc, make_float2(Rk[a_ - 1], Rk[b_ - 1])),
+                    make_float2(N1[na - 1], N1[nb - 1]));
+            if (i < nx - 1)
+                acc(half_beta2(rc, make_float2(Rk[a_ + 1], Rk[b_ + 1])),
+                    make_float2(N1[na + 1], N1[nb + 1]));
+            {
+                float2 b = half_beta2(rc, make_float2(Rk[a_ - SBX], Rk[b_ - SBX]));
+                if (!ylA) b.x = 0.f;
+                acc(b, make_float2(N1[na - RNX], N1[nb - RNX]));
+                b = half_beta2(rc, make_float2(Rk[a_ + SBX], Rk[b_ + SBX]));
+                if (!yhA) b.x = 0.f;
+                if (!yhB) b.y = 0.f;
+                acc(b, make_float2(N1[na + RNX], N1[nb + RNX]));
+            }
+            acc(bup2, make_float2(N0[na], N0[nb]));   // face (k-1, k), from the first colour of plane k-1
+            acc(bdown, make_float2(N2[na], N2[nb]));  // face (k, k+1), from the first colour of plane k+1
+            const float sa = __fdividef(num.x, den.x), sb = __fdividef(num.y, den.y);
+            const int pa = nA + (P ^ 1), pb = nB + (P ^ 1);  // first colour of plane k in the pair
+            float* xo = a.xout + (size_t)kk * plane + ib;
+            if (inA)
+                *reinterpret_cast<float2*>(xo + (size_t)jA * nx) =
+                    P ? make_float2(N1[pa], sa) : make_float2(sa, N1[pa]);
+            if (inB)
+                *reinterpret_cast<float2*>(xo + (size_t)jB * nx) =
+                    P ? make_float2(N1[pb], sb) : make_float2(sb, N1[pb]);
+        }
+        __syncthreads();
+        // refill the slot of plane k - 1 (no longer read) with plane k + 4
+        if (tid == 0 && k + 4 <= k1 + 1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 4);
+        }
+        // roll the plane window
+        bup2 = bup1;
+        bup1 = bup;
+        S1 = S2;
+        S2 = S3;
+        if (++S3 == NSLOT) {
+            S3 = 0;
+        }
+        if (S3 == 0) par3 ^= 1u;  // slot 0 starts its next fill
+        float* t = N0;
+        N0 = N1;
+        N1 = N2;
+        N2 = t;
+    }
+}
+
+// A x on the finest level with the density-formed coefficients (times h^2)
+__device__ __forceinline__ float stencil_rho(const Dims& d, const float* __restrict__ rho,
+                                             const float* __restrict__ x, int i, int j, int k) {
+    const int c = cid(d, i, j, k);
+    const float xc = x[c], rc = rho[c];
+    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, wrapk(k + 1, d.nz));
+    float s = 0.f;
+    if (i > 0) s = fmaf(beta_rho(rc, rho[c - 1]), xc - x[c - 1], s);
+    if (i < d.nx - 1) s = fmaf(beta_rho(rc, rho[c + 1]), xc - x[c + 1], s);
+    if (j > 0) s = fmaf(beta_rho(rc, rho[c - d.nx]), xc - x[c - d.nx], s);
+    if (j < d.ny - 1) s = fmaf(beta_rho(rc, rho[c + d.nx]), xc - x[c + d.nx], s);
+    s = fmaf(beta_rho(rc, rho[cb]), xc - x[cb], s);
+    s = fmaf(beta_rho(rc, rho[ct]), xc - x[ct], s);
+    return s;
+}
+
+__global__ void k_restrict_rho(Dims df, float ih2, const float* __restrict__ rho,
+                               const float* __restrict__ xf, const float* __restrict__ ff, Dims dc,
+                               float* __restrict__ fc, int kchunk) {
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    for (int K = k0; K < k1; ++K) {
+        float s = 0.f;
+        for (int c3 = 0; c3 < 8; ++c3) {
+            const int i = 2 * I + (c3 & 1), j = 2 * J + ((c3 >> 1) & 1), k = 2 * K + (c3 >> 2);
+            s += ff[cid(df, i, j, k)] - stencil_rho(df, rho, xf, i, j, k) * ih2;
+        }
+        fc[cid(dc, I, J, K)] = 0.125f * s;
+    }
+}
+
+struct Kahan32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__global__ void k_apply_A_dot_rho32(Dims d, float ih2, const float* __restrict__ rho,
+                                    const float* __restrict__ p, float* __restrict__ q,
+                                    double* __restrict__ part, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    Kahan32 ks;
+    if (act)
+        for (int k = k0; k < k1; ++k) {
+            const int c = cid(d, i, j, k);
+            const float v = stencil_rho(d, rho, p, i, j, k) * ih2;
+            q[c] = v;
+            ks.add(p[c] * v);
+        }
+    const double acc = block_sum(ks.value());
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
+// ---- tensor maps -------------------------------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// a (nx, ny, nz) FP32 array staged in SBX x SBY x 1 boxes, zero outside
+bool encode_plane_map(void* store, const Dims& d, const float* base) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * sizeof(float),
+                                   (cuuint64_t)d.nx * d.ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)SBX, (cuuint32_t)SBY, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(reinterpret_cast<CUtensorMap*>(store), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels) {
+    return sv && sv->precision == VOF_PREC_MIXED_FP32 && sv->mg_interp == VOF_MG_CONSTANT &&
+           g->nx % 4 == 0 && nlevels >= 2;
+}
+
+vof_status rho_path_setup(vof_ctx* c) {
+    const Level& L0 = c->lv[0];
+    if (!encode_plane_map(c->tmap[0], L0.d, L0.xf) || !encode_plane_map(c->tmap[1], L0.d, c->x32b) ||
+        !encode_plane_map(c->tmap[2], L0.d, c->rho32))
+        return set_err(c, VOF_ERR_CUDA, "TMA tensor-map encoding is unavailable");
+    if (cudaFuncSetAttribute(k_sweep_rho<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SWEEP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sweep_rho<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SWEEP_SMEM) != cudaSuccess)
+        return cuda_check(c, cudaGetLastError(), "smoother shared-memory attribute");
+    // z chunks: about three resident blocks per SM over the whole grid
+    const int tiles = ((L0.d.nx + STX - 1) / STX) * ((L0.d.ny + STY - 1) / STY);
+    int zc = std::max(1, (3 * c->sm_count + tiles / 2) / tiles);
+    zc = std::min(zc, L0.d.nz);
+    c->sweep_kchunk = (L0.d.nz + zc - 1) / zc;
+    return VOF_OK;
+}
+
+// one sweep: src == nullptr means the old x is zero
+void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0) {
+    const Level& L0 = c->lv[0];
+    SweepArgs a;
+    a.nx = L0.d.nx;
+    a.ny = L0.d.ny;
+    a.nz = L0.d.nz;
+    a.h2half = (float)(0.5 * L0.h * L0.h);
+    a.c0 = c0;
+    a.kchunk = c->sweep_kchunk;
+    a.f = L0.ff;
+    a.xout = dst;
+    a.err = c->scal + S_ERR;
+    const CUtensorMap* tx =
+        reinterpret_cast<const CUtensorMap*>(src == c->x32b ? c->tmap[1] : c->tmap[0]);
+    const CUtensorMap* tr = reinterpret_cast<const CUtensorMap*>(c->tmap[2]);
+    const dim3 grid((a.nx + STX - 1) / STX, (a.ny + STY - 1) / STY,
+                    (a.nz + a.kchunk - 1) / a.kchunk);
+    int m = timer_begin(c, T_SMOOTH0);
+    ++c->nlaunch;
+    if (src == nullptr)
+        k_sweep_rho<true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+    else
+        k_sweep_rho<false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+    timer_end(c, T_SMOOTH0, m);
+}
+
+void rho_restrict(vof_ctx* c) {
+    const Level &F = c->lv[0], &C = c->lv[1];
+    int m = timer_begin(c, T_RESTRICT0);
+    VOF_LAUNCH(c, k_restrict_rho, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)), c->rho32,
+               F.xf, F.ff, C.d, C.ff, C.L.kchunk);
+    timer_end(c, T_RESTRICT0, m);
+}
+
+void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
+    const Level& L = c->lv[0];
+    int m = timer_begin(c, T_RESIDUAL);
+    VOF_LAUNCH(c, k_apply_A_dot_rho32, L.L.grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
+               c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
+    timer_end(c, T_RESIDUAL, m);
+    finalize_sum(c, slot, L.L.nblocks, slot, 1.0);
+}

@@ -44,12 +44,46 @@ void readback(vof_ctx* c) {
     cudaStreamSynchronize(c->st);
 }
 
+template <class T>
+void vcycle(vof_ctx* c, int l);
+
+// Finest level of the mixed V-cycle with the density-formed coefficients:
+// nu_pre red-black sweeps from a zero guess, restriction, the coarse
+// correction, nu_post black-red sweeps. Sweeps ping-pong between xf and
+// x32b; the pre-smoothing starts on the buffer that makes it end in xf.
+void vcycle0_rho(vof_ctx* c) {
+    Level& L0 = c->lv[0];
+    float* const A = L0.xf;
+    float* const B = c->x32b;
+    const float* cur = nullptr;  // zero
+    float* dst = (c->sv.nu_pre % 2 == 1) ? A : B;
+    for (int s = 0; s < c->sv.nu_pre; ++s) {
+        rho_sweep(c, cur, dst, 0);
+        cur = dst;
+        dst = (dst == A) ? B : A;
+    }
+    rho_restrict(c);
+    vcycle<float>(c, 1);
+    mg_prolong<float>(c, c->lv[1], L0);
+    for (int s = 0; s < c->sv.nu_post; ++s) {
+        rho_sweep(c, cur, dst, 1);
+        cur = dst;
+        dst = (dst == A) ? B : A;
+    }
+    if (cur != A)
+        cudaMemcpyAsync(A, cur, sizeof(float) * (size_t)L0.ncells, cudaMemcpyDeviceToDevice, c->st);
+}
+
 // symmetric V-cycle on the level arrays of type T (x <- M f at level l)
 template <class T>
 void vcycle(vof_ctx* c, int l) {
     const Level& L = c->lv[l];
     if (l == (int)c->lv.size() - 1) {
         mg_coarse<T>(c, L);
+        return;
+    }
+    if (sizeof(T) == sizeof(float) && l == 0 && c->use_rho) {
+        vcycle0_rho(c);
         return;
     }
     mg_zero<T>(c, L);
@@ -86,11 +120,13 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
     std::vector<Dims> dims = level_dims(g);
     if (nlevels) *nlevels = (int)dims.size();
     const bool mixed = sv && sv->precision == VOF_PREC_MIXED_FP32;
+    const bool rho = rho_path_eligible(g, sv, (int)dims.size());
     const size_t elt = mixed ? sizeof(float) : sizeof(double);
     size_t b = 0;
     for (size_t l = mixed ? 0 : 1; l < dims.size(); ++l) {
         const size_t n = (size_t)dims[l].nx * dims[l].ny * dims[l].nz;
-        b += faces_bytes(dims[l], elt) + 2 * n * elt;
+        // the density-formed finest level keeps x, f, a second x and rho
+        b += (l == 0 && rho) ? 4 * n * elt : faces_bytes(dims[l], elt) + 2 * n * elt;
     }
     if (mixed) b += 3 * (size_t)dims[0].nx * dims[0].ny * dims[0].nz * sizeof(float);  // e, p, q
     if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
@@ -107,6 +143,7 @@ vof_status mg_allocate(vof_ctx* c) {
     std::vector<Dims> dims = level_dims(&c->g);
     c->lv.resize(dims.size());
     const bool mixed = c->sv.precision == VOF_PREC_MIXED_FP32;
+    c->use_rho = rho_path_eligible(&c->g, &c->sv, (int)dims.size());
     double h = c->g.h;
     for (size_t l = 0; l < dims.size(); ++l) {
         Level& L = c->lv[l];
@@ -126,6 +163,15 @@ vof_status mg_allocate(vof_ctx* c) {
         const size_t nv = (size_t)L.d.nx * (L.d.ny + 1) * L.d.nz;
         const size_t n = L.ncells;
         const size_t elt = mixed ? sizeof(float) : sizeof(double);
+        if (l == 0 && c->use_rho) {
+            float* q = (float*)dev_alloc(c, sizeof(float) * 4 * n);
+            if (!q) return set_err(c, VOF_ERR_OOM, "allocation of the finest level failed");
+            L.xf = q;
+            L.ff = q + n;
+            c->x32b = q + 2 * n;
+            c->rho32 = q + 3 * n;
+            continue;
+        }
         void* p = dev_alloc(c, elt * (nu + nv + 3 * n));
         if (!p) return set_err(c, VOF_ERR_OOM, "allocation of a multigrid level failed");
         if (mixed) {
@@ -176,6 +222,7 @@ vof_status mg_allocate(vof_ctx* c) {
         // shift: the liquid face coefficient (the smallest physical one) per face
         c->dense_shift = 1.0 / c->ph.rho_l;
     }
+    if (c->use_rho) return rho_path_setup(c);
     return VOF_OK;
 }
 
@@ -186,6 +233,14 @@ void mg_build_coefficients(vof_ctx* c) {
         return;
     }
     const Level& L0 = c->lv[0];
+    if (c->use_rho) {
+        // the finest level forms its coefficients from rho32 (written with
+        // the FP64 ones); level 1 averages the FP64 faces
+        mg_coarsen_beta_from64(c, L0, c->lv[1]);
+        for (size_t l = 2; l < c->lv.size(); ++l) mg_coarsen_beta<float>(c, c->lv[l - 1], c->lv[l]);
+        if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
+        return;
+    }
     const int nu = (L0.d.nx + 1) * L0.d.ny * L0.d.nz, nv = L0.d.nx * (L0.d.ny + 1) * L0.d.nz;
     mg_to_f32(c, c->bx, L0.bxf, nu);
     mg_to_f32(c, c->by, L0.byf, nv);
@@ -220,10 +275,15 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
         cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
         while (inner_total < c->sv.max_iter && inner_total < inner_cap) {
             ++inner_total;
-            k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
+            if (c->use_rho)
+                rho_apply_A_dot(c, c->p32, c->q32, S_PQ);
+            else
+                k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
             launch_scalar_alpha(c);
             k32_cg_update(c, n, c->e32, r32, c->p32, c->q32, S_RR);
             readback(c);
+            if (c->hbuf[S_ERR] != 0.0)
+                return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
             const double rr = c->hbuf[S_RR];
             if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
             if (rr <= tol_in * tol_in * rr0) break;
@@ -237,6 +297,8 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
         launch_residual_to32(c, P, c->b, r32, S_RR);
         readback(c);
         res = std::sqrt(c->hbuf[S_RR]) / bnorm;
+        if (c->hbuf[S_ERR] != 0.0)
+            return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
         if (!std::isfinite(res)) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
         ++outer;
         converged = res <= c->sv.rtol;
@@ -264,6 +326,7 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
     Level& L0 = c->lv[0];
     mg_build_coefficients(c);
     if (c->sv.precision == VOF_PREC_MIXED_FP32) {
+        cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), c->st);
         launch_copy(c, c->b, b_in, n);
         launch_sub_mean(c, c->b, n, S_MEAN);
         launch_dot(c, c->b, c->b, n, S_BB);

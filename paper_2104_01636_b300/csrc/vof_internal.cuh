@@ -164,6 +164,15 @@ struct vof_ctx {
     double t_ms[T_NCLASS] = {0};
     long long t_n[T_NCLASS] = {0};
 
+    // finest level of the mixed V-cycle with density-formed coefficients
+    // (k_smooth_tma.cu): FP32 density, second x buffer, TMA maps of
+    // x (level-0 xf), x32b and rho32
+    bool use_rho = false;
+    float* rho32 = nullptr;
+    float* x32b = nullptr;
+    int sweep_kchunk = 1;
+    alignas(64) unsigned char tmap[3][128];
+
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
 };
@@ -179,6 +188,7 @@ enum ScalarSlot {
     S_BETA,       // CG direction update
     S_MEAN,       // mean removed
     S_VOL0, S_VOL1, S_CLIP0, S_CLIP1, S_CLIP2, S_MAXDIV, S_MAXU, S_FALLBACK, S_CFL, S_SUM,
+    S_ERR,        // a kernel gave up a bounded wait (set to 1)
     S_NSCALARS
 };
 
@@ -235,6 +245,14 @@ void k32_p_update(vof_ctx* c, int n, float* p, const float* z);
 void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x);
 void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r32, int slot);
 void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
+
+// finest level of the mixed V-cycle from the cell density (k_smooth_tma.cu)
+bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels);
+vof_status rho_path_setup(vof_ctx* c);
+void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0);
+void rho_restrict(vof_ctx* c);
+void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
+void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
 
 // vof (k_vof.cu)
 void launch_vof_mask_volume(vof_ctx* c, const double* alpha, int slot);

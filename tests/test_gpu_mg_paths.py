@@ -1,0 +1,66 @@
+"""The two finest-level forms of the mixed-precision V-cycle: coefficients
+formed from the cell density by the TMA-staged fused sweep (grids with
+nx % 4 == 0 and at least two levels) and stored FP32 face arrays (other
+grids). Both must reach the FP64 tolerance, agree with the oracle, converge
+in about as many iterations as the FP64 path and be deterministic."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_01636_b300 import inputs as I
+from gpu_util import ctx, dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(dims, nbub, seed, d_cells=8.0):
+    g = I.Grid(*dims)
+    c = I.place_spheres(g, nbub, d_cells * g.h, seed, wall_gap=g.h)
+    a = I.sphere_alpha(g, c, d_cells * g.h / 2)
+    rng = np.random.default_rng(seed)
+    Pstar = rng.normal(size=g.shapes()[0])
+    Pstar -= Pstar.mean()
+    ph = I.Phys()
+    bx, by, bz = oracle.beta(g, ph, a)
+    b = oracle.apply_A(g, bx, by, bz, Pstar)
+    return g, ph, a, b, Pstar
+
+
+def _solve(g, ph, a, b, **kw):
+    with ctx(g, ph, **kw) as C:
+        p = dev(np.zeros_like(b))
+        rep = C.pressure_solve(dev(a), dev(b), p)
+        return host(p), rep
+
+
+@pytest.mark.parametrize("dims", [(64, 48, 64),    # density path, partial tiles in y
+                                  (96, 40, 36),    # density path, ragged in x and y
+                                  (66, 40, 32)])   # nx % 4 != 0: stored FP32 faces
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_mixed_paths_reach_fp64_tolerance(dims, nu):
+    g, ph, a, b, Pstar = _problem(dims, 4, 31)
+    P64, r64 = _solve(g, ph, a, b, rtol=1e-12, precision=0, nu_pre=nu, nu_post=nu)
+    P32, r32 = _solve(g, ph, a, b, rtol=1e-12, precision=1, nu_pre=nu, nu_post=nu)
+    assert r32["res"] <= 1e-12
+    assert r32["iters"] <= 1.5 * r64["iters"] + 6, (r32["iters"], r64["iters"])
+    assert rel_l2(P32, Pstar) < 1e-8
+    assert rel_l2(P32, P64) < 1e-8
+
+
+def test_density_path_is_deterministic():
+    g, ph, a, b, _ = _problem((128, 96, 64), 10, 41)
+    P1, r1 = _solve(g, ph, a, b, rtol=1e-10, precision=1)
+    P2, r2 = _solve(g, ph, a, b, rtol=1e-10, precision=1)
+    assert r1["iters"] == r2["iters"]
+    assert np.array_equal(P1, P2)
+
+
+def test_density_path_matches_oracle_at_paper_ratio():
+    """Air-water density ratio 833 with many bubbles on a 96 x 96 x 64 grid."""
+    g, ph, a, b, _ = _problem((96, 96, 64), 12, 43, d_cells=12.0)
+    bx, by, bz = oracle.beta(g, ph, a)
+    Po, orep, st = oracle.solve(g, bx, by, bz, b, rtol=1e-11)
+    assert st == 0
+    P, rep = _solve(g, ph, a, b, rtol=1e-11, precision=1)
+    assert rep["res"] <= 1e-11
+    assert rel_l2(P, Po) < 1e-6
