@@ -93,7 +93,14 @@ typedef struct {
     double coarse_tol;    /* relative residual target there; 0 = default      */
     int mg_interp;        /* VOF_MG_CONSTANT or VOF_MG_TRILINEAR prolongation
                              (restriction is its transpose / 8 in both)       */
+    int mg_coarsen;       /* coarse-level coefficients: VOF_COARSEN_FACE_MEAN
+                             (mean of the four fine faces a coarse face
+                             covers) or VOF_COARSEN_DENSITY_MEAN (density
+                             averaged over the eight children, faces then
+                             formed by the fine rule 2 / (rho_L + rho_R))    */
 } vof_solver;
+
+enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 

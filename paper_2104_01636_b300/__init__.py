@@ -50,7 +50,8 @@ class CSolver(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("mg_omega", ctypes.c_double), ("coarse_iters", ctypes.c_int),
-                ("coarse_tol", ctypes.c_double), ("mg_interp", ctypes.c_int)]
+                ("coarse_tol", ctypes.c_double), ("mg_interp", ctypes.c_int),
+                ("mg_coarsen", ctypes.c_int)]
 
 
 class CReport(ctypes.Structure):
@@ -145,10 +146,14 @@ def c_phys(p) -> CPhys:
                  int(p.conv_scheme), int(p.kappa_mode), float(p.kappa_exact))
 
 
+COARSEN_FACE_MEAN, COARSEN_DENSITY_MEAN = 0, 1
+
+
 def c_solver(precision=PREC_FP64, rtol=1e-10, max_iter=200, nu_pre=2, nu_post=2, mg_omega=0.0,
-             coarse_iters=0, coarse_tol=0.0, mg_interp=0) -> CSolver:
+             coarse_iters=0, coarse_tol=0.0, mg_interp=0, mg_coarsen=COARSEN_FACE_MEAN) -> CSolver:
     return CSolver(int(precision), float(rtol), int(max_iter), int(nu_pre), int(nu_post),
-                   float(mg_omega), int(coarse_iters), float(coarse_tol), int(mg_interp))
+                   float(mg_omega), int(coarse_iters), float(coarse_tol), int(mg_interp),
+                   int(mg_coarsen))
 
 
 def workspace_bytes(grid, solver: CSolver | None = None) -> int:

@@ -293,7 +293,8 @@ extern "C" {
 vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, size_t* bytes) {
     std::string why;
     if (!grid_ok(grid, why) || !bytes) return VOF_ERR_ARG;
-    vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2, 0.0, 0, 0.0, VOF_MG_CONSTANT};
+    vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2, 0.0, 0, 0.0, VOF_MG_CONSTANT,
+                   VOF_COARSEN_FACE_MEAN};
     *bytes = workspace_bytes(grid, solver ? solver : &def);
     return VOF_OK;
 }
@@ -313,6 +314,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
         solver->nu_pre != solver->nu_post || !(solver->mg_omega >= 0.0) ||
         solver->mg_omega > 2.0 || solver->coarse_iters < 0 || !(solver->coarse_tol >= 0.0) ||
         (solver->mg_interp != VOF_MG_CONSTANT && solver->mg_interp != VOF_MG_TRILINEAR) ||
+        (solver->mg_coarsen != VOF_COARSEN_FACE_MEAN &&
+         solver->mg_coarsen != VOF_COARSEN_DENSITY_MEAN) ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
         return VOF_ERR_ARG;
     const size_t need = workspace_bytes(grid, solver);

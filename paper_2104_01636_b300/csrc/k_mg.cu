@@ -247,6 +247,39 @@ __global__ void k_coarsen_beta_t(Dims df, const TI* __restrict__ bxf, const TI* 
     }
 }
 
+// density coarsening: a coarse cell's density is the mean of its eight
+// children's; coarse faces then follow the fine-grid rule 1 / mean(rho)
+template <class T>
+__global__ void k_avg8_t(Dims df, const T* __restrict__ rf, Dims dc, T* __restrict__ rc,
+                         int kchunk) {
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    for (int K = k0; K < k1; ++K) {
+        T s = T(0);
+        for (int c3 = 0; c3 < 8; ++c3)
+            s += rf[cid(df, 2 * I + (c3 & 1), 2 * J + ((c3 >> 1) & 1), 2 * K + (c3 >> 2))];
+        rc[cid(dc, I, J, K)] = T(0.125) * s;
+    }
+}
+
+template <class T>
+__global__ void k_beta_from_rho_t(Dims d, const T* __restrict__ rho, T* __restrict__ bx,
+                                  T* __restrict__ by, T* __restrict__ bz, int kchunk) {
+    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (i >= d.nx || j >= d.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    for (int k = k0; k < k1; ++k) {
+        const int c = cid(d, i, j, k);
+        const T r = rho[c];
+        bx[uid(d, i, j, k)] = i == 0 ? T(0) : T(2) / (rho[c - 1] + r);
+        if (i == d.nx - 1) bx[uid(d, d.nx, j, k)] = T(0);
+        by[vid(d, i, j, k)] = j == 0 ? T(0) : T(2) / (rho[c - d.nx] + r);
+        if (j == d.ny - 1) by[vid(d, i, d.ny, k)] = T(0);
+        bz[wid(d, i, j, k)] = T(2) / (rho[cid(d, i, j, wrapk(k - 1, d.nz))] + r);
+    }
+}
+
 // Jacobi-preconditioned CG on the coarsest level, one thread block; vectors
 // in T, reductions in FP64. Bounded iteration count; the result is made
 // mean-free (the operator's null space is the constants).
@@ -570,6 +603,16 @@ void mg_coarsen_beta(vof_ctx* c, const Level& F, const Level& C) {
     VOF_LAUNCH(c, k_coarsen_beta_t<T>, C.L.grid, C.L.block, F.d, a.bx, a.by, a.bz, C.d, b.bx, b.by,
                b.bz, C.L.kchunk);
 }
+
+template <class T>
+void mg_coarsen_density(vof_ctx* c, const T* rf, const Level& F, const Level& C) {
+    const LA<T> b = arrays<T>(C);
+    VOF_LAUNCH(c, k_avg8_t<T>, C.L.grid, C.L.block, F.d, rf, C.d, (T*)C.rho, C.L.kchunk);
+    VOF_LAUNCH(c, k_beta_from_rho_t<T>, C.L.grid, C.L.block, C.d, (const T*)C.rho, b.bx, b.by,
+               b.bz, C.L.kchunk);
+}
+template void mg_coarsen_density<double>(vof_ctx*, const double*, const Level&, const Level&);
+template void mg_coarsen_density<float>(vof_ctx*, const float*, const Level&, const Level&);
 
 // FP64 finest-level coefficients averaged straight into the FP32 level 1
 // (the mixed V-cycle's finest level keeps no FP32 face arrays)

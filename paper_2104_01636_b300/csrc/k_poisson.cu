@@ -51,14 +51,15 @@ __device__ __forceinline__ double stencil(const Dims& d, const double* __restric
 
 __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double rg,
                        double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
-                       float* __restrict__ rho32, int kchunk) {
+                       float* __restrict__ rho32, double* __restrict__ rho64, int kchunk) {
     CellIdx r = cell_range(d, kchunk);
     if (!r.act) return;
     const int i = r.i, j = r.j;
     for (int k = r.k0; k < r.k1; ++k) {
         const int c = cid(d, i, j, k);
         const double rc = a[c] * rl + (1.0 - a[c]) * rg;
-        if (rho32) rho32[c] = (float)rc;  // the mixed V-cycle's finest-level density
+        if (rho32) rho32[c] = (float)rc;  // finest-level density of the multigrid
+        if (rho64) rho64[c] = rc;
         // x-face i (between i-1 and i); the last thread also writes the wall face nx
         if (i == 0) {
             bx[uid(d, 0, j, k)] = 0.0;
@@ -242,7 +243,7 @@ inline int flat_blocks(int n) {
 void launch_beta(vof_ctx* c, const double* alpha) {
     const Launch& L = c->Lc;
     VOF_LAUNCH(c, k_beta, L.grid, L.block, c->d, alpha, c->ph.rho_l, c->ph.rho_g, c->bx, c->by,
-               c->bz, c->use_rho ? c->rho32 : nullptr, L.kchunk);
+               c->bz, c->rho32, c->rho64, L.kchunk);
 }
 
 void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y) {

@@ -247,7 +247,7 @@ void launch_reconstruct(vof_ctx* c, const double* alpha) {
     cudaMemsetAsync(c->if_count, 0, sizeof(int), c->st);
     VOF_LAUNCH(c, k_if_list, L.grid, L.block, c->d, alpha, c->has, c->if_list, c->if_count,
                L.kchunk);
-    VOF_LAUNCH(c, k_reconstruct_list, c->sm_count * 4, 128, geo(c), alpha, c->if_list,
+    VOF_LAUNCH(c, k_reconstruct_list, c->sm_count * 16, 128, geo(c), alpha, c->if_list,
                c->if_count, c->has, (Plane*)c->plane);
     timer_end(c, T_ADVECT, m);
 }

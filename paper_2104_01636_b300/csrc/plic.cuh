@@ -27,20 +27,11 @@ __device__ __forceinline__ double vol_C(double b1, double b2, double b3, double 
     const double p = a - b1, q = a - b2;
     return (a * a + a * p + p * p - q * q * q / b1) / (6.0 * b2 * b3);
 }
-__device__ __forceinline__ double dvol_C(double b1, double b2, double b3, double a) {
-    const double p = a - b1, q = a - b2;
-    return (a + p - q * q / b1) / (2.0 * b2 * b3);
-}
 // piece E: max(b3) <= a <= 1/2 with b1+b2 >= b3
 __device__ __forceinline__ double vol_E(double b1, double b2, double b3, double a) {
     const double p = a - b1, s = a - b2, r = a - b3;
     const double t = b1 > 0.0 ? (s * s * s + r * r * r) / b1 : 0.0;
     return (a * a + a * p + p * p - t) / (6.0 * b2 * b3);
-}
-__device__ __forceinline__ double dvol_E(double b1, double b2, double b3, double a) {
-    const double p = a - b1, s = a - b2, r = a - b3;
-    const double t = b1 > 0.0 ? (s * s + r * r) / b1 : 0.0;
-    return (a + p - t) / (2.0 * b2 * b3);
 }
 
 // V(a) for sorted, normalised b and a in [0, 1/2]
@@ -70,42 +61,58 @@ __device__ __forceinline__ double volume(double m0, double m1, double m2, double
     return a <= 0.5 ? vol_half(b1, b2, b3, a) : 1.0 - vol_half(b1, b2, b3, 1.0 - a);
 }
 
-// Safeguarded Newton on one cubic piece, bracket [lo, hi] with V(lo) <= V
-// <= V(hi). Bounded iteration count.
-template <bool PIECE_E>
-__device__ __forceinline__ double newton_piece(double b1, double b2, double b3, double V,
-                                               double lo, double hi, double Vlo, double Vhi) {
+__device__ __forceinline__ double rcp_approx64(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+// Normalised plane constant a in [0, 1/2] with vol_half(b, a) = V, written
+// for warps whose lanes fall in different pieces: the divisions are hoisted
+// (reciprocals formed once), and the two cubic pieces C and E share one
+// Newton loop (E adds the term of the third vertex), so lanes in C and E
+// run the same instructions. Newton steps use an approximate reciprocal of
+// the derivative; the safeguarding bracket keeps every iterate inside the
+// piece, and the iteration stops on a relative step or bracket of 2.3e-16.
+__device__ __forceinline__ double solve_half(double b1, double b2, double b3, double V) {
+    if (V <= 0.0) return 0.0;
+    if (b2 <= 0.0) return V;  // axis-aligned plane: V(a) = a
+    const double i6 = 1.0 / (6.0 * b2 * b3);  // 1 / (6 b2 b3)
+    const double ib1 = b1 > 0.0 ? 1.0 / b1 : 0.0;
+    const double V1 = b1 * b1 * i6;
+    if (V < V1) return cbrt(6.0 * b1 * b2 * b3 * V);
+    const double V2 = (3.0 * b2 * (b2 - b1) + b1 * b1) * i6;
+    if (V < V2) return 0.5 * b1 + sqrt(fmax(2.0 * b2 * b3 * V - b1 * b1 / 12.0, 0.0));
+    const double b12 = b1 + b2;
+    double lo, hi, Vlo, Vhi;
+    bool e_piece;
+    if (b12 <= b3) {
+        const double V3 = b12 / (2.0 * b3);
+        if (!(V < V3 && b1 > 0.0)) return V * b3 + 0.5 * b12;  // piece D
+        lo = b2; hi = b12; Vlo = V2; Vhi = V3; e_piece = false;
+    } else {
+        double V3 = V2;
+        if (b1 > 0.0) {
+            const double p = b3 - b1, q = b3 - b2;
+            V3 = (b3 * b3 + b3 * p + p * p - q * q * q * ib1) * i6;
+        }
+        if (V < V3) { lo = b2; hi = b3; Vlo = V2; Vhi = V3; e_piece = false; }
+        else { lo = b3; hi = 0.5; Vlo = V3; Vhi = 0.5; e_piece = true; }
+    }
+    const double i2 = 3.0 * i6;  // 1 / (2 b2 b3)
     double a = (Vhi > Vlo) ? lo + (hi - lo) * (V - Vlo) / (Vhi - Vlo) : 0.5 * (lo + hi);
     for (int it = 0; it < 48; ++it) {
-        const double f = (PIECE_E ? vol_E(b1, b2, b3, a) : vol_C(b1, b2, b3, a)) - V;
+        const double p = a - b1, q = a - b2, r = e_piece ? a - b3 : 0.0;
+        const double f = (a * a + a * p + p * p - (q * q * q + r * r * r) * ib1) * i6 - V;
+        const double df = (a + p - (q * q + r * r) * ib1) * i2;
         if (f > 0.0) hi = a; else lo = a;
-        const double df = PIECE_E ? dvol_E(b1, b2, b3, a) : dvol_C(b1, b2, b3, a);
-        double an = df > 0.0 ? a - f / df : 0.5 * (lo + hi);
+        double an = df > 0.0 ? a - f * rcp_approx64(df) : 0.5 * (lo + hi);
         if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
         const double step = fabs(an - a);
         a = an;
         if (step <= 2.3e-16 * a || hi - lo <= 2.3e-16 * hi) break;
     }
     return a;
-}
-
-// Normalised plane constant a in [0, 1/2] with vol_half(b, a) = V.
-__device__ __forceinline__ double solve_half(double b1, double b2, double b3, double V) {
-    if (V <= 0.0) return 0.0;
-    if (b2 <= 0.0) return V;  // axis-aligned plane: V(a) = a
-    const double V1 = b1 > 0.0 ? b1 * b1 / (6.0 * b2 * b3) : 0.0;
-    if (V < V1) return cbrt(6.0 * b1 * b2 * b3 * V);
-    const double V2 = (3.0 * b2 * (b2 - b1) + b1 * b1) / (6.0 * b2 * b3);
-    if (V < V2) return 0.5 * b1 + sqrt(fmax(2.0 * b2 * b3 * V - b1 * b1 / 12.0, 0.0));
-    const double b12 = b1 + b2;
-    if (b12 <= b3) {
-        const double V3 = b12 / (2.0 * b3);
-        if (V < V3 && b1 > 0.0) return newton_piece<false>(b1, b2, b3, V, b2, b12, V2, V3);
-        return V * b3 + 0.5 * b12;  // piece D
-    }
-    const double V3 = b1 > 0.0 ? vol_C(b1, b2, b3, b3) : V2;
-    if (V < V3) return newton_piece<false>(b1, b2, b3, V, b2, b3, V2, V3);
-    return newton_piece<true>(b1, b2, b3, V, b3, 0.5, V3, 0.5);
 }
 
 // Plane constant d with volume(m, d) = alpha, 0 < alpha < 1, m != 0.
@@ -116,7 +123,8 @@ __device__ __forceinline__ double plane_constant(double m0, double m1, double m2
     if (m2 < 0.0) { off += m2; m2 = -m2; }
     const double S = m0 + m1 + m2;
     if (!(S > 0.0)) return 0.0;
-    double b1 = m0 / S, b2 = m1 / S, b3 = m2 / S;
+    const double iS = 1.0 / S;
+    double b1 = m0 * iS, b2 = m1 * iS, b3 = m2 * iS;
     sort3(b1, b2, b3);
     b3 = 1.0 - b1 - b2;
     const double V = alpha <= 0.5 ? alpha : 1.0 - alpha;

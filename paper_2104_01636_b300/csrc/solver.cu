@@ -132,6 +132,13 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
     if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
         for (size_t l = 0; l + 1 < dims.size(); ++l)
             b += (size_t)dims[l].nx * dims[l].ny * dims[l].nz * elt;
+    if (sv && sv->mg_coarsen == VOF_COARSEN_DENSITY_MEAN) {
+        for (size_t l = 1; l < dims.size(); ++l)
+            b += (size_t)dims[l].nx * dims[l].ny * dims[l].nz * elt;
+        const size_t n0 = (size_t)dims[0].nx * dims[0].ny * dims[0].nz;
+        if (!mixed) b += n0 * sizeof(double);  // FP64 finest-level density
+        else if (!rho) b += n0 * sizeof(float);
+    }
     const Dims& dc = dims.back();
     const size_t nc = (size_t)dc.nx * dc.ny * dc.nz;
     b += 4 * nc * sizeof(double);
@@ -206,6 +213,22 @@ vof_status mg_allocate(vof_ctx* c) {
             c->lv[l].rs = q;
         }
     }
+    if (c->sv.mg_coarsen == VOF_COARSEN_DENSITY_MEAN) {
+        const size_t elt = mixed ? sizeof(float) : sizeof(double);
+        for (size_t l = 1; l < c->lv.size(); ++l) {
+            void* q = dev_alloc(c, elt * (size_t)c->lv[l].ncells);
+            if (!q) return set_err(c, VOF_ERR_OOM, "allocation of a coarse density failed");
+            c->lv[l].rho = q;
+        }
+        const size_t n0 = (size_t)c->lv[0].ncells;
+        if (!mixed) {
+            c->rho64 = (double*)dev_alloc(c, sizeof(double) * n0);
+            if (!c->rho64) return set_err(c, VOF_ERR_OOM, "allocation of the density failed");
+        } else if (!c->use_rho) {
+            c->rho32 = (float*)dev_alloc(c, sizeof(float) * n0);
+            if (!c->rho32) return set_err(c, VOF_ERR_OOM, "allocation of the density failed");
+        }
+    }
     const Level& Lc = c->lv.back();
     void* p = dev_alloc(c, 4 * sizeof(double) * (size_t)Lc.ncells);
     if (!p) return set_err(c, VOF_ERR_OOM, "allocation of the coarse scratch failed");
@@ -227,6 +250,30 @@ vof_status mg_allocate(vof_ctx* c) {
 }
 
 void mg_build_coefficients(vof_ctx* c) {
+    const bool dens = c->sv.mg_coarsen == VOF_COARSEN_DENSITY_MEAN;
+    if (dens && c->lv.size() > 1) {
+        // coarse levels from the averaged density; the finest level keeps
+        // its own coefficients (FP64 faces, their FP32 copies or rho32)
+        const Level& L0 = c->lv[0];
+        if (c->sv.precision == VOF_PREC_FP64) {
+            mg_coarsen_density<double>(c, c->rho64, L0, c->lv[1]);
+            for (size_t l = 2; l < c->lv.size(); ++l)
+                mg_coarsen_density<double>(c, (const double*)c->lv[l - 1].rho, c->lv[l - 1], c->lv[l]);
+            if (c->dense_n > 0) mg_dense_setup<double>(c, c->lv.back());
+            return;
+        }
+        if (!c->use_rho) {
+            const int nu = (L0.d.nx + 1) * L0.d.ny * L0.d.nz, nv = L0.d.nx * (L0.d.ny + 1) * L0.d.nz;
+            mg_to_f32(c, c->bx, L0.bxf, nu);
+            mg_to_f32(c, c->by, L0.byf, nv);
+            mg_to_f32(c, c->bz, L0.bzf, L0.ncells);
+        }
+        mg_coarsen_density<float>(c, c->rho32, L0, c->lv[1]);
+        for (size_t l = 2; l < c->lv.size(); ++l)
+            mg_coarsen_density<float>(c, (const float*)c->lv[l - 1].rho, c->lv[l - 1], c->lv[l]);
+        if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
+        return;
+    }
     if (c->sv.precision == VOF_PREC_FP64) {
         for (size_t l = 1; l < c->lv.size(); ++l) mg_coarsen_beta<double>(c, c->lv[l - 1], c->lv[l]);
         if (c->dense_n > 0) mg_dense_setup<double>(c, c->lv.back());

@@ -114,6 +114,7 @@ struct Level {
     float *bxf = nullptr, *byf = nullptr, *bzf = nullptr;  // FP32 copies (mixed)
     float *xf = nullptr, *ff = nullptr;
     void* rs = nullptr;  // residual scratch for full-weighting restriction (T per cell)
+    void* rho = nullptr; // cell density (T per cell), levels >= 1 with density coarsening
     Launch L;
 };
 
@@ -168,7 +169,8 @@ struct vof_ctx {
     // (k_smooth_tma.cu): FP32 density, second x buffer, TMA maps of
     // x (level-0 xf), x32b and rho32
     bool use_rho = false;
-    float* rho32 = nullptr;
+    float* rho32 = nullptr;   // also the mixed path's density for density coarsening
+    double* rho64 = nullptr;  // FP64 path: finest-level density for density coarsening
     float* x32b = nullptr;
     int sweep_kchunk = 1;
     alignas(64) unsigned char tmap[3][128];
@@ -235,6 +237,9 @@ template <class T> void mg_coarsen_beta(vof_ctx* c, const Level& fine, const Lev
 template <class T> void mg_coarse(vof_ctx* c, const Level& L);
 template <class T> void mg_zero(vof_ctx* c, const Level& L);
 template <class T> void mg_dense_setup(vof_ctx* c, const Level& L);
+// density coarsening: rho_c = mean of the eight children, faces 2 / (rho_L + rho_R)
+template <class T> void mg_coarsen_density(vof_ctx* c, const T* rho_fine, const Level& fine,
+                                           const Level& coarse);
 constexpr int DENSE_MAX = 1536;  // largest coarsest level solved by the dense inverse
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
 // inner FP32 Krylov of the mixed solve (k_mg.cu) and its FP64 residual (k_poisson.cu)
