@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests in the serving run (0 skips it)")
+    ap.add_argument("--ensemble-cases", type=int, default=64,
+                    help="cases in the ensemble run (0 skips it)")
     return ap.parse_args()
 
 
@@ -277,6 +279,38 @@ def serving(vd, I, n_req: int, do_fp64: bool):
     return out
 
 
+def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int = 2):
+    """n independent 48x48x96 ducts (4-16 spheres each, seeded) advanced
+    together, fields resident on the device; mixed precision, rtol 1e-8.
+    Timed on the host clock around whole ensemble steps (each call returns
+    when every case has finished), against the same cases on one stream."""
+    import numpy as np
+    import torch
+    cases = I.ensemble_cases(n_cases, dims=(48, 48, 96), seed=2109)
+    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500)
+    out = {"cases": n_cases, "grid": "48x48x96", "cells_per_case": cases[0].grid.ncells,
+           "precision": "mixed", "rtol": 1e-8, "steps": steps}
+    for label, ns in (("streams", streams), ("one_stream", 1)):
+        fields = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in c.state()]
+                  for c in cases]
+        torch.cuda.synchronize()
+        with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], sv, n_streams=ns) as E:
+            dts = [c.dt for c in cases]
+            for s in range(warmup):
+                E.step(fields, dts, s)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(warmup, warmup + steps):
+                E.step(fields, dts, s)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / steps
+        del fields
+        out[label] = {"n_streams": ns, "ms_per_ensemble_step": ms,
+                      "case_steps_per_s": n_cases / (ms / 1e3),
+                      "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3)}
+    return out
+
+
 # ----------------------------------------------------------------------------
 def main():
     args = parse()
@@ -419,6 +453,9 @@ def main():
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = serving(vd, I, args.serve_requests, not args.no_fp64_compare)
+    ens = None
+    if world == 1 and args.ensemble_cases > 0:
+        ens = ensemble(vd, I, args.ensemble_cases)
 
     if rank != 0:
         if dist is not None:
@@ -449,6 +486,7 @@ def main():
         "clocks": ck,
         "fp64_path": fp64,
         "serving": serve,
+        "ensemble": ens,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -309,6 +309,30 @@ vof_status vof_wait(vof_server* server, unsigned long long id, vof_result* resul
 /* Finishes every queued request, then frees the server. */
 vof_status vof_server_destroy(vof_server* server);
 
+/* ---- ensemble of independent ducts ---------------------------------------
+ * The paper has no ensemble mode; this advances n_cases independent cases of
+ * one grid size by one time step per call, fields resident on the device.
+ * Each case has its own context (workspace as vof_create); cases are dealt
+ * round-robin to n_streams worker threads, each with its own CUDA stream, so
+ * their kernels overlap on the GPU. A case's result is bitwise that of the
+ * same case stepped alone by step(). Uses the current device. */
+typedef struct vof_ensemble vof_ensemble;
+
+/* phys: n_phys = 1 (shared) or n_cases entries (per case, e.g. rho0).
+ * n_streams in [1, 64]. */
+vof_status vof_ensemble_create(const vof_grid* grid, const vof_phys* phys, int n_phys,
+                               const vof_solver* solver, int n_cases, int n_streams,
+                               vof_ensemble** out);
+/* fields: 8 * n_cases DEVICE pointers, case c at [8c .. 8c+7] in the order
+ * alpha, uc, vc, wc, u, v, w, p (layouts as in step()); dt: n_cases time
+ * steps (host array). Blocks until every case has finished its step.
+ * status (n_cases, may be NULL) receives each case's status, reports
+ * (n_cases, may be NULL) each case's report; the return value is the first
+ * non-OK status, else VOF_OK. */
+vof_status vof_ensemble_step(vof_ensemble* ensemble, double* const* fields, const double* dt,
+                             long long step_index, vof_status* status, vof_report* reports);
+vof_status vof_ensemble_destroy(vof_ensemble* ensemble);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,10 @@ def load() -> ctypes.CDLL:
         "vof_poll": [_VP, ctypes.c_ulonglong, P(CResult)],
         "vof_wait": [_VP, ctypes.c_ulonglong, P(CResult)],
         "vof_server_destroy": [_VP],
+        "vof_ensemble_create": [P(CGrid), P(CPhys), ctypes.c_int, P(CSolver), ctypes.c_int,
+                                ctypes.c_int, P(_VP)],
+        "vof_ensemble_step": [_VP, P(_VP), P(_D), ctypes.c_longlong, P(ctypes.c_int), P(CReport)],
+        "vof_ensemble_destroy": [_VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -382,6 +386,70 @@ class VofServer:
             self.lib.vof_server_destroy(self._srv)
             self._srv = _VP()
             self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class VofEnsemble:
+    """n independent cases of one grid advanced together by one step per call
+    (fields: per case the eight device tensors of `VofContext.step`)."""
+
+    def __init__(self, grid, phys_list, solver: CSolver | None = None, n_streams: int = 8):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        torch.cuda.init()
+        self.lib = load()
+        self.grid = grid
+        self.n = len(phys_list)
+        self._phys = (CPhys * self.n)(*[c_phys(p) for p in phys_list])
+        self._g = c_grid(grid)
+        self._s = solver or c_solver()
+        self._e = _VP()
+        st = self.lib.vof_ensemble_create(ctypes.byref(self._g), self._phys, self.n,
+                                          ctypes.byref(self._s), self.n, int(n_streams),
+                                          ctypes.byref(self._e))
+        if st:
+            raise VofError(st, "vof_ensemble_create")
+        cs = (grid.nz, grid.ny, grid.nx)
+        self.shapes = (cs, cs, cs, cs, (grid.nz, grid.ny, grid.nx + 1),
+                       (grid.nz, grid.ny + 1, grid.nx), cs, cs)
+
+    def step(self, fields, dts, step_index: int, reports: bool = False):
+        """fields: list (one per case) of the eight CUDA float64 tensors."""
+        import torch
+        if len(fields) != self.n or len(dts) != self.n:
+            raise ValueError("one field set and one dt per case")
+        ptrs = (_VP * (8 * self.n))()
+        for c, fs in enumerate(fields):
+            for q, (t, sh) in enumerate(zip(fs, self.shapes)):
+                if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                        and t.is_contiguous() and tuple(t.shape) == sh):
+                    raise TypeError(f"case {c} field {q}: need a contiguous float64 CUDA tensor {sh}")
+                ptrs[8 * c + q] = t.data_ptr()
+        dt = (_D * self.n)(*[float(x) for x in dts])
+        status = (ctypes.c_int * self.n)()
+        reps = (CReport * self.n)() if reports else None
+        torch.cuda.current_stream().synchronize()  # inputs written on torch's stream are ready
+        st = self.lib.vof_ensemble_step(self._e, ptrs, dt, int(step_index), status, reps)
+        if st:
+            raise VofError(st, "vof_ensemble_step", f"case statuses {list(status)}")
+        return [r.as_dict() for r in reps] if reports else None
+
+    def close(self):
+        if getattr(self, "_e", None) and self._e.value:
+            self.lib.vof_ensemble_destroy(self._e)
+            self._e = _VP()
 
     def __del__(self):
         try:

@@ -433,3 +433,22 @@ def _swarm_from(g: Grid, centres, d: float, seed: int, steps: int, w_b: float = 
     umax = max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
     return Case("serve", g, ph, alpha, u, v, w, np.zeros(g.shapes()[0]),
                 stable_dt(g, ph, umax), steps, centres, d / 2)
+
+
+def ensemble_cases(n: int = 64, dims=(48, 48, 96), seed: int = 2109):
+    """n independent small ducts of one grid size: per case 4-16 spheres with
+    d drawn from [8, 14]h (fewer where they do not fit) in the rising-swarm
+    flow. The paper has no ensemble workload; this is the seeded stand-in for
+    a batch of independent cases."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n):
+        g = Grid(*dims)
+        d = float(rng.uniform(8.0, 14.0)) * g.h
+        nbub = int(rng.integers(4, 17))
+        sub = seed * 1000 + c
+        centres = place_spheres(g, nbub, d, sub, max_tries=20_000, allow_fewer=True)
+        case = _swarm_from(g, centres, d, sub, 1)
+        case.name = "ensemble"
+        out.append(case)
+    return out
