@@ -392,6 +392,7 @@ vof_status vof_destroy(vof_ctx* c) {
     for (void* p : c->allocs) cudaFreeAsync(p, c->st);
     cudaStreamSynchronize(c->st);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
     delete c;
     return VOF_OK;
 }

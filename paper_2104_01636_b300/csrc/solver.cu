@@ -100,16 +100,58 @@ void vcycle(vof_ctx* c, int l) {
     }
 }
 
+// One V-cycle on the finest level's (x, f) in the context's precision. The
+// first call captures the cycle's launches into a CUDA graph; later calls
+// replay it, which removes the launch gaps between the small coarse-level
+// kernels. The cycle reads only fixed workspace pointers (coefficients and
+// the dense coarse inverse are refreshed in place each solve), so the graph
+// stays valid for the context's lifetime. Per-kernel timing, or a stream
+// that cannot be captured (the legacy default stream), keeps direct launches.
+template <class T>
+void run_vcycle(vof_ctx* c) {
+    if (c->timing || c->vgraph_state < 0) {
+        vcycle<T>(c, 0);
+        return;
+    }
+    if (c->vgraph_state == 0) {
+        c->vgraph_state = -1;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(c->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+            cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            vcycle<T>(c, 0);
+            return;
+        }
+        const long long n0 = c->nlaunch;
+        vcycle<T>(c, 0);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        c->vgraph_kernels = c->nlaunch - n0;
+        c->nlaunch = n0;
+        if (e != cudaSuccess || !g || cudaGraphInstantiate(&c->vgraph, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            c->vgraph = nullptr;
+            vcycle<T>(c, 0);
+            return;
+        }
+        cudaGraphDestroy(g);
+        c->vgraph_state = 1;
+    }
+    cudaGraphLaunch(c->vgraph, c->st);
+    c->nlaunch += c->vgraph_kernels;
+}
+
 // z = M r (one V-cycle), in the precision the context was created with
 void precondition(vof_ctx* c) {
     Level& L0 = c->lv[0];
     if (c->sv.precision == VOF_PREC_FP64) {
         L0.x = c->z;
         L0.f = c->r;
-        vcycle<double>(c, 0);
+        run_vcycle<double>(c);
     } else {
         mg_to_f32(c, c->r, L0.ff, L0.ncells);
-        vcycle<float>(c, 0);
+        run_vcycle<float>(c);
         mg_to_f64(c, L0.xf, c->z, L0.ncells);
     }
 }
@@ -317,7 +359,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
         // a stagnating FP32 inner solve must not use up the whole budget
         const int inner_cap = inner_total + std::max(20, c->sv.max_iter / 4);
         cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
-        vcycle<float>(c, 0);
+        run_vcycle<float>(c);
         k32_dot2(c, n, z32, r32, r32, S_RZ, S_ZQ);
         cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
         while (inner_total < c->sv.max_iter && inner_total < inner_cap) {
@@ -334,7 +376,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
             const double rr = c->hbuf[S_RR];
             if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
             if (rr <= tol_in * tol_in * rr0) break;
-            vcycle<float>(c, 0);
+            run_vcycle<float>(c);
             k32_dot2(c, n, z32, r32, c->q32, S_RZ, S_ZQ);
             launch_scalar_beta(c);
             k32_p_update(c, n, c->p32, z32);

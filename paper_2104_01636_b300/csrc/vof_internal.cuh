@@ -175,6 +175,12 @@ struct vof_ctx {
     int sweep_kchunk = 1;
     alignas(64) unsigned char tmap[3][128];
 
+    // the V-cycle captured once as a CUDA graph and replayed (state 0: not
+    // tried yet, 1: ready, -1: capture unavailable, e.g. the legacy stream)
+    cudaGraphExec_t vgraph = nullptr;
+    long long vgraph_kernels = 0;
+    int vgraph_state = 0;
+
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
 };
