@@ -399,22 +399,74 @@ __global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
     }
 }
 
-// One Gauss-Jordan pivot step of the in-place inversion of an SPD matrix
-// (no pivoting needed), reading A and writing B.
+// In-place Gauss-Jordan inversion of the SPD matrix (no pivoting needed):
+// a pivot on index k maps M_kk -> 1/M_kk, row k -> row k / M_kk, column k ->
+// -column k / M_kk and every other entry to M_ij - M_ik M_kj / M_kk; all n
+// pivots leave M^-1.
+// Blocked form of the same in-place inversion: pivoting on a block K of up
+// to 32 indices at once (A = M_KK, B = M_KR, C = M_RK, D = M_RR) gives
+//   M_KK <- A^-1,  M_KR <- A^-1 B,  M_RK <- -C A^-1,  M_RR <- D - C A^-1 B,
+// which equals the 32 single-pivot steps in sequence. Two launches per block:
+// the panel (A^-1 by 32 pivot steps in shared memory, padded with the
+// identity, then -C A^-1 and A^-1 B) and the rank-32 update of the rest.
+constexpr int GJB = 32;
+
 template <class S>
-__global__ void k_gauss_jordan(int n, int kp, const S* __restrict__ A, S* __restrict__ B) {
-    __shared__ S rp;
-    if (threadIdx.x == 0) rp = S(1) / A[(long)kp * n + kp];
+__global__ void k_gj_panel(int n, int k, int bs, const S* __restrict__ M, S* __restrict__ P,
+                           S* __restrict__ Cp, S* __restrict__ Bp) {
+    __shared__ S a[GJB][GJB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    a[ty][tx] = (ty < bs && tx < bs) ? M[(long)(k + ty) * n + k + tx] : S(ty == tx ? 1 : 0);
+    for (int p = 0; p < GJB; ++p) {
+        __syncthreads();
+        const S r = S(1) / a[p][p];
+        S v;
+        if (ty == p && tx == p) v = r;
+        else if (ty == p) v = a[p][tx] * r;
+        else if (tx == p) v = -a[ty][p] * r;
+        else v = a[ty][tx] - a[ty][p] * (a[p][tx] * r);
+        __syncthreads();
+        a[ty][tx] = v;
+    }
     __syncthreads();
-    const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (e >= (long)n * n) return;
-    const int i = (int)(e / n), j = (int)(e % n);
+    if (blockIdx.x == 0) P[ty * GJB + tx] = a[ty][tx];
+    const int i = blockIdx.x * GJB + ty;  // a row of -C A^-1
+    if (i < n && tx < bs) {
+        S v = S(0);
+        if (i < k || i >= k + bs) {
+            const S* row = M + (long)i * n + k;
+            for (int t = 0; t < bs; ++t) v -= row[t] * a[t][tx];
+        }
+        Cp[(long)i * GJB + tx] = v;
+    }
+    const int j = blockIdx.x * GJB + tx;  // a column of A^-1 B
+    if (j < n && ty < bs && (j < k || j >= k + bs)) {
+        S v = S(0);
+        for (int t = 0; t < bs; ++t) v += a[ty][t] * M[(long)(k + t) * n + j];
+        Bp[(long)ty * n + j] = v;
+    }
+}
+
+template <class S>
+__global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const S* __restrict__ P,
+                            const S* __restrict__ Cp, const S* __restrict__ Bp, S* __restrict__ out) {
+    __shared__ S cps[GJB][GJB + 1], mk[GJB][GJB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.y * GJB + ty, j = blockIdx.x * GJB + tx;
+    cps[ty][tx] = (i < n && tx < bs) ? Cp[(long)i * GJB + tx] : S(0);
+    mk[ty][tx] = (ty < bs && j < n) ? M[(long)(k + ty) * n + j] : S(0);
+    __syncthreads();
+    if (i >= n || j >= n) return;
+    const bool ki = i >= k && i < k + bs, kj = j >= k && j < k + bs;
     S v;
-    if (i == kp && j == kp) v = rp;
-    else if (i == kp) v = A[e] * rp;
-    else if (j == kp) v = -A[e] * rp;
-    else v = A[e] - A[(long)i * n + kp] * (A[(long)kp * n + j] * rp);
-    B[e] = v;
+    if (ki && kj) v = P[(i - k) * GJB + (j - k)];
+    else if (ki) v = Bp[(long)(i - k) * n + j];
+    else if (kj) v = Cp[(long)i * GJB + (j - k)];
+    else {
+        v = M[(long)i * n + j];
+        for (int u = 0; u < bs; ++u) v += cps[ty][u] * mk[u][tx];
+    }
+    out[(long)i * n + j] = v;
 }
 
 // x = Minv f: one warp per row, FP64 accumulation
@@ -637,13 +689,19 @@ void mg_dense_setup(vof_ctx* c, const Level& L) {
     // eigenvalue of the shifted matrix sits among the operator's own
     const double s = c->dense_shift * ih2 / n;
     const int nb = (int)std::min<long>((n2 + 255) / 256, 65535L * 8);
-    const int gj_blocks = (int)((n2 + 255) / 256);
     int m = timer_begin(c, T_COARSE);
     T* A = (T*)c->dense_a;
     T* B = (T*)c->dense_b;
     VOF_LAUNCH(c, k_dense_assemble<T>, nb, 256, L.d, ih2, a.bx, a.by, a.bz, s, A);
-    for (int kp = 0; kp < n; ++kp) {
-        VOF_LAUNCH(c, k_gauss_jordan<T>, gj_blocks, 256, n, kp, (const T*)A, B);
+    T* Pw = (T*)c->dense_w;
+    T* Cp = Pw + GJB * GJB;
+    T* Bp = Cp + (size_t)GJB * n;
+    const int nt = (n + GJB - 1) / GJB;
+    for (int k = 0; k < n; k += GJB) {
+        const int bs = std::min(GJB, n - k);
+        VOF_LAUNCH(c, k_gj_panel<T>, nt, dim3(GJB, GJB), n, k, bs, (const T*)A, Pw, Cp, Bp);
+        VOF_LAUNCH(c, k_gj_update<T>, dim3(nt, nt), dim3(GJB, GJB), n, k, bs, (const T*)A,
+                   (const T*)Pw, (const T*)Cp, (const T*)Bp, B);
         std::swap(A, B);
     }
     if (sizeof(T) == 4) c->dense_inv_f = (float*)A;

@@ -184,7 +184,7 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
     const Dims& dc = dims.back();
     const size_t nc = (size_t)dc.nx * dc.ny * dc.nz;
     b += 4 * nc * sizeof(double);
-    if (nc <= (size_t)DENSE_MAX) b += nc * nc * 2 * elt;
+    if (nc <= (size_t)DENSE_MAX) b += (nc * nc * 2 + 32 * 32 + 64 * nc) * elt;
     return b;
 }
 
@@ -280,7 +280,10 @@ vof_status mg_allocate(vof_ctx* c) {
         const size_t elt = mixed ? sizeof(float) : sizeof(double);
         void* a = dev_alloc(c, n2 * elt);
         void* b = a ? dev_alloc(c, n2 * elt) : nullptr;
-        if (!a || !b) return set_err(c, VOF_ERR_OOM, "allocation of the dense coarse inverse failed");
+        void* w = b ? dev_alloc(c, (32 * 32 + 64 * (size_t)Lc.ncells) * elt) : nullptr;
+        if (!a || !b || !w)
+            return set_err(c, VOF_ERR_OOM, "allocation of the dense coarse inverse failed");
+        c->dense_w = w;
         c->dense_a = (double*)a;
         c->dense_b = (double*)b;
         c->dense_n = Lc.ncells;

@@ -151,6 +151,7 @@ struct vof_ctx {
     double dense_shift = 0.0;  // s n / (1/h^2): regularising shift of the constants
     double *dense_a = nullptr, *dense_b = nullptr, *dense_inv = nullptr;
     float* dense_inv_f = nullptr;
+    void* dense_w = nullptr;  // blocked Gauss-Jordan panels: 32x32 + 2 x 32 n entries
 
     double* part = nullptr;  // NSLOTS x MAX_PARTIALS block partials
     double* scal = nullptr;  // device scalars
