@@ -8,6 +8,8 @@
 // Walls carry beta = 0, so the stencil reads a clamped neighbour there and
 // multiplies it by zero; z is periodic. The residual, the operator and the
 // Krylov updates are FP64 in every precision mode.
+#include <cuda_fp16.h>
+
 #include "vof_internal.cuh"
 
 namespace {
@@ -51,7 +53,8 @@ __device__ __forceinline__ double stencil(const Dims& d, const double* __restric
 
 __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double rg,
                        double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
-                       float* __restrict__ rho32, double* __restrict__ rho64, int kchunk) {
+                       float* __restrict__ rho32, __half* __restrict__ rho16,
+                       double* __restrict__ rho64, int kchunk) {
     CellIdx r = cell_range(d, kchunk);
     if (!r.act) return;
     const int i = r.i, j = r.j;
@@ -59,6 +62,7 @@ __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double r
         const int c = cid(d, i, j, k);
         const double rc = a[c] * rl + (1.0 - a[c]) * rg;
         if (rho32) rho32[c] = (float)rc;  // finest-level density of the multigrid
+        if (rho16) rho16[c] = __double2half(rc);
         if (rho64) rho64[c] = rc;
         // x-face i (between i-1 and i); the last thread also writes the wall face nx
         if (i == 0) {
@@ -243,7 +247,7 @@ inline int flat_blocks(int n) {
 void launch_beta(vof_ctx* c, const double* alpha) {
     const Launch& L = c->Lc;
     VOF_LAUNCH(c, k_beta, L.grid, L.block, c->d, alpha, c->ph.rho_l, c->ph.rho_g, c->bx, c->by,
-               c->bz, c->rho32, c->rho64, L.kchunk);
+               c->bz, c->rho32, (__half*)c->rho16, c->rho64, L.kchunk);
 }
 
 void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y) {

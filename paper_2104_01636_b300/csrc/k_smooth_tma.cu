@@ -1,23 +1,29 @@
 // Finest level of the mixed-precision V-cycle (pressure equation, Eq. 7):
-// the face coefficients are formed on the fly from one FP32 density per cell,
+// the face coefficients are formed on the fly from one density per cell,
 //   beta_f = 1 / (0.5 (rho_L + rho_R)) = 2 / (rho_L + rho_R),
 // the same face rule as the FP64 coefficients (rho the linear mix of the two
 // phases by the volume fraction), so a kernel reads one value per cell
-// instead of three face arrays. Three kernels use that operator and nothing
-// else does on this level, so the V-cycle stays a symmetric preconditioner:
+// instead of three face arrays.
 //
 //  * k_sweep_rho: one whole red-black Gauss-Seidel sweep per launch (first
 //    colour from the other colour's old values, then the other colour from
 //    the new ones). A block owns a 32 x 32 (x, y) tile and marches over a
-//    chunk of z planes; TMA (cp.async.bulk.tensor) stages the planes of x and
-//    of the density, halo included, in shared memory. The first colour is
-//    computed on the tile and on its one-cell ring (the ring redundantly with
-//    the neighbouring tiles), so a block never reads another block's result;
-//    x is read from one buffer and written to another, and the result does
-//    not depend on the order in which blocks run.
+//    chunk of z planes; TMA (cp.async.bulk.tensor) stages the planes of x
+//    (FP32) and of the density (FP16), halo included, in shared memory. The
+//    first colour is computed on the tile and on its one-cell ring (the ring
+//    redundantly with the neighbouring tiles), so a block never reads
+//    another block's result; x is read from one buffer and written to
+//    another, and the result does not depend on the order in which blocks
+//    run.
 //  * k_restrict_rho: residual f - A x averaged over the eight children.
-//  * k_apply_A_dot_rho32: q = A p with the partials of p.q (inner CG).
+//    With the sweep it forms the V-cycle's finest-level operator from the
+//    FP16 density (a preconditioner: the 11-bit density changes no
+//    convergence test), so the V-cycle stays symmetric.
+//  * k_apply_A_dot_rho32: q = A p with the partials of p.q, from the FP32
+//    density: the inner CG's operator, which the FP64 defect correction
+//    must see to within FP32 rounding.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <mutex>
@@ -26,17 +32,22 @@
 
 namespace {
 
-constexpr int STX = 32, STY = 32;           // tile of a sweep block
-constexpr int SBX = STX + 8, SBY = STY + 4;  // staged box: x from i0-4 (16-byte aligned), y from j0-2
-constexpr int RNX = STX + 2, RNY = STY + 2;  // first-colour values on the tile and its ring
-constexpr int NSLOT = 5;                     // staged planes: 3 in use, 2 in flight
-constexpr int PLANE = SBX * SBY;             // floats per staged plane
-constexpr int WAIT_LIMIT = 1 << 20;          // bounded waits on the TMA barriers
-constexpr size_t SWEEP_SMEM =
-    (size_t)(2 * NSLOT * PLANE + 3 * RNX * RNY) * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
+constexpr int STX = 32, STY = 32;            // tile of a sweep block
+constexpr int SBX = STX + 8, SBY = STY + 4;   // x box (FP32): x from i0-4 (16-byte aligned), y from j0-2
+constexpr int HBX = STX + 16;                 // density box (FP16): x from i0-8 (16-byte aligned)
+constexpr int RNX = STX + 2, RNY = STY + 2;   // first-colour values on the tile and its ring
+constexpr int NSLOT = 4;                      // staged planes: 3 in use, 1 in flight
+constexpr int XPLANE = SBX * SBY;             // floats per staged x plane
+constexpr int HPLANE = HBX * SBY;             // halves per staged density plane
+constexpr int WAIT_LIMIT = 1 << 20;           // bounded waits on the TMA barriers
+constexpr size_t SWEEP_SMEM = (size_t)NSLOT * XPLANE * sizeof(float) +
+                              (size_t)NSLOT * HPLANE * sizeof(__half) +
+                              (size_t)3 * RNX * RNY * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
 static_assert(sizeof(CUtensorMap) == 128, "tensor map storage in the context is 128 bytes");
-static_assert((SBX * sizeof(float)) % 16 == 0, "TMA box rows must be a multiple of 16 bytes");
-static_assert((PLANE * sizeof(float)) % 128 == 0, "staged planes keep 128-byte alignment");
+static_assert((SBX * sizeof(float)) % 16 == 0 && (HBX * sizeof(__half)) % 16 == 0,
+              "TMA box rows must be a multiple of 16 bytes");
+static_assert((XPLANE * sizeof(float)) % 128 == 0 && (HPLANE * sizeof(__half)) % 128 == 0,
+              "staged planes keep 128-byte alignment");
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -69,7 +80,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, uint64_t* bar,
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -97,20 +108,23 @@ __device__ __forceinline__ float2 half_beta2(float2 rc, float2 rn) {
     return make_float2(rcp_approx(s.x), rcp_approx(s.y));
 }
 
+__device__ __forceinline__ float hval(const __half* h, int o) { return __half2float(h[o]); }
+
 // Each thread owns the x-pair (ib, ib+1) in rows jA = j0+ty and jB = jA+16.
 // On every plane one member of the pair has the first colour and the other
 // the second, at the same x in both rows, so the two rows are updated with
 // packed FP32x2 arithmetic. The z-face coefficients computed for the first
-// colour are kept in registers and reused by the second colour.
+// colour are kept in registers and reused by the second colour, and the
+// right side of the next plane is loaded into registers one plane ahead.
 template <bool ZERO>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_sweep_rho(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_rho,
                 SweepArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     float* sX = reinterpret_cast<float*>(smem_raw + (((raw + 127u) & ~127u) - raw));
-    float* sR = sX + NSLOT * PLANE;
-    float* sN = sR + NSLOT * PLANE;
+    __half* sH = reinterpret_cast<__half*>(sX + NSLOT * XPLANE);
+    float* sN = reinterpret_cast<float*>(sH + NSLOT * HPLANE);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sN + 3 * RNX * RNY);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 16 * ty;
@@ -119,7 +133,8 @@ __global__ void __launch_bounds__(256, 3)
     const int k1 = min(k0 + a.kchunk, a.nz);
     if (k0 >= k1) return;  // whole block
     const int pbase = k0 - 2;  // first staged plane (unwrapped index)
-    constexpr uint32_t bytes = (ZERO ? 1u : 2u) * (uint32_t)(PLANE * sizeof(float));
+    constexpr uint32_t bytes = (ZERO ? 0u : (uint32_t)(XPLANE * sizeof(float))) +
+                               (uint32_t)(HPLANE * sizeof(__half));
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
@@ -132,12 +147,12 @@ __global__ void __launch_bounds__(256, 3)
         const int s = (p - pbase) % NSLOT;
         const int z = wrapk(p, a.nz);
         mbar_expect_tx(&bar[s], bytes);
-        if (!ZERO) tma_load_3d(sX + s * PLANE, &tm_x, &bar[s], i0 - 4, j0 - 2, z);
-        tma_load_3d(sR + s * PLANE, &tm_rho, &bar[s], i0 - 4, j0 - 2, z);
+        if (!ZERO) tma_load_3d(sX + s * XPLANE, &tm_x, &bar[s], i0 - 4, j0 - 2, z);
+        tma_load_3d(sH + s * HPLANE, &tm_rho, &bar[s], i0 - 8, j0 - 2, z);
         issued = p;
     };
     if (tid == 0)
-        for (int p = pbase; p <= k0 + 1; ++p) issue(p);
+        for (int p = pbase; p <= pbase + NSLOT - 1; ++p) issue(p);
 
     bool bad = false;
     auto wait_slot = [&](int s, uint32_t par) {
@@ -148,17 +163,53 @@ __global__ void __launch_bounds__(256, 3)
     wait_slot(1, 0);
 
     // per-thread geometry
-    const int nx = a.nx, ny = a.ny;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int ib = i0 + 2 * tx;
     const int jA = j0 + ty, jB = jA + 16;
     const bool inA = ib < nx && jA < ny, inB = ib < nx && jB < ny;
     const bool ylA = jA > 0, yhA = jA < ny - 1, yhB = jB < ny - 1;  // jB > 0 always
-    const int oA = (ty + 2) * SBX + 2 * tx + 4, oB = oA + 16 * SBX;  // staged offsets of (ib, jA/jB)
+    const int oA = (ty + 2) * SBX + 2 * tx + 4, oB = oA + 16 * SBX;  // x-box offsets of (ib, jA/jB)
+    const int hA = (ty + 2) * HBX + 2 * tx + 8, hB = hA + 16 * HBX;  // density-box offsets
     const int nA = (ty + 1) * RNX + 2 * tx + 1, nB = nA + 16 * RNX;  // first-colour offsets
     const size_t plane = (size_t)ny * nx;
     const float h2h = a.h2half;
+    const float* __restrict__ fg = a.f;
 
-    // slots of planes k, k+1, k+2 (staged) and k-1, k, k+1 (first colour)
+    // the ring: thread tid < 64 owns side tid/16, position tid%16
+    const bool ring = tid < 64;
+    const int side = tid >> 4, m = tid & 15;
+    auto ring_cell = [&](int q, int& ri, int& rj) {
+        if (side < 2) {
+            ri = side == 0 ? i0 - 1 : i0 + STX;
+            rj = j0 + 2 * m + ((a.c0 + ri + q) & 1);
+        } else {
+            rj = side == 2 ? j0 - 1 : j0 + STY;
+            ri = i0 + 2 * m + ((a.c0 + rj + q) & 1);
+        }
+    };
+    // right sides needed at iteration k: the first colour on plane k+1 and
+    // the second colour on plane k (same x), and the ring cell on plane k+1
+    auto load_f = [&](int k, float& rA, float& rB, float& bA, float& bB, float& rr) {
+        const int q = k + 1;
+        const int i = ib + ((a.c0 + jA + q) & 1);
+        const float* fq = fg + (size_t)wrapk(q, nz) * plane + i;
+        const float* fk = fg + (size_t)wrapk(k, nz) * plane + i;
+        rA = inA ? __ldg(fq + (size_t)jA * nx) : 0.f;
+        rB = inB ? __ldg(fq + (size_t)jB * nx) : 0.f;
+        bA = inA ? __ldg(fk + (size_t)jA * nx) : 0.f;
+        bB = inB ? __ldg(fk + (size_t)jB * nx) : 0.f;
+        rr = 0.f;
+        if (ring) {
+            int ri, rj;
+            ring_cell(q, ri, rj);
+            if (ri >= 0 && ri < nx && rj >= 0 && rj < ny)
+                rr = __ldg(fg + (size_t)wrapk(q, nz) * plane + (size_t)rj * nx + ri);
+        }
+    };
+    float fRA, fRB, fBA, fBB, fRR;
+    load_f(pbase, fRA, fRB, fBA, fBB, fRR);
+
+    // slots of planes k, k+1, k+2 and first-colour planes k-1, k, k+1
     int S1 = 0, S2 = 1, S3 = 2;
     uint32_t par3 = 0;  // parity of slot S3's current fill
     float* N0 = sN + 2 * (RNX * RNY);
@@ -167,69 +218,62 @@ __global__ void __launch_bounds__(256, 3)
     float2 bup1 = make_float2(0.f, 0.f), bup2 = make_float2(0.f, 0.f);  // z+ coefficients, 1 and 2 planes back
 
     for (int k = pbase; k < k1; ++k) {
+        float nRA, nRB, nBA, nBB, nRR;  // next plane's right sides, in flight during this one
+        load_f(k + 1, nRA, nRB, nBA, nBB, nRR);
         wait_slot(S3, par3);
-        const int q = k + 1, kq = wrapk(q, a.nz);
+        const int q = k + 1;
         const int P = (a.c0 + jA + q) & 1;  // x offset of the first colour in the pair on plane q
         const int i = ib + P;
         float2 bdown = make_float2(0.f, 0.f), bup = make_float2(0.f, 0.f);
         // ---- first colour on plane q: the thread's two cells, packed -------
         if (!bad) {
-            const float* Rq = sR + S2 * PLANE;
-            const float* Rm = sR + S1 * PLANE;
-            const float* Rp = sR + S3 * PLANE;
-            const float* Xq = sX + S2 * PLANE;
-            const float* Xm = sX + S1 * PLANE;
-            const float* Xp = sX + S3 * PLANE;
-            const int a_ = oA + P, b_ = oB + P;
-            const float2 rc = make_float2(Rq[a_], Rq[b_]);
-            const float* fq = a.f + (size_t)kq * plane + i;
-            float2 num = make_float2(inA ? h2h * __ldg(fq + (size_t)jA * nx) : 0.f,
-                                     inB ? h2h * __ldg(fq + (size_t)jB * nx) : 0.f);
+            const __half* Hq = sH + S2 * HPLANE;
+            const __half* Hm = sH + S1 * HPLANE;
+            const __half* Hp = sH + S3 * HPLANE;
+            const float* Xq = sX + S2 * XPLANE;
+            const float* Xm = sX + S1 * XPLANE;
+            const float* Xp = sX + S3 * XPLANE;
+            const int xa = oA + P, xb = oB + P, ha = hA + P, hb = hB + P;
+            const float2 rc = make_float2(hval(Hq, ha), hval(Hq, hb));
+            float2 num = make_float2(h2h * fRA, h2h * fRB);
             float2 den = make_float2(0.f, 0.f);
-            auto acc = [&](float2 b, int da, int db, const float* X) {
-                if (!ZERO) num = __ffma2_rn(b, make_float2(X[a_ + da], X[b_ + db]), num);
+            auto acc = [&](float2 b, int dx, const float* X) {
+                if (!ZERO) num = __ffma2_rn(b, make_float2(X[xa + dx], X[xb + dx]), num);
                 den = __fadd2_rn(den, b);
             };
-            if (i > 0) acc(half_beta2(rc, make_float2(Rq[a_ - 1], Rq[b_ - 1])), -1, -1, Xq);
-            if (i < nx - 1) acc(half_beta2(rc, make_float2(Rq[a_ + 1], Rq[b_ + 1])), 1, 1, Xq);
+            if (i > 0) acc(half_beta2(rc, make_float2(hval(Hq, ha - 1), hval(Hq, hb - 1))), -1, Xq);
+            if (i < nx - 1) acc(half_beta2(rc, make_float2(hval(Hq, ha + 1), hval(Hq, hb + 1))), 1, Xq);
             {
-                float2 b = half_beta2(rc, make_float2(Rq[a_ - SBX], Rq[b_ - SBX]));
+                float2 b = half_beta2(rc, make_float2(hval(Hq, ha - HBX), hval(Hq, hb - HBX)));
                 if (!ylA) b.x = 0.f;
-                acc(b, -SBX, -SBX, Xq);
-                b = half_beta2(rc, make_float2(Rq[a_ + SBX], Rq[b_ + SBX]));
+                acc(b, -SBX, Xq);
+                b = half_beta2(rc, make_float2(hval(Hq, ha + HBX), hval(Hq, hb + HBX)));
                 if (!yhA) b.x = 0.f;
                 if (!yhB) b.y = 0.f;
-                acc(b, SBX, SBX, Xq);
+                acc(b, SBX, Xq);
             }
-            bdown = half_beta2(rc, make_float2(Rm[a_], Rm[b_]));
-            acc(bdown, 0, 0, Xm);
-            bup = half_beta2(rc, make_float2(Rp[a_], Rp[b_]));
-            acc(bup, 0, 0, Xp);
+            bdown = half_beta2(rc, make_float2(hval(Hm, ha), hval(Hm, hb)));
+            acc(bdown, 0, Xm);
+            bup = half_beta2(rc, make_float2(hval(Hp, ha), hval(Hp, hb)));
+            acc(bup, 0, Xp);
             N2[nA + P] = inA ? __fdividef(num.x, den.x) : 0.f;
             N2[nB + P] = inB ? __fdividef(num.y, den.y) : 0.f;
 
-            if (tid < 64) {  // the ring: 16 first-colour cells per side (0 outside the domain)
-                const int side = tid >> 4, m = tid & 15;
+            if (ring) {  // 16 first-colour ring cells per side (0 outside the domain)
                 int ri, rj;
-                if (side < 2) {
-                    ri = side == 0 ? i0 - 1 : i0 + STX;
-                    rj = j0 + 2 * m + ((a.c0 + ri + q) & 1);
-                } else {
-                    rj = side == 2 ? j0 - 1 : j0 + STY;
-                    ri = i0 + 2 * m + ((a.c0 + rj + q) & 1);
-                }
+                ring_cell(q, ri, rj);
                 float v = 0.f;
                 if (ri >= 0 && ri < nx && rj >= 0 && rj < ny) {
                     const int o = (rj - j0 + 2) * SBX + (ri - i0 + 4);
-                    const float r0 = Rq[o];
-                    float rn = h2h * __ldg(a.f + (size_t)kq * plane + (size_t)rj * nx + ri), rd = 0.f;
-                    float b;
-                    if (ri > 0) { b = half_beta(r0, Rq[o - 1]); if (!ZERO) rn = fmaf(b, Xq[o - 1], rn); rd += b; }
-                    if (ri < nx - 1) { b = half_beta(r0, Rq[o + 1]); if (!ZERO) rn = fmaf(b, Xq[o + 1], rn); rd += b; }
-                    if (rj > 0) { b = half_beta(r0, Rq[o - SBX]); if (!ZERO) rn = fmaf(b, Xq[o - SBX], rn); rd += b; }
-                    if (rj < ny - 1) { b = half_beta(r0, Rq[o + SBX]); if (!ZERO) rn = fmaf(b, Xq[o + SBX], rn); rd += b; }
-                    b = half_beta(r0, Rm[o]); if (!ZERO) rn = fmaf(b, Xm[o], rn); rd += b;
-                    b = half_beta(r0, Rp[o]); if (!ZERO) rn = fmaf(b, Xp[o], rn); rd += b;
+                    const int h = (rj - j0 + 2) * HBX + (ri - i0 + 8);
+                    const float r0 = hval(Hq, h);
+                    float rn = h2h * fRR, rd = 0.f, b;
+                    if (ri > 0) { b = half_beta(r0, hval(Hq, h - 1)); if (!ZERO) rn = fmaf(b, Xq[o - 1], rn); rd += b; }
+                    if (ri < nx - 1) { b = half_beta(r0, hval(Hq, h + 1)); if (!ZERO) rn = fmaf(b, Xq[o + 1], rn); rd += b; }
+                    if (rj > 0) { b = half_beta(r0, hval(Hq, h - HBX)); if (!ZERO) rn = fmaf(b, Xq[o - SBX], rn); rd += b; }
+                    if (rj < ny - 1) { b = half_beta(r0, hval(Hq, h + HBX)); if (!ZERO) rn = fmaf(b, Xq[o + SBX], rn); rd += b; }
+                    b = half_beta(r0, hval(Hm, h)); if (!ZERO) rn = fmaf(b, Xm[o], rn); rd += b;
+                    b = half_beta(r0, hval(Hp, h)); if (!ZERO) rn = fmaf(b, Xp[o], rn); rd += b;
                     v = __fdividef(rn, rd);
                 }
                 N2[(rj - j0 + 1) * RNX + (ri - i0 + 1)] = v;
@@ -250,29 +294,27 @@ __global__ void __launch_bounds__(256, 3)
         }
         // ---- second colour on plane k at the same x, written with the first -
         if (k >= k0) {
-            const int kk = wrapk(k, a.nz);
-            const float* Rk = sR + S1 * PLANE;
-            const int a_ = oA + P, b_ = oB + P, na = nA + P, nb = nB + P;
-            const float2 rc = make_float2(Rk[a_], Rk[b_]);
-            const float* fk = a.f + (size_t)kk * plane + i;
-            float2 num = make_float2(inA ? h2h * __ldg(fk + (size_t)jA * nx) : 0.f,
-                                     inB ? h2h * __ldg(fk + (size_t)jB * nx) : 0.f);
+            const int kk = wrapk(k, nz);
+            const __half* Hk = sH + S1 * HPLANE;
+            const int ha = hA + P, hb = hB + P, na = nA + P, nb = nB + P;
+            const float2 rc = make_float2(hval(Hk, ha), hval(Hk, hb));
+            float2 num = make_float2(h2h * fBA, h2h * fBB);
             float2 den = make_float2(0.f, 0.f);
             auto acc = [&](float2 b, float2 xn) {
                 num = __ffma2_rn(b, xn, num);
                 den = __fadd2_rn(den, b);
             };
             if (i > 0)
-                acc(half_beta2(rc, make_float2(Rk[a_ - 1], Rk[b_ - 1])),
+                acc(half_beta2(rc, make_float2(hval(Hk, ha - 1), hval(Hk, hb - 1))),
                     make_float2(N1[na - 1], N1[nb - 1]));
             if (i < nx - 1)
-                acc(half_beta2(rc, make_float2(Rk[a_ + 1], Rk[b_ + 1])),
+                acc(half_beta2(rc, make_float2(hval(Hk, ha + 1), hval(Hk, hb + 1))),
                     make_float2(N1[na + 1], N1[nb + 1]));
             {
-                float2 b = half_beta2(rc, make_float2(Rk[a_ - SBX], Rk[b_ - SBX]));
+                float2 b = half_beta2(rc, make_float2(hval(Hk, ha - HBX), hval(Hk, hb - HBX)));
                 if (!ylA) b.x = 0.f;
                 acc(b, make_float2(N1[na - RNX], N1[nb - RNX]));
-                b = half_beta2(rc, make_float2(Rk[a_ + SBX], Rk[b_ + SBX]));
+                b = half_beta2(rc, make_float2(hval(Hk, ha + HBX), hval(Hk, hb + HBX)));
                 if (!yhA) b.x = 0.f;
                 if (!yhB) b.y = 0.f;
                 acc(b, make_float2(N1[na + RNX], N1[nb + RNX]));
@@ -290,10 +332,10 @@ __global__ void __launch_bounds__(256, 3)
                     P ? make_float2(N1[pb], sb) : make_float2(sb, N1[pb]);
         }
         __syncthreads();
-        // refill the slot of plane k - 1 (no longer read) with plane k + 4
-        if (tid == 0 && k + 4 <= k1 + 1) {
+        // refill the slot of plane k (no longer read) with plane k + NSLOT
+        if (tid == 0 && k + NSLOT <= k1 + 1) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(k + 4);
+            issue(k + NSLOT);
         }
         // roll the plane window
         bup2 = bup1;
@@ -302,12 +344,17 @@ __global__ void __launch_bounds__(256, 3)
         S2 = S3;
         if (++S3 == NSLOT) {
             S3 = 0;
+            par3 ^= 1u;  // slot 0 starts its next fill
         }
-        if (S3 == 0) par3 ^= 1u;  // slot 0 starts its next fill
         float* t = N0;
         N0 = N1;
         N1 = N2;
         N2 = t;
+        fRA = nRA;
+        fRB = nRB;
+        fBA = nBA;
+        fBB = nBB;
+        fRR = nRR;
     }
 }
 
@@ -327,7 +374,23 @@ __device__ __forceinline__ float stencil_rho(const Dims& d, const float* __restr
     return s;
 }
 
-__global__ void k_restrict_rho(Dims df, float ih2, const float* __restrict__ rho,
+// A x from the FP16 density (the V-cycle's finest-level operator, times h^2)
+__device__ __forceinline__ float stencil_rho16(const Dims& d, const __half* __restrict__ rho,
+                                               const float* __restrict__ x, int i, int j, int k) {
+    const int c = cid(d, i, j, k);
+    const float xc = x[c], rc = __half2float(rho[c]);
+    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, wrapk(k + 1, d.nz));
+    float s = 0.f;
+    if (i > 0) s = fmaf(beta_rho(rc, __half2float(rho[c - 1])), xc - x[c - 1], s);
+    if (i < d.nx - 1) s = fmaf(beta_rho(rc, __half2float(rho[c + 1])), xc - x[c + 1], s);
+    if (j > 0) s = fmaf(beta_rho(rc, __half2float(rho[c - d.nx])), xc - x[c - d.nx], s);
+    if (j < d.ny - 1) s = fmaf(beta_rho(rc, __half2float(rho[c + d.nx])), xc - x[c + d.nx], s);
+    s = fmaf(beta_rho(rc, __half2float(rho[cb])), xc - x[cb], s);
+    s = fmaf(beta_rho(rc, __half2float(rho[ct])), xc - x[ct], s);
+    return s;
+}
+
+__global__ void k_restrict_rho(Dims df, float ih2, const __half* __restrict__ rho,
                                const float* __restrict__ xf, const float* __restrict__ ff, Dims dc,
                                float* __restrict__ fc, int kchunk) {
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
@@ -337,7 +400,7 @@ __global__ void k_restrict_rho(Dims df, float ih2, const float* __restrict__ rho
         float s = 0.f;
         for (int c3 = 0; c3 < 8; ++c3) {
             const int i = 2 * I + (c3 & 1), j = 2 * J + ((c3 >> 1) & 1), k = 2 * K + (c3 >> 2);
-            s += ff[cid(df, i, j, k)] - stencil_rho(df, rho, xf, i, j, k) * ih2;
+            s += ff[cid(df, i, j, k)] - stencil_rho16(df, rho, xf, i, j, k) * ih2;
         }
         fc[cid(dc, I, J, K)] = 0.125f * s;
     }
@@ -393,17 +456,19 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// a (nx, ny, nz) FP32 array staged in SBX x SBY x 1 boxes, zero outside
-bool encode_plane_map(void* store, const Dims& d, const float* base) {
+// a (nx, ny, nz) array of 4- or 2-byte elements staged in box_x x SBY x 1
+// boxes, zero outside
+bool encode_plane_map(void* store, const Dims& d, const void* base, bool half, int box_x) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
+    const size_t e = half ? sizeof(__half) : sizeof(float);
     const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * sizeof(float),
-                                   (cuuint64_t)d.nx * d.ny * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)SBX, (cuuint32_t)SBY, 1u};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * e, (cuuint64_t)d.nx * d.ny * e};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)SBY, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    return fn(reinterpret_cast<CUtensorMap*>(store), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-              const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    return fn(reinterpret_cast<CUtensorMap*>(store),
+              half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -412,22 +477,23 @@ bool encode_plane_map(void* store, const Dims& d, const float* base) {
 
 bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels) {
     return sv && sv->precision == VOF_PREC_MIXED_FP32 && sv->mg_interp == VOF_MG_CONSTANT &&
-           g->nx % 4 == 0 && nlevels >= 2;
+           g->nx % 8 == 0 && nlevels >= 2;  // 16-byte rows of the FP16 density
 }
 
 vof_status rho_path_setup(vof_ctx* c) {
     const Level& L0 = c->lv[0];
-    if (!encode_plane_map(c->tmap[0], L0.d, L0.xf) || !encode_plane_map(c->tmap[1], L0.d, c->x32b) ||
-        !encode_plane_map(c->tmap[2], L0.d, c->rho32))
+    if (!encode_plane_map(c->tmap[0], L0.d, L0.xf, false, SBX) ||
+        !encode_plane_map(c->tmap[1], L0.d, c->x32b, false, SBX) ||
+        !encode_plane_map(c->tmap[2], L0.d, c->rho16, true, HBX))
         return set_err(c, VOF_ERR_CUDA, "TMA tensor-map encoding is unavailable");
     if (cudaFuncSetAttribute(k_sweep_rho<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SWEEP_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(k_sweep_rho<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SWEEP_SMEM) != cudaSuccess)
         return cuda_check(c, cudaGetLastError(), "smoother shared-memory attribute");
-    // z chunks: about three resident blocks per SM over the whole grid
+    // z chunks: about four resident blocks per SM over the whole grid
     const int tiles = ((L0.d.nx + STX - 1) / STX) * ((L0.d.ny + STY - 1) / STY);
-    int zc = std::max(1, (3 * c->sm_count + tiles / 2) / tiles);
+    int zc = std::max(1, (4 * c->sm_count + tiles / 2) / tiles);
     zc = std::min(zc, L0.d.nz);
     c->sweep_kchunk = (L0.d.nz + zc - 1) / zc;
     return VOF_OK;
@@ -463,8 +529,8 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0) {
 void rho_restrict(vof_ctx* c) {
     const Level &F = c->lv[0], &C = c->lv[1];
     int m = timer_begin(c, T_RESTRICT0);
-    VOF_LAUNCH(c, k_restrict_rho, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)), c->rho32,
-               F.xf, F.ff, C.d, C.ff, C.L.kchunk);
+    VOF_LAUNCH(c, k_restrict_rho, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)),
+               (const __half*)c->rho16, F.xf, F.ff, C.d, C.ff, C.L.kchunk);
     timer_end(c, T_RESTRICT0, m);
 }
 

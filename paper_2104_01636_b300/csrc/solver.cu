@@ -168,7 +168,7 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
     for (size_t l = mixed ? 0 : 1; l < dims.size(); ++l) {
         const size_t n = (size_t)dims[l].nx * dims[l].ny * dims[l].nz;
         // the density-formed finest level keeps x, f, a second x and rho
-        b += (l == 0 && rho) ? 4 * n * elt : faces_bytes(dims[l], elt) + 2 * n * elt;
+        b += (l == 0 && rho) ? 4 * n * elt + 2 * n + 256 : faces_bytes(dims[l], elt) + 2 * n * elt;
     }
     if (mixed) b += 3 * (size_t)dims[0].nx * dims[0].ny * dims[0].nz * sizeof(float);  // e, p, q
     if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
@@ -213,12 +213,14 @@ vof_status mg_allocate(vof_ctx* c) {
         const size_t n = L.ncells;
         const size_t elt = mixed ? sizeof(float) : sizeof(double);
         if (l == 0 && c->use_rho) {
-            float* q = (float*)dev_alloc(c, sizeof(float) * 4 * n);
+            // x, f, second x, FP32 density, then the FP16 density (n halves)
+            float* q = (float*)dev_alloc(c, sizeof(float) * 4 * n + 2 * n + 256);
             if (!q) return set_err(c, VOF_ERR_OOM, "allocation of the finest level failed");
             L.xf = q;
             L.ff = q + n;
             c->x32b = q + 2 * n;
             c->rho32 = q + 3 * n;
+            c->rho16 = (void*)(((uintptr_t)(q + 4 * n) + 255) & ~(uintptr_t)255);
             continue;
         }
         void* p = dev_alloc(c, elt * (nu + nv + 3 * n));

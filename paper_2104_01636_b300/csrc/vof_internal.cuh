@@ -167,10 +167,11 @@ struct vof_ctx {
     long long t_n[T_NCLASS] = {0};
 
     // finest level of the mixed V-cycle with density-formed coefficients
-    // (k_smooth_tma.cu): FP32 density, second x buffer, TMA maps of
-    // x (level-0 xf), x32b and rho32
+    // (k_smooth_tma.cu): FP32 and FP16 density, second x buffer, TMA maps of
+    // x (level-0 xf), x32b and rho16
     bool use_rho = false;
     float* rho32 = nullptr;   // also the mixed path's density for density coarsening
+    void* rho16 = nullptr;    // FP16 density of the V-cycle's finest level (__half)
     double* rho64 = nullptr;  // FP64 path: finest-level density for density coarsening
     float* x32b = nullptr;
     int sweep_kchunk = 1;
