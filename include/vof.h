@@ -98,9 +98,18 @@ typedef struct {
                              covers) or VOF_COARSEN_DENSITY_MEAN (density
                              averaged over the eight children, faces then
                              formed by the fine rule 2 / (rho_L + rho_R))    */
+    int mg_cycle;         /* VOF_CYCLE_W (default): every level visits its
+                             coarser level twice (once when that one is the
+                             coarsest, solved exactly); VOF_CYCLE_V: once    */
+    int graph;            /* VOF_GRAPH_AUTO (default): the first cycle of a
+                             context on a capturable stream is captured into
+                             a CUDA graph and replayed afterwards;
+                             VOF_GRAPH_OFF: direct launches always           */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
+enum { VOF_CYCLE_W = 0, VOF_CYCLE_V = 1 };
+enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 
@@ -267,7 +276,9 @@ vof_status vof_kernel_times(vof_ctx* ctx, const char** names, double* ms, long l
  * so requests overlap on the device; a result does not depend on what else
  * was running. Host arrays of a request are read when it starts and
  * overwritten with the results when it finishes; they must stay valid until
- * vof_wait/vof_poll report it finished. */
+ * vof_wait/vof_poll report it finished. A request's context exists for that
+ * request only, so it launches its kernels directly (solver.graph is taken
+ * as VOF_GRAPH_OFF). */
 typedef struct vof_server vof_server;
 
 enum { VOF_REQ_STEP = 0, VOF_REQ_SOLVE = 1 };

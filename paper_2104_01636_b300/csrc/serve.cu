@@ -81,7 +81,12 @@ vof_status run_job(Job* j, cudaStream_t st) {
     };
     vof_status status = VOF_OK;
     vof_ctx* ctx = nullptr;
-    const vof_status cs = vof_create(&g, &r.phys, &r.solver, 0, st, &ctx);
+    // a request's context lives for one request: capturing and instantiating
+    // a graph per request (from several workers at once) costs more than it
+    // saves, so server contexts launch directly
+    vof_solver sv = r.solver;
+    sv.graph = VOF_GRAPH_OFF;
+    const vof_status cs = vof_create(&g, &r.phys, &sv, 0, st, &ctx);
     if (cs != VOF_OK || !ctx) {
         cudaGetLastError();
         return cs != VOF_OK ? cs : VOF_ERR_OOM;

@@ -46,6 +46,8 @@ void readback(vof_ctx* c) {
 
 template <class T>
 void vcycle(vof_ctx* c, int l);
+template <class T>
+void cycle(vof_ctx* c, int l, bool zero_start);
 
 // Finest level of the mixed V-cycle with the density-formed coefficients:
 // nu_pre red-black sweeps from a zero guess, restriction, the coarse
@@ -63,7 +65,8 @@ void vcycle0_rho(vof_ctx* c) {
         dst = (dst == A) ? B : A;
     }
     rho_restrict(c);
-    vcycle<float>(c, 1);
+    cycle<float>(c, 1, true);
+    if (c->sv.mg_cycle == VOF_CYCLE_W && c->lv.size() > 2) cycle<float>(c, 1, false);
     mg_prolong<float>(c, c->lv[1], L0);
     for (int s = 0; s < c->sv.nu_post; ++s) {
         rho_sweep(c, cur, dst, 1);
@@ -74,9 +77,13 @@ void vcycle0_rho(vof_ctx* c) {
         cudaMemcpyAsync(A, cur, sizeof(float) * (size_t)L0.ncells, cudaMemcpyDeviceToDevice, c->st);
 }
 
-// symmetric V-cycle on the level arrays of type T (x <- M f at level l)
+// symmetric multigrid cycle on the level arrays of type T (x <- M f at level
+// l; zero_start false continues from the level's current x). A V-cycle
+// visits the coarser level once; a W-cycle twice (the second visit
+// continues from the first one's result; an exact coarsest solve is not
+// repeated), which keeps the cycle symmetric.
 template <class T>
-void vcycle(vof_ctx* c, int l) {
+void cycle(vof_ctx* c, int l, bool zero_start) {
     const Level& L = c->lv[l];
     if (l == (int)c->lv.size() - 1) {
         mg_coarse<T>(c, L);
@@ -86,18 +93,25 @@ void vcycle(vof_ctx* c, int l) {
         vcycle0_rho(c);
         return;
     }
-    mg_zero<T>(c, L);
+    if (zero_start) mg_zero<T>(c, L);
     for (int s = 0; s < c->sv.nu_pre; ++s) {
         mg_rbgs<T>(c, L, 0);
         mg_rbgs<T>(c, L, 1);
     }
     mg_restrict<T>(c, L, c->lv[l + 1]);
-    vcycle<T>(c, l + 1);
+    cycle<T>(c, l + 1, true);
+    if (c->sv.mg_cycle == VOF_CYCLE_W && l + 1 < (int)c->lv.size() - 1)
+        cycle<T>(c, l + 1, false);
     mg_prolong<T>(c, c->lv[l + 1], L);
     for (int s = 0; s < c->sv.nu_post; ++s) {
         mg_rbgs<T>(c, L, 1);
         mg_rbgs<T>(c, L, 0);
     }
+}
+
+template <class T>
+void vcycle(vof_ctx* c, int l) {
+    cycle<T>(c, l, true);
 }
 
 // One V-cycle on the finest level's (x, f) in the context's precision. The
@@ -109,7 +123,7 @@ void vcycle(vof_ctx* c, int l) {
 // that cannot be captured (the legacy default stream), keeps direct launches.
 template <class T>
 void run_vcycle(vof_ctx* c) {
-    if (c->timing || c->vgraph_state < 0) {
+    if (c->timing || c->vgraph_state < 0 || c->sv.graph == VOF_GRAPH_OFF) {
         vcycle<T>(c, 0);
         return;
     }

@@ -36,11 +36,13 @@ def _solve(g, ph, a, b, **kw):
 @pytest.mark.parametrize("dims", [(64, 48, 64),    # density path, partial tiles in y
                                   (96, 40, 36),    # density path, ragged in x and y
                                   (66, 40, 32)])   # nx % 4 != 0: stored FP32 faces
-@pytest.mark.parametrize("nu", [1, 2, 3])
-def test_mixed_paths_reach_fp64_tolerance(dims, nu):
+@pytest.mark.parametrize("nu,cyc", [(1, 0), (2, 0), (3, 0), (2, 1)])
+def test_mixed_paths_reach_fp64_tolerance(dims, nu, cyc):
+    """cyc 0: W-cycle (default), 1: V-cycle."""
     g, ph, a, b, Pstar = _problem(dims, 4, 31)
-    P64, r64 = _solve(g, ph, a, b, rtol=1e-12, precision=0, nu_pre=nu, nu_post=nu)
-    P32, r32 = _solve(g, ph, a, b, rtol=1e-12, precision=1, nu_pre=nu, nu_post=nu)
+    kw = dict(nu_pre=nu, nu_post=nu, mg_cycle=cyc)
+    P64, r64 = _solve(g, ph, a, b, rtol=1e-12, precision=0, **kw)
+    P32, r32 = _solve(g, ph, a, b, rtol=1e-12, precision=1, **kw)
     assert r32["res"] <= 1e-12
     assert r32["iters"] <= 1.5 * r64["iters"] + 6, (r32["iters"], r64["iters"])
     assert rel_l2(P32, Pstar) < 1e-8
@@ -64,3 +66,11 @@ def test_density_path_matches_oracle_at_paper_ratio():
     P, rep = _solve(g, ph, a, b, rtol=1e-11, precision=1)
     assert rep["res"] <= 1e-11
     assert rel_l2(P, Po) < 1e-6
+
+
+def test_w_cycle_needs_fewer_iterations_than_v():
+    g, ph, a, b, _ = _problem((96, 96, 64), 12, 47, d_cells=12.0)
+    _, rw = _solve(g, ph, a, b, rtol=1e-10, precision=1, mg_cycle=0)
+    _, rv = _solve(g, ph, a, b, rtol=1e-10, precision=1, mg_cycle=1)
+    assert rw["res"] <= 1e-10 and rv["res"] <= 1e-10
+    assert rw["iters"] < rv["iters"]
