@@ -101,6 +101,10 @@ typedef struct {
     int mg_cycle;         /* VOF_CYCLE_W (default): every level visits its
                              coarser level twice (once when that one is the
                              coarsest, solved exactly); VOF_CYCLE_V: once    */
+    int mg_w_depth;       /* W-cycle only: the levels l < mg_w_depth visit
+                             their coarser level twice, deeper levels once;
+                             0 selects 3 (the tiny levels, launch-latency
+                             bound, gain nothing from a second visit)        */
     int graph;            /* VOF_GRAPH_AUTO (default): the first cycle of a
                              context on a capturable stream is captured into
                              a CUDA graph and replayed afterwards;

@@ -49,6 +49,13 @@ void vcycle(vof_ctx* c, int l);
 template <class T>
 void cycle(vof_ctx* c, int l, bool zero_start);
 
+// does level l visit its coarser level twice (W-cycle within mg_w_depth,
+// default 3; never when the coarser level is the exactly solved coarsest)?
+bool twice(const vof_ctx* c, int l) {
+    const int depth = c->sv.mg_w_depth > 0 ? c->sv.mg_w_depth : 3;
+    return c->sv.mg_cycle == VOF_CYCLE_W && l + 1 < (int)c->lv.size() - 1 && l < depth;
+}
+
 // Finest level of the mixed V-cycle with the density-formed coefficients:
 // nu_pre red-black sweeps from a zero guess, restriction, the coarse
 // correction, nu_post black-red sweeps. Sweeps ping-pong between xf and
@@ -66,7 +73,7 @@ void vcycle0_rho(vof_ctx* c) {
     }
     rho_restrict(c);
     cycle<float>(c, 1, true);
-    if (c->sv.mg_cycle == VOF_CYCLE_W && c->lv.size() > 2) cycle<float>(c, 1, false);
+    if (twice(c, 0)) cycle<float>(c, 1, false);
     mg_prolong<float>(c, c->lv[1], L0);
     for (int s = 0; s < c->sv.nu_post; ++s) {
         rho_sweep(c, cur, dst, 1);
@@ -100,8 +107,7 @@ void cycle(vof_ctx* c, int l, bool zero_start) {
     }
     mg_restrict<T>(c, L, c->lv[l + 1]);
     cycle<T>(c, l + 1, true);
-    if (c->sv.mg_cycle == VOF_CYCLE_W && l + 1 < (int)c->lv.size() - 1)
-        cycle<T>(c, l + 1, false);
+    if (twice(c, l)) cycle<T>(c, l + 1, false);
     mg_prolong<T>(c, c->lv[l + 1], L);
     for (int s = 0; s < c->sv.nu_post; ++s) {
         mg_rbgs<T>(c, L, 1);
