@@ -51,6 +51,7 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     b += 3 * s.n * sizeof(double);                    // alpha scratch
     b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
     b += mg_workspace_bytes(g, sv, nullptr);
+    if (sv->precision == VOF_PREC_MIXED_FP32) b += 3 * s.n * sizeof(float);  // FP32 cell velocities
     b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
     return b;
 }
@@ -374,6 +375,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     A((void**)&c->part, (size_t)NSLOTS * MAX_PARTIALS * D);
     A((void**)&c->scal, S_NSCALARS * D);
     A((void**)&c->dflag, 64);
+    if (c->sv.precision == VOF_PREC_MIXED_FP32)
+        for (int q = 0; q < 3; ++q) A((void**)&c->u32[q], s.n * sizeof(float));
     if (st == VOF_OK) st = mg_allocate(c);
     if (st == VOF_OK) c->hbuf = c->hbuf_store.data();
     if (st == VOF_OK) {

@@ -20,6 +20,7 @@ struct Pred {
     Dims d;
     const double *an, *a1;    // alpha^n, alpha^{n+1}
     const double* U[3];       // cell velocities at level n
+    const float* U32[3];      // their FP32 copies (mixed path: viscous term)
     const double *u, *v, *w;  // face velocities that advected alpha
     const double *fx, *fy, *fz;
     double rl, rg, ml, mg, rho0, gz, dpdz, dt, h;
@@ -28,14 +29,32 @@ struct Pred {
 
 // velocity component with no-slip ghosts: every component changes sign
 // across a wall (the sign is applied as a negation, not a multiply)
-__device__ __forceinline__ double vcell(const Pred& P, int comp, int i, int j, int k) {
+template <class VT>
+__device__ __forceinline__ VT vcell(const Pred& P, const VT* const* U, int comp, int i, int j,
+                                    int k) {
     bool flip = false;
     if (i < 0) { i = 0; flip = !flip; } else if (i >= P.d.nx) { i = P.d.nx - 1; flip = !flip; }
     if (j < 0) { j = 0; flip = !flip; } else if (j >= P.d.ny) { j = P.d.ny - 1; flip = !flip; }
-    const double q = P.U[comp][cid(P.d, i, j, wrapk(k, P.d.nz))];
+    const VT q = U[comp][cid(P.d, i, j, wrapk(k, P.d.nz))];
     return flip ? -q : q;
 }
 
+template <class VT> __device__ __forceinline__ const VT* const* visc_src(const Pred& P);
+template <> __device__ __forceinline__ const double* const* visc_src<double>(const Pred& P) {
+    return P.U;
+}
+template <> __device__ __forceinline__ const float* const* visc_src<float>(const Pred& P) {
+    return P.U32;
+}
+
+// VT: arithmetic of the viscous term (double on the FP64 path; float on the
+// mixed path, where it changes the velocity by ~1e-4 of itself per step).
+// Convection, densities and the update are FP64 on both paths. Central
+// convection uses sum_f (+-) M_f (q_c + q_nb)/2 = (q_c net + sum_f (+-) M_f
+// q_nb)/2 with the net outward mass flux formed once per cell; each
+// tangential derivative at the cell is formed once and shared by its two
+// faces.
+template <class VT>
 __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ o1,
                           double* __restrict__ o2, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
@@ -43,9 +62,10 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
     const double inv_h = 1.0 / P.h;
-    const double inv_h2 = inv_h * inv_h;
+    const VT inv_h2 = (VT)(inv_h * inv_h);
     const double drho = P.rl - P.rg, dmu = P.ml - P.mg;
     const double rg_dth = P.rg * (P.dt * inv_h);
+    const VT* const* UV = visc_src<VT>(P);
     for (int k = k0; k < k1; ++k) {
         const int c = cid(d, i, j, k);
         const double an = P.an[c];
@@ -53,11 +73,14 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
         const double rn1 = fma(P.a1[c], drho, P.rg);
         const double muc = fma(an, dmu, P.mg);
         // per face f (0,1: -x,+x; 2,3: -y,+y; 4,5: -z,+z): neighbour cell
-        // (clamped at walls), face viscosity, mass flux (0 on walls), donor side
+        // (clamped at walls), face viscosity, signed outward mass flux (0 on
+        // walls), donor side
         int nbc[6];
-        double muf[6], M[6];
+        VT muf[6];
+        double Ms[6];  // outward-signed: -M on minus faces, +M on plus faces
         bool left_donor[6];
-        #pragma unroll
+        double net = 0.0;
+#pragma unroll
         for (int f = 0; f < 6; ++f) {
             const int dd = f >> 1, side = f & 1;
             int ni = i, nj = j, nk = k;
@@ -81,49 +104,71 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
             }
             const int ci = min(max(ni, 0), d.nx - 1), cj = min(max(nj, 0), d.ny - 1);
             nbc[f] = cid(d, ci, cj, wrapk(nk, d.nz));
-            muf[f] = 0.5 * (muc + fma(P.an[nbc[f]], dmu, P.mg));
-            M[f] = wall ? 0.0 : fma(drho, F, rg_dth * uf);
+            muf[f] = (VT)(0.5 * (muc + fma(P.an[nbc[f]], dmu, P.mg)));
+            const double M = wall ? 0.0 : fma(drho, F, rg_dth * uf);
+            Ms[f] = side ? M : -M;
+            net += Ms[f];
             left_donor[f] = uf > 0.0;
         }
         const double r_rn1 = 1.0 / rn1;
         double out[3];
-        #pragma unroll
+#pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
             const double qc = P.U[comp][c];
             // convection: outward mass flux times the transported velocity
             double C = 0.0;
-            #pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const double qn = P.U[comp][nbc[f]];
-                const double qL = (f & 1) ? qc : qn, qR = (f & 1) ? qn : qc;
-                const double qs = P.upwind ? (left_donor[f] ? qL : qR) : 0.5 * (qL + qR);
-                C = (f & 1) ? fma(M[f], qs, C) : fma(-M[f], qs, C);
+            if (P.upwind) {
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    const double qn = P.U[comp][nbc[f]];
+                    // donor: the left cell when u_f > 0 (plus face: this cell)
+                    const bool own = (f & 1) ? left_donor[f] : !left_donor[f];
+                    C = fma(Ms[f], own ? qc : qn, C);
+                }
+            } else {
+                double s = 0.0;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) s = fma(Ms[f], P.U[comp][nbc[f]], s);
+                C = 0.5 * fma(net, qc, s);
             }
             // viscous: (1/h^2) sum_f mu_f [(q_nb - q_c) + s_f (tangential difference)/4]
-            double V = 0.0;
-            #pragma unroll
+            const VT qcv = UV[comp][c];
+            VT g1[3];  // central difference of component dd along comp at the cell
+#pragma unroll
+            for (int dd = 0; dd < 3; ++dd) {
+                if (dd == comp) { g1[dd] = VT(0); continue; }
+                int e[3] = {0, 0, 0};
+                e[comp] = 1;
+                g1[dd] = vcell<VT>(P, UV, dd, i + e[0], j + e[1], k + e[2]) -
+                         vcell<VT>(P, UV, dd, i - e[0], j - e[1], k - e[2]);
+            }
+            VT V = VT(0);
+#pragma unroll
             for (int f = 0; f < 6; ++f) {
                 const int dd = f >> 1;
                 int o[3] = {0, 0, 0};
                 o[dd] = (f & 1) ? 1 : -1;
                 const int ni = i + o[0], nj = j + o[1], nk = k + o[2];
-                const double diff = vcell(P, comp, ni, nj, nk) - qc;
-                double t;
+                const VT diff = vcell<VT>(P, UV, comp, ni, nj, nk) - qcv;
+                VT t;
                 if (dd == comp) {
                     t = diff + diff;
                 } else {
                     int e[3] = {0, 0, 0};
                     e[comp] = 1;
-                    const double g1 = vcell(P, dd, i + e[0], j + e[1], k + e[2]) -
-                                      vcell(P, dd, i - e[0], j - e[1], k - e[2]);
-                    const double g2 = vcell(P, dd, ni + e[0], nj + e[1], nk + e[2]) -
-                                      vcell(P, dd, ni - e[0], nj - e[1], nk - e[2]);
-                    t = fma((f & 1) ? 0.25 : -0.25, g1 + g2, diff);
+                    const VT g2 = vcell<VT>(P, UV, dd, ni + e[0], nj + e[1], nk + e[2]) -
+                                  vcell<VT>(P, UV, dd, ni - e[0], nj - e[1], nk - e[2]);
+                    t = fma((f & 1) ? VT(0.25) : VT(-0.25), g1[dd] + g2, diff);
                 }
                 V = fma(muf[f], t, V);
             }
             const double B = comp == 2 ? (rn - P.rho0) * P.gz + P.dpdz : 0.0;
-            out[comp] = (fma(rn, qc, -C) + P.dt * fma(V, inv_h2, B)) * r_rn1;
+            double force;
+            if (sizeof(VT) == sizeof(double))
+                force = fma((double)V, (double)inv_h2, B);
+            else
+                force = (double)(V * inv_h2) + B;
+            out[comp] = (fma(rn, qc, -C) + P.dt * force) * r_rn1;
         }
         o0[c] = out[0];
         o1[c] = out[1];
@@ -177,7 +222,18 @@ void launch_predict(vof_ctx* c, const double* alpha_n, const double* alpha_np1,
     P.h = c->g.h;
     P.upwind = c->ph.conv_scheme == VOF_CONV_UPWIND;
     int m = timer_begin(c, T_PREDICT);
-    VOF_LAUNCH(c, k_predict, L.grid, L.block, P, out[0], out[1], out[2], L.kchunk);
+    if (c->sv.precision == VOF_PREC_MIXED_FP32) {
+        // FP32 copies of the cell velocities for the viscous term
+        const int n = c->d.nx * c->d.ny * c->d.nz;
+        for (int q = 0; q < 3; ++q) {
+            mg_to_f32(c, U[q], c->u32[q], n);
+            P.U32[q] = c->u32[q];
+        }
+        VOF_LAUNCH(c, k_predict<float>, L.grid, L.block, P, out[0], out[1], out[2], L.kchunk);
+    } else {
+        for (int q = 0; q < 3; ++q) P.U32[q] = nullptr;
+        VOF_LAUNCH(c, k_predict<double>, L.grid, L.block, P, out[0], out[1], out[2], L.kchunk);
+    }
     timer_end(c, T_PREDICT, m);
 }
 

@@ -169,6 +169,7 @@ struct vof_ctx {
     // finest level of the mixed V-cycle with density-formed coefficients
     // (k_smooth_tma.cu): FP32 and FP16 density, second x buffer, TMA maps of
     // x (level-0 xf), x32b and rho16
+    float* u32[3] = {nullptr, nullptr, nullptr};  // mixed: FP32 cell velocities (viscous term)
     bool use_rho = false;
     float* rho32 = nullptr;   // also the mixed path's density for density coarsening
     void* rho16 = nullptr;    // FP16 density of the V-cycle's finest level (__half)
