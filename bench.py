@@ -41,12 +41,12 @@ WORKLOAD = "paper-shaped duct 224x224x640 (32.1M cells), 864 spheres d=12h, Re_b
 #  restrict_l0 residual of 8 children averaged: x, f (16), betas (24),
 #              coarse f written (1)                                  = 41
 #  prolong_l0  fine x read and written (16), coarse x (1)            = 17
-# Mixed path (FP32 V-cycle, finest level from the FP32 cell density, one
+# Mixed path (FP32 V-cycle, finest level from the FP16 cell density, one
 # launch per whole red-black sweep, x ping-ponged between two buffers):
-#  smooth_l0   full sweep: old x (4), density (4), f (4), new x (4) = 16;
-#              the first pre-smoothing sweep starts from zero (12); with
-#              nu sweeps before and after: (12 + 16 (2 nu - 1)) / (2 nu)
-#  restrict_l0 x, density, f (12), coarse f written (0.5)           = 12.5
+#  smooth_l0   full sweep: old x (4), density (2), f (4), new x (4) = 14;
+#              the first pre-smoothing sweep starts from zero (10); with
+#              nu sweeps before and after: (10 + 14 (2 nu - 1)) / (2 nu)
+#  restrict_l0 x, density, f (10), coarse f written (0.5)           = 10.5
 #  prolong_l0  fine x read and written (8), coarse x (0.5)          = 8.5
 #  residual_l0 FP64 outer residual (P 8, b 8, betas 24, FP32 r 4)   = 44
 NU = 2
@@ -56,7 +56,7 @@ def algo_bytes_per_cell(cls: str, precision: str) -> float:
     if precision == "fp64":
         return {"smooth_l0": 36.0, "restrict_l0": 41.0, "prolong_l0": 17.0,
                 "residual_l0": 40.0}[cls]
-    return {"smooth_l0": (12.0 + 16.0 * (2 * NU - 1)) / (2 * NU), "restrict_l0": 12.5,
+    return {"smooth_l0": (10.0 + 14.0 * (2 * NU - 1)) / (2 * NU), "restrict_l0": 10.5,
             "prolong_l0": 8.5, "residual_l0": 44.0}[cls]
 
 
