@@ -358,51 +358,39 @@ __global__ void __launch_bounds__(256, 4)
     }
 }
 
-// A x on the finest level with the density-formed coefficients (times h^2)
-__device__ __forceinline__ float stencil_rho(const Dims& d, const float* __restrict__ rho,
-                                             const float* __restrict__ x, int i, int j, int k) {
-    const int c = cid(d, i, j, k);
-    const float xc = x[c], rc = rho[c];
-    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, wrapk(k + 1, d.nz));
-    float s = 0.f;
-    if (i > 0) s = fmaf(beta_rho(rc, rho[c - 1]), xc - x[c - 1], s);
-    if (i < d.nx - 1) s = fmaf(beta_rho(rc, rho[c + 1]), xc - x[c + 1], s);
-    if (j > 0) s = fmaf(beta_rho(rc, rho[c - d.nx]), xc - x[c - d.nx], s);
-    if (j < d.ny - 1) s = fmaf(beta_rho(rc, rho[c + d.nx]), xc - x[c + d.nx], s);
-    s = fmaf(beta_rho(rc, rho[cb]), xc - x[cb], s);
-    s = fmaf(beta_rho(rc, rho[ct]), xc - x[ct], s);
-    return s;
-}
-
-// A x from the FP16 density (the V-cycle's finest-level operator, times h^2)
-__device__ __forceinline__ float stencil_rho16(const Dims& d, const __half* __restrict__ rho,
-                                               const float* __restrict__ x, int i, int j, int k) {
-    const int c = cid(d, i, j, k);
-    const float xc = x[c], rc = __half2float(rho[c]);
-    const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, wrapk(k + 1, d.nz));
-    float s = 0.f;
-    if (i > 0) s = fmaf(beta_rho(rc, __half2float(rho[c - 1])), xc - x[c - 1], s);
-    if (i < d.nx - 1) s = fmaf(beta_rho(rc, __half2float(rho[c + 1])), xc - x[c + 1], s);
-    if (j > 0) s = fmaf(beta_rho(rc, __half2float(rho[c - d.nx])), xc - x[c - d.nx], s);
-    if (j < d.ny - 1) s = fmaf(beta_rho(rc, __half2float(rho[c + d.nx])), xc - x[c + d.nx], s);
-    s = fmaf(beta_rho(rc, __half2float(rho[cb])), xc - x[cb], s);
-    s = fmaf(beta_rho(rc, __half2float(rho[ct])), xc - x[ct], s);
-    return s;
-}
-
+// Restriction of the residual: the 8 children's residuals summed. The
+// fluxes through the 12 faces inside the 2x2x2 block cancel in that sum
+// (each leaves one child and enters another), so only the 24 faces on the
+// block's boundary are formed:
+//   sum_c r_c = sum_c f_c - (1/h^2) sum_{boundary f} beta_f (x_in - x_out).
 __global__ void k_restrict_rho(Dims df, float ih2, const __half* __restrict__ rho,
                                const float* __restrict__ xf, const float* __restrict__ ff, Dims dc,
                                float* __restrict__ fc, int kchunk) {
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    const int sx = 1, sy = df.nx;
+    const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     for (int K = k0; K < k1; ++K) {
-        float s = 0.f;
+        float fs = 0.f, flux = 0.f;
+        const int kk[2] = {2 * K, 2 * K + 1};
+        const int kout[2] = {wrapk(2 * K - 1, df.nz), wrapk(2 * K + 2, df.nz)};
+#pragma unroll
         for (int c3 = 0; c3 < 8; ++c3) {
-            const int i = 2 * I + (c3 & 1), j = 2 * J + ((c3 >> 1) & 1), k = 2 * K + (c3 >> 2);
-            s += ff[cid(df, i, j, k)] - stencil_rho16(df, rho, xf, i, j, k) * ih2;
+            const int a = c3 & 1, b = (c3 >> 1) & 1, e = c3 >> 2;
+            const int c = cid(df, 2 * I + a, 2 * J + b, kk[e]);
+            const float xc = xf[c], rc = __half2float(rho[c]);
+            fs += ff[c];
+            // boundary faces of this child: the outer side in x, y and z
+            const int ox = a ? sx : -sx, oy = b ? sy : -sy;
+            if (a ? xh : xl)
+                flux = fmaf(beta_rho(rc, __half2float(rho[c + ox])), xc - xf[c + ox], flux);
+            if (b ? yh : yl)
+                flux = fmaf(beta_rho(rc, __half2float(rho[c + oy])), xc - xf[c + oy], flux);
+            const int cz = cid(df, 2 * I + a, 2 * J + b, kout[e]);
+            flux = fmaf(beta_rho(rc, __half2float(rho[cz])), xc - xf[cz], flux);
         }
-        fc[cid(dc, I, J, K)] = 0.125f * s;
+        fc[cid(dc, I, J, K)] = 0.125f * (fs - flux * ih2);
     }
 }
 
@@ -417,20 +405,61 @@ struct Kahan32 {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// q = A p on the FP32 density with the block partials of p.q. Each thread
+// marches up its z chunk and carries the coefficient of the face below;
+// the coefficient of the face to the +x neighbour is the neighbour lane's
+// -x coefficient (a warp spans 32 consecutive x).
 __global__ void k_apply_A_dot_rho32(Dims d, float ih2, const float* __restrict__ rho,
                                     const float* __restrict__ p, float* __restrict__ q,
                                     double* __restrict__ part, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     const bool act = i < d.nx && j < d.ny;
+    const int ic = min(i, d.nx - 1), jc = min(j, d.ny - 1);  // inactive lanes mirror a valid cell
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    const int lane = threadIdx.x & 31;
     Kahan32 ks;
-    if (act)
+    if (k0 < k1) {
+        int c = cid(d, ic, jc, k0);
+        const int cb0 = cid(d, ic, jc, wrapk(k0 - 1, d.nz));
+        float rc = rho[c], pc = p[c];
+        float bzm = beta_rho(rc, rho[cb0]);
+        float pm = p[cb0];
         for (int k = k0; k < k1; ++k) {
-            const int c = cid(d, i, j, k);
-            const float v = stencil_rho(d, rho, p, i, j, k) * ih2;
-            q[c] = v;
-            ks.add(p[c] * v);
+            const int ct = cid(d, ic, jc, wrapk(k + 1, d.nz));
+            const float rt = rho[ct], pt = p[ct];
+            // x faces: own -x face, +x face from the next lane
+            const float rw = ic > 0 ? rho[c - 1] : rc;
+            const float pw = ic > 0 ? p[c - 1] : pc;
+            const float bxm = ic > 0 ? beta_rho(rc, rw) : 0.f;
+            float bxp = __shfl_down_sync(0xffffffffu, bxm, 1);
+            float pe = __shfl_down_sync(0xffffffffu, pc, 1);
+            if (lane == 31 || ic + 1 >= d.nx) {
+                bxp = ic + 1 < d.nx ? beta_rho(rc, rho[c + 1]) : 0.f;
+                pe = ic + 1 < d.nx ? p[c + 1] : pc;
+            }
+            const float bym = jc > 0 ? beta_rho(rc, rho[c - d.nx]) : 0.f;
+            const float byp = jc + 1 < d.ny ? beta_rho(rc, rho[c + d.nx]) : 0.f;
+            const float ps = jc > 0 ? p[c - d.nx] : pc, pn = jc + 1 < d.ny ? p[c + d.nx] : pc;
+            const float bzp = beta_rho(rc, rt);
+            float s = bxm * (pc - pw);
+            s = fmaf(bxp, pc - pe, s);
+            s = fmaf(bym, pc - ps, s);
+            s = fmaf(byp, pc - pn, s);
+            s = fmaf(bzm, pc - pm, s);
+            s = fmaf(bzp, pc - pt, s);
+            const float v = s * ih2;
+            if (act) {
+                q[c] = v;
+                ks.add(pc * v);
+            }
+            // move up one plane
+            bzm = bzp;
+            pm = pc;
+            rc = rt;
+            pc = pt;
+            c = ct;
         }
+    }
     const double acc = block_sum(ks.value());
     if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
 }
