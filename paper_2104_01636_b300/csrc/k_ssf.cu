@@ -1,4 +1,5 @@
 // Height-function curvature and the sharp surface force (Eq. 6; steps 5-7).
+// The curvature runs only for the interface cells, compacted into a list.
 //
 // kappa is the divergence of the unit normal pointing into the liquid
 // (a gas sphere of radius R has kappa = 2/R). At an interface cell the
@@ -21,30 +22,60 @@
 
 namespace {
 
-__global__ void k_curvature(Geo g, const double* __restrict__ a, double* __restrict__ kappa,
-                            unsigned char* __restrict__ valid, double inv_h, int exact,
-                            double kappa_exact, int kchunk) {
+// Pass 1: zero kappa and the validity flags of every cell and append the
+// interface cells to a list (warp-aggregated atomic; the order never
+// changes a value), so that the FP64 height-function work runs only for
+// them, in full warps.
+__global__ void k_curv_list(Dims d, const double* __restrict__ a, double* __restrict__ kappa,
+                            unsigned char* __restrict__ valid, int* __restrict__ list,
+                            int* __restrict__ count, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
-    if (i >= g.d.nx || j >= g.d.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.d.nz);
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    const unsigned lane = (threadIdx.x + TBX * threadIdx.y) & 31;
     for (int k = k0; k < k1; ++k) {
-        const int c = cid(g.d, i, j, k);
-        const double ac = a[c];
+        int c = 0;
+        bool itf = false;
+        if (act) {
+            c = cid(d, i, j, k);
+            const double ac = a[c];
+            itf = ac > EPS_IF && ac < 1.0 - EPS_IF;
+            kappa[c] = 0.0;
+            valid[c] = 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, itf);
+        if (m) {
+            int base = 0;
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = atomicAdd(count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (itf) list[base + __popc(m & ((1u << lane) - 1u))] = c;
+        }
+    }
+}
+
+// Pass 2: curvature of every listed interface cell.
+__global__ void k_curvature_list(Geo g, const double* __restrict__ a,
+                                 const int* __restrict__ list, const int* __restrict__ count,
+                                 double* __restrict__ kappa, unsigned char* __restrict__ valid,
+                                 double inv_h, int exact, double kappa_exact) {
+    const int n = *count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int c = list[t];
+        const int i = c % g.d.nx, j = (c / g.d.nx) % g.d.ny, k = c / (g.d.nx * g.d.ny);
         double kap = 0.0;
-        unsigned char ok = 0;
+        unsigned char ok = 1;
         if (exact) {
-            ok = ac > EPS_IF && ac < 1.0 - EPS_IF;
-            kap = ok ? kappa_exact : 0.0;
-        } else if (ac > EPS_IF && ac < 1.0 - EPS_IF) {
-            double n[3];
-            smoothed_normal(g, a, i, j, k, n);
+            kap = kappa_exact;
+        } else {
+            double n3[3];
+            smoothed_normal(g, a, i, j, k, n3);
             int dir = 0;
-            double best = fabs(n[0]);
-            if (fabs(n[1]) > best * (1.0 + 1e-9)) { dir = 1; best = fabs(n[1]); }
-            if (fabs(n[2]) > best * (1.0 + 1e-9)) dir = 2;
+            double best = fabs(n3[0]);
+            if (fabs(n3[1]) > best * (1.0 + 1e-9)) { dir = 1; best = fabs(n3[1]); }
+            if (fabs(n3[2]) > best * (1.0 + 1e-9)) dir = 2;
             const int t1 = dir == 0 ? 1 : 0, t2 = dir == 2 ? 1 : 2;
             double col[3][3];
-            ok = 1;
             for (int p = -1; p <= 1; ++p)
                 for (int q = -1; q <= 1; ++q) {
                     double s = 0.0, lo = 0.0, hi = 0.0;
@@ -155,9 +186,12 @@ __global__ void k_ssf_faces(SsfArgs A, double* __restrict__ sx, double* __restri
 void launch_curvature(vof_ctx* c, const double* alpha, double* kappa, unsigned char* valid) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_SSF);
-    VOF_LAUNCH(c, k_curvature, L.grid, L.block, Geo{c->d, 0, 0}, alpha, kappa, valid, 1.0 / c->g.h,
-                                               c->ph.kappa_mode == VOF_KAPPA_EXACT,
-                                               c->ph.kappa_exact, L.kchunk);
+    cudaMemsetAsync(c->if_count, 0, sizeof(int), c->st);
+    VOF_LAUNCH(c, k_curv_list, L.grid, L.block, c->d, alpha, kappa, valid, c->if_list, c->if_count,
+               L.kchunk);
+    VOF_LAUNCH(c, k_curvature_list, c->sm_count * 16, 128, Geo{c->d, 0, 0}, alpha, c->if_list,
+               c->if_count, kappa, valid, 1.0 / c->g.h, c->ph.kappa_mode == VOF_KAPPA_EXACT,
+               c->ph.kappa_exact);
     timer_end(c, T_SSF, m);
 }
 
