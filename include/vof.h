@@ -109,6 +109,11 @@ typedef struct {
                              context on a capturable stream is captured into
                              a CUDA graph and replayed afterwards;
                              VOF_GRAPH_OFF: direct launches always           */
+    int ssf_solves;       /* 1 (or 0, the default): one solve for the total
+                             pressure P = p + p~ with b carrying div(beta s);
+                             2: the paper's two solves (steps 6 and 11), p~
+                             from div(beta s) and p from div(u_hat)/dt, then
+                             P = p + p~ (equal up to the solver tolerance)   */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };

@@ -1,5 +1,6 @@
 // C ABI of the projection step (include/vof.h): context lifetime, argument
 // validation, the workspace, and the five entry points of the time step.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -52,6 +53,7 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
     b += mg_workspace_bytes(g, sv, nullptr);
     if (sv->precision == VOF_PREC_MIXED_FP32) b += 3 * s.n * sizeof(float);  // FP32 cell velocities
+    if (sv->ssf_solves == 2) b += 2 * s.n * sizeof(double);                  // p~ and p
     b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
     return b;
 }
@@ -224,9 +226,32 @@ void timer_end(vof_ctx* c, int, int mark) {
 static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* const Uc[3],
                                double* u, double* v, double* w, double* p, const double* sx,
                                const double* sy, const double* sz, double dt, vof_report* r) {
-    launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, -1);
-    vof_status st = solve_pressure(c, c->rhs, p, r);
-    if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
+    vof_status st;
+    if (c->sv.ssf_solves == 2) {
+        // the paper's steps 6 and 11: p~ from the surface force, p from the
+        // velocity divergence, both with beta^{n+1}; P = p + p~. The guess
+        // for p is P^n - p~^n; p~ starts from its previous solution.
+        const int n = c->d.nx * c->d.ny * c->d.nz;
+        launch_lincomb(c, n, 1.0, p, -1.0, c->ptilde, c->pflow);
+        launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, 2);
+        vof_report r1;
+        std::memset(&r1, 0, sizeof(r1));
+        st = solve_pressure(c, c->rhs, c->ptilde, &r1);
+        if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
+        launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, 1);
+        const vof_status st2 = solve_pressure(c, c->rhs, c->pflow, r);
+        if (st2 != VOF_OK && st2 != VOF_ERR_NOT_CONVERGED) return st2;
+        launch_lincomb(c, n, 1.0, c->pflow, 1.0, c->ptilde, p);
+        r->iters += r1.iters;
+        r->refinements += r1.refinements;
+        r->res = std::max(r->res, r1.res);
+        r->b_mean += r1.b_mean;
+        st = st != VOF_OK ? st : st2;
+    } else {
+        launch_rhs(c, u, v, w, sx, sy, sz, dt, c->rhs, 3);
+        st = solve_pressure(c, c->rhs, p, r);
+        if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
+    }
     launch_correct(c, p, sx, sy, sz, dt, Uh, Uc, u, v, w, P_A, P_B);
     readback(c);
     r->max_div = c->hbuf[S_MAXDIV];
@@ -295,7 +320,7 @@ vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, s
     std::string why;
     if (!grid_ok(grid, why) || !bytes) return VOF_ERR_ARG;
     vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2, 0.0, 0, 0.0, VOF_MG_CONSTANT,
-                   VOF_COARSEN_FACE_MEAN, VOF_CYCLE_W, 0, VOF_GRAPH_AUTO};
+                   VOF_COARSEN_FACE_MEAN, VOF_CYCLE_W, 0, VOF_GRAPH_AUTO, 1};
     *bytes = workspace_bytes(grid, solver ? solver : &def);
     return VOF_OK;
 }
@@ -319,7 +344,7 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
          solver->mg_coarsen != VOF_COARSEN_DENSITY_MEAN) ||
         (solver->mg_cycle != VOF_CYCLE_V && solver->mg_cycle != VOF_CYCLE_W) ||
         (solver->graph != VOF_GRAPH_AUTO && solver->graph != VOF_GRAPH_OFF) ||
-        solver->mg_w_depth < 0 ||
+        solver->mg_w_depth < 0 || solver->ssf_solves < 0 || solver->ssf_solves > 2 ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
         return VOF_ERR_ARG;
     const size_t need = workspace_bytes(grid, solver);
@@ -377,10 +402,15 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     A((void**)&c->dflag, 64);
     if (c->sv.precision == VOF_PREC_MIXED_FP32)
         for (int q = 0; q < 3; ++q) A((void**)&c->u32[q], s.n * sizeof(float));
+    if (c->sv.ssf_solves == 2) {
+        A((void**)&c->ptilde, s.n * D);
+        A((void**)&c->pflow, s.n * D);
+    }
     if (st == VOF_OK) st = mg_allocate(c);
     if (st == VOF_OK) c->hbuf = c->hbuf_store.data();
     if (st == VOF_OK) {
         cudaMemsetAsync(c->scal, 0, S_NSCALARS * D, c->st);
+        if (c->ptilde) cudaMemsetAsync(c->ptilde, 0, s.n * D, c->st);
         cudaMemsetAsync(c->part, 0, (size_t)NSLOTS * MAX_PARTIALS * D, c->st);
         st = cuda_check(c, cudaStreamSynchronize(c->st), "vof_create");
     }

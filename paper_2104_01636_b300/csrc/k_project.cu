@@ -12,7 +12,7 @@ __global__ void k_rhs(Dims d, const double* __restrict__ u, const double* __rest
                       const double* __restrict__ by, const double* __restrict__ bz,
                       const double* __restrict__ sx, const double* __restrict__ sy,
                       const double* __restrict__ sz, double inv_h, double inv_dt,
-                      double* __restrict__ b, int kchunk) {
+                      double wu, double ws, double* __restrict__ b, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -26,7 +26,7 @@ __global__ void k_rhs(Dims d, const double* __restrict__ u, const double* __rest
         const double ds = (wx1 ? 0.0 : bx[uh] * sx[uh]) - (wx0 ? 0.0 : bx[ul] * sx[ul]) +
                           (wy1 ? 0.0 : by[vh] * sy[vh]) - (wy0 ? 0.0 : by[vl] * sy[vl]) +
                           bz[wh] * sz[wh] - bz[wl] * sz[wl];
-        b[cid(d, i, j, k)] = -du * inv_h * inv_dt - ds * inv_h;
+        b[cid(d, i, j, k)] = -wu * du * inv_h * inv_dt - ws * ds * inv_h;
     }
 }
 
@@ -112,13 +112,27 @@ __global__ void k_div_max(Dims d, const double* __restrict__ u, const double* __
 
 }  // namespace
 
+// terms: bit 0 the velocity divergence -div(u_hat)/dt, bit 1 the surface
+// force -div(beta s)
 void launch_rhs(vof_ctx* c, const double* u, const double* v, const double* w, const double* sx,
-                const double* sy, const double* sz, double dt, double* b, int) {
+                const double* sy, const double* sz, double dt, double* b, int terms) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_RHS);
     VOF_LAUNCH(c, k_rhs, L.grid, L.block, c->d, u, v, w, c->bx, c->by, c->bz, sx, sy, sz,
-                                         1.0 / c->g.h, 1.0 / dt, b, L.kchunk);
+               1.0 / c->g.h, 1.0 / dt, (terms & 1) ? 1.0 : 0.0, (terms & 2) ? 1.0 : 0.0, b,
+               L.kchunk);
     timer_end(c, T_RHS, m);
+}
+
+__global__ void k_lincomb(int n, double a, const double* __restrict__ x, double b,
+                          const double* __restrict__ y, double* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        out[e] = a * x[e] + b * y[e];
+}
+
+void launch_lincomb(vof_ctx* c, int n, double a, const double* x, double b, const double* y,
+                    double* out) {
+    VOF_LAUNCH(c, k_lincomb, 4 * c->sm_count, 256, n, a, x, b, y, out);
 }
 
 void launch_correct(vof_ctx* c, const double* P, const double* sx, const double* sy,

@@ -434,6 +434,20 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
     return VOF_OK;
 }
 
+// A right side that is exactly zero after its mean is removed has the
+// mean-free solution P = 0.
+static vof_status zero_solution(vof_ctx* c, double* P, vof_report* rep, double b_mean) {
+    launch_zero(c, P, c->lv[0].ncells);
+    if (rep) {
+        rep->iters = 0;
+        rep->refinements = 0;
+        rep->res0 = 0.0;
+        rep->res = 0.0;
+        rep->b_mean = b_mean;
+    }
+    return cuda_check(c, cudaGetLastError(), "pressure solve");
+}
+
 // Solves A P = b_in - mean(b_in) with the fine-level beta already built.
 vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report* rep) {
     const int n = c->lv[0].ncells;
@@ -448,6 +462,7 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
         readback(c);
         vof_status st = cuda_check(c, cudaGetLastError(), "pressure solve setup");
         if (st != VOF_OK) return st;
+        if (c->hbuf[S_BB] == 0.0) return zero_solution(c, P, rep, c->hbuf[S_MEAN]);
         double bnorm = std::sqrt(c->hbuf[S_BB]);
         if (!(bnorm >= 1e-300)) bnorm = 1e-300;
         const double res0 = std::sqrt(c->hbuf[S_RR]) / bnorm;
@@ -463,6 +478,7 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
     vof_status st = cuda_check(c, cudaGetLastError(), "pressure solve setup");
     if (st != VOF_OK) return st;
     const double b_mean = c->hbuf[S_MEAN];
+    if (c->hbuf[S_BB] == 0.0) return zero_solution(c, P, rep, b_mean);
     double bnorm = std::sqrt(c->hbuf[S_BB]);
     if (!(bnorm >= 1e-300)) bnorm = 1e-300;
     double res = std::sqrt(c->hbuf[S_RR]) / bnorm;

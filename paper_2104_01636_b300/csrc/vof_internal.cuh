@@ -170,6 +170,7 @@ struct vof_ctx {
     // (k_smooth_tma.cu): FP32 and FP16 density, second x buffer, TMA maps of
     // x (level-0 xf), x32b and rho16
     float* u32[3] = {nullptr, nullptr, nullptr};  // mixed: FP32 cell velocities (viscous term)
+    double *ptilde = nullptr, *pflow = nullptr;   // two-solve mode: p~ (kept) and p
     bool use_rho = false;
     float* rho32 = nullptr;   // also the mixed path's density for density coarsening
     void* rho16 = nullptr;    // FP16 density of the V-cycle's finest level (__half)
@@ -294,6 +295,8 @@ void launch_cell_to_face(vof_ctx* c, const double* uc, const double* vc, const d
 // projection (k_project.cu)
 void launch_rhs(vof_ctx* c, const double* u, const double* v, const double* w, const double* sx,
                 const double* sy, const double* sz, double dt, double* b, int slot);
+void launch_lincomb(vof_ctx* c, int n, double a, const double* x, double b, const double* y,
+                    double* out);  // out = a x + b y
 void launch_correct(vof_ctx* c, const double* P, const double* sx, const double* sy,
                     const double* sz, double dt, const double* const Uh[3], double* const Uc[3],
                     double* u, double* v, double* w, int slot_div, int slot_u);
