@@ -353,6 +353,30 @@ vof_status vof_ensemble_step(vof_ensemble* ensemble, double* const* fields, cons
                              long long step_index, vof_status* status, vof_report* reports);
 vof_status vof_ensemble_destroy(vof_ensemble* ensemble);
 
+/* ---- duct statistics ------------------------------------------------------
+ * Running sums for the profiles of Section 4 (averages over the streamwise
+ * direction z and over time, mixture and liquid phase). For every column
+ * (i, j) of the cross-section, over all z and all samples, the FP64 sums of
+ *   q = 0..9:   phi = 1 - alpha, u, v, w, uu, vv, ww, uv, uw, vw
+ *   q = 10..19: alpha, and alpha times each of u, v, w, uu, vv, ww, uv, uw, vw
+ * (u, v, w the cell-centred velocities). Mixture means are sums / (samples *
+ * nz); liquid means are the alpha-weighted sums / sum of alpha. Each column
+ * is summed by one thread in z order, so the sums are deterministic. Uses
+ * the current device. */
+#define VOF_NSTAT 20
+typedef struct vof_stats vof_stats;
+
+vof_status vof_stats_create(const vof_grid* grid, vof_stats** out);
+/* One sample: DEVICE fields (cell layout) of one state, on the given stream
+ * (a cudaStream_t; NULL for the legacy default stream). */
+vof_status vof_stats_accumulate(vof_stats* stats, const double* alpha, const double* uc,
+                                const double* vc, const double* wc, void* stream);
+/* Waits for the device, then copies the sums to sums (host, VOF_NSTAT x ny x
+ * nx, q slowest) and the sample count. */
+vof_status vof_stats_read(vof_stats* stats, double* sums, long long* samples);
+vof_status vof_stats_reset(vof_stats* stats);
+vof_status vof_stats_destroy(vof_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

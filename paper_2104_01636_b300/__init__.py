@@ -131,6 +131,11 @@ def load() -> ctypes.CDLL:
                                 ctypes.c_int, P(_VP)],
         "vof_ensemble_step": [_VP, P(_VP), P(_D), ctypes.c_longlong, P(ctypes.c_int), P(CReport)],
         "vof_ensemble_destroy": [_VP],
+        "vof_stats_create": [P(CGrid), P(_VP)],
+        "vof_stats_accumulate": [_VP, _VP, _VP, _VP, _VP, _VP],
+        "vof_stats_read": [_VP, P(_D), P(ctypes.c_longlong)],
+        "vof_stats_reset": [_VP],
+        "vof_stats_destroy": [_VP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -467,3 +472,100 @@ class VofEnsemble:
 
     def __exit__(self, *a):
         self.close()
+
+
+NSTAT = 20
+STAT_NAMES = ("phi", "u", "v", "w", "uu", "vv", "ww", "uv", "uw", "vw")
+
+
+class VofStats:
+    """Running z- and time-sums of the duct statistics on the device
+    (`vof_stats_*`); `means()` turns them into profiles over the cross-section."""
+
+    def __init__(self, grid):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        torch.cuda.init()
+        self.lib = load()
+        self.grid = grid
+        self._g = c_grid(grid)
+        self._s = _VP()
+        st = self.lib.vof_stats_create(ctypes.byref(self._g), ctypes.byref(self._s))
+        if st:
+            raise VofError(st, "vof_stats_create")
+
+    def accumulate(self, alpha, uc, vc, wc, stream=None):
+        import torch
+        shape = (self.grid.nz, self.grid.ny, self.grid.nx)
+        for t in (alpha, uc, vc, wc):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                    and t.is_contiguous() and tuple(t.shape) == shape):
+                raise TypeError(f"need contiguous float64 CUDA tensors of shape {shape}")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        st = self.lib.vof_stats_accumulate(self._s, alpha.data_ptr(), uc.data_ptr(), vc.data_ptr(),
+                                           wc.data_ptr(), _VP(s.cuda_stream))
+        if st:
+            raise VofError(st, "vof_stats_accumulate")
+
+    def sums(self):
+        import numpy as np
+        out = np.zeros((NSTAT, self.grid.ny, self.grid.nx))
+        n = ctypes.c_longlong(0)
+        st = self.lib.vof_stats_read(self._s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     ctypes.byref(n))
+        if st:
+            raise VofError(st, "vof_stats_read")
+        return out, int(n.value)
+
+    def means(self):
+        """Mixture means of phi, u, v, w and the second moments; the liquid
+        means (alpha-weighted, prefixed 'l_'); and the Reynolds stresses
+        ('rs_uu' = <uu> - <u><u>, ...), each a (ny, nx) array."""
+        import numpy as np
+        S, n = self.sums()
+        if n == 0:
+            raise ValueError("no samples")
+        N = n * self.grid.nz
+        out = {name: S[q] / N for q, name in enumerate(STAT_NAMES)}
+        wa = np.where(S[10] > 0, S[10], 1.0)
+        for q, name in enumerate(STAT_NAMES[1:], start=1):
+            out["l_" + name] = S[10 + q] / wa
+        for p in ("l_", ""):
+            for a, b in (("u", "u"), ("v", "v"), ("w", "w"), ("u", "v"), ("u", "w"), ("v", "w")):
+                out[p + "rs_" + a + b] = out[p + a + b] - out[p + a] * out[p + b]
+        out["samples"] = n
+        return out
+
+    def reset(self):
+        st = self.lib.vof_stats_reset(self._s)
+        if st:
+            raise VofError(st, "vof_stats_reset")
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            self.lib.vof_stats_destroy(self._s)
+            self._s = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fold_quadrants(profile, parity_x: int = 1, parity_y: int = 1):
+    """Average a (ny, nx) cross-section profile over the duct's four
+    quadrants (mirror symmetry about both centre lines). parity_x/_y = -1
+    for a quantity odd under the mirror in x/y (u under x-mirror, v under
+    y-mirror, uv under either, ...)."""
+    import numpy as np
+    p = np.asarray(profile)
+    return 0.25 * (p + parity_x * p[:, ::-1] + parity_y * p[::-1, :] +
+                   parity_x * parity_y * p[::-1, ::-1])
