@@ -71,10 +71,17 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
 // are disjoint, so x is read and written through separate restrict
 // pointers to the same array, which lets loads of later planes be issued
 // early. Needs an even nx (every smoothed level has one).
-template <class T>
+// MODE 1: the first pass from a zero x (the neighbours count as zero, so
+// no separate zeroing pass is needed). MODE 2: the first pass after the
+// coarse-grid correction, which reads each neighbour as x + omega x_coarse
+// of its parent: Gauss-Seidel never reads a cell's own old value, and this
+// pass and the next overwrite every cell, so no separate prolongation pass
+// is needed.
+template <class T, int MODE>
 __global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* __restrict__ by,
                               const T* __restrict__ bz, const T* __restrict__ xr,
-                              T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk) {
+                              T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk,
+                              Dims dc, const T* __restrict__ xc, T omega) {
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (t >= (d.nx >> 1) || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -82,17 +89,34 @@ __global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* _
     for (int k = k0; k < k1; ++k) {
         const int i = 2 * t + ((j + k + color) & 1);
         const int c = cid(d, i, j, k);
-        const int cw = i > 0 ? c - 1 : c;
-        const int ce = i < d.nx - 1 ? c + 1 : c;
-        const int cs = j > 0 ? c - d.nx : c;
-        const int cn = j < d.ny - 1 ? c + d.nx : c;
-        const int kp = wrapk(k + 1, d.nz);
-        const int cb = cid(d, i, j, wrapk(k - 1, d.nz)), ct = cid(d, i, j, kp);
+        const int kp = wrapk(k + 1, d.nz), km = wrapk(k - 1, d.nz);
+        const int iw = i > 0 ? i - 1 : i, ie = i < d.nx - 1 ? i + 1 : i;
+        const int js = j > 0 ? j - 1 : j, jn = j < d.ny - 1 ? j + 1 : j;
+        const int cw = cid(d, iw, j, k), ce = cid(d, ie, j, k);
+        const int cs = cid(d, i, js, k), cn = cid(d, i, jn, k);
+        const int cb = cid(d, i, j, km), ct = cid(d, i, j, kp);
         const T b0 = bx[uid(d, i, j, k)], b1 = bx[uid(d, i + 1, j, k)];
         const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
         const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
-        const T num = h2 * f[c] + b0 * xr[cw] + b1 * xr[ce] + b2 * xr[cs] + b3 * xr[cn] +
-                      b4 * xr[cb] + b5 * xr[ct];
+        // across a wall (beta = 0) the neighbour is taken as 0, never read:
+        // the cell's own value may not have been written yet (MODE 1)
+        const bool hw = i > 0, he = i < d.nx - 1, hs = j > 0, hn = j < d.ny - 1;
+        T num;
+        if (MODE == 1) {
+            num = h2 * f[c];
+        } else if (MODE == 2) {
+            auto xv = [&](int cc, int ii, int jj, int kk) {
+                return xr[cc] + omega * xc[cid(dc, ii >> 1, jj >> 1, kk >> 1)];
+            };
+            num = h2 * f[c] + b0 * (hw ? xv(cw, iw, j, k) : T(0)) +
+                  b1 * (he ? xv(ce, ie, j, k) : T(0)) + b2 * (hs ? xv(cs, i, js, k) : T(0)) +
+                  b3 * (hn ? xv(cn, i, jn, k) : T(0)) + b4 * xv(cb, i, j, km) +
+                  b5 * xv(ct, i, j, kp);
+        } else {
+            num = h2 * f[c] + b0 * (hw ? xr[cw] : T(0)) + b1 * (he ? xr[ce] : T(0)) +
+                  b2 * (hs ? xr[cs] : T(0)) + b3 * (hn ? xr[cn] : T(0)) + b4 * xr[cb] +
+                  b5 * xr[ct];
+        }
         const T den = b0 + b1 + b2 + b3 + b4 + b5;
         xw[c] = den > T(0) ? num / den : T(0);
     }
@@ -602,18 +626,29 @@ LA<float> arrays<float>(const Level& L) {
 }  // namespace
 
 template <class T>
-void mg_rbgs(vof_ctx* c, const Level& L, int color) {
+void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
     const LA<T> a = arrays<T>(L);
     const int cls = L.idx == 0 ? T_SMOOTH0 : T_SMOOTH;
-    int m = timer_begin(c, cls);
-    if (L.d.nx % 2 == 0) {
-        const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
-        VOF_LAUNCH(c, k_rbgs_pair_t<T>, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
-                   (const T*)a.x, a.x, a.f, color, L.L.kchunk);
-    } else {
+    if (L.d.nx % 2 != 0) {  // odd rows: separate zeroing / prolongation passes
+        if (mode == 1) mg_zero<T>(c, L);
+        if (mode == 2) mg_prolong<T>(c, *C, L);
+        int m = timer_begin(c, cls);
         VOF_LAUNCH(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
                    a.x, a.f, color, L.L.kchunk);
+        timer_end(c, cls, m);
+        return;
     }
+    using K = void (*)(Dims, T, const T*, const T*, const T*, const T*, T*, const T*, int, int,
+                       Dims, const T*, T);
+    const K kern = mode == 1 ? k_rbgs_pair_t<T, 1> : (mode == 2 ? k_rbgs_pair_t<T, 2>
+                                                              : k_rbgs_pair_t<T, 0>);
+    const Dims dc = C ? C->d : L.d;
+    const T* xc = C ? arrays<T>(*C).x : nullptr;
+    const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
+    const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
+    int m = timer_begin(c, cls);
+    VOF_LAUNCH(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
+               a.x, a.f, color, L.L.kchunk, dc, xc, omega);
     timer_end(c, cls, m);
 }
 
@@ -783,8 +818,8 @@ void mg_to_f64(vof_ctx* c, const float* a, double* b, int n) {
     VOF_LAUNCH(c, k_to_f64, flat_blocks(n), 256, n, a, b);
 }
 
-template void mg_rbgs<double>(vof_ctx*, const Level&, int);
-template void mg_rbgs<float>(vof_ctx*, const Level&, int);
+template void mg_rbgs<double>(vof_ctx*, const Level&, int, int, const Level*);
+template void mg_rbgs<float>(vof_ctx*, const Level&, int, int, const Level*);
 template void mg_restrict<double>(vof_ctx*, const Level&, const Level&);
 template void mg_restrict<float>(vof_ctx*, const Level&, const Level&);
 template void mg_prolong<double>(vof_ctx*, const Level&, const Level&);

@@ -100,17 +100,16 @@ void cycle(vof_ctx* c, int l, bool zero_start) {
         vcycle0_rho(c);
         return;
     }
-    if (zero_start) mg_zero<T>(c, L);
     for (int s = 0; s < c->sv.nu_pre; ++s) {
-        mg_rbgs<T>(c, L, 0);
+        mg_rbgs<T>(c, L, 0, (s == 0 && zero_start) ? 1 : 0);  // from zero: no zeroing pass
         mg_rbgs<T>(c, L, 1);
     }
     mg_restrict<T>(c, L, c->lv[l + 1]);
     cycle<T>(c, l + 1, true);
     if (twice(c, l)) cycle<T>(c, l + 1, false);
-    mg_prolong<T>(c, c->lv[l + 1], L);
     for (int s = 0; s < c->sv.nu_post; ++s) {
-        mg_rbgs<T>(c, L, 1);
+        // the first pass adds the coarse correction to what it reads
+        mg_rbgs<T>(c, L, 1, s == 0 ? 2 : 0, &c->lv[l + 1]);
         mg_rbgs<T>(c, L, 0);
     }
 }

@@ -240,7 +240,11 @@ void launch_scalar_alpha(vof_ctx* c);
 void launch_scalar_beta(vof_ctx* c);
 
 // multigrid (k_mg.cu), T = double (FP64 path) or float (mixed path)
-template <class T> void mg_rbgs(vof_ctx* c, const Level& L, int color);
+// one red-black colour pass; mode 1: the first pass from a zero x, mode 2:
+// the first pass after the coarse correction from level *coarse (folds in
+// the prolongation)
+template <class T> void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode = 0,
+                                const Level* coarse = nullptr);
 template <class T> void mg_restrict(vof_ctx* c, const Level& fine, const Level& coarse);
 template <class T> void mg_prolong(vof_ctx* c, const Level& coarse, const Level& fine);
 template <class T> void mg_coarsen_beta(vof_ctx* c, const Level& fine, const Level& coarse);
