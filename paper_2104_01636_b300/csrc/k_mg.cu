@@ -122,6 +122,10 @@ __global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* _
     }
 }
 
+// Restriction of the residual averaged over the 8 children. The fluxes
+// through the 12 faces inside the 2x2x2 block cancel in the children's sum,
+// so only the 24 faces on the block's boundary are formed:
+//   sum_c r_c = sum_c f_c - (1/h^2) sum_{boundary f} beta_f (x_in - x_out).
 template <class T>
 __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T* __restrict__ by,
                              const T* __restrict__ bz, const T* __restrict__ xf,
@@ -129,13 +133,30 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     for (int K = k0; K < k1; ++K) {
-        T s = T(0);
+        T fs = T(0), flux = T(0);
+        const int kk[2] = {2 * K, 2 * K + 1};
+        const int kout[2] = {wrapk(2 * K - 1, df.nz), wrapk(2 * K + 2, df.nz)};
+#pragma unroll
         for (int c3 = 0; c3 < 8; ++c3) {
-            const int i = 2 * I + (c3 & 1), j = 2 * J + ((c3 >> 1) & 1), k = 2 * K + (c3 >> 2);
-            s += ff[cid(df, i, j, k)] - stencil_t(df, bx, by, bz, xf, i, j, k) * ih2f;
+            const int a = c3 & 1, b = (c3 >> 1) & 1, e = c3 >> 2;
+            const int i = 2 * I + a, j = 2 * J + b, k = kk[e];
+            const int c = cid(df, i, j, k);
+            const T xc = xf[c];
+            fs += ff[c];
+            if (a ? xh : xl) {
+                const int ci = a ? c + 1 : c - 1;
+                flux += bx[uid(df, i + a, j, k)] * (xc - xf[ci]);
+            }
+            if (b ? yh : yl) {
+                const int cj = b ? c + df.nx : c - df.nx;
+                flux += by[vid(df, i, j + b, k)] * (xc - xf[cj]);
+            }
+            const int cz = cid(df, i, j, kout[e]);
+            flux += bz[wid(df, i, j, e ? kout[1] : k)] * (xc - xf[cz]);
         }
-        fc[cid(dc, I, J, K)] = T(0.125) * s;
+        fc[cid(dc, I, J, K)] = T(0.125) * (fs - flux * ih2f);
     }
 }
 
