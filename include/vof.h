@@ -109,6 +109,8 @@ typedef struct {
                              context on a capturable stream is captured into
                              a CUDA graph and replayed afterwards;
                              VOF_GRAPH_OFF: direct launches always           */
+    int nu_fine;          /* sweeps before and after on the finest level
+                             (0: nu_pre, like every other level)             */
     int ssf_solves;       /* 1 (or 0, the default): one solve for the total
                              pressure P = p + p~ with b carrying div(beta s);
                              2: the paper's two solves (steps 6 and 11), p~

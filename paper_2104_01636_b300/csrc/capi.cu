@@ -320,7 +320,7 @@ vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, s
     std::string why;
     if (!grid_ok(grid, why) || !bytes) return VOF_ERR_ARG;
     vof_solver def{VOF_PREC_FP64, 1e-10, 200, 2, 2, 0.0, 0, 0.0, VOF_MG_CONSTANT,
-                   VOF_COARSEN_FACE_MEAN, VOF_CYCLE_W, 0, VOF_GRAPH_AUTO, 1};
+                   VOF_COARSEN_FACE_MEAN, VOF_CYCLE_W, 0, VOF_GRAPH_AUTO, 0, 1};
     *bytes = workspace_bytes(grid, solver ? solver : &def);
     return VOF_OK;
 }
@@ -345,6 +345,7 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
         (solver->mg_cycle != VOF_CYCLE_V && solver->mg_cycle != VOF_CYCLE_W) ||
         (solver->graph != VOF_GRAPH_AUTO && solver->graph != VOF_GRAPH_OFF) ||
         solver->mg_w_depth < 0 || solver->ssf_solves < 0 || solver->ssf_solves > 2 ||
+        solver->nu_fine < 0 ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
         return VOF_ERR_ARG;
     const size_t need = workspace_bytes(grid, solver);

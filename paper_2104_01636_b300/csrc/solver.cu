@@ -64,9 +64,10 @@ void vcycle0_rho(vof_ctx* c) {
     Level& L0 = c->lv[0];
     float* const A = L0.xf;
     float* const B = c->x32b;
+    const int nu = c->sv.nu_fine > 0 ? c->sv.nu_fine : c->sv.nu_pre;
     const float* cur = nullptr;  // zero
-    float* dst = (c->sv.nu_pre % 2 == 1) ? A : B;
-    for (int s = 0; s < c->sv.nu_pre; ++s) {
+    float* dst = (nu % 2 == 1) ? A : B;
+    for (int s = 0; s < nu; ++s) {
         rho_sweep(c, cur, dst, 0);
         cur = dst;
         dst = (dst == A) ? B : A;
@@ -75,7 +76,7 @@ void vcycle0_rho(vof_ctx* c) {
     cycle<float>(c, 1, true);
     if (twice(c, 0)) cycle<float>(c, 1, false);
     mg_prolong<float>(c, c->lv[1], L0);
-    for (int s = 0; s < c->sv.nu_post; ++s) {
+    for (int s = 0; s < nu; ++s) {
         rho_sweep(c, cur, dst, 1);
         cur = dst;
         dst = (dst == A) ? B : A;
@@ -100,14 +101,15 @@ void cycle(vof_ctx* c, int l, bool zero_start) {
         vcycle0_rho(c);
         return;
     }
-    for (int s = 0; s < c->sv.nu_pre; ++s) {
+    const int nu = (l == 0 && c->sv.nu_fine > 0) ? c->sv.nu_fine : c->sv.nu_pre;
+    for (int s = 0; s < nu; ++s) {
         mg_rbgs<T>(c, L, 0, (s == 0 && zero_start) ? 1 : 0);  // from zero: no zeroing pass
         mg_rbgs<T>(c, L, 1);
     }
     mg_restrict<T>(c, L, c->lv[l + 1]);
     cycle<T>(c, l + 1, true);
     if (twice(c, l)) cycle<T>(c, l + 1, false);
-    for (int s = 0; s < c->sv.nu_post; ++s) {
+    for (int s = 0; s < nu; ++s) {
         // the first pass adds the coarse correction to what it reads
         mg_rbgs<T>(c, L, 1, s == 0 ? 2 : 0, &c->lv[l + 1]);
         mg_rbgs<T>(c, L, 0);

@@ -65,7 +65,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
         "vof_phys": (vd.CPhys, ["rho_l", "conv_scheme", "kappa_exact"]),
         "vof_solver": (vd.CSolver, ["precision", "rtol", "mg_omega", "coarse_tol", "mg_interp",
                                     "mg_coarsen", "mg_cycle", "mg_w_depth", "graph",
-                                    "ssf_solves"]),
+                                    "nu_fine", "ssf_solves"]),
         "vof_report": (vd.CReport, ["iters", "res0", "hf_fallbacks", "ms"]),
         "vof_request": (vd.CRequest, ["kind", "grid", "phys", "solver", "n_steps", "dt", "step0",
                                       "alpha", "p", "b"]),
