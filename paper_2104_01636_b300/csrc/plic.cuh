@@ -105,8 +105,17 @@ __device__ __forceinline__ double solve_half(double b1, double b2, double b3, do
         const double p = a - b1, q = a - b2, r = e_piece ? a - b3 : 0.0;
         const double f = (a * a + a * p + p * p - (q * q * q + r * r * r) * ib1) * i6 - V;
         const double df = (a + p - (q * q + r * r) * ib1) * i2;
+        if (f == 0.0) break;
         if (f > 0.0) hi = a; else lo = a;
-        double an = df > 0.0 ? a - f * rcp_approx64(df) : 0.5 * (lo + hi);
+        const double dn = df > 0.0 ? f * rcp_approx64(df) : 0.0;
+        // a Newton correction below the rounding of a means a is the root to
+        // working precision; take it before the bracket test, which would
+        // reject the unchanged a (it sits on the bracket) and bisect
+        if (df > 0.0 && fabs(dn) <= 2.3e-16 * a) {
+            a -= dn;
+            break;
+        }
+        double an = df > 0.0 ? a - dn : 0.5 * (lo + hi);
         if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
         const double step = fabs(an - a);
         a = an;
