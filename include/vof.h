@@ -116,11 +116,21 @@ typedef struct {
                              2: the paper's two solves (steps 6 and 11), p~
                              from div(beta s) and p from div(u_hat)/dt, then
                              P = p + p~ (equal up to the solver tolerance)   */
+    int mg_tail;          /* VOF_TAIL_LAUNCHES (default): one launch per
+                             smoothing pass, restriction and coarsest solve
+                             on every level (replayed from the cycle's CUDA
+                             graph); VOF_TAIL_CLUSTER (mixed path with the
+                             dense coarsest solve): from the first level of
+                             at most 8192 cells down, each visit of the cycle
+                             runs as one launch on one thread-block cluster,
+                             its operations separated by cluster barriers,
+                             with the same arithmetic (equal iterates)      */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
 enum { VOF_CYCLE_W = 0, VOF_CYCLE_V = 1 };
 enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1 };
+enum { VOF_TAIL_LAUNCHES = 0, VOF_TAIL_CLUSTER = 1 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 

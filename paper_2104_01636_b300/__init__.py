@@ -53,7 +53,8 @@ class CSolver(ctypes.Structure):
                 ("coarse_tol", ctypes.c_double), ("mg_interp", ctypes.c_int),
                 ("mg_coarsen", ctypes.c_int), ("mg_cycle", ctypes.c_int),
                 ("mg_w_depth", ctypes.c_int), ("graph", ctypes.c_int),
-                ("nu_fine", ctypes.c_int), ("ssf_solves", ctypes.c_int)]
+                ("nu_fine", ctypes.c_int), ("ssf_solves", ctypes.c_int),
+                ("mg_tail", ctypes.c_int)]
 
 
 class CReport(ctypes.Structure):
@@ -160,16 +161,17 @@ def c_phys(p) -> CPhys:
 COARSEN_FACE_MEAN, COARSEN_DENSITY_MEAN = 0, 1
 CYCLE_W, CYCLE_V = 0, 1
 GRAPH_AUTO, GRAPH_OFF = 0, 1
+TAIL_LAUNCHES, TAIL_CLUSTER = 0, 1
 
 
 def c_solver(precision=PREC_FP64, rtol=1e-10, max_iter=200, nu_pre=2, nu_post=2, mg_omega=0.0,
              coarse_iters=0, coarse_tol=0.0, mg_interp=0, mg_coarsen=COARSEN_FACE_MEAN,
              mg_cycle=CYCLE_W, mg_w_depth=0, graph=GRAPH_AUTO, nu_fine=0,
-             ssf_solves=1) -> CSolver:
+             ssf_solves=1, mg_tail=0) -> CSolver:
     return CSolver(int(precision), float(rtol), int(max_iter), int(nu_pre), int(nu_post),
                    float(mg_omega), int(coarse_iters), float(coarse_tol), int(mg_interp),
                    int(mg_coarsen), int(mg_cycle), int(mg_w_depth), int(graph), int(nu_fine),
-                   int(ssf_solves))
+                   int(ssf_solves), int(mg_tail))
 
 
 def workspace_bytes(grid, solver: CSolver | None = None) -> int:

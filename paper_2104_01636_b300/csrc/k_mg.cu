@@ -14,6 +14,7 @@
 // coarsest levels fall back to Jacobi-preconditioned CG in one thread block.
 #include <algorithm>
 
+#include "mg_cell.cuh"
 #include "vof_internal.cuh"
 
 namespace {
@@ -86,46 +87,12 @@ __global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* _
     if (t >= (d.nx >> 1) || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
 #pragma unroll 2
-    for (int k = k0; k < k1; ++k) {
-        const int i = 2 * t + ((j + k + color) & 1);
-        const int c = cid(d, i, j, k);
-        const int kp = wrapk(k + 1, d.nz), km = wrapk(k - 1, d.nz);
-        const int iw = i > 0 ? i - 1 : i, ie = i < d.nx - 1 ? i + 1 : i;
-        const int js = j > 0 ? j - 1 : j, jn = j < d.ny - 1 ? j + 1 : j;
-        const int cw = cid(d, iw, j, k), ce = cid(d, ie, j, k);
-        const int cs = cid(d, i, js, k), cn = cid(d, i, jn, k);
-        const int cb = cid(d, i, j, km), ct = cid(d, i, j, kp);
-        const T b0 = bx[uid(d, i, j, k)], b1 = bx[uid(d, i + 1, j, k)];
-        const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
-        const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
-        // across a wall (beta = 0) the neighbour is taken as 0, never read:
-        // the cell's own value may not have been written yet (MODE 1)
-        const bool hw = i > 0, he = i < d.nx - 1, hs = j > 0, hn = j < d.ny - 1;
-        T num;
-        if (MODE == 1) {
-            num = h2 * f[c];
-        } else if (MODE == 2) {
-            auto xv = [&](int cc, int ii, int jj, int kk) {
-                return xr[cc] + omega * xc[cid(dc, ii >> 1, jj >> 1, kk >> 1)];
-            };
-            num = h2 * f[c] + b0 * (hw ? xv(cw, iw, j, k) : T(0)) +
-                  b1 * (he ? xv(ce, ie, j, k) : T(0)) + b2 * (hs ? xv(cs, i, js, k) : T(0)) +
-                  b3 * (hn ? xv(cn, i, jn, k) : T(0)) + b4 * xv(cb, i, j, km) +
-                  b5 * xv(ct, i, j, kp);
-        } else {
-            num = h2 * f[c] + b0 * (hw ? xr[cw] : T(0)) + b1 * (he ? xr[ce] : T(0)) +
-                  b2 * (hs ? xr[cs] : T(0)) + b3 * (hn ? xr[cn] : T(0)) + b4 * xr[cb] +
-                  b5 * xr[ct];
-        }
-        const T den = b0 + b1 + b2 + b3 + b4 + b5;
-        xw[c] = den > T(0) ? num / den : T(0);
-    }
+    for (int k = k0; k < k1; ++k)
+        rbgs_cell<T, MODE>(d, h2, bx, by, bz, xr, xw, f, 2 * t + ((j + k + color) & 1), j, k, dc,
+                           xc, omega, LdPlain());
 }
 
-// Restriction of the residual averaged over the 8 children. The fluxes
-// through the 12 faces inside the 2x2x2 block cancel in the children's sum,
-// so only the 24 faces on the block's boundary are formed:
-//   sum_c r_c = sum_c f_c - (1/h^2) sum_{boundary f} beta_f (x_in - x_out).
+// Restriction of the residual averaged over the 8 children (restrict_cell).
 template <class T>
 __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T* __restrict__ by,
                              const T* __restrict__ bz, const T* __restrict__ xf,
@@ -133,31 +100,8 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
-    const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
-    for (int K = k0; K < k1; ++K) {
-        T fs = T(0), flux = T(0);
-        const int kk[2] = {2 * K, 2 * K + 1};
-        const int kout[2] = {wrapk(2 * K - 1, df.nz), wrapk(2 * K + 2, df.nz)};
-#pragma unroll
-        for (int c3 = 0; c3 < 8; ++c3) {
-            const int a = c3 & 1, b = (c3 >> 1) & 1, e = c3 >> 2;
-            const int i = 2 * I + a, j = 2 * J + b, k = kk[e];
-            const int c = cid(df, i, j, k);
-            const T xc = xf[c];
-            fs += ff[c];
-            if (a ? xh : xl) {
-                const int ci = a ? c + 1 : c - 1;
-                flux += bx[uid(df, i + a, j, k)] * (xc - xf[ci]);
-            }
-            if (b ? yh : yl) {
-                const int cj = b ? c + df.nx : c - df.nx;
-                flux += by[vid(df, i, j + b, k)] * (xc - xf[cj]);
-            }
-            const int cz = cid(df, i, j, kout[e]);
-            flux += bz[wid(df, i, j, e ? kout[1] : k)] * (xc - xf[cz]);
-        }
-        fc[cid(dc, I, J, K)] = T(0.125) * (fs - flux * ih2f);
-    }
+    for (int K = k0; K < k1; ++K)
+        restrict_cell(df, ih2f, bx, by, bz, xf, ff, dc, fc, I, J, K, LdPlain());
 }
 
 template <class T>
@@ -514,17 +458,14 @@ __global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const
     out[(long)i * n + j] = v;
 }
 
-// x = Minv f: one warp per row, FP64 accumulation
+// x = Minv f: one warp per row (dense_row)
 template <class T>
 __global__ void k_dense_apply(int n, const T* __restrict__ Minv, const T* __restrict__ f,
                               T* __restrict__ x) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
-    const T* row = Minv + (long)warp * n;
-    double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += (double)row[j] * (double)f[j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[warp] = (T)acc;
+    const double s = dense_row(Minv + (long)warp * n, [&](int j) { return f[j]; }, n, lane);
+    if (lane == 0) x[warp] = (T)s;
 }
 
 template <class T>

@@ -93,6 +93,10 @@ void vcycle0_rho(vof_ctx* c) {
 template <class T>
 void cycle(vof_ctx* c, int l, bool zero_start) {
     const Level& L = c->lv[l];
+    if (sizeof(T) == sizeof(float) && l == c->tail_level && l > 0) {
+        mg_tail_run(c, zero_start);  // this level and every coarser one, one launch
+        return;
+    }
     if (l == (int)c->lv.size() - 1) {
         mg_coarse<T>(c, L);
         return;
@@ -114,6 +118,55 @@ void cycle(vof_ctx* c, int l, bool zero_start) {
         mg_rbgs<T>(c, L, 1, s == 0 ? 2 : 0, &c->lv[l + 1]);
         mg_rbgs<T>(c, L, 0);
     }
+}
+
+// The operations cycle<float>(c, l, zero_start) launches for a level l >= 1
+// and everything below it, appended to a coarse-tail program in the same
+// order (level indices relative to the tail level t0); false when the
+// program does not fit.
+bool tail_emit(const vof_ctx* c, int l, int t0, bool zero_start, TailProg& p) {
+    auto push = [&](int kind, int lev, int color, int mode) {
+        if (p.nops >= TAIL_MAX_OPS) return false;
+        p.op[p.nops++] = TailOp{(unsigned char)kind, (unsigned char)(lev - t0),
+                                (unsigned char)color, (unsigned char)mode};
+        return true;
+    };
+    if (l == (int)c->lv.size() - 1) return push(TAIL_DENSE, l, 0, 0);
+    const int nu = c->sv.nu_pre;
+    for (int s = 0; s < nu; ++s)
+        if (!push(TAIL_SMOOTH, l, 0, (s == 0 && zero_start) ? 1 : 0) || !push(TAIL_SMOOTH, l, 1, 0))
+            return false;
+    if (!push(TAIL_RESTRICT, l, 0, 0) || !tail_emit(c, l + 1, t0, true, p)) return false;
+    if (twice(c, l) && !tail_emit(c, l + 1, t0, false, p)) return false;
+    for (int s = 0; s < nu; ++s)
+        if (!push(TAIL_SMOOTH, l, 1, s == 0 ? 2 : 0) || !push(TAIL_SMOOTH, l, 0, 0)) return false;
+    return true;
+}
+
+// VOF_TAIL_CLUSTER on the mixed path with the dense coarsest solve: the
+// first level l >= 1 of at most TAIL_MAX_CELLS cells runs its part of the
+// cycle as one cluster launch per visit.
+vof_status tail_setup(vof_ctx* c) {
+    const int nl = (int)c->lv.size();
+    if (c->sv.precision != VOF_PREC_MIXED_FP32 || c->sv.mg_interp != VOF_MG_CONSTANT ||
+        c->dense_n <= 0 || c->sv.mg_tail != VOF_TAIL_CLUSTER)
+        return VOF_OK;
+    for (int t0 = 1; t0 + 1 < nl; ++t0) {
+        if (c->lv[t0].ncells > TAIL_MAX_CELLS || nl - t0 > TAIL_MAX_LEVELS) continue;
+        TailProg p[2];
+        for (int z = 0; z < 2; ++z) {
+            p[z] = TailProg{};
+            p[z].omega = (float)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
+            for (int l = t0; l < nl; ++l) {
+                const Level& L = c->lv[l];
+                p[z].L[l - t0] = TailLevel{L.d, (float)(L.h * L.h), (float)(1.0 / (L.h * L.h)),
+                                           L.bxf, L.byf, L.bzf, L.xf, L.ff};
+            }
+        }
+        if (tail_emit(c, t0, t0, true, p[0]) && tail_emit(c, t0, t0, false, p[1]))
+            return mg_tail_setup(c, t0, &p[0], &p[1]);
+    }
+    return VOF_OK;
 }
 
 template <class T>
@@ -205,6 +258,7 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
     const Dims& dc = dims.back();
     const size_t nc = (size_t)dc.nx * dc.ny * dc.nz;
     b += 4 * nc * sizeof(double);
+    if (mixed) b += 2 * sizeof(TailProg);  // coarse-tail programs
     if (nc <= (size_t)DENSE_MAX) b += (nc * nc * 2 + 32 * 32 + 64 * nc) * elt;
     return b;
 }
@@ -313,8 +367,11 @@ vof_status mg_allocate(vof_ctx* c) {
         // shift: the liquid face coefficient (the smallest physical one) per face
         c->dense_shift = 1.0 / c->ph.rho_l;
     }
-    if (c->use_rho) return rho_path_setup(c);
-    return VOF_OK;
+    if (c->use_rho) {
+        const vof_status st = rho_path_setup(c);
+        if (st != VOF_OK) return st;
+    }
+    return tail_setup(c);
 }
 
 void mg_build_coefficients(vof_ctx* c) {

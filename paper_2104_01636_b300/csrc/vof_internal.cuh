@@ -118,6 +118,30 @@ struct Level {
     Launch L;
 };
 
+// ---------------------------------------------------------------------------
+// coarse tail of the mixed cycle in one cluster launch (k_mg_tail.cu): the
+// operations of the cycle from level tail_level down, as a program
+// ---------------------------------------------------------------------------
+constexpr int TAIL_MAX_LEVELS = 16;
+constexpr int TAIL_MAX_OPS = 256;
+constexpr int TAIL_MAX_CELLS = 8192;  // largest level the tail starts from
+enum TailKind { TAIL_SMOOTH = 0, TAIL_RESTRICT = 1, TAIL_DENSE = 2 };
+struct TailLevel {
+    Dims d;
+    float h2, ih2;  // h^2 (smoother), 1/h^2 (restriction)
+    const float *bx, *by, *bz;
+    float *x, *f;
+};
+struct TailOp {
+    unsigned char kind, lev, color, mode;  // lev: index relative to the tail level
+};
+struct alignas(16) TailProg {
+    TailLevel L[TAIL_MAX_LEVELS];
+    TailOp op[TAIL_MAX_OPS];
+    int nops;
+    float omega;
+};
+
 struct vof_ctx {
     vof_grid g;
     vof_phys ph;
@@ -184,6 +208,12 @@ struct vof_ctx {
     cudaGraphExec_t vgraph = nullptr;
     long long vgraph_kernels = 0;
     int vgraph_state = 0;
+
+    // coarse tail (0: not used); programs from zero / from the current x
+    int tail_level = 0;
+    int tail_cluster = 0;
+    TailProg* tail_prog = nullptr;  // device copies of tail_host
+    TailProg tail_host[2];
 
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
@@ -272,6 +302,10 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0);
 void rho_restrict(vof_ctx* c);
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
 void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
+
+// coarse tail (k_mg_tail.cu)
+vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero, const TailProg* from_x);
+void mg_tail_run(vof_ctx* c, bool zero_start);
 
 // vof (k_vof.cu)
 void launch_vof_mask_volume(vof_ctx* c, const double* alpha, int slot);

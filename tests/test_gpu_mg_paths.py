@@ -74,3 +74,30 @@ def test_w_cycle_needs_fewer_iterations_than_v():
     _, rv = _solve(g, ph, a, b, rtol=1e-10, precision=1, mg_cycle=1)
     assert rw["res"] <= 1e-10 and rv["res"] <= 1e-10
     assert rw["iters"] < rv["iters"]
+
+
+def _solve_counted(g, ph, a, b, **kw):
+    with ctx(g, ph, **kw) as C:
+        p = dev(np.zeros_like(b))
+        n0 = C.launch_count()
+        rep = C.pressure_solve(dev(a), dev(b), p)
+        return host(p), rep, C.launch_count() - n0
+
+
+@pytest.mark.parametrize("dims,kw", [((64, 48, 64), {}),                 # tail from level 2
+                                     ((128, 96, 64), {}),                # tail from level 3
+                                     ((64, 32, 32), {"mg_w_depth": 8}),  # W visits inside the tail
+                                     ((64, 32, 32), {"mg_cycle": 1}),    # V-cycle
+                                     ((88, 40, 32), {"nu_pre": 3, "nu_post": 3})])
+def test_coarse_tail_equals_launch_per_operation(dims, kw):
+    """The coarse levels run as one launch per smoothing pass, restriction
+    and coarsest solve (default) or, from a level of at most 8192 cells down,
+    as one thread-block-cluster launch per visit: same cell arithmetic in the
+    same order, so the same iterates bit for bit, with fewer launches."""
+    g, ph, a, b, _ = _problem(dims, 4, 53)
+    Pt, rt, nt = _solve_counted(g, ph, a, b, rtol=1e-10, precision=1, graph=1, mg_tail=1, **kw)
+    Po, ro, no = _solve_counted(g, ph, a, b, rtol=1e-10, precision=1, graph=1, **kw)
+    assert rt["res"] <= 1e-10 and ro["res"] <= 1e-10
+    assert rt["iters"] == ro["iters"]
+    assert np.array_equal(Pt, Po), rel_l2(Pt, Po)
+    assert nt < no, (nt, no)
