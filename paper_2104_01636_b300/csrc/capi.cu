@@ -52,7 +52,7 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     b += 3 * s.n * sizeof(double);                    // alpha scratch
     b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
     b += mg_workspace_bytes(g, sv, nullptr);
-    if (sv->precision == VOF_PREC_MIXED_FP32) b += 3 * s.n * sizeof(float);  // FP32 cell velocities
+    if (sv->precision == VOF_PREC_MIXED_FP32) b += 4 * s.n * sizeof(float);  // FP32 velocities, alpha
     if (sv->ssf_solves == 2) b += 2 * s.n * sizeof(double);                  // p~ and p
     b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
     return b;
@@ -403,7 +403,7 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     A((void**)&c->scal, S_NSCALARS * D);
     A((void**)&c->dflag, 64);
     if (c->sv.precision == VOF_PREC_MIXED_FP32)
-        for (int q = 0; q < 3; ++q) A((void**)&c->u32[q], s.n * sizeof(float));
+        for (int q = 0; q < 4; ++q) A((void**)&c->u32[q], s.n * sizeof(float));
     if (c->sv.ssf_solves == 2) {
         A((void**)&c->ptilde, s.n * D);
         A((void**)&c->pflow, s.n * D);

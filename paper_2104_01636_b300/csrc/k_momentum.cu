@@ -21,6 +21,7 @@ struct Pred {
     const double *an, *a1;    // alpha^n, alpha^{n+1}
     const double* U[3];       // cell velocities at level n
     const float* U32[3];      // their FP32 copies (mixed path: viscous term)
+    const float* a32;         // alpha^n in FP32 (mixed path: face viscosities)
     const double *u, *v, *w;  // face velocities that advected alpha
     const double *fx, *fy, *fz;
     double rl, rg, ml, mg, rho0, gz, dpdz, dt, h;
@@ -47,9 +48,30 @@ template <> __device__ __forceinline__ const float* const* visc_src<float>(const
     return P.U32;
 }
 
+// 1 / s without a division: an FP32 reciprocal seed (relative error below
+// 2^-22) refined by two Newton steps r <- r + r (1 - s r), which leaves FP64
+// rounding (a few ulp); s is a density, a normal positive number
+__device__ __forceinline__ double rcp_newton(double s) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)s));
+    double r = (double)r0;
+    r = fma(r, fma(-s, r, 1.0), r);
+    return fma(r, fma(-s, r, 1.0), r);
+}
+
+// mu of a cell from its volume fraction, in the viscous term's precision
+template <class VT> __device__ __forceinline__ VT mu_cell(const Pred& P, int c);
+template <> __device__ __forceinline__ double mu_cell<double>(const Pred& P, int c) {
+    return fma(P.an[c], P.ml - P.mg, P.mg);
+}
+template <> __device__ __forceinline__ float mu_cell<float>(const Pred& P, int c) {
+    return fmaf(P.a32[c], (float)(P.ml - P.mg), (float)P.mg);
+}
+
 // VT: arithmetic of the viscous term (double on the FP64 path; float on the
 // mixed path, where it changes the velocity by ~1e-4 of itself per step).
-// Convection, densities and the update are FP64 on both paths. Central
+// Convection, densities and the update are FP64 on both paths; the face
+// viscosities are formed in VT. Central
 // convection uses sum_f (+-) M_f (q_c + q_nb)/2 = (q_c net + sum_f (+-) M_f
 // q_nb)/2 with the net outward mass flux formed once per cell; each
 // tangential derivative at the cell is formed once and shared by its two
@@ -63,7 +85,7 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
     const double inv_h = 1.0 / P.h;
     const VT inv_h2 = (VT)(inv_h * inv_h);
-    const double drho = P.rl - P.rg, dmu = P.ml - P.mg;
+    const double drho = P.rl - P.rg;
     const double rg_dth = P.rg * (P.dt * inv_h);
     const VT* const* UV = visc_src<VT>(P);
     for (int k = k0; k < k1; ++k) {
@@ -71,7 +93,7 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
         const double an = P.an[c];
         const double rn = fma(an, drho, P.rg);
         const double rn1 = fma(P.a1[c], drho, P.rg);
-        const double muc = fma(an, dmu, P.mg);
+        const VT muc = mu_cell<VT>(P, c);
         // per face f (0,1: -x,+x; 2,3: -y,+y; 4,5: -z,+z): neighbour cell
         // (clamped at walls), face viscosity, signed outward mass flux (0 on
         // walls), donor side
@@ -104,13 +126,14 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
             }
             const int ci = min(max(ni, 0), d.nx - 1), cj = min(max(nj, 0), d.ny - 1);
             nbc[f] = cid(d, ci, cj, wrapk(nk, d.nz));
-            muf[f] = (VT)(0.5 * (muc + fma(P.an[nbc[f]], dmu, P.mg)));
+            muf[f] = VT(0.5) * (muc + mu_cell<VT>(P, nbc[f]));
             const double M = wall ? 0.0 : fma(drho, F, rg_dth * uf);
             Ms[f] = side ? M : -M;
             net += Ms[f];
-            left_donor[f] = uf > 0.0;
+            // u_f > 0 as a sign test of the bits (no FP64 compare; +-0 is not > 0)
+            left_donor[f] = __double_as_longlong(uf) > 0LL;
         }
-        const double r_rn1 = 1.0 / rn1;
+        const double r_rn1 = rcp_newton(rn1);
         double out[3];
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
@@ -223,15 +246,18 @@ void launch_predict(vof_ctx* c, const double* alpha_n, const double* alpha_np1,
     P.upwind = c->ph.conv_scheme == VOF_CONV_UPWIND;
     int m = timer_begin(c, T_PREDICT);
     if (c->sv.precision == VOF_PREC_MIXED_FP32) {
-        // FP32 copies of the cell velocities for the viscous term
+        // FP32 copies of the cell velocities and of alpha^n for the viscous term
         const int n = c->d.nx * c->d.ny * c->d.nz;
         for (int q = 0; q < 3; ++q) {
             mg_to_f32(c, U[q], c->u32[q], n);
             P.U32[q] = c->u32[q];
         }
+        mg_to_f32(c, alpha_n, c->u32[3], n);
+        P.a32 = c->u32[3];
         VOF_LAUNCH(c, k_predict<float>, L.grid, L.block, P, out[0], out[1], out[2], L.kchunk);
     } else {
         for (int q = 0; q < 3; ++q) P.U32[q] = nullptr;
+        P.a32 = nullptr;
         VOF_LAUNCH(c, k_predict<double>, L.grid, L.block, P, out[0], out[1], out[2], L.kchunk);
     }
     timer_end(c, T_PREDICT, m);

@@ -63,6 +63,8 @@ __device__ __forceinline__ double two_over(double s) {
     return 2.0 * r;
 }
 
+// rho = alpha rho_l + (1 - alpha) rho_g as one FMA, alpha (rho_l - rho_g) + rho_g;
+// each thread marches up z and carries the density of the cell below
 __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double rg,
                        double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
                        float* __restrict__ rho32, __half* __restrict__ rho16,
@@ -70,30 +72,22 @@ __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double r
     CellIdx r = cell_range(d, kchunk);
     if (!r.act) return;
     const int i = r.i, j = r.j;
+    const double drho = rl - rg;
+    auto rho = [&](int c) { return fma(a[c], drho, rg); };
+    double rb = rho(cid(d, i, j, wrapk(r.k0 - 1, d.nz)));
     for (int k = r.k0; k < r.k1; ++k) {
         const int c = cid(d, i, j, k);
-        const double rc = a[c] * rl + (1.0 - a[c]) * rg;
+        const double rc = rho(c);
         if (rho32) rho32[c] = (float)rc;  // finest-level density of the multigrid
         if (rho16) rho16[c] = __double2half(rc);
         if (rho64) rho64[c] = rc;
         // x-face i (between i-1 and i); the last thread also writes the wall face nx
-        if (i == 0) {
-            bx[uid(d, 0, j, k)] = 0.0;
-        } else {
-            const double rw = a[c - 1] * rl + (1.0 - a[c - 1]) * rg;
-            bx[uid(d, i, j, k)] = two_over(rw + rc);
-        }
+        bx[uid(d, i, j, k)] = i == 0 ? 0.0 : two_over(rho(c - 1) + rc);
         if (i == d.nx - 1) bx[uid(d, d.nx, j, k)] = 0.0;
-        if (j == 0) {
-            by[vid(d, i, 0, k)] = 0.0;
-        } else {
-            const double rs = a[c - d.nx] * rl + (1.0 - a[c - d.nx]) * rg;
-            by[vid(d, i, j, k)] = two_over(rs + rc);
-        }
+        by[vid(d, i, j, k)] = j == 0 ? 0.0 : two_over(rho(c - d.nx) + rc);
         if (j == d.ny - 1) by[vid(d, i, d.ny, k)] = 0.0;
-        const int cb = cid(d, i, j, wrapk(k - 1, d.nz));
-        const double rb = a[cb] * rl + (1.0 - a[cb]) * rg;
         bz[wid(d, i, j, k)] = two_over(rb + rc);
+        rb = rc;
     }
 }
 

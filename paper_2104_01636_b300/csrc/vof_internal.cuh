@@ -193,7 +193,8 @@ struct vof_ctx {
     // finest level of the mixed V-cycle with density-formed coefficients
     // (k_smooth_tma.cu): FP32 and FP16 density, second x buffer, TMA maps of
     // x (level-0 xf), x32b and rho16
-    float* u32[3] = {nullptr, nullptr, nullptr};  // mixed: FP32 cell velocities (viscous term)
+    // mixed: FP32 cell velocities and alpha^n (viscous term of the predictor)
+    float* u32[4] = {nullptr, nullptr, nullptr, nullptr};
     double *ptilde = nullptr, *pflow = nullptr;   // two-solve mode: p~ (kept) and p
     bool use_rho = false;
     float* rho32 = nullptr;   // also the mixed path's density for density coarsening
