@@ -11,8 +11,8 @@ __global__ void k_rhs(Dims d, const double* __restrict__ u, const double* __rest
                       const double* __restrict__ w, const double* __restrict__ bx,
                       const double* __restrict__ by, const double* __restrict__ bz,
                       const double* __restrict__ sx, const double* __restrict__ sy,
-                      const double* __restrict__ sz, double inv_h, double inv_dt,
-                      double wu, double ws, double* __restrict__ b, int kchunk) {
+                      const double* __restrict__ sz, double cu, double cs,
+                      double* __restrict__ b, int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -26,7 +26,7 @@ __global__ void k_rhs(Dims d, const double* __restrict__ u, const double* __rest
         const double ds = (wx1 ? 0.0 : bx[uh] * sx[uh]) - (wx0 ? 0.0 : bx[ul] * sx[ul]) +
                           (wy1 ? 0.0 : by[vh] * sy[vh]) - (wy0 ? 0.0 : by[vl] * sy[vl]) +
                           bz[wh] * sz[wh] - bz[wl] * sz[wl];
-        b[cid(d, i, j, k)] = -wu * du * inv_h * inv_dt - ws * ds * inv_h;
+        b[cid(d, i, j, k)] = fma(cu, du, cs * ds);  // cu = -1/(h dt), cs = -1/h (or 0)
     }
 }
 
@@ -93,20 +93,24 @@ __global__ void k_div_max(Dims d, const double* __restrict__ u, const double* __
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     const bool act = i < d.nx && j < d.ny;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
-    double md = 0.0, mu = 0.0;
+    // maxima of magnitudes on the integer pipe: for non-negative doubles the
+    // order of the bit patterns is the order of the values
+    constexpr long long MAG = 0x7FFFFFFFFFFFFFFFLL;
+    auto mag = [](double x) { return __double_as_longlong(x) & MAG; };
+    long long md = 0, mu = 0;
     if (act)
         for (int k = k0; k < k1; ++k) {
             const int ul = uid(d, i, j, k), vl = vid(d, i, j, k), wl = wid(d, i, j, k);
             const int wh = wid(d, i, j, wrapk(k + 1, d.nz));
             const double dv = (u[ul + 1] - u[ul] + v[vl + d.nx] - v[vl] + w[wh] - w[wl]) * inv_h;
-            md = fmax(md, fabs(dv));
-            mu = fmax(mu, fmax(fabs(u[ul + 1]), fmax(fabs(v[vl + d.nx]), fabs(w[wl]))));
+            md = max(md, mag(dv));
+            mu = max(mu, max(mag(u[ul + 1]), max(mag(v[vl + d.nx]), mag(w[wl]))));
         }
-    md = block_max(md);
-    mu = block_max(mu);
+    const double mdd = block_max(__longlong_as_double(md));
+    const double mud = block_max(__longlong_as_double(mu));
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        pdiv[block_linear()] = md;
-        pmax[block_linear()] = mu;
+        pdiv[block_linear()] = mdd;
+        pmax[block_linear()] = mud;
     }
 }
 
@@ -118,9 +122,10 @@ void launch_rhs(vof_ctx* c, const double* u, const double* v, const double* w, c
                 const double* sy, const double* sz, double dt, double* b, int terms) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_RHS);
-    VOF_LAUNCH(c, k_rhs, L.grid, L.block, c->d, u, v, w, c->bx, c->by, c->bz, sx, sy, sz,
-               1.0 / c->g.h, 1.0 / dt, (terms & 1) ? 1.0 : 0.0, (terms & 2) ? 1.0 : 0.0, b,
-               L.kchunk);
+    const double cu = (terms & 1) ? -1.0 / (c->g.h * dt) : 0.0;
+    const double cs = (terms & 2) ? -1.0 / c->g.h : 0.0;
+    VOF_LAUNCH(c, k_rhs, L.grid, L.block, c->d, u, v, w, c->bx, c->by, c->bz, sx, sy, sz, cu, cs,
+               b, L.kchunk);
     timer_end(c, T_RHS, m);
 }
 

@@ -95,12 +95,14 @@ __global__ void k_face_flux_simple(Geo g, int dir, const double* __restrict__ a,
             cL = cid(d, i, j, wrapk(k - 1, d.nz));
         }
         const double u = wall ? 0.0 : vel[f];
-        const int dn = u > 0.0 ? cL : cR;
-        if (u == 0.0) {
+        // sign and zero tests on the bits (integer pipe): u > 0, u == +-0
+        const long long ub = __double_as_longlong(u);
+        const int dn = ub > 0 ? cL : cR;
+        if ((ub << 1) == 0) {
             flux[f] = 0.0;
         } else if (!has[dn]) {
-            const double V = fabs(u) * dt_h * a[dn];
-            flux[f] = u > 0.0 ? V : -V;
+            // (u dt/h) a is -(|u| dt/h a) exactly when u < 0
+            flux[f] = u * dt_h * a[dn];
         }
         // the far wall (or periodic duplicate) face is never a minus face
         if (dir == 0 && i == d.nx - 1) flux[uid(d, d.nx, j, k)] = 0.0;
@@ -182,9 +184,19 @@ __global__ void k_vof_update(Geo g, int dir, const double* __restrict__ ain,
             }
             const double Fm = wm ? 0.0 : flux[fm], Fp = wp ? 0.0 : flux[fp];
             const double vm = wm ? 0.0 : vel[fm], vp = wp ? 0.0 : vel[fp];
-            const double an = ain[c] - (Fp - Fm) + (cm[c] ? 1.0 : 0.0) * (vp - vm) * dt_h;
-            const double ac = fmin(fmax(an, 0.0), 1.0);
-            clip += an - ac;
+            const double an0 = ain[c] - (Fp - Fm);
+            const double an = cm[c] ? an0 + (vp - vm) * dt_h : an0;
+            // clip to [0, 1] with the range tests on the bits: negative
+            // (sign set), above 1 (a larger pattern than that of 1.0)
+            const long long ab = __double_as_longlong(an);
+            double ac = an;
+            if (ab < 0) {
+                ac = 0.0;
+                clip += an;
+            } else if (ab > 0x3FF0000000000000LL) {
+                ac = 1.0;
+                clip += an - 1.0;
+            }
             aout[c] = ac;
         }
     clip = block_sum(clip);
