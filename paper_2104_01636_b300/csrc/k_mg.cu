@@ -44,6 +44,7 @@ template <class T>
 __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __restrict__ by,
                          const T* __restrict__ bz, T* __restrict__ x, const T* __restrict__ f,
                          int color, int kchunk) {
+    pdl_wait();
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -83,6 +84,7 @@ __global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* _
                               const T* __restrict__ bz, const T* __restrict__ xr,
                               T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk,
                               Dims dc, const T* __restrict__ xc, T omega) {
+    pdl_wait();
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (t >= (d.nx >> 1) || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -97,6 +99,7 @@ template <class T>
 __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T* __restrict__ by,
                              const T* __restrict__ bz, const T* __restrict__ xf,
                              const T* __restrict__ ff, Dims dc, T* __restrict__ fc, int kchunk) {
+    pdl_wait();
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
@@ -107,6 +110,7 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
 template <class T>
 __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __restrict__ xf,
                             T omega, int kchunk) {
+    pdl_wait();
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (i >= df.nx || j >= df.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
@@ -462,6 +466,7 @@ __global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const
 template <class T>
 __global__ void k_dense_apply(int n, const T* __restrict__ Minv, const T* __restrict__ f,
                               T* __restrict__ x) {
+    pdl_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const double s = dense_row(Minv + (long)warp * n, [&](int j) { return f[j]; }, n, lane);
@@ -470,6 +475,7 @@ __global__ void k_dense_apply(int n, const T* __restrict__ Minv, const T* __rest
 
 template <class T>
 __global__ void k_zero_t(int n, T* __restrict__ x) {
+    pdl_wait();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         x[c] = T(0);
 }
@@ -595,7 +601,7 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
         if (mode == 1) mg_zero<T>(c, L);
         if (mode == 2) mg_prolong<T>(c, *C, L);
         int m = timer_begin(c, cls);
-        VOF_LAUNCH(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
+        launch_pdl(c, k_rbgs_t<T>, L.L.grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz,
                    a.x, a.f, color, L.L.kchunk);
         timer_end(c, cls, m);
         return;
@@ -609,7 +615,7 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
     const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
     const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
     int m = timer_begin(c, cls);
-    VOF_LAUNCH(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
+    launch_pdl(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
                a.x, a.f, color, L.L.kchunk, dc, xc, omega);
     timer_end(c, cls, m);
 }
@@ -626,7 +632,7 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
         VOF_LAUNCH(c, k_restrict_fw_t<T>, C.L.grid, C.L.block, F.d, (const T*)r, C.d, b.f,
                    C.L.kchunk);
     } else {
-        VOF_LAUNCH(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx,
+        launch_pdl(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx,
                    a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
     }
     timer_end(c, cls, m);
@@ -642,7 +648,7 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
         VOF_LAUNCH(c, k_prolong_tri_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega,
                    F.L.kchunk);
     else
-        VOF_LAUNCH(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
+        launch_pdl(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
     timer_end(c, cls, m);
 }
 
@@ -713,7 +719,7 @@ void mg_coarse(vof_ctx* c, const Level& L) {
     if (c->dense_n > 0) {
         const int n = L.ncells;
         const T* Minv = sizeof(T) == 4 ? (const T*)c->dense_inv_f : (const T*)c->dense_inv;
-        VOF_LAUNCH(c, k_dense_apply<T>, (n * 32 + 255) / 256, 256, n, Minv, a.f, a.x);
+        launch_pdl(c, k_dense_apply<T>, dim3((n * 32 + 255) / 256), dim3(256), n, Minv, a.f, a.x);
         timer_end(c, T_COARSE, m);
         return;
     }
@@ -728,7 +734,7 @@ void mg_coarse(vof_ctx* c, const Level& L) {
 template <class T>
 void mg_zero(vof_ctx* c, const Level& L) {
     const LA<T> a = arrays<T>(L);
-    VOF_LAUNCH(c, k_zero_t<T>, flat_blocks(L.ncells), 256, L.ncells, a.x);
+    launch_pdl(c, k_zero_t<T>, dim3(flat_blocks(L.ncells)), dim3(256), L.ncells, a.x);
 }
 
 void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {

@@ -220,6 +220,34 @@ struct vof_ctx {
     std::string err;
 };
 
+// ---------------------------------------------------------------------------
+// programmatic dependent launch: a kernel launched by launch_pdl is set up
+// while the previous kernel on the stream runs, and its blocks start as that
+// kernel completes, which shortens the gap between the small kernels of the
+// coarse multigrid levels. Such a kernel calls pdl_wait() before it touches
+// global memory: it returns once the previous grid has completed and its
+// writes are visible (at once for a kernel launched the ordinary way).
+// Measured with an early trigger (griddepcontrol.launch_dependents at the
+// top of each kernel) the step was slower: the waiting blocks held SM slots.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+void launch_pdl(vof_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c->st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ++c->nlaunch;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // scalar slots in ctx->scal
 enum ScalarSlot {
     S_RR = 0,     // ||r||^2
