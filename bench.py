@@ -85,6 +85,30 @@ def parse():
 
 
 # ----------------------------------------------------------------------------
+# Multi-GPU: every rank advances an independent replica (its own seeded duct);
+# the job's time is the slowest rank's, and the value counts every rank's steps.
+def replica_seed(rank: int) -> int:
+    return 2106 + rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the process group (x itself when dist
+    is None); device is where the reduction tensor lives (cuda for NCCL, cpu
+    for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, ms_max: float) -> float:
+    """time-steps/s of the whole job: every rank's steps over the slowest rank's time."""
+    return world * steps / (ms_max / 1e3)
+
+
+# ----------------------------------------------------------------------------
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -339,7 +363,7 @@ def main():
         torch.cuda.synchronize()
 
     nbub = round(864 * args.nz / 640)
-    case = I.paper_shaped(224, 224, args.nz, nbub=nbub, seed=2106 + rank)
+    case = I.paper_shaped(224, 224, args.nz, nbub=nbub, seed=replica_seed(rank))
     g = case.grid
     N = g.ncells
     prec = vd.PREC_FP64 if args.precision == "fp64" else vd.PREC_MIXED_FP32
@@ -370,12 +394,9 @@ def main():
         launches = ctx.launch_count() - n0
         ck = clocks.stop()
         ms = e0.elapsed_time(e1)
-        t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        ms_max = float(t_local.item())
+        ms_max = max_over_ranks(ms, dist, "cuda")
         ms_per_step = ms_max / args.steps
-        value = world * args.steps / (ms_max / 1e3)
+        value = whole_job_rate(world, args.steps, ms_max)
 
         # ---- roofline: per-kernel CUDA events on the library stream --------
         ctx.set_timing(True)
@@ -422,10 +443,7 @@ def main():
         e3.record(stream)
         barrier()
         ms_e2e = e2.elapsed_time(e3)
-        te = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_value = world * args.steps / (float(te.item()) / 1e3)
+        e2e_value = whole_job_rate(world, args.steps, max_over_ranks(ms_e2e, dist, "cuda"))
         ctx.close()
 
         # ---- the FP64 path on the same workload, for comparison ------------
