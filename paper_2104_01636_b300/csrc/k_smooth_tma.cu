@@ -241,8 +241,16 @@ __global__ void __launch_bounds__(256, 4)
                 if (!ZERO) num = __ffma2_rn(b, make_float2(X[xa + dx], X[xb + dx]), num);
                 den = __fadd2_rn(den, b);
             };
-            if (i > 0) acc(half_beta2(rc, make_float2(hval(Hq, ha - 1), hval(Hq, hb - 1))), -1, Xq);
-            if (i < nx - 1) acc(half_beta2(rc, make_float2(hval(Hq, ha + 1), hval(Hq, hb + 1))), 1, Xq);
+            // a wall face gets coefficient 0 (no branch: the staged value
+            // beyond the wall is the TMA zero fill)
+            {
+                float2 b = half_beta2(rc, make_float2(hval(Hq, ha - 1), hval(Hq, hb - 1)));
+                if (i == 0) b = make_float2(0.f, 0.f);
+                acc(b, -1, Xq);
+                b = half_beta2(rc, make_float2(hval(Hq, ha + 1), hval(Hq, hb + 1)));
+                if (i == nx - 1) b = make_float2(0.f, 0.f);
+                acc(b, 1, Xq);
+            }
             {
                 float2 b = half_beta2(rc, make_float2(hval(Hq, ha - HBX), hval(Hq, hb - HBX)));
                 if (!ylA) b.x = 0.f;
@@ -304,12 +312,16 @@ __global__ void __launch_bounds__(256, 4)
                 num = __ffma2_rn(b, xn, num);
                 den = __fadd2_rn(den, b);
             };
-            if (i > 0)
-                acc(half_beta2(rc, make_float2(hval(Hk, ha - 1), hval(Hk, hb - 1))),
-                    make_float2(N1[na - 1], N1[nb - 1]));
-            if (i < nx - 1)
-                acc(half_beta2(rc, make_float2(hval(Hk, ha + 1), hval(Hk, hb + 1))),
-                    make_float2(N1[na + 1], N1[nb + 1]));
+            // a wall face gets coefficient 0 (the first-colour value beyond the
+            // wall is the ring's 0)
+            {
+                float2 b = half_beta2(rc, make_float2(hval(Hk, ha - 1), hval(Hk, hb - 1)));
+                if (i == 0) b = make_float2(0.f, 0.f);
+                acc(b, make_float2(N1[na - 1], N1[nb - 1]));
+                b = half_beta2(rc, make_float2(hval(Hk, ha + 1), hval(Hk, hb + 1)));
+                if (i == nx - 1) b = make_float2(0.f, 0.f);
+                acc(b, make_float2(N1[na + 1], N1[nb + 1]));
+            }
             {
                 float2 b = half_beta2(rc, make_float2(hval(Hk, ha - HBX), hval(Hk, hb - HBX)));
                 if (!ylA) b.x = 0.f;
