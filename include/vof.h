@@ -105,10 +105,20 @@ typedef struct {
                              their coarser level twice, deeper levels once;
                              0 selects 3 (the tiny levels, launch-latency
                              bound, gain nothing from a second visit)        */
-    int graph;            /* VOF_GRAPH_AUTO (default): the first cycle of a
-                             context on a capturable stream is captured into
-                             a CUDA graph and replayed afterwards;
-                             VOF_GRAPH_OFF: direct launches always           */
+    int graph;            /* on a capturable stream (not the legacy default
+                             stream), VOF_GRAPH_AUTO (default): the FP64
+                             path captures its V-cycle into a CUDA graph and
+                             replays it; the mixed path captures its whole
+                             pressure solve, with the inner and refinement
+                             loops as conditional WHILE nodes steered by
+                             device-side control kernels, and replays it
+                             (one launch and one host wait per solve; a
+                             graph per right-side/solution pointer pair, two
+                             kept); VOF_GRAPH_CYCLE: the V-cycle graph with
+                             the loops driven from the host (faster for many
+                             contexts running side by side); VOF_GRAPH_OFF:
+                             direct launches always. All three give the
+                             same iterates.                                */
     int nu_fine;          /* sweeps before and after on the finest level
                              (0: nu_pre, like every other level)             */
     int ssf_solves;       /* 1 (or 0, the default): one solve for the total
@@ -129,7 +139,7 @@ typedef struct {
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
 enum { VOF_CYCLE_W = 0, VOF_CYCLE_V = 1 };
-enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1 };
+enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1, VOF_GRAPH_CYCLE = 2 };
 enum { VOF_TAIL_LAUNCHES = 0, VOF_TAIL_CLUSTER = 1 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
@@ -347,7 +357,9 @@ vof_status vof_server_destroy(vof_server* server);
  * Each case has its own context (workspace as vof_create); cases are dealt
  * round-robin to n_streams worker threads, each with its own CUDA stream, so
  * their kernels overlap on the GPU. A case's result is bitwise that of the
- * same case stepped alone by step(). Uses the current device. */
+ * same case stepped alone by step(). Uses the current device. With
+ * solver->graph VOF_GRAPH_AUTO the cases run as VOF_GRAPH_CYCLE (their
+ * solves' loops on the host), which is faster for many cases side by side. */
 typedef struct vof_ensemble vof_ensemble;
 
 /* phys: n_phys = 1 (shared) or n_cases entries (per case, e.g. rho0).

@@ -160,7 +160,7 @@ def c_phys(p) -> CPhys:
 
 COARSEN_FACE_MEAN, COARSEN_DENSITY_MEAN = 0, 1
 CYCLE_W, CYCLE_V = 0, 1
-GRAPH_AUTO, GRAPH_OFF = 0, 1
+GRAPH_AUTO, GRAPH_OFF, GRAPH_CYCLE = 0, 1, 2
 TAIL_LAUNCHES, TAIL_CLUSTER = 0, 1
 
 

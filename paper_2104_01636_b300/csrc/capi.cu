@@ -343,7 +343,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
         (solver->mg_coarsen != VOF_COARSEN_FACE_MEAN &&
          solver->mg_coarsen != VOF_COARSEN_DENSITY_MEAN) ||
         (solver->mg_cycle != VOF_CYCLE_V && solver->mg_cycle != VOF_CYCLE_W) ||
-        (solver->graph != VOF_GRAPH_AUTO && solver->graph != VOF_GRAPH_OFF) ||
+        (solver->graph != VOF_GRAPH_AUTO && solver->graph != VOF_GRAPH_OFF &&
+         solver->graph != VOF_GRAPH_CYCLE) ||
         (solver->mg_tail != VOF_TAIL_LAUNCHES && solver->mg_tail != VOF_TAIL_CLUSTER) ||
         solver->mg_w_depth < 0 || solver->ssf_solves < 0 || solver->ssf_solves > 2 ||
         solver->nu_fine < 0 ||
@@ -431,6 +432,10 @@ vof_status vof_destroy(vof_ctx* c) {
     cudaStreamSynchronize(c->st);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->vgraph) cudaGraphExecDestroy(c->vgraph);
+    for (auto& sg : c->sgraph)
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    for (cudaStream_t s : c->cap_st)
+        if (s) cudaStreamDestroy(s);
     delete c;
     return VOF_OK;
 }

@@ -183,7 +183,7 @@ void vcycle(vof_ctx* c, int l) {
 // that cannot be captured (the legacy default stream), keeps direct launches.
 template <class T>
 void run_vcycle(vof_ctx* c) {
-    if (c->timing || c->vgraph_state < 0 || c->sv.graph == VOF_GRAPH_OFF) {
+    if (c->timing || c->vgraph_state < 0 || c->sv.graph == VOF_GRAPH_OFF || c->in_solve_capture) {
         vcycle<T>(c, 0);
         return;
     }
@@ -492,6 +492,303 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
     return VOF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The mixed solve as one CUDA graph. The decisions the host loop of
+// solve_mixed takes after each readback (inner convergence, the inner
+// iteration cap, another refinement, errors) are taken on the device by
+// single-thread control kernels that set the handles of two nested
+// conditional WHILE nodes; the kernels of the solve and their order are those
+// of solve_mixed, so the iterates are the same and the host waits once per
+// solve instead of once per iteration. Every pass of either loop body adds
+// one inner iteration, and both loops stop at max_iter (a guard counter
+// stops them in any case), so the loops end.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum SolveStatus { ST_OK = 0, ST_TIMEOUT = 1, ST_NONFINITE = 2 };
+
+struct SolveCtl {
+    double rtol;
+    int max_iter;
+    int cap_add;  // inner iterations per refinement: max(20, max_iter / 4)
+};
+
+__global__ void k_ctl_setup(double* s, SolveCtl p, cudaGraphConditionalHandle h_out) {
+    const double bb = s[S_BB];
+    double bnorm = sqrt(bb);
+    if (!(bnorm >= 1e-300)) bnorm = 1e-300;
+    const bool zero = bb == 0.0;
+    const double res0 = zero ? 0.0 : sqrt(s[S_RR]) / bnorm;
+    s[S_BNORM] = bnorm;
+    s[S_RES0] = res0;
+    s[S_RES] = res0;
+    s[S_INNER] = 0.0;
+    s[S_OUTER] = 0.0;
+    s[S_GUARD] = 0.0;
+    s[S_ZERO] = zero ? 1.0 : 0.0;
+    const int status = (!zero && !isfinite(res0)) ? ST_NONFINITE : ST_OK;
+    s[S_STATUS] = status;
+    const bool conv = zero || res0 <= p.rtol;
+    s[S_CONV] = conv ? 1.0 : 0.0;
+    cudaGraphSetConditional(h_out, (!conv && status == ST_OK) ? 1u : 0u);
+}
+
+__global__ void k_ctl_outer_begin(double* s, SolveCtl p) {
+    const double res = s[S_RES], bnorm = s[S_BNORM];
+    const double rr0 = res * bnorm * res * bnorm;
+    const double tol_in = fmax(1e-5, 0.2 * p.rtol / res);
+    s[S_THR] = tol_in * tol_in * rr0;
+    s[S_CAP] = s[S_INNER] + p.cap_add;
+}
+
+// after an inner CG update: count it, check the wait flag and the residual,
+// and continue while the inner tolerance, max_iter and the cap allow
+__global__ void k_ctl_inner(double* s, SolveCtl p, cudaGraphConditionalHandle h_in) {
+    const double inner = s[S_INNER] + 1.0, guard = s[S_GUARD] + 1.0;
+    s[S_INNER] = inner;
+    s[S_GUARD] = guard;
+    int status = (int)s[S_STATUS];
+    if (s[S_ERR] != 0.0) status = ST_TIMEOUT;
+    const double rr = s[S_RR];
+    if (status == ST_OK && !isfinite(rr)) status = ST_NONFINITE;
+    s[S_STATUS] = status;
+    const bool cont = status == ST_OK && !(rr <= s[S_THR]) && inner < p.max_iter &&
+                      inner < s[S_CAP] && guard < p.max_iter + 8;
+    cudaGraphSetConditional(h_in, cont ? 1u : 0u);
+}
+
+// after the FP64 update and residual of a refinement
+__global__ void k_ctl_outer_end(double* s, SolveCtl p, cudaGraphConditionalHandle h_out) {
+    const double res = sqrt(s[S_RR]) / s[S_BNORM];
+    s[S_RES] = res;
+    int status = (int)s[S_STATUS];
+    if (s[S_ERR] != 0.0) status = ST_TIMEOUT;
+    if (status == ST_OK && !isfinite(res)) status = ST_NONFINITE;
+    s[S_STATUS] = status;
+    const double outer = s[S_OUTER] + 1.0;
+    s[S_OUTER] = outer;
+    const bool conv = res <= p.rtol;
+    s[S_CONV] = conv ? 1.0 : 0.0;
+    const bool cont = !conv && status == ST_OK && s[S_INNER] < p.max_iter && outer < 50.0 &&
+                      s[S_GUARD] < p.max_iter + 8;
+    cudaGraphSetConditional(h_out, cont ? 1u : 0u);
+}
+
+__global__ void k_zero_if(double* __restrict__ x, const double* __restrict__ s, int n) {
+    if (s[S_ZERO] == 0.0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = 0.0;
+}
+
+// the graph being captured on stream s
+cudaGraph_t capture_graph(cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return nullptr;
+    return g;
+}
+
+// appends a conditional WHILE node on handle h after the work captured so
+// far on s; later captures on s follow the node; returns its body graph
+cudaGraph_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return nullptr;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, edges, nd, &np) != cudaSuccess) return nullptr;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return nullptr;
+    return np.conditional.phGraph_out[0];
+}
+
+// the first CG step of a refinement or the later ones: z = M r, the
+// direction, q = A p and the update of e and r, then the inner control
+void inner_tail(vof_ctx* c, const SolveCtl& p, cudaGraphConditionalHandle h_in) {
+    const int n = c->lv[0].ncells;
+    if (c->use_rho)
+        rho_apply_A_dot(c, c->p32, c->q32, S_PQ);
+    else
+        k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
+    launch_scalar_alpha(c);
+    k32_cg_update(c, n, c->e32, c->lv[0].ff, c->p32, c->q32, S_RR);
+    ++c->nlaunch;
+    k_ctl_inner<<<1, 1, 0, c->st>>>(c->scal, p, h_in);
+}
+
+// Captures the whole mixed solve for right side b_in and solution P into
+// the graph slot sg. False (nothing left captured, the error cleared) when
+// stream capture or conditional nodes are unavailable.
+bool build_solve_graph(vof_ctx* c, vof_ctx::SolveGraph& sg, const double* b_in, double* P) {
+    Level& L0 = c->lv[0];
+    const int n = L0.ncells;
+    float* r32 = L0.ff;
+    float* z32 = L0.xf;
+    cudaStream_t st0 = c->st;
+    for (cudaStream_t& s : c->cap_st)
+        if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st0, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+        cudaStreamBeginCapture(st0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const long long n0 = c->nlaunch;
+    long long k_outer = 0, k_inner = 0;
+    const SolveCtl p{c->sv.rtol, c->sv.max_iter, std::max(20, c->sv.max_iter / 4)};
+    bool ok = true;
+    c->in_solve_capture = true;
+    cudaGraph_t g_top = capture_graph(st0);
+    cudaGraphConditionalHandle h_out = 0, h_in = 0;
+    ok = ok && g_top && cudaGraphConditionalHandleCreate(&h_out, g_top, 0,
+                                                         cudaGraphCondAssignDefault) == cudaSuccess;
+    // setup: b, its mean and norm, the initial FP64 residual
+    cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), st0);
+    launch_copy(c, c->b, b_in, n);
+    launch_sub_mean(c, c->b, n, S_MEAN);
+    launch_dot(c, c->b, c->b, n, S_BB);
+    launch_residual_to32(c, P, c->b, r32, S_RR);
+    ++c->nlaunch;
+    k_ctl_setup<<<1, 1, 0, st0>>>(c->scal, p, h_out);
+    cudaGraph_t g_out = ok ? capture_while(st0, h_out) : nullptr;
+    ok = ok && g_out;
+    if (ok) {
+        // one refinement: the inner FP32 solve of A e = r, then P += e and
+        // the FP64 residual
+        const long long m0 = c->nlaunch;
+        c->st = c->cap_st[0];
+        ok = cudaStreamBeginCaptureToGraph(c->st, g_out, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess &&
+             cudaGraphConditionalHandleCreate(&h_in, g_out, 0, cudaGraphCondAssignDefault) ==
+                 cudaSuccess;
+        if (ok) {
+            ++c->nlaunch;
+            k_ctl_outer_begin<<<1, 1, 0, c->st>>>(c->scal, p);
+            cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
+            vcycle<float>(c, 0);
+            k32_dot2(c, n, z32, r32, r32, S_RZ, S_ZQ);
+            cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
+            inner_tail(c, p, h_in);
+            cudaGraph_t g_in = capture_while(c->st, h_in);
+            ok = g_in != nullptr;
+            if (ok) {
+                const long long i0 = c->nlaunch;
+                c->st = c->cap_st[1];
+                ok = cudaStreamBeginCaptureToGraph(c->st, g_in, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    vcycle<float>(c, 0);
+                    k32_dot2(c, n, z32, r32, c->q32, S_RZ, S_ZQ);
+                    launch_scalar_beta(c);
+                    k32_p_update(c, n, c->p32, z32);
+                    inner_tail(c, p, h_in);
+                    cudaGraph_t gb = nullptr;
+                    ok = cudaStreamEndCapture(c->st, &gb) == cudaSuccess;
+                }
+                c->st = c->cap_st[0];
+                k_inner = c->nlaunch - i0;
+            }
+            k32_add_to_f64(c, n, c->e32, P);
+            launch_residual_to32(c, P, c->b, r32, S_RR);
+            ++c->nlaunch;
+            k_ctl_outer_end<<<1, 1, 0, c->st>>>(c->scal, p, h_out);
+            cudaGraph_t gb = nullptr;
+            ok = (cudaStreamEndCapture(c->st, &gb) == cudaSuccess) && ok;
+        }
+        c->st = st0;
+        k_outer = c->nlaunch - m0 - k_inner;
+    }
+    // P = 0 for a zero right side, then mean-free
+    ++c->nlaunch;
+    k_zero_if<<<4 * c->sm_count, 256, 0, st0>>>(P, c->scal, n);
+    launch_sub_mean(c, P, n, S_SUM);
+    c->in_solve_capture = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st0, &g);
+    const long long k_all = c->nlaunch - n0;
+    c->nlaunch = n0;
+    if (sg.exec) {
+        cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
+    }
+    ok = ok && e == cudaSuccess && g && cudaGraphInstantiate(&sg.exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!ok) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
+        return false;
+    }
+    sg.b = b_in;
+    sg.P = P;
+    sg.k_outer = k_outer;
+    sg.k_inner = k_inner;
+    sg.k_fixed = k_all - k_outer - k_inner;
+    return true;
+}
+
+// The mixed solve through its captured graph: one launch, one readback.
+vof_status solve_mixed_graph(vof_ctx* c, const vof_ctx::SolveGraph& sg, vof_report* rep) {
+    cudaGraphLaunch(sg.exec, c->st);
+    readback(c);
+    const long long inner = (long long)c->hbuf[S_INNER], outer = (long long)c->hbuf[S_OUTER];
+    c->nlaunch += sg.k_fixed + outer * sg.k_outer + (inner - outer) * sg.k_inner;
+    vof_status st = cuda_check(c, cudaGetLastError(), "pressure solve");
+    if (rep) {
+        rep->iters = (int)inner;
+        rep->refinements = (int)outer;
+        rep->res0 = c->hbuf[S_RES0];
+        rep->res = c->hbuf[S_RES];
+        rep->b_mean = c->hbuf[S_MEAN];
+    }
+    if (st != VOF_OK) return st;
+    const int status = (int)c->hbuf[S_STATUS];
+    if (status == ST_TIMEOUT)
+        return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+    if (status == ST_NONFINITE) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
+    if (c->hbuf[S_CONV] == 0.0)
+        return set_err(c, VOF_ERR_NOT_CONVERGED,
+                       "pressure solve did not reach rtol within max_iter (res=" +
+                           std::to_string(c->hbuf[S_RES]) + ")");
+    return VOF_OK;
+}
+
+// the cached graph for (b_in, P), captured on first use (the least recently
+// used of the two slots is replaced); nullptr when capture is unavailable
+const vof_ctx::SolveGraph* solve_graph_for(vof_ctx* c, const double* b_in, double* P) {
+    ++c->sgraph_clock;
+    for (auto& sg : c->sgraph)
+        if (sg.exec && sg.b == b_in && sg.P == P) {
+            sg.used = c->sgraph_clock;
+            return &sg;
+        }
+    auto& slot = c->sgraph[0].used <= c->sgraph[1].used ? c->sgraph[0] : c->sgraph[1];
+    if (!build_solve_graph(c, slot, b_in, P)) {
+        c->sgraph_state = -1;
+        return nullptr;
+    }
+    c->sgraph_state = 1;
+    slot.used = c->sgraph_clock;
+    return &slot;
+}
+
+}  // namespace
+
 // A right side that is exactly zero after its mean is removed has the
 // mean-free solution P = 0.
 static vof_status zero_solution(vof_ctx* c, double* P, vof_report* rep, double b_mean) {
@@ -511,6 +808,14 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
     const int n = c->lv[0].ncells;
     Level& L0 = c->lv[0];
     mg_build_coefficients(c);
+    if (c->sv.precision == VOF_PREC_MIXED_FP32 && !c->timing && c->sv.graph == VOF_GRAPH_AUTO &&
+        c->sgraph_state >= 0) {
+        // the kernels are captured with the coarsest inverse and the
+        // coefficients in place, which mg_build_coefficients refreshes in
+        // place before every launch of the graph
+        const vof_ctx::SolveGraph* sg = solve_graph_for(c, b_in, P);
+        if (sg) return solve_mixed_graph(c, *sg, rep);
+    }
     if (c->sv.precision == VOF_PREC_MIXED_FP32) {
         cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), c->st);
         launch_copy(c, c->b, b_in, n);

@@ -210,6 +210,23 @@ struct vof_ctx {
     long long vgraph_kernels = 0;
     int vgraph_state = 0;
 
+    // the mixed solve captured once as a CUDA graph whose loops are
+    // conditional WHILE nodes driven by device-side control kernels (state
+    // 0: not tried, 1: ready, -1: unavailable); rebuilt when the right side
+    // or the solution pointer changes
+    // (two cached graphs: the two-solve mode alternates its solution pointer)
+    struct SolveGraph {
+        cudaGraphExec_t exec = nullptr;
+        const double* b = nullptr;
+        double* P = nullptr;
+        long long k_fixed = 0, k_outer = 0, k_inner = 0;  // kernels per solve
+        long long used = 0;
+    } sgraph[2];
+    long long sgraph_clock = 0;
+    int sgraph_state = 0;
+    cudaStream_t cap_st[2] = {nullptr, nullptr};  // streams capturing the loop bodies
+    bool in_solve_capture = false;
+
     // coarse tail (0: not used); programs from zero / from the current x
     int tail_level = 0;
     int tail_cluster = 0;
@@ -243,7 +260,7 @@ void launch_pdl(vof_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, Args&
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = c->in_solve_capture ? 0 : 1;  // plain edges inside conditional bodies
     ++c->nlaunch;
     cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
@@ -260,6 +277,8 @@ enum ScalarSlot {
     S_MEAN,       // mean removed
     S_VOL0, S_VOL1, S_CLIP0, S_CLIP1, S_CLIP2, S_MAXDIV, S_MAXU, S_FALLBACK, S_CFL, S_SUM,
     S_ERR,        // a kernel gave up a bounded wait (set to 1)
+    // device-side control of the captured mixed solve (solver.cu)
+    S_INNER, S_OUTER, S_RES, S_RES0, S_BNORM, S_THR, S_CAP, S_CONV, S_STATUS, S_ZERO, S_GUARD,
     S_NSCALARS
 };
 
