@@ -246,6 +246,8 @@ struct vof_ctx {
 // writes are visible (at once for a kernel launched the ordinary way).
 // Measured with an early trigger (griddepcontrol.launch_dependents at the
 // top of each kernel) the step was slower: the waiting blocks held SM slots.
+// The programmatic edges are kept inside the conditional bodies of the
+// captured mixed solve as well.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
@@ -260,7 +262,7 @@ void launch_pdl(vof_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, Args&
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = c->in_solve_capture ? 0 : 1;  // plain edges inside conditional bodies
+    cfg.numAttrs = 1;
     ++c->nlaunch;
     cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
