@@ -75,6 +75,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--nz", type=int, default=640, help="z cells (smaller for quick runs)")
+    ap.add_argument("--graph", default="auto", choices=["auto", "cycle", "off"],
+                    help="solver graph mode: auto captures the whole mixed solve (its loops "
+                         "as conditional graph nodes); cycle replays only the V-cycle with the "
+                         "loops on the host: the same kernels in the same order, and the mode "
+                         "ncu can profile (it cannot profile kernel nodes of graphs with "
+                         "conditional nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32,
@@ -369,7 +375,9 @@ def main():
     prec = vd.PREC_FP64 if args.precision == "fp64" else vd.PREC_MIXED_FP32
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = vd.VofContext(g, case.phys, vd.c_solver(prec, rtol=args.rtol, max_iter=500),
+        gmode = {"auto": vd.GRAPH_AUTO, "cycle": vd.GRAPH_CYCLE, "off": vd.GRAPH_OFF}[args.graph]
+        ctx = vd.VofContext(g, case.phys,
+                            vd.c_solver(prec, rtol=args.rtol, max_iter=500, graph=gmode),
                             stream=stream)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         T = [dev(x) for x in case.state()]
@@ -491,6 +499,7 @@ def main():
         "config": {"workload": WORKLOAD if args.nz == 640 else WORKLOAD.replace("640", str(args.nz)),
                    "cells": N, "spheres": nbub, "rtol": args.rtol,
                    "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "graph": args.graph,
                    "l2": "inputs larger than L2 (257 MB per cell field), no flush",
                    "dt": case.dt},
         "poisson_cell_updates_per_s": poisson,
