@@ -51,7 +51,7 @@ typedef enum {
     VOF_ERR_CFL = 6,            /* |u| dt / h > 1 on some face                */
     VOF_ERR_TIMEOUT = 7,        /* a bounded device wait ran out              */
     VOF_ERR_ADMISSION = 8,      /* workspace exceeds the memory budget        */
-    VOF_ERR_UNSUPPORTED = 9     /* valid request this build does not support  */
+    VOF_ERR_UNSUPPORTED = 9     /* valid request the library does not support */
 } vof_status;
 
 typedef struct {
