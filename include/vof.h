@@ -281,6 +281,29 @@ vof_status vof_step(vof_ctx* ctx, double* alpha, double* uc, double* vc, double*
                     double* v, double* w, double* p, double dt, long long step_index,
                     vof_report* report);
 
+/* One time step on a state held in HOST memory: the same step as step(),
+ * with the eight arrays (same order, sizes and layouts) in host memory.
+ * The context keeps a device copy of the state, allocated by the first call
+ * (8 fields, in addition to vof_workspace_bytes; VOF_ERR_OOM if the device
+ * has no room). Each call copies the state in on a stream of its own, u, v,
+ * w and alpha first (the CFL check and the advection read them) and the
+ * cell velocities and p while the advection, beta and the face force run;
+ * it copies each field out as soon as the step has finished writing it:
+ * alpha after the advection, p after the solve, the velocities after the
+ * projection, while the context stream goes on. Page-locked host arrays
+ * (cudaHostAlloc, pinned tensors) let the copies overlap the kernels;
+ * pageable ones work, with copies staged by the CUDA runtime.
+ * Ordering: the copies in start after all work already on the context
+ * stream, and the context stream does not pass the end of this call until
+ * every copy out has finished, so the host arrays hold the new state once
+ * the context stream is synchronised (a report, when requested, is read
+ * before the last copies out finish). The host arrays must stay valid and
+ * untouched until then. Errors as for step(); after an error other than
+ * VOF_ERR_NOT_CONVERGED the host arrays are unspecified. */
+vof_status vof_step_host(vof_ctx* ctx, double* alpha, double* uc, double* vc, double* wc,
+                         double* u, double* v, double* w, double* p, double dt,
+                         long long step_index, vof_report* report);
+
 /* Number of CUDA kernels this context has launched since creation. */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
 

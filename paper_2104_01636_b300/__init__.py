@@ -119,6 +119,7 @@ def load() -> ctypes.CDLL:
         "vof_predict": [_VP] * 12 + [_D],
         "project": [_VP] * 12 + [_D, P(CReport)],
         "step": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
+        "vof_step_host": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
         "vof_set_timing": [_VP, ctypes.c_int],
         "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
         "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
@@ -298,6 +299,28 @@ class VofContext:
                            self._ptr(v, 2, "v"), self._ptr(w, 3, "w"), self._ptr(p, 0, "p"),
                            float(dt), int(step_index), ctypes.byref(rep) if report else None)
         self._chk(st, "step", rep)
+        return rep.as_dict() if report else None
+
+    def _hptr(self, t, kind: int, name: str):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.device.type == "cpu"
+                and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{name}: need a contiguous float64 host tensor")
+        if tuple(t.shape) != self.shapes[kind]:
+            raise ValueError(f"{name}: shape {tuple(t.shape)} != {self.shapes[kind]}")
+        return _VP(t.data_ptr())
+
+    def step_host(self, alpha, uc, vc, wc, u, v, w, p, dt: float, step_index: int,
+                  report: bool = True):
+        """One step on host tensors (pinned for overlapped copies). The
+        tensors hold the new state once the context stream is synchronised."""
+        rep = CReport()
+        st = self.lib.vof_step_host(
+            self._ctx, self._hptr(alpha, 0, "alpha"), self._hptr(uc, 0, "uc"),
+            self._hptr(vc, 0, "vc"), self._hptr(wc, 0, "wc"), self._hptr(u, 1, "u"),
+            self._hptr(v, 2, "v"), self._hptr(w, 3, "w"), self._hptr(p, 0, "p"), float(dt),
+            int(step_index), ctypes.byref(rep) if report else None)
+        self._chk(st, "vof_step_host", rep)
         return rep.as_dict() if report else None
 
     def launch_count(self) -> int:

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 
 #include "vof_internal.cuh"
 
@@ -221,12 +222,38 @@ void timer_end(vof_ctx* c, int, int mark) {
     cudaEventRecord(c->ev_pool[c->ev_marks[mark].second.second], c->st);
 }
 
+// copies of vof_step_host: the state's host arrays and device copies, in
+// the order alpha, uc, vc, wc, u, v, w, p
+struct StepIO {
+    double* const* host;
+    double* const* dev;
+    size_t bytes[8];
+};
+enum { IO_ALPHA = 0, IO_UC, IO_VC, IO_WC, IO_U, IO_V, IO_W, IO_P };
+// events of vof_step_host: inputs arrived (u, v, w, alpha; cell velocities;
+// P), a point of the context stream where fields are final, copies out
+// finished, start of the call
+enum { EV_IN_FACES = 0, EV_IN_CELLS, EV_IN_P, EV_OUT_POINT, EV_OUT_DONE, EV_CALL };
+
+// device-to-host copies of fields that the context stream has finished
+// writing, on the copy-out stream once the stream's work so far is done
+static void io_out(vof_ctx* c, const StepIO* io, std::initializer_list<int> fields) {
+    if (!io) return;
+    cudaEventRecord(c->io_ev[EV_OUT_POINT], c->st);
+    cudaStreamWaitEvent(c->io_st[1], c->io_ev[EV_OUT_POINT], 0);
+    for (int q : fields)
+        cudaMemcpyAsync(io->host[q], io->dev[q], io->bytes[q], cudaMemcpyDeviceToHost,
+                        c->io_st[1]);
+}
+
 // steps 11-12 on (u_hat_c in Uh, u_hat_f in u, v, w): right side, solve,
 // correction of faces (in place) and cells (written to Uc)
 static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* const Uc[3],
                                double* u, double* v, double* w, double* p, const double* sx,
-                               const double* sy, const double* sz, double dt, vof_report* r) {
+                               const double* sy, const double* sz, double dt, vof_report* r,
+                               const StepIO* io = nullptr) {
     vof_status st;
+    if (io) cudaStreamWaitEvent(c->st, c->io_ev[EV_IN_P], 0);  // the guess P has arrived
     if (c->sv.ssf_solves == 2) {
         // the paper's steps 6 and 11: p~ from the surface force, p from the
         // velocity divergence, both with beta^{n+1}; P = p + p~. The guess
@@ -252,7 +279,9 @@ static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* co
         st = solve_pressure(c, c->rhs, p, r);
         if (st != VOF_OK && st != VOF_ERR_NOT_CONVERGED) return st;
     }
+    io_out(c, io, {IO_P});  // P is final; the correction only reads it
     launch_correct(c, p, sx, sy, sz, dt, Uh, Uc, u, v, w, P_A, P_B);
+    io_out(c, io, {IO_U, IO_V, IO_W, IO_UC, IO_VC, IO_WC});
     readback(c);
     r->max_div = c->hbuf[S_MAXDIV];
     r->max_u = c->hbuf[S_MAXU];
@@ -260,11 +289,14 @@ static vof_status project_impl(vof_ctx* c, const double* const Uh[3], double* co
     return st2 ? st2 : st;
 }
 
-// the whole time step behind step() and vof_step(); internal callers (the
-// request server) use this name, never the exported one
-vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
-                      double* v, double* w, double* p, double dt, long long step_index,
-                      vof_report* report) {
+// the whole time step. With io (vof_step_host) the fields are the device
+// copies, whose inputs arrive on the copy-in stream: u, v, w and alpha
+// before the call (the context stream already waits for them), the cell
+// velocities before the predictor and P before the solve; each field is
+// copied out as soon as the step has finished writing it.
+static vof_status step_run(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc,
+                           double* u, double* v, double* w, double* p, double dt,
+                           long long step_index, vof_report* report, const StepIO* io) {
     vof_status st = check_ctx(c);
     if (st) return st;
     REQUIRE_PTR(c, alpha);
@@ -286,20 +318,24 @@ vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double*
     // step 3: advect alpha with u_f^n, keeping the liquid face fluxes
     double* const flux[3] = {c->fx, c->fy, c->fz};
     advect_impl(c, alpha, u, v, w, dt, step_index, flux);
+    io_out(c, io, {IO_ALPHA});  // alpha^{n+1} is final
+    // step 4 (beta from alpha^{n+1}) and steps 5-7 (curvature, face force):
+    // they read alpha^{n+1} only, so they run while the cell velocities may
+    // still be arriving
+    launch_beta(c, alpha);
+    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
+    if (io) cudaStreamWaitEvent(c->st, c->io_ev[EV_IN_CELLS], 0);
     // steps 8-9: cell-centred intermediate velocity
     const double* const U[3] = {uc, vc, wc};
     launch_predict(c, c->an, alpha, U, u, v, w, c->fx, c->fy, c->fz, dt, c->uh);
     // step 10: face intermediate velocity
     launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], u, v, w);
-    // step 4 (beta from alpha^{n+1}) and steps 5-7 (curvature, face force)
-    launch_beta(c, alpha);
-    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
     // steps 11-12
     vof_report r;
     std::memset(&r, 0, sizeof(r));
     const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
     double* const Uc[3] = {uc, vc, wc};
-    st = project_impl(c, Uh, Uc, u, v, w, p, c->sx, c->sy, c->sz, dt, &r);
+    st = project_impl(c, Uh, Uc, u, v, w, p, c->sx, c->sy, c->sz, dt, &r, io);
     if (report) {
         readback(c);
         fill_vof_report(c, &r);
@@ -308,6 +344,39 @@ vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double*
         report_timing_end(c, snap, report);
     }
     return st;
+}
+
+// the whole time step behind step() and vof_step(); internal callers (the
+// request server) use this name, never the exported one
+vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
+                      double* v, double* w, double* p, double dt, long long step_index,
+                      vof_report* report) {
+    return step_run(c, alpha, uc, vc, wc, u, v, w, p, dt, step_index, report, nullptr);
+}
+
+// vof_step_host: the device copies of the state and the copy streams, made
+// at the first call
+static vof_status host_step_setup(vof_ctx* c) {
+    if (c->hs[0]) return VOF_OK;
+    const Sizes s = sizes_of(&c->g);
+    const size_t n[8] = {s.n, s.n, s.n, s.n, s.nu, s.nv, s.nw, s.n};
+    for (int q = 0; q < 8; ++q) {
+        c->hs[q] = (double*)dev_alloc(c, n[q] * sizeof(double));
+        if (!c->hs[q]) {
+            for (int r = 0; r < q; ++r) {
+                cudaFreeAsync(c->hs[r], c->st);
+                c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void*)c->hs[r]));
+                c->hs[r] = nullptr;
+            }
+            return set_err(c, VOF_ERR_OOM, "vof_step_host: no device memory for the state");
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto& q : c->io_st)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+    for (auto& ev : c->io_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    return cuda_check(c, e, "vof_step_host");
 }
 
 
@@ -436,6 +505,10 @@ vof_status vof_destroy(vof_ctx* c) {
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
     for (cudaStream_t s : c->cap_st)
         if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : c->io_st)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->io_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
     return VOF_OK;
 }
@@ -593,6 +666,54 @@ vof_status vof_step(vof_ctx* c, double* alpha, double* uc, double* vc, double* w
                     double* v, double* w, double* p, double dt, long long step_index,
                     vof_report* report) {
     return step_entry(c, alpha, uc, vc, wc, u, v, w, p, dt, step_index, report);
+}
+
+vof_status vof_step_host(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc,
+                         double* u, double* v, double* w, double* p, double dt,
+                         long long step_index, vof_report* report) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    REQUIRE_PTR(c, alpha);
+    REQUIRE_PTR(c, uc);
+    REQUIRE_PTR(c, vc);
+    REQUIRE_PTR(c, wc);
+    REQUIRE_PTR(c, u);
+    REQUIRE_PTR(c, v);
+    REQUIRE_PTR(c, w);
+    REQUIRE_PTR(c, p);
+    if ((st = walls_only(c, "vof_step_host"))) return st;
+    if ((st = host_step_setup(c))) return st;
+    const Sizes s = sizes_of(&c->g);
+    double* const host[8] = {alpha, uc, vc, wc, u, v, w, p};
+    StepIO io{host, c->hs, {s.n * 8, s.n * 8, s.n * 8, s.n * 8, s.nu * 8, s.nv * 8, s.nw * 8,
+                            s.n * 8}};
+    // copy-in after everything already on the context stream (the previous
+    // step and its copies out); u, v, w and alpha first: the CFL check and
+    // the advection need them, the cell velocities and P come later
+    cudaStream_t in = c->io_st[0];
+    cudaEventRecord(c->io_ev[EV_CALL], c->st);
+    cudaStreamWaitEvent(in, c->io_ev[EV_CALL], 0);
+    for (int q : {IO_U, IO_V, IO_W, IO_ALPHA})
+        cudaMemcpyAsync(c->hs[q], host[q], io.bytes[q], cudaMemcpyHostToDevice, in);
+    cudaEventRecord(c->io_ev[EV_IN_FACES], in);
+    for (int q : {IO_UC, IO_VC, IO_WC})
+        cudaMemcpyAsync(c->hs[q], host[q], io.bytes[q], cudaMemcpyHostToDevice, in);
+    cudaEventRecord(c->io_ev[EV_IN_CELLS], in);
+    cudaMemcpyAsync(c->hs[IO_P], host[IO_P], io.bytes[IO_P], cudaMemcpyHostToDevice, in);
+    cudaEventRecord(c->io_ev[EV_IN_P], in);
+    cudaStreamWaitEvent(c->st, c->io_ev[EV_IN_FACES], 0);
+    if ((st = launch_check(c, "vof_step_host"))) return st;
+    st = step_run(c, c->hs[IO_ALPHA], c->hs[IO_UC], c->hs[IO_VC], c->hs[IO_WC], c->hs[IO_U],
+                  c->hs[IO_V], c->hs[IO_W], c->hs[IO_P], dt, step_index, report, &io);
+    // the context stream reaches this point when every copy out has finished
+    // (also after an error: the next call's copies in must not overtake them)
+    // (and for the copies in: an error can return before the step waited)
+    cudaEventRecord(c->io_ev[EV_OUT_DONE], c->io_st[1]);
+    cudaStreamWaitEvent(c->st, c->io_ev[EV_OUT_DONE], 0);
+    cudaEventRecord(c->io_ev[EV_OUT_DONE], c->io_st[0]);
+    cudaStreamWaitEvent(c->st, c->io_ev[EV_OUT_DONE], 0);
+    const vof_status st2 = launch_check(c, "vof_step_host");
+    return st ? st : st2;
 }
 
 vof_status vof_launch_count(const vof_ctx* c, long long* n) {

@@ -233,6 +233,13 @@ struct vof_ctx {
     TailProg* tail_prog = nullptr;  // device copies of tail_host
     TailProg tail_host[2];
 
+    // vof_step_host: the state on the device (alpha, uc, vc, wc, u, v, w, p),
+    // allocated at the first call; a stream that copies it in and one that
+    // copies it out beside the context stream, and the events ordering them
+    double* hs[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t io_st[2] = {nullptr, nullptr};  // host to device, device to host
+    cudaEvent_t io_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
 };
