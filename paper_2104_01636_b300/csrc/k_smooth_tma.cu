@@ -97,6 +97,9 @@ struct SweepArgs {
     const float* f;
     float* xout;
     double* err;  // set to 1 when a wait on a TMA barrier gives up
+    // DOT sweeps: block partials of (x_new, f) and (x_new, q) into pa, pb
+    const float* q;
+    double *pa, *pb;
 };
 
 // 1 / (rho_L + rho_R), half the face coefficient: every finest-level kernel
@@ -116,7 +119,10 @@ __device__ __forceinline__ float hval(const __half* h, int o) { return __half2fl
 // packed FP32x2 arithmetic. The z-face coefficients computed for the first
 // colour are kept in registers and reused by the second colour, and the
 // right side of the next plane is loaded into registers one plane ahead.
-template <bool ZERO>
+// DOT: as the pair is written, its products with f and with q are summed
+// (the preconditioner's last sweep forms the Krylov dots (z, r), (z, q)
+// from the z it writes, r being its right side).
+template <bool ZERO, bool DOT>
 __global__ void __launch_bounds__(256, 4)
     k_sweep_rho(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_rho,
                 SweepArgs a) {
@@ -131,7 +137,10 @@ __global__ void __launch_bounds__(256, 4)
     const int i0 = blockIdx.x * STX, j0 = blockIdx.y * STY;
     const int k0 = blockIdx.z * a.kchunk;
     const int k1 = min(k0 + a.kchunk, a.nz);
-    if (k0 >= k1) return;  // whole block
+    if (k0 >= k1) {  // whole block
+        if (DOT && threadIdx.x == 0 && threadIdx.y == 0) a.pa[block_linear()] = a.pb[block_linear()] = 0.0;
+        return;
+    }
     const int pbase = k0 - 2;  // first staged plane (unwrapped index)
     constexpr uint32_t bytes = (ZERO ? 0u : (uint32_t)(XPLANE * sizeof(float))) +
                                (uint32_t)(HPLANE * sizeof(__half));
@@ -208,6 +217,8 @@ __global__ void __launch_bounds__(256, 4)
     };
     float fRA, fRB, fBA, fBB, fRR;
     load_f(pbase, fRA, fRB, fBA, fBB, fRR);
+    float fPA = 0.f, fPB = 0.f;  // right sides of plane k's first colour (DOT)
+    float2 dzf = make_float2(0.f, 0.f), dzq = make_float2(0.f, 0.f);
 
     // slots of planes k, k+1, k+2 and first-colour planes k-1, k, k+1
     int S1 = 0, S2 = 1, S3 = 2;
@@ -220,6 +231,13 @@ __global__ void __launch_bounds__(256, 4)
     for (int k = pbase; k < k1; ++k) {
         float nRA, nRB, nBA, nBB, nRR;  // next plane's right sides, in flight during this one
         load_f(k + 1, nRA, nRB, nBA, nBB, nRR);
+        // DOT: q of this plane's pair, in flight during the first colour
+        float2 qa = make_float2(0.f, 0.f), qb = make_float2(0.f, 0.f);
+        if (DOT && k >= k0) {
+            const float* qo = a.q + (size_t)wrapk(k, nz) * plane + ib;
+            if (inA) qa = __ldg(reinterpret_cast<const float2*>(qo + (size_t)jA * nx));
+            if (inB) qb = __ldg(reinterpret_cast<const float2*>(qo + (size_t)jB * nx));
+        }
         wait_slot(S3, par3);
         const int q = k + 1;
         const int P = (a.c0 + jA + q) & 1;  // x offset of the first colour in the pair on plane q
@@ -297,6 +315,7 @@ __global__ void __launch_bounds__(256, 4)
                     for (int it = 0; !mbar_try_wait(&bar[s], par) && it < WAIT_LIMIT; ++it) {
                     }
                 }
+                if (DOT) a.pa[block_linear()] = a.pb[block_linear()] = 0.0;
             }
             return;
         }
@@ -336,12 +355,20 @@ __global__ void __launch_bounds__(256, 4)
             const float sa = __fdividef(num.x, den.x), sb = __fdividef(num.y, den.y);
             const int pa = nA + (P ^ 1), pb = nB + (P ^ 1);  // first colour of plane k in the pair
             float* xo = a.xout + (size_t)kk * plane + ib;
-            if (inA)
-                *reinterpret_cast<float2*>(xo + (size_t)jA * nx) =
-                    P ? make_float2(N1[pa], sa) : make_float2(sa, N1[pa]);
-            if (inB)
-                *reinterpret_cast<float2*>(xo + (size_t)jB * nx) =
-                    P ? make_float2(N1[pb], sb) : make_float2(sb, N1[pb]);
+            const float2 za = P ? make_float2(N1[pa], sa) : make_float2(sa, N1[pa]);
+            const float2 zb = P ? make_float2(N1[pb], sb) : make_float2(sb, N1[pb]);
+            if (inA) *reinterpret_cast<float2*>(xo + (size_t)jA * nx) = za;
+            if (inB) *reinterpret_cast<float2*>(xo + (size_t)jB * nx) = zb;
+            if (DOT) {
+                if (inA) {
+                    dzf = __ffma2_rn(za, P ? make_float2(fPA, fBA) : make_float2(fBA, fPA), dzf);
+                    dzq = __ffma2_rn(za, qa, dzq);
+                }
+                if (inB) {
+                    dzf = __ffma2_rn(zb, P ? make_float2(fPB, fBB) : make_float2(fBB, fPB), dzf);
+                    dzq = __ffma2_rn(zb, qb, dzq);
+                }
+            }
         }
         __syncthreads();
         // refill the slot of plane k (no longer read) with plane k + NSLOT
@@ -362,11 +389,21 @@ __global__ void __launch_bounds__(256, 4)
         N0 = N1;
         N1 = N2;
         N2 = t;
+        fPA = fRA;
+        fPB = fRB;
         fRA = nRA;
         fRB = nRB;
         fBA = nBA;
         fBB = nBB;
         fRR = nRR;
+    }
+    if (DOT) {
+        const double sf = block_sum((double)dzf.x + (double)dzf.y);
+        const double sq = block_sum((double)dzq.x + (double)dzq.y);
+        if (tid == 0) {
+            a.pa[block_linear()] = sf;
+            a.pb[block_linear()] = sq;
+        }
     }
 }
 
@@ -527,9 +564,11 @@ vof_status rho_path_setup(vof_ctx* c) {
         !encode_plane_map(c->tmap[1], L0.d, c->x32b, false, SBX) ||
         !encode_plane_map(c->tmap[2], L0.d, c->rho16, true, HBX))
         return set_err(c, VOF_ERR_CUDA, "TMA tensor-map encoding is unavailable");
-    if (cudaFuncSetAttribute(k_sweep_rho<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_sweep_rho<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SWEEP_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sweep_rho<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_sweep_rho<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SWEEP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sweep_rho<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SWEEP_SMEM) != cudaSuccess)
         return cuda_check(c, cudaGetLastError(), "smoother shared-memory attribute");
     // z chunks: about four resident blocks per SM over the whole grid
@@ -537,11 +576,13 @@ vof_status rho_path_setup(vof_ctx* c) {
     int zc = std::max(1, (4 * c->sm_count + tiles / 2) / tiles);
     zc = std::min(zc, L0.d.nz);
     c->sweep_kchunk = (L0.d.nz + zc - 1) / zc;
+    c->sweep_dot = (long)tiles * ((L0.d.nz + c->sweep_kchunk - 1) / c->sweep_kchunk) <= MAX_PARTIALS;
     return VOF_OK;
 }
 
-// one sweep: src == nullptr means the old x is zero
-void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0) {
+// one sweep: src == nullptr means the old x is zero; dot: also the dots of
+// the new x with the level's right side (slot S_RZ) and with q32 (S_ZQ)
+void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
     const Level& L0 = c->lv[0];
     SweepArgs a;
     a.nx = L0.d.nx;
@@ -553,6 +594,9 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0) {
     a.f = L0.ff;
     a.xout = dst;
     a.err = c->scal + S_ERR;
+    a.q = c->q32;
+    a.pa = c->part + (size_t)S_RZ * MAX_PARTIALS;
+    a.pb = c->part + (size_t)S_ZQ * MAX_PARTIALS;
     const CUtensorMap* tx =
         reinterpret_cast<const CUtensorMap*>(src == c->x32b ? c->tmap[1] : c->tmap[0]);
     const CUtensorMap* tr = reinterpret_cast<const CUtensorMap*>(c->tmap[2]);
@@ -561,10 +605,17 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0) {
     int m = timer_begin(c, T_SMOOTH0);
     ++c->nlaunch;
     if (src == nullptr)
-        k_sweep_rho<true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+        k_sweep_rho<true, false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+    else if (!dot)
+        k_sweep_rho<false, false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     else
-        k_sweep_rho<false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+        k_sweep_rho<false, true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     timer_end(c, T_SMOOTH0, m);
+    if (dot) {
+        const int nb = (int)(grid.x * grid.y * grid.z);
+        finalize_sum(c, S_RZ, nb, S_RZ, 1.0);
+        finalize_sum(c, S_ZQ, nb, S_ZQ, 1.0);
+    }
 }
 
 void rho_restrict(vof_ctx* c) {

@@ -60,6 +60,8 @@ bool twice(const vof_ctx* c, int l) {
 // nu_pre red-black sweeps from a zero guess, restriction, the coarse
 // correction, nu_post black-red sweeps. Sweeps ping-pong between xf and
 // x32b; the pre-smoothing starts on the buffer that makes it end in xf.
+// With sweep_dot the last sweep also forms (z, r) -> S_RZ and (z, q32) ->
+// S_ZQ, the dots the flexible CG takes after every preconditioning.
 void vcycle0_rho(vof_ctx* c) {
     Level& L0 = c->lv[0];
     float* const A = L0.xf;
@@ -77,7 +79,7 @@ void vcycle0_rho(vof_ctx* c) {
     if (twice(c, 0)) cycle<float>(c, 1, false);
     mg_prolong<float>(c, c->lv[1], L0);
     for (int s = 0; s < nu; ++s) {
-        rho_sweep(c, cur, dst, 1);
+        rho_sweep(c, cur, dst, 1, c->sweep_dot && s == nu - 1);
         cur = dst;
         dst = (dst == A) ? B : A;
     }
@@ -216,6 +218,14 @@ void run_vcycle(vof_ctx* c) {
     c->nlaunch += c->vgraph_kernels;
 }
 
+// (z, r) -> S_RZ and (z, q) -> S_ZQ after z = M r on the mixed path; the
+// fused last sweep has formed them already (with q32 as q: the first
+// iteration of a refinement, which passes q = r, does not use (z, q))
+void krylov_dots(vof_ctx* c, int n, const float* z, const float* r, const float* q) {
+    if (c->use_rho && c->sweep_dot) return;
+    k32_dot2(c, n, z, r, q, S_RZ, S_ZQ);
+}
+
 // z = M r (one V-cycle), in the precision the context was created with
 void precondition(vof_ctx* c) {
     Level& L0 = c->lv[0];
@@ -322,6 +332,8 @@ vof_status mg_allocate(vof_ctx* c) {
             void* q = dev_alloc(c, sizeof(float) * (size_t)c->lv[0].ncells);
             if (!q) return set_err(c, VOF_ERR_OOM, "allocation of inner Krylov vectors failed");
             *v = (float*)q;
+            // finite from the start: the fused dots read q32 before its first use
+            cudaMemsetAsync(q, 0, sizeof(float) * (size_t)c->lv[0].ncells, c->st);
         }
     }
     if (c->sv.mg_interp == VOF_MG_TRILINEAR) {
@@ -443,7 +455,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
         const int inner_cap = inner_total + std::max(20, c->sv.max_iter / 4);
         cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
         run_vcycle<float>(c);
-        k32_dot2(c, n, z32, r32, r32, S_RZ, S_ZQ);
+        krylov_dots(c, n, z32, r32, r32);
         cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
         while (inner_total < c->sv.max_iter && inner_total < inner_cap) {
             ++inner_total;
@@ -460,7 +472,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
             if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
             if (rr <= tol_in * tol_in * rr0) break;
             run_vcycle<float>(c);
-            k32_dot2(c, n, z32, r32, c->q32, S_RZ, S_ZQ);
+            krylov_dots(c, n, z32, r32, c->q32);
             launch_scalar_beta(c);
             k32_p_update(c, n, c->p32, z32);
         }
@@ -681,7 +693,7 @@ bool build_solve_graph(vof_ctx* c, vof_ctx::SolveGraph& sg, const double* b_in, 
             k_ctl_outer_begin<<<1, 1, 0, c->st>>>(c->scal, p);
             cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
             vcycle<float>(c, 0);
-            k32_dot2(c, n, z32, r32, r32, S_RZ, S_ZQ);
+            krylov_dots(c, n, z32, r32, r32);
             cudaMemcpyAsync(c->p32, z32, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
             inner_tail(c, p, h_in);
             cudaGraph_t g_in = capture_while(c->st, h_in);
@@ -693,7 +705,7 @@ bool build_solve_graph(vof_ctx* c, vof_ctx::SolveGraph& sg, const double* b_in, 
                                                    cudaStreamCaptureModeThreadLocal) == cudaSuccess;
                 if (ok) {
                     vcycle<float>(c, 0);
-                    k32_dot2(c, n, z32, r32, c->q32, S_RZ, S_ZQ);
+                    krylov_dots(c, n, z32, r32, c->q32);
                     launch_scalar_beta(c);
                     k32_p_update(c, n, c->p32, z32);
                     inner_tail(c, p, h_in);

@@ -202,6 +202,7 @@ struct vof_ctx {
     double* rho64 = nullptr;  // FP64 path: finest-level density for density coarsening
     float* x32b = nullptr;
     int sweep_kchunk = 1;
+    bool sweep_dot = false;  // the V-cycle's last sweep forms the Krylov dots
     alignas(64) unsigned char tmap[3][128];
 
     // the V-cycle captured once as a CUDA graph and replayed (state 0: not
@@ -355,7 +356,7 @@ void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
 // finest level of the mixed V-cycle from the cell density (k_smooth_tma.cu)
 bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels);
 vof_status rho_path_setup(vof_ctx* c);
-void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0);
+void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot = false);
 void rho_restrict(vof_ctx* c);
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
 void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
