@@ -48,15 +48,16 @@ template <> __device__ __forceinline__ const float* const* visc_src<float>(const
     return P.U32;
 }
 
-// 1 / s without a division: an FP32 reciprocal seed (relative error below
-// 2^-22) refined by two Newton steps r <- r + r (1 - s r), which leaves FP64
-// rounding (a few ulp); s is a density, a normal positive number
-__device__ __forceinline__ double rcp_newton(double s) {
+// 1 / s without a division: an FP32 reciprocal seed r (relative error e0
+// below 2^-22) refined by one third-order step r + r (e + e^2), e = 1 - s r,
+// whose truncation error e0^3 < 2^-66 lies below FP64 rounding; s is a
+// density, a normal positive number
+__device__ __forceinline__ double rcp_cubic(double s) {
     float r0;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)s));
-    double r = (double)r0;
-    r = fma(r, fma(-s, r, 1.0), r);
-    return fma(r, fma(-s, r, 1.0), r);
+    const double r = (double)r0;
+    const double e = fma(-s, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // mu of a cell from its volume fraction, in the viscous term's precision
@@ -75,18 +76,24 @@ template <> __device__ __forceinline__ float mu_cell<float>(const Pred& P, int c
 // convection uses sum_f (+-) M_f (q_c + q_nb)/2 = (q_c net + sum_f (+-) M_f
 // q_nb)/2 with the net outward mass flux formed once per cell; each
 // tangential derivative at the cell is formed once and shared by its two
-// faces.
+// faces. The mixed variant is held to 128 registers: two blocks per SM.
 template <class VT>
-__global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ o1,
-                          double* __restrict__ o2, int kchunk) {
+__global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1)
+    k_predict(Pred P, double* __restrict__ o0, double* __restrict__ o1, double* __restrict__ o2,
+              int kchunk) {
     const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     const Dims& d = P.d;
     if (i >= d.nx || j >= d.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
     const double inv_h = 1.0 / P.h;
-    const VT inv_h2 = (VT)(inv_h * inv_h);
+    const VT dt_ih2 = (VT)(P.dt * inv_h * inv_h);  // dt / h^2, the viscous term's scale
     const double drho = P.rl - P.rg;
-    const double rg_dth = P.rg * (P.dt * inv_h);
+    // half mass fluxes M / 2 (exact halving: the central average's 1/2 is
+    // folded into them)
+    const double drho_h = 0.5 * drho;
+    const double rg_dth_h = 0.5 * P.rg * (P.dt * inv_h);
+    // dt B on z: dt ((rho^n - rho0) g_z + dpdz) = rho^n (dt g_z) + dt (dpdz - rho0 g_z)
+    const double dt_gz = P.dt * P.gz, dt_b0 = P.dt * (P.dpdz - P.rho0 * P.gz);
     const VT* const* UV = visc_src<VT>(P);
     for (int k = k0; k < k1; ++k) {
         const int c = cid(d, i, j, k);
@@ -99,7 +106,7 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
         // walls), donor side
         int nbc[6];
         VT muf[6];
-        double Ms[6];  // outward-signed: -M on minus faces, +M on plus faces
+        double Ms[6];  // outward-signed half fluxes: -M/2 on minus faces, +M/2 on plus faces
         bool left_donor[6];
         double net = 0.0;
 #pragma unroll
@@ -127,13 +134,13 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
             const int ci = min(max(ni, 0), d.nx - 1), cj = min(max(nj, 0), d.ny - 1);
             nbc[f] = cid(d, ci, cj, wrapk(nk, d.nz));
             muf[f] = VT(0.5) * (muc + mu_cell<VT>(P, nbc[f]));
-            const double M = wall ? 0.0 : fma(drho, F, rg_dth * uf);
+            const double M = wall ? 0.0 : fma(drho_h, F, rg_dth_h * uf);
             Ms[f] = side ? M : -M;
             net += Ms[f];
             // u_f > 0 as a sign test of the bits (no FP64 compare; +-0 is not > 0)
             left_donor[f] = __double_as_longlong(uf) > 0LL;
         }
-        const double r_rn1 = rcp_newton(rn1);
+        const double r_rn1 = rcp_cubic(rn1);
         double out[3];
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
@@ -148,11 +155,12 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
                     const bool own = (f & 1) ? left_donor[f] : !left_donor[f];
                     C = fma(Ms[f], own ? qc : qn, C);
                 }
+                C = 2.0 * C;
             } else {
                 double s = 0.0;
 #pragma unroll
                 for (int f = 0; f < 6; ++f) s = fma(Ms[f], P.U[comp][nbc[f]], s);
-                C = 0.5 * fma(net, qc, s);
+                C = fma(net, qc, s);
             }
             // viscous: (1/h^2) sum_f mu_f [(q_nb - q_c) + s_f (tangential difference)/4]
             const VT qcv = UV[comp][c];
@@ -185,13 +193,10 @@ __global__ void k_predict(Pred P, double* __restrict__ o0, double* __restrict__ 
                 }
                 V = fma(muf[f], t, V);
             }
-            const double B = comp == 2 ? (rn - P.rho0) * P.gz + P.dpdz : 0.0;
-            double force;
-            if (sizeof(VT) == sizeof(double))
-                force = fma((double)V, (double)inv_h2, B);
-            else
-                force = (double)(V * inv_h2) + B;
-            out[comp] = (fma(rn, qc, -C) + P.dt * force) * r_rn1;
+            // rho^n q - C + dt (V / h^2 + B), B on z only
+            double num = fma(rn, qc, -C) + (double)(V * dt_ih2);
+            if (comp == 2) num += fma(rn, dt_gz, dt_b0);
+            out[comp] = num * r_rn1;
         }
         o0[c] = out[0];
         o1[c] = out[1];

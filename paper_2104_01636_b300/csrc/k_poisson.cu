@@ -51,20 +51,24 @@ __device__ __forceinline__ double stencil(const Dims& d, const double* __restric
     return s;
 }
 
-// 2 / s in FP64 without a division: an FP32 reciprocal seed (relative
-// error below 2^-22) refined by two Newton steps r <- r + r (1 - s r), each
-// squaring the error, which leaves FP64 rounding (a few ulp).
-__device__ __forceinline__ double two_over(double s) {
+// 1 / s in FP64 without a division: an FP32 reciprocal seed r (relative
+// error e0 below 2^-22) refined by one third-order step r + r (e + e^2),
+// e = 1 - s r, whose truncation error e0^3 < 2^-66 lies far below FP64
+// rounding; one FMA fewer than two Newton steps. s is a positive normal
+// number (a sum of densities).
+__device__ __forceinline__ double rcp_cubic(double s) {
     float r0;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)s));
-    double r = (double)r0;
-    r = fma(r, fma(-s, r, 1.0), r);
-    r = fma(r, fma(-s, r, 1.0), r);
-    return 2.0 * r;
+    const double r = (double)r0;
+    const double e = fma(-s, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
-// rho = alpha rho_l + (1 - alpha) rho_g as one FMA, alpha (rho_l - rho_g) + rho_g;
-// each thread marches up z and carries the density of the cell below
+// rho = alpha rho_l + (1 - alpha) rho_g as one FMA, alpha (rho_l - rho_g) + rho_g.
+// The kernel works with half densities h = rho / 2 (the same FMA on halved
+// constants, exactly half of rho), so that a face coefficient
+// 2 / (rho_L + rho_R) is the reciprocal of h_L + h_R with no multiply. Each
+// thread marches up z and carries the half density of the cell below.
 __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double rg,
                        double* __restrict__ bx, double* __restrict__ by, double* __restrict__ bz,
                        float* __restrict__ rho32, __half* __restrict__ rho16,
@@ -72,22 +76,24 @@ __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double r
     CellIdx r = cell_range(d, kchunk);
     if (!r.act) return;
     const int i = r.i, j = r.j;
-    const double drho = rl - rg;
-    auto rho = [&](int c) { return fma(a[c], drho, rg); };
-    double rb = rho(cid(d, i, j, wrapk(r.k0 - 1, d.nz)));
+    const double dh = 0.5 * (rl - rg), gh = 0.5 * rg;
+    auto half_rho = [&](int c) { return fma(a[c], dh, gh); };
+    double hb = half_rho(cid(d, i, j, wrapk(r.k0 - 1, d.nz)));
     for (int k = r.k0; k < r.k1; ++k) {
         const int c = cid(d, i, j, k);
-        const double rc = rho(c);
-        if (rho32) rho32[c] = (float)rc;  // finest-level density of the multigrid
-        if (rho16) rho16[c] = __double2half(rc);
-        if (rho64) rho64[c] = rc;
+        const double hc = half_rho(c);
+        // densities of the multigrid's finest level: 2 h, scaled after the
+        // rounding (exact: a power of two)
+        if (rho32) rho32[c] = 2.f * (float)hc;
+        if (rho16) rho16[c] = __hmul(__double2half(hc), __float2half(2.f));
+        if (rho64) rho64[c] = 2.0 * hc;
         // x-face i (between i-1 and i); the last thread also writes the wall face nx
-        bx[uid(d, i, j, k)] = i == 0 ? 0.0 : two_over(rho(c - 1) + rc);
+        bx[uid(d, i, j, k)] = i == 0 ? 0.0 : rcp_cubic(half_rho(c - 1) + hc);
         if (i == d.nx - 1) bx[uid(d, d.nx, j, k)] = 0.0;
-        by[vid(d, i, j, k)] = j == 0 ? 0.0 : two_over(rho(c - d.nx) + rc);
+        by[vid(d, i, j, k)] = j == 0 ? 0.0 : rcp_cubic(half_rho(c - d.nx) + hc);
         if (j == d.ny - 1) by[vid(d, i, d.ny, k)] = 0.0;
-        bz[wid(d, i, j, k)] = two_over(rb + rc);
-        rb = rc;
+        bz[wid(d, i, j, k)] = rcp_cubic(hb + hc);
+        hb = hc;
     }
 }
 
