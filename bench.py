@@ -447,6 +447,7 @@ def main():
         e2.record(stream)
         for s in range(args.steps):
             ctx.step_host(*H, case.dt, base + 1 + s, report=False)
+        ctx.host_join()  # the last step's copies out
         e3.record(stream)
         barrier()
         ms_e2e = e2.elapsed_time(e3)

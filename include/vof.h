@@ -285,24 +285,34 @@ vof_status vof_step(vof_ctx* ctx, double* alpha, double* uc, double* vc, double*
  * with the eight arrays (same order, sizes and layouts) in host memory.
  * The context keeps a device copy of the state, allocated by the first call
  * (8 fields, in addition to vof_workspace_bytes; VOF_ERR_OOM if the device
- * has no room). Each call copies the state in on a stream of its own, u, v,
- * w and alpha first (the CFL check and the advection read them) and the
- * cell velocities and p while the advection, beta and the face force run;
- * it copies each field out as soon as the step has finished writing it:
- * alpha after the advection, p after the solve, the velocities after the
- * projection, while the context stream goes on. Page-locked host arrays
- * (cudaHostAlloc, pinned tensors) let the copies overlap the kernels;
- * pageable ones work, with copies staged by the CUDA runtime.
- * Ordering: the copies in start after all work already on the context
- * stream, and the context stream does not pass the end of this call until
- * every copy out has finished, so the host arrays hold the new state once
- * the context stream is synchronised (a report, when requested, is read
- * before the last copies out finish). The host arrays must stay valid and
- * untouched until then. Errors as for step(); after an error other than
+ * has no room). Each call copies the state in on a stream of its own, alpha,
+ * u, v and w first (the CFL check and the advection read them) and the cell
+ * velocities and p while the advection, beta and the face force run; it
+ * copies each field out, on a second stream, as soon as the step has
+ * finished writing it: alpha after the advection, p after the solve, the
+ * velocities after the projection. Page-locked host arrays (cudaHostAlloc,
+ * pinned tensors) let the copies overlap the kernels; pageable ones work,
+ * with copies staged by the CUDA runtime.
+ * Ordering. The copies in start after all work already on the context
+ * stream and, field by field, after the previous call's copy out of the
+ * same field. So consecutive calls on the same arrays form a time loop in
+ * which a call's copies in overlap the previous call's copies out (the two
+ * directions of the bus at once).
+ * Completion. With report != NULL the call returns when the step and all
+ * its copies have finished: the host arrays hold the new state. With
+ * report == NULL the copies out may still run when the call returns and the
+ * context stream does not wait for them; vof_host_join orders them before
+ * later work on the context stream, so that synchronising the stream after
+ * it leaves the host arrays complete. Until then the arrays must stay
+ * valid and untouched. Errors as for step(); after an error other than
  * VOF_ERR_NOT_CONVERGED the host arrays are unspecified. */
 vof_status vof_step_host(vof_ctx* ctx, double* alpha, double* uc, double* vc, double* wc,
                          double* u, double* v, double* w, double* p, double dt,
                          long long step_index, vof_report* report);
+
+/* Makes the context stream wait for every copy of earlier vof_step_host
+ * calls (no-op if there were none); returns at once. */
+vof_status vof_host_join(vof_ctx* ctx);
 
 /* Number of CUDA kernels this context has launched since creation. */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);

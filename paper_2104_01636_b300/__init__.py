@@ -120,6 +120,7 @@ def load() -> ctypes.CDLL:
         "project": [_VP] * 12 + [_D, P(CReport)],
         "step": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
         "vof_step_host": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
+        "vof_host_join": [_VP],
         "vof_set_timing": [_VP, ctypes.c_int],
         "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
         "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
@@ -312,8 +313,9 @@ class VofContext:
 
     def step_host(self, alpha, uc, vc, wc, u, v, w, p, dt: float, step_index: int,
                   report: bool = True):
-        """One step on host tensors (pinned for overlapped copies). The
-        tensors hold the new state once the context stream is synchronised."""
+        """One step on host tensors (pinned for overlapped copies). With a
+        report the tensors hold the new state on return; without, after
+        host_join() and a synchronisation of the context stream."""
         rep = CReport()
         st = self.lib.vof_step_host(
             self._ctx, self._hptr(alpha, 0, "alpha"), self._hptr(uc, 0, "uc"),
@@ -322,6 +324,11 @@ class VofContext:
             int(step_index), ctypes.byref(rep) if report else None)
         self._chk(st, "vof_step_host", rep)
         return rep.as_dict() if report else None
+
+    def host_join(self):
+        """Order the copies of earlier step_host calls before later work on
+        the context stream."""
+        self._chk(self.lib.vof_host_join(self._ctx), "vof_host_join")
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong(0)

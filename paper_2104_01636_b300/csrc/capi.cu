@@ -65,11 +65,6 @@ vof_status alloc(vof_ctx* c, void** p, size_t bytes) {
     return VOF_OK;
 }
 
-void readback(vof_ctx* c) {
-    cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost, c->st);
-    cudaStreamSynchronize(c->st);
-}
-
 void flush_timers(vof_ctx* c) {
     if (c->ev_marks.empty()) return;
     cudaStreamSynchronize(c->st);
@@ -236,14 +231,18 @@ enum { IO_ALPHA = 0, IO_UC, IO_VC, IO_WC, IO_U, IO_V, IO_W, IO_P };
 enum { EV_IN_FACES = 0, EV_IN_CELLS, EV_IN_P, EV_OUT_POINT, EV_OUT_DONE, EV_CALL };
 
 // device-to-host copies of fields that the context stream has finished
-// writing, on the copy-out stream once the stream's work so far is done
+// writing, on the copy-out stream once the stream's work so far is done;
+// each copy records its field's event, which the next call's copy in of
+// that field waits for
 static void io_out(vof_ctx* c, const StepIO* io, std::initializer_list<int> fields) {
     if (!io) return;
     cudaEventRecord(c->io_ev[EV_OUT_POINT], c->st);
     cudaStreamWaitEvent(c->io_st[1], c->io_ev[EV_OUT_POINT], 0);
-    for (int q : fields)
+    for (int q : fields) {
         cudaMemcpyAsync(io->host[q], io->dev[q], io->bytes[q], cudaMemcpyDeviceToHost,
                         c->io_st[1]);
+        cudaEventRecord(c->io_d2h[q], c->io_st[1]);
+    }
 }
 
 // steps 11-12 on (u_hat_c in Uh, u_hat_f in u, v, w): right side, solve,
@@ -376,6 +375,8 @@ static vof_status host_step_setup(vof_ctx* c) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
     for (auto& ev : c->io_ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (auto& ev : c->io_d2h)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     return cuda_check(c, e, "vof_step_host");
 }
 
@@ -479,7 +480,18 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
         A((void**)&c->pflow, s.n * D);
     }
     if (st == VOF_OK) st = mg_allocate(c);
-    if (st == VOF_OK) c->hbuf = c->hbuf_store.data();
+    if (st == VOF_OK) {
+        // the scalar mirror: a mapped page-locked slot, else pageable memory
+        c->hbuf = mirror_acquire();
+        if (c->hbuf && cudaHostGetDevicePointer((void**)&c->hmirror_dev, c->hbuf, 0) != cudaSuccess) {
+            cudaGetLastError();
+            mirror_release(c->hbuf);
+            c->hbuf = nullptr;
+            c->hmirror_dev = nullptr;
+        }
+        if (c->hbuf) std::memset(c->hbuf, 0, MIRROR_DOUBLES * sizeof(double));
+        else c->hbuf = c->hbuf_store.data();
+    }
     if (st == VOF_OK) {
         cudaMemsetAsync(c->scal, 0, S_NSCALARS * D, c->st);
         if (c->ptilde) cudaMemsetAsync(c->ptilde, 0, s.n * D, c->st);
@@ -496,6 +508,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
 
 vof_status vof_destroy(vof_ctx* c) {
     if (!c) return VOF_ERR_ARG;
+    for (cudaStream_t s : c->io_st)  // copies of vof_step_host still running
+        if (s) cudaStreamSynchronize(s);
     cudaStreamSynchronize(c->st);
     for (void* p : c->allocs) cudaFreeAsync(p, c->st);
     cudaStreamSynchronize(c->st);
@@ -509,6 +523,9 @@ vof_status vof_destroy(vof_ctx* c) {
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->io_ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->io_d2h)
+        if (e) cudaEventDestroy(e);
+    if (c->hmirror_dev) mirror_release(c->hbuf);
     delete c;
     return VOF_OK;
 }
@@ -687,33 +704,47 @@ vof_status vof_step_host(vof_ctx* c, double* alpha, double* uc, double* vc, doub
     double* const host[8] = {alpha, uc, vc, wc, u, v, w, p};
     StepIO io{host, c->hs, {s.n * 8, s.n * 8, s.n * 8, s.n * 8, s.nu * 8, s.nv * 8, s.nw * 8,
                             s.n * 8}};
-    // copy-in after everything already on the context stream (the previous
-    // step and its copies out); u, v, w and alpha first: the CFL check and
-    // the advection need them, the cell velocities and P come later
+    // copies in after everything already on the context stream and, field
+    // by field, after the previous call's copy out of the same field (those
+    // run on in the background: the context stream does not wait for them).
+    // alpha, u, v and w first: the CFL check and the advection need them;
+    // alpha's copy out finished early in the previous call, u, v, w are the
+    // previous call's first copies out after its projection. The cell
+    // velocities and P come later.
     cudaStream_t in = c->io_st[0];
     cudaEventRecord(c->io_ev[EV_CALL], c->st);
     cudaStreamWaitEvent(in, c->io_ev[EV_CALL], 0);
-    for (int q : {IO_U, IO_V, IO_W, IO_ALPHA})
+    auto copy_in = [&](int q) {
+        cudaStreamWaitEvent(in, c->io_d2h[q], 0);
         cudaMemcpyAsync(c->hs[q], host[q], io.bytes[q], cudaMemcpyHostToDevice, in);
+    };
+    for (int q : {IO_ALPHA, IO_U, IO_V, IO_W}) copy_in(q);
     cudaEventRecord(c->io_ev[EV_IN_FACES], in);
-    for (int q : {IO_UC, IO_VC, IO_WC})
-        cudaMemcpyAsync(c->hs[q], host[q], io.bytes[q], cudaMemcpyHostToDevice, in);
+    for (int q : {IO_UC, IO_VC, IO_WC}) copy_in(q);
     cudaEventRecord(c->io_ev[EV_IN_CELLS], in);
-    cudaMemcpyAsync(c->hs[IO_P], host[IO_P], io.bytes[IO_P], cudaMemcpyHostToDevice, in);
+    copy_in(IO_P);
     cudaEventRecord(c->io_ev[EV_IN_P], in);
     cudaStreamWaitEvent(c->st, c->io_ev[EV_IN_FACES], 0);
     if ((st = launch_check(c, "vof_step_host"))) return st;
     st = step_run(c, c->hs[IO_ALPHA], c->hs[IO_UC], c->hs[IO_VC], c->hs[IO_WC], c->hs[IO_U],
                   c->hs[IO_V], c->hs[IO_W], c->hs[IO_P], dt, step_index, report, &io);
-    // the context stream reaches this point when every copy out has finished
-    // (also after an error: the next call's copies in must not overtake them)
-    // (and for the copies in: an error can return before the step waited)
-    cudaEventRecord(c->io_ev[EV_OUT_DONE], c->io_st[1]);
-    cudaStreamWaitEvent(c->st, c->io_ev[EV_OUT_DONE], 0);
-    cudaEventRecord(c->io_ev[EV_OUT_DONE], c->io_st[0]);
-    cudaStreamWaitEvent(c->st, c->io_ev[EV_OUT_DONE], 0);
+    // with a report the call returns when every copy has finished
+    if (report) {
+        for (cudaStream_t q : c->io_st) cudaStreamSynchronize(q);
+    }
     const vof_status st2 = launch_check(c, "vof_step_host");
     return st ? st : st2;
+}
+
+vof_status vof_host_join(vof_ctx* c) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    for (cudaStream_t q : c->io_st) {
+        if (!q) continue;
+        cudaEventRecord(c->io_ev[EV_OUT_DONE], q);
+        cudaStreamWaitEvent(c->st, c->io_ev[EV_OUT_DONE], 0);
+    }
+    return launch_check(c, "vof_host_join");
 }
 
 vof_status vof_launch_count(const vof_ctx* c, long long* n) {

@@ -1,4 +1,7 @@
-// Launch geometry and the deterministic second pass of every reduction.
+// Launch geometry, the deterministic second pass of every reduction, and the
+// host mirror of the device scalars.
+#include <mutex>
+
 #include "vof_internal.cuh"
 
 Launch launch_cells(int nx, int ny, int nz, int sm_count) {
@@ -39,4 +42,54 @@ void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale) {
 void finalize_max(vof_ctx* c, int slot, int nparts, int dst) {
     VOF_LAUNCH(c, k_finalize_max, 1, 1024, c->part + (size_t)slot * MAX_PARTIALS, nparts,
                                           c->scal + dst);
+}
+
+// ---- host mirror of the device scalars --------------------------------------
+// A readback is a one-block kernel that writes the scalars into page-locked,
+// mapped host memory, then a wait on the context stream. No copy engine is
+// involved, so a readback never queues behind a large copy running on another
+// stream (the copies of vof_step_host), and nothing is staged through
+// pageable memory. The mirrors come from a process-wide arena that is never
+// freed: freeing page-locked memory would synchronise the whole device.
+namespace {
+std::mutex g_mirror_mu;
+std::vector<double*> g_mirror_free;
+
+__global__ void k_to_mirror(const double* __restrict__ s, double* __restrict__ h, int n) {
+    if ((int)threadIdx.x < n) h[threadIdx.x] = s[threadIdx.x];
+    __threadfence_system();
+}
+}  // namespace
+
+double* mirror_acquire() {
+    std::lock_guard<std::mutex> lock(g_mirror_mu);
+    if (g_mirror_free.empty()) {
+        constexpr int SLOTS = 64;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, (size_t)SLOTS * MIRROR_DOUBLES * sizeof(double),
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int q = SLOTS - 1; q >= 0; --q) g_mirror_free.push_back((double*)p + q * MIRROR_DOUBLES);
+    }
+    double* p = g_mirror_free.back();
+    g_mirror_free.pop_back();
+    return p;
+}
+
+void mirror_release(double* p) {
+    std::lock_guard<std::mutex> lock(g_mirror_mu);
+    g_mirror_free.push_back(p);
+}
+
+void readback(vof_ctx* c) {
+    if (c->hmirror_dev) {
+        ++c->nlaunch;
+        k_to_mirror<<<1, MIRROR_DOUBLES, 0, c->st>>>(c->scal, c->hmirror_dev, S_NSCALARS);
+    } else {
+        cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost,
+                        c->st);
+    }
+    cudaStreamSynchronize(c->st);
 }

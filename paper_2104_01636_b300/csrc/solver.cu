@@ -39,11 +39,6 @@ size_t faces_bytes(const Dims& d, size_t elt) {
                   (size_t)d.nx * d.ny * d.nz);
 }
 
-void readback(vof_ctx* c) {
-    cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost, c->st);
-    cudaStreamSynchronize(c->st);
-}
-
 template <class T>
 void vcycle(vof_ctx* c, int l);
 template <class T>

@@ -20,6 +20,7 @@ constexpr int TBX = 32;
 constexpr int TBY = 8;
 constexpr int TB = TBX * TBY;
 constexpr int MAX_PARTIALS = 4096;  // per reduction slot
+constexpr int MIRROR_DOUBLES = 64;  // host mirror of the device scalars
 constexpr int NSLOTS = 24;          // reduction slots in the partials buffer
 
 struct Dims {
@@ -179,8 +180,11 @@ struct vof_ctx {
 
     double* part = nullptr;  // NSLOTS x MAX_PARTIALS block partials
     double* scal = nullptr;  // device scalars
-    double* hbuf = nullptr;  // host mirror of scal (points into hbuf_store)
-    std::vector<double> hbuf_store = std::vector<double>(64, 0.0);
+    // host mirror of scal: a mapped page-locked slot (hmirror_dev its device
+    // address), else hbuf_store
+    double* hbuf = nullptr;
+    double* hmirror_dev = nullptr;
+    std::vector<double> hbuf_store = std::vector<double>(MIRROR_DOUBLES, 0.0);
     int* dflag = nullptr;    // device error flags
 
     // timing
@@ -240,6 +244,8 @@ struct vof_ctx {
     double* hs[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t io_st[2] = {nullptr, nullptr};  // host to device, device to host
     cudaEvent_t io_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t io_d2h[8] = {nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr};  // last copy out, per field
 
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
@@ -291,6 +297,7 @@ enum ScalarSlot {
     S_INNER, S_OUTER, S_RES, S_RES0, S_BNORM, S_THR, S_CAP, S_CONV, S_STATUS, S_ZERO, S_GUARD,
     S_NSCALARS
 };
+static_assert(S_NSCALARS <= MIRROR_DOUBLES, "the host mirror holds every device scalar");
 
 // ---------------------------------------------------------------------------
 // helpers implemented in capi.cu
@@ -303,6 +310,10 @@ int timer_begin(vof_ctx* c, int cls);
 void timer_end(vof_ctx* c, int cls, int mark);
 
 // reductions (k_common.cu): sum / max of the block partials of slot into scal[dst]
+// the device scalars into c->hbuf, then a wait on the context stream
+void readback(vof_ctx* c);
+double* mirror_acquire();
+void mirror_release(double* p);
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale);
 void finalize_max(vof_ctx* c, int slot, int nparts, int dst);
 

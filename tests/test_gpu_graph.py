@@ -38,8 +38,10 @@ def test_graph_replay_matches_direct_launches(prec):
     assert [r["res"] for r in rd] == [r["res"] for r in rg]
     if prec == 0:
         assert nd == ng
-    else:  # the captured solve adds its control kernels, one per iteration
-        assert nd < ng < 1.2 * nd
+    else:
+        # the captured solve adds a control kernel per iteration and drops
+        # the host loop's readback kernel per iteration
+        assert abs(ng - nd) < 0.2 * nd
 
 
 def _solve(case, solver, stream, b, p0=None):

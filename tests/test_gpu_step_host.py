@@ -2,8 +2,9 @@
 copied in and out by the library around and during the step, and the result
 is bitwise that of step() on device arrays. Covers pinned and pageable host
 memory, the FP64 and mixed paths, a context on the legacy default stream and
-one on a side stream (captured solve), several steps in a row, and an error
-(CFL) that leaves the context usable."""
+one on a side stream (captured solve), several steps in a row with and
+without reports (the pipelined loop, completed by vof_host_join), and an
+error (CFL) that leaves the context usable."""
 import numpy as np
 import pytest
 import torch
@@ -25,13 +26,15 @@ def _device_steps(case, sv, stream, steps):
     return [host(t) for t in T], reps
 
 
-def _host_steps(case, sv, stream, steps, pinned):
+def _host_steps(case, sv, stream, steps, pinned, report=True):
     H = [torch.from_numpy(np.array(a, dtype=np.float64, order="C", copy=True)) for a in case.state()]
     if pinned:
         H = [h.pin_memory() for h in H]
     with torch.cuda.stream(stream):
         with vd.VofContext(case.grid, case.phys, sv, stream=stream) as C:
-            reps = [C.step_host(*H, case.dt, s) for s in steps]
+            reps = [C.step_host(*H, case.dt, s, report=report) for s in steps]
+            if not report:  # the last call's copies out may still be running
+                C.host_join()
             stream.synchronize()
     return [h.numpy().copy() for h in H], reps
 
@@ -49,6 +52,20 @@ def test_step_host_equals_device_step(prec, side_stream):
     for a, b in zip(rg, rr):
         assert a["iters"] == b["iters"] and a["res"] == b["res"]
         assert a["vol_after"] == b["vol_after"] and a["max_div"] == b["max_div"]
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_step_host_pipelined_loop(side_stream):
+    """Calls without a report: each call's copies in overlap the previous
+    call's copies out; after host_join and a synchronisation the host state
+    is bitwise that of device steps."""
+    case = I.rising_swarm(48, 40, 64, nbub=4, d_cells=9, seed=99, steps=4)
+    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-9, max_iter=300)
+    stream = torch.cuda.Stream() if side_stream else torch.cuda.default_stream()
+    ref, _ = _device_steps(case, sv, stream, range(4))
+    got, _ = _host_steps(case, sv, stream, range(4), pinned=True, report=False)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
 
 
 def test_step_host_pageable_memory():
