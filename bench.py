@@ -56,7 +56,10 @@ def algo_bytes_per_cell(cls: str, precision: str) -> float:
     if precision == "fp64":
         return {"smooth_l0": 36.0, "restrict_l0": 41.0, "prolong_l0": 17.0,
                 "residual_l0": 40.0}[cls]
-    return {"smooth_l0": (10.0 + 14.0 * (2 * NU - 1)) / (2 * NU), "restrict_l0": 10.5,
+    # finest-level sweeps per cycle: one from zero (density 2, f 4, x out 4),
+    # 2 NU - 2 from x (+ old x 4), and the last one, which also reads q for
+    # the Krylov dots (+ 4)
+    return {"smooth_l0": (10.0 + 14.0 * (2 * NU - 2) + 18.0) / (2 * NU), "restrict_l0": 10.5,
             "prolong_l0": 8.5, "residual_l0": 44.0}[cls]
 
 
