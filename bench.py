@@ -72,8 +72,8 @@ KERNEL_SOURCE = {"fp64": {"smooth_l0": "k_mg.cu", "residual_l0": "k_poisson.cu",
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--rtol", type=float, default=1e-8)
@@ -85,6 +85,10 @@ def parse():
                          "ncu can profile (it cannot profile kernel nodes of graphs with "
                          "conditional nodes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-one-thread", action="store_true",
+                    help="also time the oracle's sample on one host thread (slow)")
+    ap.add_argument("--no-regular-array", action="store_true",
+                    help="skip the 6x6x24 regular-array variant of the workload")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests in the serving run (0 skips it)")
@@ -192,14 +196,26 @@ def traffic_for(cls: str, precision: str):
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline(args, steps=1, label="bounded sample"):
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(args, steps=1, label="bounded sample", nz_s=16, threads=0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    the same generator with 16 z-planes (224x224x16, ~0.8M cells). Its
-    steps/s is scaled to the 32.1M-cell metric by the cell ratio."""
+    the same generator with nz_s z-planes (224x224x16, ~0.8M cells, by
+    default). Its steps/s is scaled to the 32.1M-cell metric by the cell
+    ratio. threads > 0 caps the oracle's OpenMP threads."""
     import oracle
     from paper_2104_01636_b300 import inputs as I
     full = 224 * 224 * 640
-    nz_s = 16
+    if threads > 0:
+        oracle.set_num_threads(threads)
     case = I.paper_shaped(224, 224, nz_s, nbub=round(864 * nz_s / 640), seed=2106)
     g, ph = case.grid, case.phys
     state = case.state()
@@ -214,6 +230,8 @@ def cpu_baseline(args, steps=1, label="bounded sample"):
         "value": sps_sample * g.ncells / full,
         "unit": UNIT,
         "cores": oracle.num_threads(),
+        "cpu_model": cpu_model(),
+        "host_cores": os.cpu_count(),
         "kind": "oracle",
         "sample": (f"{steps} oracle step(s) of the same generator on 224x224x{nz_s} "
                    f"({g.ncells} cells, {round(864 * nz_s / 640)} spheres), rtol {args.rtol:g}, "
@@ -227,16 +245,21 @@ def cpu_baseline(args, steps=1, label="bounded sample"):
 def run_reference(args, rank):
     if rank != 0:
         return
+    # each step a bounded sample: 16 z-planes (about 8 s of oracle work on 16
+    # host cores) up to 13 steps in all, fewer planes for longer runs, so that
+    # the whole run stays within a few minutes
+    nz_s = max(4, min(16, (16 * 13) // max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(args, steps=1)
-    cb = cpu_baseline(args, steps=max(1, args.steps), label="reference arm")
+        cpu_baseline(args, steps=1, nz_s=nz_s)
+    cb = cpu_baseline(args, steps=max(1, args.steps), label="reference arm", nz_s=nz_s)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": cb["sample"]},
-        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "cpu_model", "kind",
+                                            "sample")},
         "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "poisson_cell_updates_per_s": cb["poisson_cell_updates_per_s"],
@@ -434,6 +457,7 @@ def main():
                     "share_of_step": kms / k_steps / step_ms_timed if step_ms_timed else None,
                     "classes_ms_per_step": {k: round(v[0] / k_steps, 4) for k, v in kt.items()}}
         poisson = N * it2 / (solve_ms / 1e3) if solve_ms > 0 else None
+        solves = k_steps / (solve_ms / 1e3) if solve_ms > 0 else None
 
         # ---- end to end: the state in pinned host memory, copied in and out
         # every step by the host-buffer step of the C ABI (vof_step_host) --
@@ -479,6 +503,30 @@ def main():
             ctx64.close()
             del T64
 
+        # ---- the paper's regular 6 x 6 x 24 bubble array (same grid) -------
+        regular = None
+        if not args.no_regular_array:
+            rcase = I.paper_shaped(224, 224, args.nz, regular=True)
+            ctxr = vd.VofContext(g, rcase.phys, vd.c_solver(prec, rtol=args.rtol, max_iter=500),
+                                 stream=stream)
+            TR = [dev(x) for x in rcase.state()]
+            for s in range(2):
+                ctxr.step(*TR, rcase.dt, s)
+            nr = max(1, min(args.steps, 10))
+            itr = 0
+            barrier()
+            e0.record(stream)
+            for s in range(2, 2 + nr):
+                itr += ctxr.step(*TR, rcase.dt, s)["iters"]
+            e1.record(stream)
+            barrier()
+            msr = e0.elapsed_time(e1)
+            regular = {"value": nr / (msr / 1e3), "unit": UNIT, "ms_per_step": msr / nr,
+                       "pcg_iters_per_step": itr / nr, "steps": nr, "spheres": 864,
+                       "layout": "regular 6 x 6 x 24 array (Section 4)"}
+            ctxr.close()
+            del TR
+
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = serving(vd, I, args.serve_requests, not args.no_fp64_compare)
@@ -493,6 +541,11 @@ def main():
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args, steps=1)
+        if args.cpu_one_thread:
+            one = cpu_baseline(args, steps=1, label="one host thread", threads=1)
+            cb["one_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample",
+                                                     "sample_s_per_step",
+                                                     "poisson_cell_updates_per_s")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -507,14 +560,19 @@ def main():
                    "dt": case.dt},
         "poisson_cell_updates_per_s": poisson,
         "pcg_iters_per_step": iters / args.steps,
+        "solves_per_s": solves,
         "roofline": roofline,
         "cpu_baseline": (None if cb is None else
-                         {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}),
+                         {k: cb[k] for k in ("value", "unit", "cores", "cpu_model", "host_cores",
+                                             "kind", "sample", "sample_s_per_step",
+                                             "poisson_cell_updates_per_s", "one_thread")
+                          if k in cb}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
         "gpu_launches": launches,
         "clocks": ck,
         "fp64_path": fp64,
+        "regular_array": regular,
         "serving": serve,
         "ensemble": ens,
     }

@@ -77,6 +77,7 @@ def lib():
         _lib.or_normal.argtypes = [P(Grid), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         _lib.or_hf_direction.argtypes = [dp]
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_set_num_threads.argtypes = [ctypes.c_int]
     return _lib
 
 
@@ -106,6 +107,11 @@ def shapes(g):
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Cap the OpenMP threads of later oracle calls (timing only)."""
+    lib().or_set_num_threads(int(n))
 
 
 # --- geometry -----------------------------------------------------------------

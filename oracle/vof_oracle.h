@@ -125,8 +125,10 @@ int or_step(const or_grid* g, const or_phys* p, double* alpha, double* uc, doubl
             double* wc, double* u, double* v, double* w, double* P, double dt,
             long step_index, double rtol, int max_iter, or_report* rep);
 
-/* Threads used by the OpenMP loops (for the CPU-baseline report). */
+/* Threads used by the OpenMP loops (for the CPU-baseline report), and a
+ * cap on them for later calls (n <= 0: unchanged). */
 int or_num_threads(void);
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
