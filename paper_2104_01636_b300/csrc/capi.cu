@@ -356,27 +356,29 @@ vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double*
 // vof_step_host: the device copies of the state and the copy streams, made
 // at the first call
 static vof_status host_step_setup(vof_ctx* c) {
-    if (c->hs[0]) return VOF_OK;
-    const Sizes s = sizes_of(&c->g);
-    const size_t n[8] = {s.n, s.n, s.n, s.n, s.nu, s.nv, s.nw, s.n};
-    for (int q = 0; q < 8; ++q) {
-        c->hs[q] = (double*)dev_alloc(c, n[q] * sizeof(double));
-        if (!c->hs[q]) {
-            for (int r = 0; r < q; ++r) {
-                cudaFreeAsync(c->hs[r], c->st);
-                c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void*)c->hs[r]));
-                c->hs[r] = nullptr;
+    if (!c->hs[0]) {
+        const Sizes s = sizes_of(&c->g);
+        const size_t n[8] = {s.n, s.n, s.n, s.n, s.nu, s.nv, s.nw, s.n};
+        for (int q = 0; q < 8; ++q) {
+            c->hs[q] = (double*)dev_alloc(c, n[q] * sizeof(double));
+            if (!c->hs[q]) {
+                for (int r = 0; r < q; ++r) {
+                    cudaFreeAsync(c->hs[r], c->st);
+                    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void*)c->hs[r]));
+                    c->hs[r] = nullptr;
+                }
+                return set_err(c, VOF_ERR_OOM, "vof_step_host: no device memory for the state");
             }
-            return set_err(c, VOF_ERR_OOM, "vof_step_host: no device memory for the state");
         }
     }
+    // streams and events (each made once; a failed call is retried next time)
     cudaError_t e = cudaSuccess;
     for (auto& q : c->io_st)
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+        if (!q && e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
     for (auto& ev : c->io_ev)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (!ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     for (auto& ev : c->io_d2h)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (!ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     return cuda_check(c, e, "vof_step_host");
 }
 
