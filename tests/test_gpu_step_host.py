@@ -68,6 +68,19 @@ def test_step_host_pipelined_loop(side_stream):
         assert np.array_equal(a, b)
 
 
+def test_step_host_two_solves():
+    """The paper's two pressure solves per step (p~ kept in the context):
+    P is copied out after the two solutions are combined."""
+    case = I.rising_swarm(40, 32, 48, nbub=3, d_cells=8, seed=100, steps=3)
+    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-9, max_iter=300, ssf_solves=2)
+    stream = torch.cuda.Stream()
+    ref, rr = _device_steps(case, sv, stream, range(3))
+    got, rg = _host_steps(case, sv, stream, range(3), pinned=True)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    assert [r["iters"] for r in rg] == [r["iters"] for r in rr]
+
+
 def test_step_host_pageable_memory():
     case = I.rising_swarm(40, 32, 48, nbub=3, d_cells=8, seed=96, steps=2)
     sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-9, max_iter=300)
