@@ -89,6 +89,9 @@ def parse():
                     help="also time the oracle's sample on one host thread (slow)")
     ap.add_argument("--no-regular-array", action="store_true",
                     help="skip the 6x6x24 regular-array variant of the workload")
+    ap.add_argument("--no-small-configs", action="store_true",
+                    help="skip the static bubble (32^3, 20 steps) and the 64x64x128 swarm "
+                         "(200 steps, FP64 against mixed)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests in the serving run (0 skips it)")
@@ -368,6 +371,67 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
 
 
 # ----------------------------------------------------------------------------
+def small_configs(vd, I):
+    """The two small configurations on the GPU, fields resident on the device:
+    the static bubble (32^3, R = 8h, 20 steps, FP64 at rtol 1e-10) with exact
+    and height-function curvature, reporting the pressure jump against the
+    Laplace value 2 sigma / R and the spurious currents; and the rising swarm
+    (64x64x128, 8 spheres, 200 steps) on the FP64 and the mixed path at rtol
+    1e-8, reporting time per step and the mixed path's difference from FP64."""
+    import numpy as np
+    import torch
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def run(case, sv, steps):
+        T = [dev(x) for x in case.state()]
+        torch.cuda.synchronize()
+        reps = []
+        stream = torch.cuda.Stream()  # capturable: the solver replays its graphs
+        with torch.cuda.stream(stream):
+            with vd.VofContext(case.grid, case.phys, sv, stream=stream) as C:
+                C.step(*T, case.dt, 0)  # the first step captures the graphs
+                stream.synchronize()
+                t0 = time.perf_counter()
+                for s in range(1, steps):
+                    reps.append(C.step(*T, case.dt, s))
+                stream.synchronize()
+                ms = (time.perf_counter() - t0) * 1e3 / max(steps - 1, 1)
+        return [t.cpu().numpy() for t in T], reps, ms
+
+    out = {}
+    for name, km in (("exact_curvature", 1), ("height_function", 0)):
+        case = I.static_bubble(kappa_mode=km)
+        st, reps, ms = run(case, vd.c_solver(vd.PREC_FP64, rtol=1e-10, max_iter=400), 20)
+        g, R, c = case.grid, case.radius, case.centres[0]
+        x = (np.arange(g.nx) + 0.5) * g.h
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        r = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+        a, P = st[0], st[7]
+        dp = P[(a < 1e-9) & (r < R - 2 * g.h)].mean() - P[(a > 1 - 1e-9) & (r > R + 2 * g.h)].mean()
+        dpl = 2 * case.phys.sigma / R
+        out.setdefault("static_bubble", {"grid": "32^3", "radius": "8h", "steps": 20,
+                                         "laplace_pa": dpl})[name] = {
+            "dp_over_laplace": dp / dpl, "max_u": reps[-1]["max_u"],
+            "capillary_number": case.phys.mu_l * reps[-1]["max_u"] / case.phys.sigma,
+            "ms_per_step": ms}
+    case = I.rising_swarm(64, 64, 128, nbub=8, d_cells=12, seed=2104, steps=200)
+    sw = {"grid": "64x64x128", "spheres": 8, "steps": 200, "rtol": 1e-8}
+    states = {}
+    for name, prec in (("fp64", vd.PREC_FP64), ("mixed", vd.PREC_MIXED_FP32)):
+        st, reps, ms = run(case, vd.c_solver(prec, rtol=1e-8, max_iter=500), 200)
+        states[name] = st
+        sw[name] = {"ms_per_step": ms, "pcg_iters_per_step": float(np.mean([r["iters"] for r in reps])),
+                    "max_div_dt": max(r["max_div"] for r in reps) * case.dt}
+    f, m = states["fp64"], states["mixed"]
+    vel = lambda s: np.concatenate([np.ravel(t) for t in s[1:7]])
+    sw["mixed_vs_fp64"] = {
+        "velocity_rel_l2": float(np.linalg.norm(vel(m) - vel(f)) / np.linalg.norm(vel(f))),
+        "alpha_max_abs": float(np.abs(m[0] - f[0]).max()),
+        "volume_rel_diff": float(abs(m[0].sum() - f[0].sum()) / f[0].sum())}
+    out["rising_swarm"] = sw
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -533,6 +597,9 @@ def main():
     ens = None
     if world == 1 and args.ensemble_cases > 0:
         ens = ensemble(vd, I, args.ensemble_cases)
+    small = None
+    if world == 1 and not args.no_small_configs:
+        small = small_configs(vd, I)
 
     if rank != 0:
         if dist is not None:
@@ -575,6 +642,7 @@ def main():
         "regular_array": regular,
         "serving": serve,
         "ensemble": ens,
+        "small_configs": small,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
