@@ -34,6 +34,36 @@ __global__ void k_finalize_max(const double* __restrict__ part, int n, double* o
     if (threadIdx.x == 0) *out = s;
 }
 
+__global__ void k_finalize_dots_beta(const double* __restrict__ pa, const double* __restrict__ pb,
+                                     int n, double* scal) {
+    const double rz = sum_partials(pa, n);
+    const double zq = sum_partials(pb, n);
+    if (threadIdx.x == 0) {
+        scal[S_RZ] = rz * 1.0;
+        scal[S_ZQ] = zq * 1.0;
+        const double pq = scal[S_PQ];  // of the previous direction
+        scal[S_BETA] = pq > 0.0 ? -zq / pq : 0.0;
+    }
+}
+
+__global__ void k_finalize_pq_alpha(const double* __restrict__ part, int n, double* scal) {
+    const double pq = sum_partials(part, n);
+    if (threadIdx.x == 0) {
+        scal[S_PQ] = pq * 1.0;
+        scal[S_ALPHA] = pq > 0.0 ? scal[S_RZ] / pq : 0.0;
+    }
+}
+
+void finalize_dots_beta(vof_ctx* c, int nparts) {
+    VOF_LAUNCH(c, k_finalize_dots_beta, 1, 1024, c->part + (size_t)S_RZ * MAX_PARTIALS,
+               c->part + (size_t)S_ZQ * MAX_PARTIALS, nparts, c->scal);
+}
+
+void finalize_pq_alpha(vof_ctx* c, int nparts) {
+    VOF_LAUNCH(c, k_finalize_pq_alpha, 1, 1024, c->part + (size_t)S_PQ * MAX_PARTIALS, nparts,
+               c->scal);
+}
+
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale) {
     VOF_LAUNCH(c, k_finalize_sum, 1, 1024, c->part + (size_t)slot * MAX_PARTIALS, nparts,
                                           c->scal + dst, scale);

@@ -743,27 +743,27 @@ void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     VOF_LAUNCH(c, k_apply_A_dot32, L.L.grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)), L.bxf,
                L.byf, L.bzf, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
-    finalize_sum(c, slot, L.L.nblocks, slot, 1.0);
+    finalize_pq_alpha(c, L.L.nblocks);
 }
 
-void k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q,
-                   int slot) {
+int k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q, int slot,
+                  bool finalize) {
     const int nb = flat_blocks(n);
     int m = timer_begin(c, T_KRYLOV);
     VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
                c->part + (size_t)slot * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
-    finalize_sum(c, slot, nb, slot, 1.0);
+    if (finalize) finalize_sum(c, slot, nb, slot, 1.0);
+    return nb;
 }
 
-void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q, int sa, int sb) {
+void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q) {
     const int nb = flat_blocks(n);
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_dot2_32, nb, 256, n, z, r, q, c->part + (size_t)sa * MAX_PARTIALS,
-               c->part + (size_t)sb * MAX_PARTIALS);
+    VOF_LAUNCH(c, k_dot2_32, nb, 256, n, z, r, q, c->part + (size_t)S_RZ * MAX_PARTIALS,
+               c->part + (size_t)S_ZQ * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
-    finalize_sum(c, sa, nb, sa, 1.0);
-    finalize_sum(c, sb, nb, sb, 1.0);
+    finalize_dots_beta(c, nb);
 }
 
 void k32_p_update(vof_ctx* c, int n, float* p, const float* z) {

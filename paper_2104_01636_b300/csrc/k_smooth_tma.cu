@@ -611,11 +611,7 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
     else
         k_sweep_rho<false, true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     timer_end(c, T_SMOOTH0, m);
-    if (dot) {
-        const int nb = (int)(grid.x * grid.y * grid.z);
-        finalize_sum(c, S_RZ, nb, S_RZ, 1.0);
-        finalize_sum(c, S_ZQ, nb, S_ZQ, 1.0);
-    }
+    if (dot) finalize_dots_beta(c, (int)(grid.x * grid.y * grid.z));
 }
 
 void rho_restrict(vof_ctx* c) {
@@ -632,5 +628,5 @@ void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     VOF_LAUNCH(c, k_apply_A_dot_rho32, L.L.grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
                c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
-    finalize_sum(c, slot, L.L.nblocks, slot, 1.0);
+    finalize_pq_alpha(c, L.L.nblocks);
 }

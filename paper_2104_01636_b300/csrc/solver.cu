@@ -218,7 +218,7 @@ void run_vcycle(vof_ctx* c) {
 // iteration of a refinement, which passes q = r, does not use (z, q))
 void krylov_dots(vof_ctx* c, int n, const float* z, const float* r, const float* q) {
     if (c->use_rho && c->sweep_dot) return;
-    k32_dot2(c, n, z, r, q, S_RZ, S_ZQ);
+    k32_dot2(c, n, z, r, q);
 }
 
 // z = M r (one V-cycle), in the precision the context was created with
@@ -457,8 +457,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
             if (c->use_rho)
                 rho_apply_A_dot(c, c->p32, c->q32, S_PQ);
             else
-                k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
-            launch_scalar_alpha(c);
+                k32_apply_A_dot(c, c->p32, c->q32, S_PQ);  // and alpha
             k32_cg_update(c, n, c->e32, r32, c->p32, c->q32, S_RR);
             readback(c);
             if (c->hbuf[S_ERR] != 0.0)
@@ -467,8 +466,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
             if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
             if (rr <= tol_in * tol_in * rr0) break;
             run_vcycle<float>(c);
-            krylov_dots(c, n, z32, r32, c->q32);
-            launch_scalar_beta(c);
+            krylov_dots(c, n, z32, r32, c->q32);  // and beta
             k32_p_update(c, n, c->p32, z32);
         }
         // FP64 update and true residual
@@ -550,7 +548,11 @@ __global__ void k_ctl_outer_begin(double* s, SolveCtl p) {
 
 // after an inner CG update: count it, check the wait flag and the residual,
 // and continue while the inner tolerance, max_iter and the cap allow
-__global__ void k_ctl_inner(double* s, SolveCtl p, cudaGraphConditionalHandle h_in) {
+__global__ void k_ctl_inner(double* s, const double* __restrict__ part_rr, int nparts, SolveCtl p,
+                            cudaGraphConditionalHandle h_in) {
+    const double rr_sum = sum_partials(part_rr, nparts);  // (r, r), as finalize_sum forms it
+    if (threadIdx.x != 0) return;
+    s[S_RR] = rr_sum * 1.0;
     const double inner = s[S_INNER] + 1.0, guard = s[S_GUARD] + 1.0;
     s[S_INNER] = inner;
     s[S_GUARD] = guard;
@@ -628,11 +630,10 @@ void inner_tail(vof_ctx* c, const SolveCtl& p, cudaGraphConditionalHandle h_in) 
     if (c->use_rho)
         rho_apply_A_dot(c, c->p32, c->q32, S_PQ);
     else
-        k32_apply_A_dot(c, c->p32, c->q32, S_PQ);
-    launch_scalar_alpha(c);
-    k32_cg_update(c, n, c->e32, c->lv[0].ff, c->p32, c->q32, S_RR);
+        k32_apply_A_dot(c, c->p32, c->q32, S_PQ);  // and alpha
+    const int nb = k32_cg_update(c, n, c->e32, c->lv[0].ff, c->p32, c->q32, S_RR, false);
     ++c->nlaunch;
-    k_ctl_inner<<<1, 1, 0, c->st>>>(c->scal, p, h_in);
+    k_ctl_inner<<<1, 1024, 0, c->st>>>(c->scal, c->part + (size_t)S_RR * MAX_PARTIALS, nb, p, h_in);
 }
 
 // Captures the whole mixed solve for right side b_in and solution P into
@@ -700,8 +701,7 @@ bool build_solve_graph(vof_ctx* c, vof_ctx::SolveGraph& sg, const double* b_in, 
                                                    cudaStreamCaptureModeThreadLocal) == cudaSuccess;
                 if (ok) {
                     vcycle<float>(c, 0);
-                    krylov_dots(c, n, z32, r32, c->q32);
-                    launch_scalar_beta(c);
+                    krylov_dots(c, n, z32, r32, c->q32);  // and beta
                     k32_p_update(c, n, c->p32, z32);
                     inner_tail(c, p, h_in);
                     cudaGraph_t gb = nullptr;

@@ -76,6 +76,13 @@ __device__ __forceinline__ double block_sum(double v) {
     __syncthreads();
     return v;
 }
+// the sum of n block partials by one block, in k_finalize_sum's order
+// (every thread calls it; the result is valid in thread 0)
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    return block_sum(s);
+}
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double sh_bm[32];
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -315,6 +322,11 @@ void readback(vof_ctx* c);
 double* mirror_acquire();
 void mirror_release(double* p);
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale);
+// the inner FP32 CG's scalars with their reductions, one launch each:
+// (z, r) -> S_RZ and (z, q) -> S_ZQ from the partials in slots S_RZ, S_ZQ,
+// then beta; (p, q) -> S_PQ from slot S_PQ, then alpha
+void finalize_dots_beta(vof_ctx* c, int nparts);
+void finalize_pq_alpha(vof_ctx* c, int nparts);
 void finalize_max(vof_ctx* c, int slot, int nparts, int dst);
 
 // ---------------------------------------------------------------------------
@@ -357,8 +369,12 @@ constexpr int DENSE_MAX = 1536;  // largest coarsest level solved by the dense i
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
 // inner FP32 Krylov of the mixed solve (k_mg.cu) and its FP64 residual (k_poisson.cu)
 void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
-void k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q, int slot);
-void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q, int sa, int sb);
+// returns the number of block partials of (r, r) in slot; finalize false
+// leaves their sum to the caller
+int k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q, int slot,
+                  bool finalize = true);
+// (z, r) -> S_RZ, (z, q) -> S_ZQ and beta (finalize_dots_beta)
+void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q);
 void k32_p_update(vof_ctx* c, int n, float* p, const float* z);
 void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x);
 void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r32, int slot);
