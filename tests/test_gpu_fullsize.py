@@ -161,6 +161,17 @@ def test_step_full_size_conserves_volume(duct, bench_ctx):
     for rep in (rep0, rep1):
         assert rep["res"] <= 1e-8
         assert abs(rep["vol_clipped"]) <= 1e-12 * rep["vol_before"]
+    # the projection: the divergence of the new face velocities, recomputed
+    # here in FP64, is the one the step reports, and it is at the solver's
+    # tolerance (div u^{n+1} = -dt (b - A P) for the solve's residual)
+    u, v, w = (host(t) for t in T[4:7])
+    inv_h = 1.0 / duct.grid.h
+    # the same operations in the same order as the step's reduction
+    div = ((((u[:, :, 1:] - u[:, :, :-1]) + v[:, 1:, :]) - v[:, :-1, :]) +
+           np.roll(w, -1, axis=0) - w) * inv_h
+    dmax = np.abs(div).max()
+    assert dmax == pytest.approx(rep1["max_div"], rel=1e-12)
+    assert dmax * duct.dt < 1e-8
     assert float(np.sum(a0, dtype=np.float64)) == pytest.approx(vol0, rel=1e-12)
     assert float(np.sum(a1, dtype=np.float64)) == pytest.approx(vol0, rel=1e-9)
     assert a1.min() >= 0.0 and a1.max() <= 1.0
