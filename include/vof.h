@@ -314,6 +314,14 @@ vof_status vof_step_host(vof_ctx* ctx, double* alpha, double* uc, double* vc, do
  * calls (no-op if there were none); returns at once. */
 vof_status vof_host_join(vof_ctx* ctx);
 
+/* Diagnostic of the failure path of the bounded device waits: one block
+ * waits, with the same bounded wait as the staged sweep, on a shared-memory
+ * barrier that nothing completes (no copy is in flight). The limit runs
+ * out, the block sets the context's device error flag, and the call returns
+ * VOF_ERR_TIMEOUT, as a solve does when a staged plane never arrives. The
+ * flag is cleared again, so the context stays usable. Synchronous. */
+vof_status vof_diag_wait_timeout(vof_ctx* ctx);
+
 /* Number of CUDA kernels this context has launched since creation. */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
 

@@ -121,6 +121,7 @@ def load() -> ctypes.CDLL:
         "step": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
         "vof_step_host": [_VP] * 9 + [_D, ctypes.c_longlong, P(CReport)],
         "vof_host_join": [_VP],
+        "vof_diag_wait_timeout": [_VP],
         "vof_set_timing": [_VP, ctypes.c_int],
         "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
         "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
@@ -329,6 +330,11 @@ class VofContext:
         """Order the copies of earlier step_host calls before later work on
         the context stream."""
         self._chk(self.lib.vof_host_join(self._ctx), "vof_host_join")
+
+    def diag_wait_timeout(self):
+        """Runs the bounded-wait failure path once (raises VofError
+        VOF_ERR_TIMEOUT); the context stays usable."""
+        self._chk(self.lib.vof_diag_wait_timeout(self._ctx), "vof_diag_wait_timeout")
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong(0)

@@ -738,6 +738,19 @@ vof_status vof_step_host(vof_ctx* c, double* alpha, double* uc, double* vc, doub
     return st ? st : st2;
 }
 
+vof_status vof_diag_wait_timeout(vof_ctx* c) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), c->st);
+    wait_probe(c, 1000);
+    readback(c);
+    const bool out = c->hbuf[S_ERR] != 0.0;
+    cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), c->st);  // the context stays usable
+    if ((st = launch_check(c, "vof_diag_wait_timeout"))) return st;
+    if (out) return set_err(c, VOF_ERR_TIMEOUT, "a bounded device wait ran out (diagnostic probe)");
+    return VOF_OK;
+}
+
 vof_status vof_host_join(vof_ctx* c) {
     vof_status st = check_ctx(c);
     if (st) return st;

@@ -513,6 +513,23 @@ __global__ void k_apply_A_dot_rho32(Dims d, float ih2, const float* __restrict__
     if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
 }
 
+// One block waits, with the sweep's bounded wait, on a shared-memory barrier
+// that nothing completes (no copy is issued): the limit runs out and the
+// block sets the error flag, as the sweep does when a staged plane never
+// arrives (the diagnostic behind vof_diag_wait_timeout).
+__global__ void k_wait_probe(double* __restrict__ err, int limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int it = 0; !bad && !mbar_try_wait(&bar, 0u);)
+        if (++it > limit) bad = true;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) *err = 1.0;
+}
+
 // ---- tensor maps -------------------------------------------------------------
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -612,6 +629,11 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
         k_sweep_rho<false, true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     timer_end(c, T_SMOOTH0, m);
     if (dot) finalize_dots_beta(c, (int)(grid.x * grid.y * grid.z));
+}
+
+void wait_probe(vof_ctx* c, int limit) {
+    ++c->nlaunch;
+    k_wait_probe<<<1, 32, 0, c->st>>>(c->scal + S_ERR, limit);
 }
 
 void rho_restrict(vof_ctx* c) {

@@ -384,6 +384,8 @@ void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
 bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels);
 vof_status rho_path_setup(vof_ctx* c);
 void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot = false);
+// one block waiting out a bounded wait on a barrier nothing completes
+void wait_probe(vof_ctx* c, int limit);
 void rho_restrict(vof_ctx* c);
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
 void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);

@@ -1,5 +1,6 @@
-"""Error behaviour of the C ABI on a GPU (host-detected conditions only: no
-kernel is driven into a fault)."""
+"""Error behaviour of the C ABI on a GPU: host-detected conditions, and a
+bounded device wait that runs out (no kernel is driven into a fault or a
+hang)."""
 import ctypes
 
 import numpy as np
@@ -65,3 +66,17 @@ def test_periodic_walls_unsupported_in_solve():
         with pytest.raises(vd.VofError) as e:
             C.pressure_solve(dev(np.ones(cs)), dev(np.zeros(cs)), dev(np.zeros(cs)))
         assert e.value.name == "VOF_ERR_UNSUPPORTED"
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    """A bounded device wait that runs out (a barrier nothing completes) sets
+    the device error flag and becomes VOF_ERR_TIMEOUT, without a fault or a
+    hang; the same context then steps normally."""
+    case = I.rising_swarm(32, 32, 32, nbub=1, d_cells=8, seed=101, steps=1)
+    with vd.VofContext(case.grid, case.phys, vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-9)) as C:
+        with pytest.raises(vd.VofError) as ei:
+            C.diag_wait_timeout()
+        assert ei.value.name == "VOF_ERR_TIMEOUT"
+        T = [dev(a) for a in case.state()]
+        rep = C.step(*T, case.dt, 0)
+        assert rep["res"] <= 1e-9
