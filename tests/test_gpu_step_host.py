@@ -120,3 +120,28 @@ def test_step_host_rejects_device_tensors():
         T = [dev(a) for a in case.state()]
         with pytest.raises(TypeError):
             C.step_host(*T, case.dt, 0)
+
+
+def test_step_host_copies_stay_inside_the_host_arrays():
+    """Every host array sits inside a larger pinned buffer whose margins hold
+    a canary: the copies in and out read and write exactly the fields."""
+    case = I.rising_swarm(40, 32, 48, nbub=3, d_cells=8, seed=103, steps=2)
+    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-9, max_iter=300)
+    stream = torch.cuda.Stream()
+    ref, _ = _device_steps(case, sv, stream, range(2))
+    guard, canary = 4096, -12345.6789
+    bigs, views = [], []
+    for a in case.state():
+        big = torch.full((a.size + 2 * guard,), canary, dtype=torch.float64).pin_memory()
+        big[guard:guard + a.size] = torch.from_numpy(np.ascontiguousarray(a).ravel())
+        bigs.append(big)
+        views.append(big[guard:guard + a.size].view(a.shape))
+    with torch.cuda.stream(stream):
+        with vd.VofContext(case.grid, case.phys, sv, stream=stream) as C:
+            for s in range(2):
+                C.step_host(*views, case.dt, s, report=False)
+            C.host_join()
+            stream.synchronize()
+    for big, view, r in zip(bigs, views, ref):
+        assert bool((big[:guard] == canary).all()) and bool((big[-guard:] == canary).all())
+        assert np.array_equal(view.numpy(), r)
