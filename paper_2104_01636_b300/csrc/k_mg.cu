@@ -14,6 +14,8 @@
 // coarsest levels fall back to Jacobi-preconditioned CG in one thread block.
 #include <algorithm>
 
+#include <initializer_list>
+
 #include "mg_cell.cuh"
 #include "vof_internal.cuh"
 
@@ -555,6 +557,58 @@ __global__ void k_p_update32(int n, float* __restrict__ p, const float* __restri
         p[c] = z[c] + be * p[c];
 }
 
+// the same with 16-byte loads and stores (n4 = n / 4, 16-byte aligned arrays)
+__global__ void k_p_update32x4(int n4, float4* __restrict__ p, const float4* __restrict__ z,
+                               const double* __restrict__ scal) {
+    const float be = (float)scal[S_BETA];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
+        const float4 zv = z[c];
+        float4 pv = p[c];
+        pv.x = zv.x + be * pv.x;
+        pv.y = zv.y + be * pv.y;
+        pv.z = zv.z + be * pv.z;
+        pv.w = zv.w + be * pv.w;
+        p[c] = pv;
+    }
+}
+
+// k_cg_update32 with 16-byte loads and stores; each thread's (r, r) terms
+// are summed four at a time, in order
+__global__ void k_cg_update32x4(int n4, float4* __restrict__ e, float4* __restrict__ r,
+                                const float4* __restrict__ p, const float4* __restrict__ q,
+                                const double* __restrict__ scal, double* __restrict__ part) {
+    const float al = (float)scal[S_ALPHA];
+    Kahan ks;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
+        const float4 pv = p[c], qv = q[c];
+        float4 ev = e[c], rv = r[c];
+        ev.x += al * pv.x;
+        ev.y += al * pv.y;
+        ev.z += al * pv.z;
+        ev.w += al * pv.w;
+        rv.x = rv.x - al * qv.x;
+        rv.y = rv.y - al * qv.y;
+        rv.z = rv.z - al * qv.z;
+        rv.w = rv.w - al * qv.w;
+        e[c] = ev;
+        r[c] = rv;
+        ks.add(rv.x * rv.x);
+        ks.add(rv.y * rv.y);
+        ks.add(rv.z * rv.z);
+        ks.add(rv.w * rv.w);
+    }
+    const double acc = block_sum(ks.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// 16-byte vector access is possible: n a multiple of 4, every array aligned
+inline bool vec4_ok(int n, std::initializer_list<const void*> ptrs) {
+    if (n % 4) return false;
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16) return false;
+    return true;
+}
+
 // x64 += e32 (the outer FP64 update of the defect correction)
 __global__ void k_add_f32_to_f64(int n, const float* __restrict__ e, double* __restrict__ x) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
@@ -748,10 +802,15 @@ void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
 
 int k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const float* q, int slot,
                   bool finalize) {
-    const int nb = flat_blocks(n);
+    const bool v4 = vec4_ok(n, {e, r, p, q});
+    const int nb = flat_blocks(v4 ? n / 4 : n);
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
-               c->part + (size_t)slot * MAX_PARTIALS);
+    if (v4)
+        VOF_LAUNCH(c, k_cg_update32x4, nb, 256, n / 4, (float4*)e, (float4*)r, (const float4*)p,
+                   (const float4*)q, c->scal, c->part + (size_t)slot * MAX_PARTIALS);
+    else
+        VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
+                   c->part + (size_t)slot * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
     if (finalize) finalize_sum(c, slot, nb, slot, 1.0);
     return nb;
@@ -768,7 +827,11 @@ void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q)
 
 void k32_p_update(vof_ctx* c, int n, float* p, const float* z) {
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_p_update32, flat_blocks(n), 256, n, p, z, c->scal);
+    if (vec4_ok(n, {p, z}))
+        VOF_LAUNCH(c, k_p_update32x4, flat_blocks(n / 4), 256, n / 4, (float4*)p,
+                   (const float4*)z, c->scal);
+    else
+        VOF_LAUNCH(c, k_p_update32, flat_blocks(n), 256, n, p, z, c->scal);
     timer_end(c, T_KRYLOV, m);
 }
 
