@@ -10,6 +10,8 @@
 // Krylov updates are FP64 in every precision mode.
 #include <cuda_fp16.h>
 
+#include <initializer_list>
+
 #include "vof_internal.cuh"
 
 namespace {
@@ -233,6 +235,99 @@ __global__ void k_p_update(int n, double* __restrict__ p, const double* __restri
         p[c] = z[c] + be * p[c];
 }
 
+// the flat kernels above with 16-byte accesses, two values per thread and
+// pass (n2 = n / 2; arrays 16-byte aligned); a thread's terms are summed in
+// index order
+__global__ void k_dot_x2(int n2, const double2* __restrict__ x, const double2* __restrict__ y,
+                         double* __restrict__ part) {
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        const double2 a = x[c], b = y[c];
+        acc += a.x * b.x;
+        acc += a.y * b.y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_x2(int n2, const double2* __restrict__ x, double* __restrict__ part) {
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        const double2 a = x[c];
+        acc += a.x;
+        acc += a.y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sub_scalar_x2(int n2, double2* __restrict__ x, const double* __restrict__ s) {
+    const double m = *s;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        double2 a = x[c];
+        a.x -= m;
+        a.y -= m;
+        x[c] = a;
+    }
+}
+
+__global__ void k_copy_x2(int n2, double2* __restrict__ dst, const double2* __restrict__ src) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x)
+        dst[c] = src[c];
+}
+
+__global__ void k_cg_update_x2(int n2, double2* __restrict__ x, double2* __restrict__ r,
+                               const double2* __restrict__ p, const double2* __restrict__ q,
+                               const double* __restrict__ scal, double* __restrict__ part) {
+    const double al = scal[S_ALPHA];
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        const double2 pv = p[c], qv = q[c];
+        double2 xv = x[c], rv = r[c];
+        xv.x += al * pv.x;
+        xv.y += al * pv.y;
+        rv.x = rv.x - al * qv.x;
+        rv.y = rv.y - al * qv.y;
+        x[c] = xv;
+        r[c] = rv;
+        acc += rv.x * rv.x;
+        acc += rv.y * rv.y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_dot2_x2(int n2, const double2* __restrict__ z, const double2* __restrict__ r,
+                          const double2* __restrict__ q, double* __restrict__ pa,
+                          double* __restrict__ pb) {
+    double a = 0.0, b = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        const double2 zv = z[c], rv = r[c], qv = q[c];
+        a += zv.x * rv.x;
+        a += zv.y * rv.y;
+        b += zv.x * qv.x;
+        b += zv.y * qv.y;
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_p_update_x2(int n2, double2* __restrict__ p, const double2* __restrict__ z,
+                              const double* __restrict__ scal) {
+    const double be = scal[S_BETA];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += gridDim.x * blockDim.x) {
+        const double2 zv = z[c];
+        double2 pv = p[c];
+        pv.x = zv.x + be * pv.x;
+        pv.y = zv.y + be * pv.y;
+        p[c] = pv;
+    }
+}
+
 __global__ void k_scalar_alpha(double* scal) {
     const double pq = scal[S_PQ];
     scal[S_ALPHA] = pq > 0.0 ? scal[S_RZ] / pq : 0.0;
@@ -295,21 +390,47 @@ void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r
     finalize_sum(c, slot, l.L.nblocks, slot, 1.0);
 }
 
+// 16-byte accesses are possible: n even, every array 16-byte aligned
+inline bool vec2_ok(int n, std::initializer_list<const void*> ptrs) {
+    if (n % 2) return false;
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16) return false;
+    return true;
+}
+
 void launch_dot(vof_ctx* c, const double* x, const double* y, int n, int slot) {
-    const int nb = flat_blocks(n);
-    VOF_LAUNCH(c, k_dot, nb, FLAT_THREADS, n, x, y, c->part + (size_t)slot * MAX_PARTIALS);
+    double* part = c->part + (size_t)slot * MAX_PARTIALS;
+    const bool v2 = vec2_ok(n, {x, y});
+    const int nb = flat_blocks(v2 ? n / 2 : n);
+    if (v2)
+        VOF_LAUNCH(c, k_dot_x2, nb, FLAT_THREADS, n / 2, (const double2*)x, (const double2*)y,
+                   part);
+    else
+        VOF_LAUNCH(c, k_dot, nb, FLAT_THREADS, n, x, y, part);
     finalize_sum(c, slot, nb, slot, 1.0);
 }
 
 void launch_sub_mean(vof_ctx* c, double* x, int n, int slot_mean) {
-    const int nb = flat_blocks(n);
-    VOF_LAUNCH(c, k_sum, nb, FLAT_THREADS, n, x, c->part + (size_t)slot_mean * MAX_PARTIALS);
+    double* part = c->part + (size_t)slot_mean * MAX_PARTIALS;
+    const bool v2 = vec2_ok(n, {x});
+    const int nb = flat_blocks(v2 ? n / 2 : n);
+    if (v2)
+        VOF_LAUNCH(c, k_sum_x2, nb, FLAT_THREADS, n / 2, (const double2*)x, part);
+    else
+        VOF_LAUNCH(c, k_sum, nb, FLAT_THREADS, n, x, part);
     finalize_sum(c, slot_mean, nb, slot_mean, 1.0 / (double)n);
-    VOF_LAUNCH(c, k_sub_scalar, nb, FLAT_THREADS, n, x, c->scal + slot_mean);
+    if (v2)
+        VOF_LAUNCH(c, k_sub_scalar_x2, nb, FLAT_THREADS, n / 2, (double2*)x, c->scal + slot_mean);
+    else
+        VOF_LAUNCH(c, k_sub_scalar, nb, FLAT_THREADS, n, x, c->scal + slot_mean);
 }
 
 void launch_copy(vof_ctx* c, double* dst, const double* src, int n) {
-    VOF_LAUNCH(c, k_copy, flat_blocks(n), FLAT_THREADS, n, dst, src);
+    if (vec2_ok(n, {dst, src}))
+        VOF_LAUNCH(c, k_copy_x2, flat_blocks(n / 2), FLAT_THREADS, n / 2, (double2*)dst,
+                   (const double2*)src);
+    else
+        VOF_LAUNCH(c, k_copy, flat_blocks(n), FLAT_THREADS, n, dst, src);
 }
 
 void launch_zero(vof_ctx* c, double* x, int n) {
@@ -318,20 +439,32 @@ void launch_zero(vof_ctx* c, double* x, int n) {
 
 void launch_cg_update(vof_ctx* c, int n, double* x, double* r, const double* p, const double* q,
                       int slot) {
-    const int nb = flat_blocks(n);
+    const bool v2 = vec2_ok(n, {x, r, p, q});
+    const int nb = flat_blocks(v2 ? n / 2 : n);
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_cg_update, nb, FLAT_THREADS, n, x, r, p, q, c->scal,
-                                                c->part + (size_t)slot * MAX_PARTIALS);
+    if (v2)
+        VOF_LAUNCH(c, k_cg_update_x2, nb, FLAT_THREADS, n / 2, (double2*)x, (double2*)r,
+                   (const double2*)p, (const double2*)q, c->scal,
+                   c->part + (size_t)slot * MAX_PARTIALS);
+    else
+        VOF_LAUNCH(c, k_cg_update, nb, FLAT_THREADS, n, x, r, p, q, c->scal,
+                   c->part + (size_t)slot * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
     finalize_sum(c, slot, nb, slot, 1.0);
 }
 
 void launch_dot2(vof_ctx* c, int n, const double* z, const double* r, const double* q, int sa,
                  int sb) {
-    const int nb = flat_blocks(n);
+    const bool v2 = vec2_ok(n, {z, r, q});
+    const int nb = flat_blocks(v2 ? n / 2 : n);
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_dot2, nb, FLAT_THREADS, n, z, r, q, c->part + (size_t)sa * MAX_PARTIALS,
-                                           c->part + (size_t)sb * MAX_PARTIALS);
+    if (v2)
+        VOF_LAUNCH(c, k_dot2_x2, nb, FLAT_THREADS, n / 2, (const double2*)z, (const double2*)r,
+                   (const double2*)q, c->part + (size_t)sa * MAX_PARTIALS,
+                   c->part + (size_t)sb * MAX_PARTIALS);
+    else
+        VOF_LAUNCH(c, k_dot2, nb, FLAT_THREADS, n, z, r, q, c->part + (size_t)sa * MAX_PARTIALS,
+                   c->part + (size_t)sb * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
     finalize_sum(c, sa, nb, sa, 1.0);
     finalize_sum(c, sb, nb, sb, 1.0);
@@ -339,7 +472,11 @@ void launch_dot2(vof_ctx* c, int n, const double* z, const double* r, const doub
 
 void launch_p_update(vof_ctx* c, int n, double* p, const double* z) {
     int m = timer_begin(c, T_KRYLOV);
-    VOF_LAUNCH(c, k_p_update, flat_blocks(n), FLAT_THREADS, n, p, z, c->scal);
+    if (vec2_ok(n, {p, z}))
+        VOF_LAUNCH(c, k_p_update_x2, flat_blocks(n / 2), FLAT_THREADS, n / 2, (double2*)p,
+                   (const double2*)z, c->scal);
+    else
+        VOF_LAUNCH(c, k_p_update, flat_blocks(n), FLAT_THREADS, n, p, z, c->scal);
     timer_end(c, T_KRYLOV, m);
 }
 
