@@ -120,6 +120,24 @@ __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __res
         xf[cid(df, i, j, k)] += omega * xc[cid(dc, i >> 1, j >> 1, k >> 1)];
 }
 
+// The same for a fine level with an even nx: a thread adds the correction
+// of parent I to the fine pair (2I, 2I+1) with one 8-byte load and store.
+__global__ void k_prolong_pair_f(Dims dc, const float* __restrict__ xc, Dims df,
+                                 float* __restrict__ xf, float omega, int kchunk) {
+    pdl_wait();
+    const int I = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    if (2 * I >= df.nx || j >= df.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
+    for (int k = k0; k < k1; ++k) {
+        const float cv = xc[cid(dc, I, j >> 1, k >> 1)];
+        float2* p = reinterpret_cast<float2*>(xf + cid(df, 2 * I, j, k));
+        float2 v = *p;
+        v.x += omega * cv;
+        v.y += omega * cv;
+        *p = v;
+    }
+}
+
 // Cell-centred trilinear prolongation along one axis: the fine cell 2I
 // takes 3/4 of coarse I and 1/4 of I-1, the fine cell 2I+1 3/4 of I and 1/4
 // of I+1; across a wall the outside share goes to the parent (constant
@@ -731,6 +749,9 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
     if (c->sv.mg_interp == VOF_MG_TRILINEAR)
         VOF_LAUNCH(c, k_prolong_tri_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega,
                    F.L.kchunk);
+    else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
+        launch_pdl(c, k_prolong_pair_f, dim3((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, F.L.grid.z),
+                   F.L.block, C.d, (const float*)a.x, F.d, (float*)b.x, (float)omega, F.L.kchunk);
     else
         launch_pdl(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
     timer_end(c, cls, m);

@@ -418,27 +418,42 @@ __global__ void k_restrict_rho(Dims df, float ih2, const __half* __restrict__ rh
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
-    const int sx = 1, sy = df.nx;
+    const int sy = df.nx;
     const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
+    // the two children of a row (a = 0, 1) are adjacent in x: their x, f and
+    // density, and those of their neighbours above, below and across in y,
+    // come as pairs (8 and 4 bytes; 2I is even and so is nx)
+    auto x2 = [&](int c) { return *reinterpret_cast<const float2*>(xf + c); };
+    auto r2 = [&](int c) { return __half22float2(*reinterpret_cast<const __half2*>(rho + c)); };
     for (int K = k0; K < k1; ++K) {
         float fs = 0.f, flux = 0.f;
         const int kk[2] = {2 * K, 2 * K + 1};
         const int kout[2] = {wrapk(2 * K - 1, df.nz), wrapk(2 * K + 2, df.nz)};
 #pragma unroll
-        for (int c3 = 0; c3 < 8; ++c3) {
-            const int a = c3 & 1, b = (c3 >> 1) & 1, e = c3 >> 2;
-            const int c = cid(df, 2 * I + a, 2 * J + b, kk[e]);
-            const float xc = xf[c], rc = __half2float(rho[c]);
-            fs += ff[c];
-            // boundary faces of this child: the outer side in x, y and z
-            const int ox = a ? sx : -sx, oy = b ? sy : -sy;
-            if (a ? xh : xl)
-                flux = fmaf(beta_rho(rc, __half2float(rho[c + ox])), xc - xf[c + ox], flux);
-            if (b ? yh : yl)
-                flux = fmaf(beta_rho(rc, __half2float(rho[c + oy])), xc - xf[c + oy], flux);
-            const int cz = cid(df, 2 * I + a, 2 * J + b, kout[e]);
-            flux = fmaf(beta_rho(rc, __half2float(rho[cz])), xc - xf[cz], flux);
-        }
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int c = cid(df, 2 * I, 2 * J + b, kk[e]);  // the row's child a = 0
+                const int oy = b ? sy : -sy;
+                const int cz = cid(df, 2 * I, 2 * J + b, kout[e]);
+                const float2 xc = x2(c), rc = r2(c), fc2 = *reinterpret_cast<const float2*>(ff + c);
+                const bool hy = b ? yh : yl;
+                const float2 xy = hy ? x2(c + oy) : make_float2(0.f, 0.f);
+                const float2 ry = hy ? r2(c + oy) : make_float2(0.f, 0.f);
+                const float2 xz = x2(cz), rz = r2(cz);
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    // the child's boundary faces: the outer side in x, y and z
+                    const float xv = a ? xc.y : xc.x, rv = a ? rc.y : rc.x;
+                    fs += a ? fc2.y : fc2.x;
+                    const int cx = a ? c + 2 : c - 1;  // its x neighbour outside the block
+                    if (a ? xh : xl)
+                        flux = fmaf(beta_rho(rv, __half2float(rho[cx])), xv - xf[cx], flux);
+                    if (hy)
+                        flux = fmaf(beta_rho(rv, a ? ry.y : ry.x), xv - (a ? xy.y : xy.x), flux);
+                    flux = fmaf(beta_rho(rv, a ? rz.y : rz.x), xv - (a ? xz.y : xz.x), flux);
+                }
+            }
         fc[cid(dc, I, J, K)] = 0.125f * (fs - flux * ih2);
     }
 }
