@@ -545,6 +545,75 @@ __global__ void k_wait_probe(double* __restrict__ err, int limit) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) *err = 1.0;
 }
 
+// The same operator on x-pairs: a thread owns cells (2t, 2t+1) of its row
+// and walks up its z chunk carrying the pair's plane below; p and the density
+// of the pair, of the pairs across in y and of the pair above come as 8-byte
+// loads, the two outer x neighbours as scalars. Each cell's stencil is
+// summed in the order of k_apply_A_dot_rho32; the thread's partial of p.q
+// takes the pair's two cells in turn.
+__global__ void k_apply_A_dot_rho32_pair(Dims d, float ih2, const float* __restrict__ rho,
+                                         const float* __restrict__ p, float* __restrict__ q,
+                                         double* __restrict__ part, int kchunk) {
+    const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
+    const int i = 2 * t;
+    const bool act = i < d.nx && j < d.ny;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    Kahan32 ks;
+    if (act && k0 < k1) {
+        auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
+        const bool hw = i > 0, he = i + 2 < d.nx, hs = j > 0, hn = j + 1 < d.ny;
+        int c = cid(d, i, j, k0);
+        const int cb0 = cid(d, i, j, wrapk(k0 - 1, d.nz));
+        float2 rc = ld2(rho, c), pc = ld2(p, c);
+        const float2 rb = ld2(rho, cb0), pb = ld2(p, cb0);
+        float2 bzm = make_float2(beta_rho(rc.x, rb.x), beta_rho(rc.y, rb.y));
+        float2 pm = pb;
+        for (int k = k0; k < k1; ++k) {
+            const int ct = cid(d, i, j, wrapk(k + 1, d.nz));
+            const float2 rt = ld2(rho, ct), pt = ld2(p, ct);
+            // x: the pair's inner face, and one outer face on either side
+            const float rw = hw ? rho[c - 1] : 0.f, pw = hw ? p[c - 1] : 0.f;
+            const float re = he ? rho[c + 2] : 0.f, pe = he ? p[c + 2] : 0.f;
+            const float bin = beta_rho(rc.x, rc.y);
+            const float bxm0 = hw ? beta_rho(rc.x, rw) : 0.f;
+            const float bxp1 = he ? beta_rho(rc.y, re) : 0.f;
+            const float2 rs = hs ? ld2(rho, c - d.nx) : rc, ps = hs ? ld2(p, c - d.nx) : pc;
+            const float2 rn = hn ? ld2(rho, c + d.nx) : rc, pn = hn ? ld2(p, c + d.nx) : pc;
+            const float2 bym = hs ? make_float2(beta_rho(rc.x, rs.x), beta_rho(rc.y, rs.y))
+                                  : make_float2(0.f, 0.f);
+            const float2 byp = hn ? make_float2(beta_rho(rc.x, rn.x), beta_rho(rc.y, rn.y))
+                                  : make_float2(0.f, 0.f);
+            const float2 bzp = make_float2(beta_rho(rc.x, rt.x), beta_rho(rc.y, rt.y));
+            // cell 2t: west neighbour outside the pair, east the pair's other cell
+            float s0 = bxm0 * (pc.x - (hw ? pw : pc.x));
+            s0 = fmaf(bin, pc.x - pc.y, s0);
+            s0 = fmaf(bym.x, pc.x - ps.x, s0);
+            s0 = fmaf(byp.x, pc.x - pn.x, s0);
+            s0 = fmaf(bzm.x, pc.x - pm.x, s0);
+            s0 = fmaf(bzp.x, pc.x - pt.x, s0);
+            // cell 2t+1: west the pair's other cell, east neighbour outside
+            float s1 = bin * (pc.y - pc.x);
+            s1 = fmaf(bxp1, pc.y - (he ? pe : pc.y), s1);
+            s1 = fmaf(bym.y, pc.y - ps.y, s1);
+            s1 = fmaf(byp.y, pc.y - pn.y, s1);
+            s1 = fmaf(bzm.y, pc.y - pm.y, s1);
+            s1 = fmaf(bzp.y, pc.y - pt.y, s1);
+            const float v0 = s0 * ih2, v1 = s1 * ih2;
+            *reinterpret_cast<float2*>(q + c) = make_float2(v0, v1);
+            ks.add(pc.x * v0);
+            ks.add(pc.y * v1);
+            // move up one plane
+            bzm = bzp;
+            pm = pc;
+            rc = rt;
+            pc = pt;
+            c = ct;
+        }
+    }
+    const double acc = block_sum(ks.value());
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+}
+
 // ---- tensor maps -------------------------------------------------------------
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -662,8 +731,10 @@ void rho_restrict(vof_ctx* c) {
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     const Level& L = c->lv[0];
     int m = timer_begin(c, T_RESIDUAL);
-    VOF_LAUNCH(c, k_apply_A_dot_rho32, L.L.grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
+    // x-pairs (the density path has nx % 8 == 0)
+    const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
+    VOF_LAUNCH(c, k_apply_A_dot_rho32_pair, grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
                c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
-    finalize_pq_alpha(c, L.L.nblocks);
+    finalize_pq_alpha(c, (int)(grid.x * grid.y * grid.z));
 }
