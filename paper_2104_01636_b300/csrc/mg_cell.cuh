@@ -18,25 +18,8 @@ struct LdL2 {
     __device__ __forceinline__ double operator()(const double* p) const { return __ldcg(p); }
 };
 
-// The red-black Gauss-Seidel update of one cell from its right side, its six
-// face coefficients and its six neighbour values (0 across a wall):
-//   x_c = (h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f,
-// ZERO: from a zero x (neighbours ignored). Every coarse-level smoother
-// (colour passes, fused sweeps, the cluster tail) evaluates this one
-// expression, so they produce the same bits.
-template <class T, bool ZERO>
-__device__ __forceinline__ T rbgs_update(T h2, T fc, T b0, T b1, T b2, T b3, T b4, T b5, T x0,
-                                         T x1, T x2, T x3, T x4, T x5) {
-    T num;
-    if (ZERO)
-        num = h2 * fc;
-    else
-        num = h2 * fc + b0 * x0 + b1 * x1 + b2 * x2 + b3 * x3 + b4 * x4 + b5 * x5;
-    const T den = b0 + b1 + b2 + b3 + b4 + b5;
-    return den > T(0) ? num / den : T(0);
-}
-
-// Red-black Gauss-Seidel update of cell (i, j, k) on one level (rbgs_update).
+// Red-black Gauss-Seidel update of cell (i, j, k) on one level:
+//   x_c = (h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f.
 // Across a wall (beta = 0) the neighbour counts as 0 and is not read.
 // MODE 1: x is zero (first pass from a zero guess), neighbours are not read.
 // MODE 2: each neighbour is read as x + omega x_coarse(parent): the first
@@ -59,24 +42,23 @@ __device__ __forceinline__ void rbgs_cell(const Dims& d, T h2, const T* __restri
     const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
     const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
     const bool hw = i > 0, he = i < d.nx - 1, hs = j > 0, hn = j < d.ny - 1;
-    const T fc = ld(f + c);
+    T num;
     if (MODE == 1) {
-        xw[c] = rbgs_update<T, true>(h2, fc, b0, b1, b2, b3, b4, b5, T(0), T(0), T(0), T(0), T(0),
-                                     T(0));
+        num = h2 * ld(f + c);
     } else if (MODE == 2) {
         auto xv = [&](int cc, int ii, int jj, int kk) {
             return ld(xr + cc) + omega * ld(xc + cid(dc, ii >> 1, jj >> 1, kk >> 1));
         };
-        xw[c] = rbgs_update<T, false>(h2, fc, b0, b1, b2, b3, b4, b5,
-                                      hw ? xv(cw, iw, j, k) : T(0), he ? xv(ce, ie, j, k) : T(0),
-                                      hs ? xv(cs, i, js, k) : T(0), hn ? xv(cn, i, jn, k) : T(0),
-                                      xv(cb, i, j, km), xv(ct, i, j, kp));
+        num = h2 * ld(f + c) + b0 * (hw ? xv(cw, iw, j, k) : T(0)) +
+              b1 * (he ? xv(ce, ie, j, k) : T(0)) + b2 * (hs ? xv(cs, i, js, k) : T(0)) +
+              b3 * (hn ? xv(cn, i, jn, k) : T(0)) + b4 * xv(cb, i, j, km) + b5 * xv(ct, i, j, kp);
     } else {
-        xw[c] = rbgs_update<T, false>(h2, fc, b0, b1, b2, b3, b4, b5,
-                                      hw ? ld(xr + cw) : T(0), he ? ld(xr + ce) : T(0),
-                                      hs ? ld(xr + cs) : T(0), hn ? ld(xr + cn) : T(0),
-                                      ld(xr + cb), ld(xr + ct));
+        num = h2 * ld(f + c) + b0 * (hw ? ld(xr + cw) : T(0)) + b1 * (he ? ld(xr + ce) : T(0)) +
+              b2 * (hs ? ld(xr + cs) : T(0)) + b3 * (hn ? ld(xr + cn) : T(0)) + b4 * ld(xr + cb) +
+              b5 * ld(xr + ct);
     }
+    const T den = b0 + b1 + b2 + b3 + b4 + b5;
+    xw[c] = den > T(0) ? num / den : T(0);
 }
 
 // Restriction of the residual to coarse cell (I, J, K): the mean of the 8
