@@ -715,10 +715,14 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
     const Dims dc = C ? C->d : L.d;
     const T* xc = C ? arrays<T>(*C).x : nullptr;
     const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
-    const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
+    // a thread per x-pair halves the blocks of the level's cell geometry:
+    // halve the z chunks to keep about as many blocks in flight
+    const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
+    const int kchunk = std::max(1, (L.L.kchunk + 1) / 2);
+    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
     int m = timer_begin(c, cls);
     launch_pdl(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
-               a.x, a.f, color, L.L.kchunk, dc, xc, omega);
+               a.x, a.f, color, kchunk, dc, xc, omega);
     timer_end(c, cls, m);
 }
 
