@@ -718,7 +718,7 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
     // a thread per x-pair halves the blocks of the level's cell geometry:
     // halve the z chunks to keep about as many blocks in flight
     const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
-    const int kchunk = std::max(1, (L.L.kchunk + 1) / 2);
+    const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
     const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
     int m = timer_begin(c, cls);
     launch_pdl(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
