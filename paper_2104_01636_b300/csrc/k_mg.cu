@@ -753,9 +753,12 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
     if (c->sv.mg_interp == VOF_MG_TRILINEAR)
         VOF_LAUNCH(c, k_prolong_tri_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega,
                    F.L.kchunk);
-    else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
-        launch_pdl(c, k_prolong_pair_f, dim3((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, F.L.grid.z),
-                   F.L.block, C.d, (const float*)a.x, F.d, (float*)b.x, (float)omega, F.L.kchunk);
+    else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
+        const int kchunk = std::max(1, (F.L.kchunk + 1) / 2);  // half the blocks across
+        launch_pdl(c, k_prolong_pair_f,
+                   dim3((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, (F.d.nz + kchunk - 1) / kchunk),
+                   F.L.block, C.d, (const float*)a.x, F.d, (float*)b.x, (float)omega, kchunk);
+    }
     else
         launch_pdl(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
     timer_end(c, cls, m);

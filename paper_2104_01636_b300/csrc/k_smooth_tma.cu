@@ -731,10 +731,14 @@ void rho_restrict(vof_ctx* c) {
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     const Level& L = c->lv[0];
     int m = timer_begin(c, T_RESIDUAL);
-    // x-pairs (the density path has nx % 8 == 0)
-    const dim3 grid((L.d.nx / 2 + TBX - 1) / TBX, L.L.grid.y, L.L.grid.z);
+    // x-pairs (the density path has nx % 8 == 0): half the blocks across,
+    // so twice the z chunks
+    const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
+    int kchunk = std::max(1, (L.L.kchunk + 1) / 2);
+    if ((long)gx * L.L.grid.y * ((L.d.nz + kchunk - 1) / kchunk) > MAX_PARTIALS) kchunk = L.L.kchunk;
+    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
     VOF_LAUNCH(c, k_apply_A_dot_rho32_pair, grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
-               c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, L.L.kchunk);
+               c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, kchunk);
     timer_end(c, T_RESIDUAL, m);
     finalize_pq_alpha(c, (int)(grid.x * grid.y * grid.z));
 }
