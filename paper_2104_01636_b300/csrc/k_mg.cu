@@ -109,6 +109,50 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
         restrict_cell(df, ih2f, bx, by, bz, xf, ff, dc, fc, I, J, K, LdPlain());
 }
 
+// restrict_cell in FP32 with the children of a row loaded as pairs: the
+// two children of a row (2I, 2I+1) are adjacent, and so are their right
+// sides, their y and z faces and their neighbours across in y and z
+// (8-byte loads; 2I and nx are even). Same terms in the same order.
+__global__ void k_restrict_pair_f(Dims df, float ih2f, const float* __restrict__ bx,
+                                  const float* __restrict__ by, const float* __restrict__ bz,
+                                  const float* __restrict__ xf, const float* __restrict__ ff,
+                                  Dims dc, float* __restrict__ fc, int kchunk) {
+    pdl_wait();
+    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
+    auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
+    for (int K = k0; K < k1; ++K) {
+        float fs = 0.f, flux = 0.f;
+        const int kk[2] = {2 * K, 2 * K + 1};
+        const int kout[2] = {wrapk(2 * K - 1, df.nz), wrapk(2 * K + 2, df.nz)};
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int j = 2 * J + b, k = kk[e];
+                const int c = cid(df, 2 * I, j, k);
+                const float2 xc = ld2(xf, c), f2 = ld2(ff, c);
+                const bool hy = b ? yh : yl;
+                const float2 byf = ld2(by, vid(df, 2 * I, j + b, k));
+                const float2 xy = hy ? ld2(xf, b ? c + df.nx : c - df.nx) : make_float2(0.f, 0.f);
+                const float2 bzf = ld2(bz, wid(df, 2 * I, j, e ? kout[1] : k));
+                const float2 xz = ld2(xf, cid(df, 2 * I, j, kout[e]));
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const float xv = a ? xc.y : xc.x;
+                    fs += a ? f2.y : f2.x;
+                    if (a ? xh : xl)
+                        flux += bx[uid(df, 2 * I + a + a, j, k)] * (xv - xf[a ? c + 2 : c - 1]);
+                    if (hy) flux += (a ? byf.y : byf.x) * (xv - (a ? xy.y : xy.x));
+                    flux += (a ? bzf.y : bzf.x) * (xv - (a ? xz.y : xz.x));
+                }
+            }
+        fc[cid(dc, I, J, K)] = 0.125f * (fs - flux * ih2f);
+    }
+}
+
 template <class T>
 __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __restrict__ xf,
                             T omega, int kchunk) {
@@ -738,8 +782,13 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
         VOF_LAUNCH(c, k_restrict_fw_t<T>, C.L.grid, C.L.block, F.d, (const T*)r, C.d, b.f,
                    C.L.kchunk);
     } else {
-        launch_pdl(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)), a.bx,
-                   a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
+        if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
+            launch_pdl(c, k_restrict_pair_f, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)),
+                       (const float*)a.bx, (const float*)a.by, (const float*)a.bz,
+                       (const float*)a.x, (const float*)a.f, C.d, (float*)b.f, C.L.kchunk);
+        else
+            launch_pdl(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)),
+                       a.bx, a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
     }
     timer_end(c, cls, m);
 }
