@@ -38,8 +38,10 @@ __global__ void k_curv_list(Dims d, const double* __restrict__ a, double* __rest
         bool itf = false;
         if (act) {
             c = cid(d, i, j, k);
-            const double ac = a[c];
-            itf = ac > EPS_IF && ac < 1.0 - EPS_IF;
+            // eps < alpha < 1 - eps on the integer pipe (bit-pattern order of
+            // doubles >= +0; a negative alpha compares below eps)
+            const long long ab = __double_as_longlong(a[c]);
+            itf = ab > __double_as_longlong(EPS_IF) && ab < __double_as_longlong(1.0 - EPS_IF);
             kappa[c] = 0.0;
             valid[c] = 0;
         }

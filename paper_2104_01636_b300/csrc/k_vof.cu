@@ -34,8 +34,11 @@ __global__ void k_if_list(Dims d, const double* __restrict__ a, unsigned char* _
         bool itf = false;
         if (act) {
             c = cid(d, i, j, k);
-            const double ac = a[c];
-            itf = ac > EPS_IF && ac < 1.0 - EPS_IF;
+            // eps < alpha < 1 - eps on the integer pipe: for doubles >= +0
+            // the order of the bit patterns is the order of the values, and
+            // a negative alpha (sign bit set) compares below eps
+            const long long ab = __double_as_longlong(a[c]);
+            itf = ab > __double_as_longlong(EPS_IF) && ab < __double_as_longlong(1.0 - EPS_IF);
             has[c] = 0;
         }
         const unsigned m = __ballot_sync(0xffffffffu, itf);
@@ -212,8 +215,11 @@ __global__ void k_mask_volume(Dims d, const double* __restrict__ a, unsigned cha
     if (act)
         for (int k = k0; k < k1; ++k) {
             const int c = cid(d, i, j, k);
-            s += a[c];
-            if (cm) cm[c] = a[c] > 0.5;
+            const double ac = a[c];
+            s += ac;
+            // alpha > 1/2 on the integer pipe (bit-pattern order of doubles >= +0;
+            // a negative alpha has the sign bit and compares below)
+            if (cm) cm[c] = __double_as_longlong(ac) > __double_as_longlong(0.5);
         }
     s = block_sum(s);
     if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = s;
@@ -226,14 +232,18 @@ __global__ void k_cfl(Geo g, const double* __restrict__ u, const double* __restr
     const Dims& d = g.d;
     const bool act = i < d.nx && j < d.ny;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
-    double m = 0.0;
+    // the largest magnitude on the integer pipe: with the sign bit cleared,
+    // the order of the bit patterns is the order of the values
+    constexpr long long MAG = 0x7FFFFFFFFFFFFFFFLL;
+    auto mag = [](double x) { return __double_as_longlong(x) & MAG; };
+    long long mb = 0;
     if (act)
         for (int k = k0; k < k1; ++k) {
-            if (i > 0 || g.per_x) m = fmax(m, fabs(u[uid(d, i, j, k)]));
-            if (j > 0 || g.per_y) m = fmax(m, fabs(v[vid(d, i, j, k)]));
-            m = fmax(m, fabs(w[wid(d, i, j, k)]));
+            if (i > 0 || g.per_x) mb = max(mb, mag(u[uid(d, i, j, k)]));
+            if (j > 0 || g.per_y) mb = max(mb, mag(v[vid(d, i, j, k)]));
+            mb = max(mb, mag(w[wid(d, i, j, k)]));
         }
-    m = block_max(m);
+    const double m = block_max(__longlong_as_double(mb));
     if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = m;
 }
 
