@@ -126,8 +126,12 @@ __device__ double face_force(const SsfArgs& A, int dir, int i, int j, int k, int
     int r[3] = {i, j, k};
     r[dir] += 1;
     const int cL = cid(d, i, j, wrapk(k, d.nz)), cR = cid(d, r[0], r[1], wrapk(r[2], d.nz));
-    const double GL = A.a[cL] < 0.5 ? 1.0 : 0.0, GR = A.a[cR] < 0.5 ? 1.0 : 0.0;
-    if (GL == GR) return 0.0;
+    // G = [alpha < 1/2] on the integer pipe: for doubles >= +0 the order of
+    // the bit patterns is the order of the values, and a negative alpha (sign
+    // bit set) compares below; most faces end here, with no FP64 operation
+    const long long half = __double_as_longlong(0.5);
+    const bool gL = __double_as_longlong(A.a[cL]) < half, gR = __double_as_longlong(A.a[cR]) < half;
+    if (gL == gR) return 0.0;
     double kf;
     if (A.exact) {
         kf = A.kappa_exact;
@@ -161,7 +165,9 @@ __device__ double face_force(const SsfArgs& A, int dir, int i, int j, int k, int
             kf = cnt ? s / cnt : 0.0;
         }
     }
-    return A.sigma_h * kf * (GR - GL);
+    // (sigma / h) kappa_f (G_R - G_L), G_R - G_L = +-1: a sign, exactly
+    const double f = A.sigma_h * kf;
+    return gR ? f : -f;
 }
 
 __global__ void k_ssf_faces(SsfArgs A, double* __restrict__ sx, double* __restrict__ sy,
