@@ -81,9 +81,11 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
 // of its parent: Gauss-Seidel never reads a cell's own old value, and this
 // pass and the next overwrite every cell, so no separate prolongation pass
 // is needed.
-template <class T, int MODE>
-__global__ void k_rbgs_pair_t(Dims d, T h2, const T* __restrict__ bx, const T* __restrict__ by,
-                              const T* __restrict__ bz, const T* __restrict__ xr,
+// CT is the coefficients' storage type (T, or FP16 copies on a large coarse
+// level of the FP32 cycle).
+template <class T, int MODE, class CT>
+__global__ void k_rbgs_pair_t(Dims d, T h2, const CT* __restrict__ bx, const CT* __restrict__ by,
+                              const CT* __restrict__ bz, const T* __restrict__ xr,
                               T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk,
                               Dims dc, const T* __restrict__ xc, T omega) {
     pdl_wait();
@@ -109,12 +111,23 @@ __global__ void k_restrict_t(Dims df, T ih2f, const T* __restrict__ bx, const T*
         restrict_cell(df, ih2f, bx, by, bz, xf, ff, dc, fc, I, J, K, LdPlain());
 }
 
+// two adjacent coefficients (even index) as FP32
+__device__ __forceinline__ float2 cpair(const float* a, int c) {
+    return *reinterpret_cast<const float2*>(a + c);
+}
+__device__ __forceinline__ float2 cpair(const __half* a, int c) {
+    return __half22float2(*reinterpret_cast<const __half2*>(a + c));
+}
+
 // restrict_cell in FP32 with the children of a row loaded as pairs: the
 // two children of a row (2I, 2I+1) are adjacent, and so are their right
 // sides, their y and z faces and their neighbours across in y and z
 // (8-byte loads; 2I and nx are even). Same terms in the same order.
-__global__ void k_restrict_pair_f(Dims df, float ih2f, const float* __restrict__ bx,
-                                  const float* __restrict__ by, const float* __restrict__ bz,
+// CT: FP32 coefficients, or the level's FP16 copies (the colour passes of
+// the same level read the same copies, so the cycle keeps one operator).
+template <class CT>
+__global__ void k_restrict_pair_f(Dims df, float ih2f, const CT* __restrict__ bx,
+                                  const CT* __restrict__ by, const CT* __restrict__ bz,
                                   const float* __restrict__ xf, const float* __restrict__ ff,
                                   Dims dc, float* __restrict__ fc, int kchunk) {
     pdl_wait();
@@ -123,6 +136,7 @@ __global__ void k_restrict_pair_f(Dims df, float ih2f, const float* __restrict__
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
     const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
+    auto cp2 = [](const CT* a, int c) { return cpair(a, c); };
     for (int K = k0; K < k1; ++K) {
         float fs = 0.f, flux = 0.f;
         const int kk[2] = {2 * K, 2 * K + 1};
@@ -135,16 +149,16 @@ __global__ void k_restrict_pair_f(Dims df, float ih2f, const float* __restrict__
                 const int c = cid(df, 2 * I, j, k);
                 const float2 xc = ld2(xf, c), f2 = ld2(ff, c);
                 const bool hy = b ? yh : yl;
-                const float2 byf = ld2(by, vid(df, 2 * I, j + b, k));
+                const float2 byf = cp2(by, vid(df, 2 * I, j + b, k));
                 const float2 xy = hy ? ld2(xf, b ? c + df.nx : c - df.nx) : make_float2(0.f, 0.f);
-                const float2 bzf = ld2(bz, wid(df, 2 * I, j, e ? kout[1] : k));
+                const float2 bzf = cp2(bz, wid(df, 2 * I, j, e ? kout[1] : k));
                 const float2 xz = ld2(xf, cid(df, 2 * I, j, kout[e]));
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const float xv = a ? xc.y : xc.x;
                     fs += a ? f2.y : f2.x;
                     if (a ? xh : xl)
-                        flux += bx[uid(df, 2 * I + a + a, j, k)] * (xv - xf[a ? c + 2 : c - 1]);
+                        flux += cval(bx[uid(df, 2 * I + a + a, j, k)]) * (xv - xf[a ? c + 2 : c - 1]);
                     if (hy) flux += (a ? byf.y : byf.x) * (xv - (a ? xy.y : xy.x));
                     flux += (a ? bzf.y : bzf.x) * (xv - (a ? xz.y : xz.x));
                 }
@@ -682,6 +696,13 @@ __global__ void k_to_f32(int n, const double* __restrict__ a, float* __restrict_
         b[c] = (float)a[c];
 }
 
+// FP16 copy of FP32 coefficients divided by a power of two (exact before the
+// rounding to FP16)
+__global__ void k_to_f16(int n, const float* __restrict__ a, __half* __restrict__ b, float inv_s) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        b[c] = __float2half_rn(a[c] * inv_s);
+}
+
 __global__ void k_to_f64(int n, const float* __restrict__ a, double* __restrict__ b) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         b[c] = (double)a[c];
@@ -739,6 +760,29 @@ LA<float> arrays<float>(const Level& L) {
 
 }  // namespace
 
+// one colour pass on a level with an even nx, a thread per x-pair; CT is
+// the coefficients' storage type
+template <class T, class CT>
+void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, const CT* bz,
+               const LA<T>& a, int color, int mode, const Level* C, int cls) {
+    using K = void (*)(Dims, T, const CT*, const CT*, const CT*, const T*, T*, const T*, int, int,
+                       Dims, const T*, T);
+    const K kern = mode == 1 ? k_rbgs_pair_t<T, 1, CT>
+                             : (mode == 2 ? k_rbgs_pair_t<T, 2, CT> : k_rbgs_pair_t<T, 0, CT>);
+    const Dims dc = C ? C->d : L.d;
+    const T* xc = C ? arrays<T>(*C).x : nullptr;
+    const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
+    // a thread per x-pair halves the blocks of the level's cell geometry:
+    // halve the z chunks to keep about as many blocks in flight
+    const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
+    const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
+    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
+    int m = timer_begin(c, cls);
+    launch_pdl(c, kern, grid, L.L.block, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f, color,
+               kchunk, dc, xc, omega);
+    timer_end(c, cls, m);
+}
+
 template <class T>
 void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
     const LA<T> a = arrays<T>(L);
@@ -752,22 +796,15 @@ void mg_rbgs(vof_ctx* c, const Level& L, int color, int mode, const Level* C) {
         timer_end(c, cls, m);
         return;
     }
-    using K = void (*)(Dims, T, const T*, const T*, const T*, const T*, T*, const T*, int, int,
-                       Dims, const T*, T);
-    const K kern = mode == 1 ? k_rbgs_pair_t<T, 1> : (mode == 2 ? k_rbgs_pair_t<T, 2>
-                                                              : k_rbgs_pair_t<T, 0>);
-    const Dims dc = C ? C->d : L.d;
-    const T* xc = C ? arrays<T>(*C).x : nullptr;
-    const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
-    // a thread per x-pair halves the blocks of the level's cell geometry:
-    // halve the z chunks to keep about as many blocks in flight
-    const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
-    const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
-    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
-    int m = timer_begin(c, cls);
-    launch_pdl(c, kern, grid, L.L.block, L.d, (T)(L.h * L.h), a.bx, a.by, a.bz, (const T*)a.x,
-               a.x, a.f, color, kchunk, dc, xc, omega);
-    timer_end(c, cls, m);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (L.bxh) {
+            // coefficients stored over s: the same update with h^2 / s
+            rbgs_pair(c, L, (T)(L.h * L.h) / L.hscale, L.bxh, L.byh, L.bzh, a, color, mode, C,
+                      cls);
+            return;
+        }
+    }
+    rbgs_pair(c, L, (T)(L.h * L.h), a.bx, a.by, a.bz, a, color, mode, C, cls);
 }
 
 template <class T>
@@ -782,10 +819,16 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
         VOF_LAUNCH(c, k_restrict_fw_t<T>, C.L.grid, C.L.block, F.d, (const T*)r, C.d, b.f,
                    C.L.kchunk);
     } else {
-        if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
-            launch_pdl(c, k_restrict_pair_f, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)),
-                       (const float*)a.bx, (const float*)a.by, (const float*)a.bz,
-                       (const float*)a.x, (const float*)a.f, C.d, (float*)b.f, C.L.kchunk);
+        if (sizeof(T) == sizeof(float) && F.bxh)
+            launch_pdl(c, k_restrict_pair_f<__half>, C.L.grid, C.L.block, F.d,
+                       (float)(1.0 / (F.h * F.h)) * F.hscale, (const __half*)F.bxh, (const __half*)F.byh,
+                       (const __half*)F.bzh, (const float*)a.x, (const float*)a.f, C.d,
+                       (float*)b.f, C.L.kchunk);
+        else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
+            launch_pdl(c, k_restrict_pair_f<float>, C.L.grid, C.L.block, F.d,
+                       (float)(1.0 / (F.h * F.h)), (const float*)a.bx, (const float*)a.by,
+                       (const float*)a.bz, (const float*)a.x, (const float*)a.f, C.d, (float*)b.f,
+                       C.L.kchunk);
         else
             launch_pdl(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)),
                        a.bx, a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
@@ -957,6 +1000,17 @@ void mg_to_f32(vof_ctx* c, const double* a, float* b, int n) {
         VOF_LAUNCH(c, k_to_f32x4, flat_blocks(n / 4), 256, n / 4, (const double2*)a, (float4*)b);
     else
         VOF_LAUNCH(c, k_to_f32, flat_blocks(n), 256, n, a, b);
+}
+
+void mg_half_coefficients(vof_ctx* c) {
+    for (const Level& L : c->lv) {
+        if (!L.bxh) continue;
+        const int nu = (L.d.nx + 1) * L.d.ny * L.d.nz, nv = L.d.nx * (L.d.ny + 1) * L.d.nz;
+        const float inv_s = 1.f / L.hscale;
+        VOF_LAUNCH(c, k_to_f16, flat_blocks(nu), 256, nu, L.bxf, L.bxh, inv_s);
+        VOF_LAUNCH(c, k_to_f16, flat_blocks(nv), 256, nv, L.byf, L.byh, inv_s);
+        VOF_LAUNCH(c, k_to_f16, flat_blocks(L.ncells), 256, L.ncells, L.bzf, L.bzh, inv_s);
+    }
 }
 
 void mg_to_f64(vof_ctx* c, const float* a, double* b, int n) {

@@ -18,15 +18,21 @@ struct LdL2 {
     __device__ __forceinline__ double operator()(const double* p) const { return __ldcg(p); }
 };
 
+// a coefficient as the level's arithmetic type: FP32 and FP64 coefficients
+// as stored, FP16 copies widened exactly to FP32
+__device__ __forceinline__ float cval(float v) { return v; }
+__device__ __forceinline__ double cval(double v) { return v; }
+__device__ __forceinline__ float cval(__half v) { return __half2float(v); }
+
 // Red-black Gauss-Seidel update of cell (i, j, k) on one level:
 //   x_c = (h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f.
 // Across a wall (beta = 0) the neighbour counts as 0 and is not read.
 // MODE 1: x is zero (first pass from a zero guess), neighbours are not read.
 // MODE 2: each neighbour is read as x + omega x_coarse(parent): the first
 // pass after the coarse correction, with the prolongation folded in.
-template <class T, int MODE, class LD>
-__device__ __forceinline__ void rbgs_cell(const Dims& d, T h2, const T* __restrict__ bx,
-                                          const T* __restrict__ by, const T* __restrict__ bz,
+template <class T, int MODE, class LD, class CT>
+__device__ __forceinline__ void rbgs_cell(const Dims& d, T h2, const CT* __restrict__ bx,
+                                          const CT* __restrict__ by, const CT* __restrict__ bz,
                                           const T* __restrict__ xr, T* __restrict__ xw,
                                           const T* __restrict__ f, int i, int j, int k,
                                           const Dims& dc, const T* __restrict__ xc, T omega,
@@ -38,9 +44,9 @@ __device__ __forceinline__ void rbgs_cell(const Dims& d, T h2, const T* __restri
     const int cw = cid(d, iw, j, k), ce = cid(d, ie, j, k);
     const int cs = cid(d, i, js, k), cn = cid(d, i, jn, k);
     const int cb = cid(d, i, j, km), ct = cid(d, i, j, kp);
-    const T b0 = bx[uid(d, i, j, k)], b1 = bx[uid(d, i + 1, j, k)];
-    const T b2 = by[vid(d, i, j, k)], b3 = by[vid(d, i, j + 1, k)];
-    const T b4 = bz[wid(d, i, j, k)], b5 = bz[wid(d, i, j, kp)];
+    const T b0 = cval(bx[uid(d, i, j, k)]), b1 = cval(bx[uid(d, i + 1, j, k)]);
+    const T b2 = cval(by[vid(d, i, j, k)]), b3 = cval(by[vid(d, i, j + 1, k)]);
+    const T b4 = cval(bz[wid(d, i, j, k)]), b5 = cval(bz[wid(d, i, j, kp)]);
     const bool hw = i > 0, he = i < d.nx - 1, hs = j > 0, hn = j < d.ny - 1;
     T num;
     if (MODE == 1) {

@@ -237,6 +237,13 @@ void precondition(vof_ctx* c) {
 
 }  // namespace
 
+// does coarse level l of the mixed cycle keep FP16 copies of its coefficients?
+static bool half_coef_level(const Dims& d, int l, const vof_solver* sv) {
+    return l >= 1 && sv && sv->precision == VOF_PREC_MIXED_FP32 &&
+           sv->mg_interp == VOF_MG_CONSTANT && d.nx % 2 == 0 &&
+           (long)d.nx * d.ny * d.nz >= HALF_COEF_MIN_CELLS;
+}
+
 size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels) {
     std::vector<Dims> dims = level_dims(g);
     if (nlevels) *nlevels = (int)dims.size();
@@ -248,6 +255,7 @@ size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels)
         const size_t n = (size_t)dims[l].nx * dims[l].ny * dims[l].nz;
         // the density-formed finest level keeps x, f, a second x and rho
         b += (l == 0 && rho) ? 4 * n * elt + 2 * n + 256 : faces_bytes(dims[l], elt) + 2 * n * elt;
+        if (half_coef_level(dims[l], (int)l, sv)) b += faces_bytes(dims[l], sizeof(__half)) + 32;
     }
     if (mixed) b += 3 * (size_t)dims[0].nx * dims[0].ny * dims[0].nz * sizeof(float);  // e, p, q
     if (sv && sv->mg_interp == VOF_MG_TRILINEAR)  // residual scratch per non-coarsest level
@@ -312,6 +320,21 @@ vof_status mg_allocate(vof_ctx* c) {
             L.bzf = q + nu + nv;
             L.xf = q + nu + nv + n;
             L.ff = q + nu + nv + 2 * n;
+            const double rmin = std::min(c->ph.rho_l, c->ph.rho_g);
+            const double rmax = std::max(c->ph.rho_l, c->ph.rho_g);
+            if (half_coef_level(L.d, (int)l, &c->sv) && rmin > 0.0 && rmax <= 8192.0 * rmin) {
+                // every nonzero coefficient is a mean of 2/(rho_a + rho_b), so it
+                // lies in [1/rmax, 1/rmin]; stored over s, the power of two at or
+                // above 1/rmin, it lies in [2^-14, 1]: FP16's normal range
+                L.hscale = (float)std::exp2(std::ceil(std::log2(1.0 / rmin)));
+                // offsets rounded to 8 halves: the paired loads stay aligned
+                const size_t ou = (nu + 7) & ~(size_t)7, ov = (nv + 7) & ~(size_t)7;
+                __half* hq = (__half*)dev_alloc(c, sizeof(__half) * (ou + ov + n));
+                if (!hq) return set_err(c, VOF_ERR_OOM, "allocation of a multigrid level failed");
+                L.bxh = hq;
+                L.byh = hq + ou;
+                L.bzh = hq + ou + ov;
+            }
         } else {
             double* q = (double*)p;
             L.bx = q;
@@ -381,7 +404,14 @@ vof_status mg_allocate(vof_ctx* c) {
     return tail_setup(c);
 }
 
+static void build_level_coefficients(vof_ctx* c);
+
 void mg_build_coefficients(vof_ctx* c) {
+    build_level_coefficients(c);
+    mg_half_coefficients(c);
+}
+
+static void build_level_coefficients(vof_ctx* c) {
     const bool dens = c->sv.mg_coarsen == VOF_COARSEN_DENSITY_MEAN;
     if (dens && c->lv.size() > 1) {
         // coarse levels from the averaged density; the finest level keeps

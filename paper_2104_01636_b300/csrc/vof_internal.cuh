@@ -3,6 +3,7 @@
 // walls in x and y, periodic z).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -121,6 +122,10 @@ struct Level {
     double *x = nullptr, *f = nullptr;                    // correction / right side
     float *bxf = nullptr, *byf = nullptr, *bzf = nullptr;  // FP32 copies (mixed)
     float *xf = nullptr, *ff = nullptr;
+    // FP16 copies of the FP32 coefficients, read by the colour passes and
+    // the restriction of a large coarse level (mixed cycle; see HALF_COEF_MIN_CELLS)
+    __half *bxh = nullptr, *byh = nullptr, *bzh = nullptr;
+    float hscale = 1.f;  // the FP16 copies hold beta / hscale (a power of two)
     void* rs = nullptr;  // residual scratch for full-weighting restriction (T per cell)
     void* rho = nullptr; // cell density (T per cell), levels >= 1 with density coarsening
     Launch L;
@@ -130,6 +135,12 @@ struct Level {
 // coarse tail of the mixed cycle in one cluster launch (k_mg_tail.cu): the
 // operations of the cycle from level tail_level down, as a program
 // ---------------------------------------------------------------------------
+// A coarse level of the mixed cycle with at least this many cells (and an
+// even nx, constant prolongation) smooths and restricts with FP16 copies of
+// its face coefficients: its colour passes are bound by memory traffic, two
+// thirds of it coefficients. Smaller levels are bound by latency and keep
+// FP32, so the one-launch coarse tail (at most TAIL_MAX_CELLS) never sees them.
+constexpr int HALF_COEF_MIN_CELLS = 1 << 20;
 constexpr int TAIL_MAX_LEVELS = 16;
 constexpr int TAIL_MAX_OPS = 256;
 constexpr int TAIL_MAX_CELLS = 8192;  // largest level the tail starts from
@@ -389,6 +400,8 @@ void wait_probe(vof_ctx* c, int limit);
 void rho_restrict(vof_ctx* c);
 void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
 void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
+// FP16 copies of the FP32 coefficients of the levels that carry them
+void mg_half_coefficients(vof_ctx* c);
 
 // coarse tail (k_mg_tail.cu)
 vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero, const TailProg* from_x);
