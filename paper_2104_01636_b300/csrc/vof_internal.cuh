@@ -137,10 +137,11 @@ struct Level {
 // ---------------------------------------------------------------------------
 // A coarse level of the mixed cycle with at least this many cells (and an
 // even nx, constant prolongation) smooths and restricts with FP16 copies of
-// its face coefficients: its colour passes are bound by memory traffic, two
-// thirds of it coefficients. Smaller levels are bound by latency and keep
-// FP32, so the one-launch coarse tail (at most TAIL_MAX_CELLS) never sees them.
-constexpr int HALF_COEF_MIN_CELLS = 1 << 20;
+// its face coefficients: two thirds of a colour pass's bytes are
+// coefficients, and from about 2^18 cells up the pass moves enough of them
+// for the saving to show. Smaller levels are bound by latency and keep FP32,
+// so the one-launch coarse tail (at most TAIL_MAX_CELLS) never sees them.
+constexpr int HALF_COEF_MIN_CELLS = 1 << 18;
 constexpr int TAIL_MAX_LEVELS = 16;
 constexpr int TAIL_MAX_OPS = 256;
 constexpr int TAIL_MAX_CELLS = 8192;  // largest level the tail starts from
