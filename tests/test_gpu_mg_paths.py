@@ -101,3 +101,20 @@ def test_coarse_tail_equals_launch_per_operation(dims, kw):
     assert rt["iters"] == ro["iters"]
     assert np.array_equal(Pt, Po), rel_l2(Pt, Po)
     assert nt < no, (nt, no)
+
+
+def test_fp16_coarse_coefficients_reach_fp64_tolerance():
+    """On 128^3, level 1 (64^3 = 262144 cells) is large enough to smooth and
+    restrict with FP16 copies of its face coefficients (stored over a power
+    of two). The cycle still has a single operator per level, so the mixed
+    solve reaches the FP64 tolerance in about the FP64 path's iterations and
+    is deterministic. Air-water density ratio, 16 bubbles of 12 cells."""
+    g, ph, a, b, Pstar = _problem((128, 128, 128), 16, 59, d_cells=12.0)
+    P64, r64 = _solve(g, ph, a, b, rtol=1e-11, precision=0)
+    P32, r32 = _solve(g, ph, a, b, rtol=1e-11, precision=1)
+    P32b, r32b = _solve(g, ph, a, b, rtol=1e-11, precision=1)
+    assert r32["res"] <= 1e-11
+    assert r32["iters"] <= 1.5 * r64["iters"] + 6, (r32["iters"], r64["iters"])
+    assert rel_l2(P32, Pstar) < 1e-6
+    assert rel_l2(P32, P64) < 1e-6
+    assert r32b["iters"] == r32["iters"] and np.array_equal(P32, P32b)
