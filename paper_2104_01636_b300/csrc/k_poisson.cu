@@ -80,43 +80,9 @@ __global__ void k_beta(Dims d, const double* __restrict__ a, double rl, double r
     const int i = r.i, j = r.j;
     const double dh = 0.5 * (rl - rg), gh = 0.5 * rg;
     auto half_rho = [&](int c) { return fma(a[c], dh, gh); };
-    // A pure cell whose -x, -y and -z neighbours hold the same alpha, exactly
-    // 0 or 1 (compared as bit patterns on the integer pipe), has the values
-    // of that phase, formed once here by the same operations: the stores are
-    // bitwise those of the general path, with no FP64 work per cell.
-    const long long one = __double_as_longlong(1.0);
-    double hp[2], bp[2];
-    float r32p[2];
-    __half r16p[2];
-    for (int q = 0; q < 2; ++q) {
-        hp[q] = fma(q ? 1.0 : 0.0, dh, gh);
-        bp[q] = rcp_cubic(hp[q] + hp[q]);
-        r32p[q] = 2.f * (float)hp[q];
-        r16p[q] = __hmul(__double2half(hp[q]), __float2half(2.f));
-    }
-    const int cb0 = cid(d, i, j, wrapk(r.k0 - 1, d.nz));
-    double hb = half_rho(cb0);
-    long long qb = __double_as_longlong(a[cb0]);
+    double hb = half_rho(cid(d, i, j, wrapk(r.k0 - 1, d.nz)));
     for (int k = r.k0; k < r.k1; ++k) {
         const int c = cid(d, i, j, k);
-        const long long qc = __double_as_longlong(a[c]);
-        const long long qw = i == 0 ? qc : __double_as_longlong(a[c - 1]);
-        const long long qs = j == 0 ? qc : __double_as_longlong(a[c - d.nx]);
-        const bool pure = (qc == 0 || qc == one) && qw == qc && qs == qc && qb == qc;
-        qb = qc;
-        if (pure) {
-            const int q = qc != 0;
-            if (rho32) rho32[c] = r32p[q];
-            if (rho16) rho16[c] = r16p[q];
-            if (rho64) rho64[c] = 2.0 * hp[q];
-            bx[uid(d, i, j, k)] = i == 0 ? 0.0 : bp[q];
-            if (i == d.nx - 1) bx[uid(d, d.nx, j, k)] = 0.0;
-            by[vid(d, i, j, k)] = j == 0 ? 0.0 : bp[q];
-            if (j == d.ny - 1) by[vid(d, i, d.ny, k)] = 0.0;
-            bz[wid(d, i, j, k)] = bp[q];
-            hb = hp[q];
-            continue;
-        }
         const double hc = half_rho(c);
         // densities of the multigrid's finest level: 2 h, scaled after the
         // rounding (exact: a power of two)
