@@ -217,23 +217,27 @@ vof_status vof_apply_operator(vof_ctx* ctx, const double* alpha, const double* x
  * accepts: its fixed scratch holds this many doubles (24 MiB). */
 #define VOF_NOALLOC_MAX_FACES (3u << 20)
 
-/* y = A x as vof_apply_operator computes it, but with no context and no
- * device allocation at all. The paper has no counterpart: it exists for
- * callers that cannot call cudaMalloc -- code running while its stream is
- * being captured into a CUDA graph, hosts that reserve all device memory up
- * front in their own arena, latency-critical loops where an allocation
- * could synchronise the device. The face coefficients beta it builds from
- * alpha go into one fixed device array inside the library (24 MiB, held by
- * every GPU that loads the library until the process exits), so
+/* y = A x as vof_apply_operator computes it (the same kernels, so the same
+ * bits), but with no context and no device allocation at all. The paper has
+ * no counterpart: it exists for callers that cannot call cudaMalloc -- hosts
+ * that reserve all device memory up front in their own arena, where a
+ * cudaMalloc would fail or escape their accounting, and latency-critical
+ * loops where an allocation could synchronise the device. The face
+ * coefficients beta it builds from alpha go into one fixed device array
+ * inside the library (24 MiB, held by every GPU that loads the library
+ * until the process exits), so
  *  - grids with more than VOF_NOALLOC_MAX_FACES faces in total are
- *    rejected with VOF_ERR_ADMISSION before anything is launched;
+ *    rejected with VOF_ERR_ADMISSION before anything is launched; other
+ *    grids and properties are checked as vof_create checks them
+ *    (VOF_ERR_ARG);
  *  - every call shares that array and overwrites all of it that it reads,
  *    so nothing needs clearing between calls, but calls whose kernels
  *    overlap on the GPU (different streams, or different host threads on
  *    one device) race on it: serialise them;
- *  - the first call on each device looks up the array's device address
+ *  - the first call in each CUDA context (each device's primary context,
+ *    and again after cudaDeviceReset) looks up the array's device address
  *    (cudaGetSymbolAddress, which may load the library's module), so make
- *    that first call before any stream capture on that device.
+ *    that first call before any stream capture in that context.
  * alpha, x, y: device arrays in the cell layout; stream: cudaStream_t (NULL
  * = legacy default stream); the call is asynchronous on it. Walls only
  * (VOF_ERR_UNSUPPORTED for periodic x or y). */

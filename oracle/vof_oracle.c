@@ -30,6 +30,16 @@
  *    single combined pressure P = p + p_tilde (Eqs. 6-7 and step 11 are
  *    linear in the source, so one solve equals the two of steps 6 and 11);
  *  - linear face averaging rho_f = (rho_L + rho_R)/2 (step 10), beta = 1/rho_f.
+ *
+ * Every step is pinned by CPU tests against something other than this file:
+ * exact rational volumes, closed-form eigenvalues and series, the symbolic
+ * curvature of quadric surfaces, polynomial fields on which the stencils are
+ * exact (the viscous full stress, walls included), brute-force enumeration
+ * and conservation invariants. The viscous term and the face curvature are
+ * also checked by planting mistakes in a copy of this file
+ * (tests/test_oracle_mutants.py). Only the size of the spurious currents
+ * with height-function curvature is not fixed by the paper (reported, not
+ * pinned).
  */
 #include "vof_oracle.h"
 

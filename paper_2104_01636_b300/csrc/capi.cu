@@ -24,22 +24,6 @@ Sizes sizes_of(const vof_grid* g) {
     return s;
 }
 
-bool grid_ok(const vof_grid* g, std::string& why) {
-    if (!g) { why = "grid is NULL"; return false; }
-    if (g->nx < 2 || g->ny < 2 || g->nz < 4) { why = "need nx, ny >= 2 and nz >= 4"; return false; }
-    if (g->nz % 2) { why = "nz must be even (red-black ordering on the periodic axis)"; return false; }
-    if (!(g->h > 0.0) || !std::isfinite(g->h)) { why = "h must be positive"; return false; }
-    if ((g->periodic_x && g->nx % 2) || (g->periodic_y && g->ny % 2)) {
-        why = "periodic x/y need an even cell count";
-        return false;
-    }
-    const double faces = (double)(g->nx + 1) * (double)(g->ny + 1) * (double)g->nz;
-    if (faces >= 2147483647.0) { why = "grid too large for 32-bit indexing"; return false; }
-    const long tiles = (long)((g->nx + TBX - 1) / TBX) * ((g->ny + TBY - 1) / TBY);
-    if (tiles > MAX_PARTIALS) { why = "cross-section too large"; return false; }
-    return true;
-}
-
 size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     const Sizes s = sizes_of(g);
     const size_t faces = s.nu + s.nv + s.nw;
@@ -166,6 +150,28 @@ void report_timing_end(vof_ctx* c, const double snap[T_NCLASS], vof_report* r) {
 }
 
 }  // namespace
+
+bool grid_ok(const vof_grid* g, std::string& why) {
+    if (!g) { why = "grid is NULL"; return false; }
+    if (g->nx < 2 || g->ny < 2 || g->nz < 4) { why = "need nx, ny >= 2 and nz >= 4"; return false; }
+    if (g->nz % 2) { why = "nz must be even (red-black ordering on the periodic axis)"; return false; }
+    if (!(g->h > 0.0) || !std::isfinite(g->h)) { why = "h must be positive"; return false; }
+    if ((g->periodic_x && g->nx % 2) || (g->periodic_y && g->ny % 2)) {
+        why = "periodic x/y need an even cell count";
+        return false;
+    }
+    const double faces = (double)(g->nx + 1) * (double)(g->ny + 1) * (double)g->nz;
+    if (faces >= 2147483647.0) { why = "grid too large for 32-bit indexing"; return false; }
+    const long tiles = (long)((g->nx + TBX - 1) / TBX) * ((g->ny + TBY - 1) / TBY);
+    if (tiles > MAX_PARTIALS) { why = "cross-section too large"; return false; }
+    return true;
+}
+
+bool phys_ok(const vof_phys* p) {
+    return p && p->rho_l > 0 && p->rho_g > 0 && p->mu_l >= 0 && p->mu_g >= 0 && p->sigma >= 0 &&
+           (p->conv_scheme == VOF_CONV_CENTRAL || p->conv_scheme == VOF_CONV_UPWIND) &&
+           (p->kappa_mode == VOF_KAPPA_HEIGHT_FUNCTION || p->kappa_mode == VOF_KAPPA_EXACT);
+}
 
 // ---------------------------------------------------------------------------
 // helpers used by the other translation units
@@ -402,12 +408,7 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     if (!out) return VOF_ERR_ARG;
     *out = nullptr;
     std::string why;
-    if (!grid_ok(grid, why) || !phys || !solver) return VOF_ERR_ARG;
-    if (!(phys->rho_l > 0) || !(phys->rho_g > 0) || !(phys->mu_l >= 0) || !(phys->mu_g >= 0) ||
-        !(phys->sigma >= 0) || (phys->conv_scheme != VOF_CONV_CENTRAL &&
-                                phys->conv_scheme != VOF_CONV_UPWIND) ||
-        (phys->kappa_mode != VOF_KAPPA_HEIGHT_FUNCTION && phys->kappa_mode != VOF_KAPPA_EXACT))
-        return VOF_ERR_ARG;
+    if (!grid_ok(grid, why) || !phys_ok(phys) || !solver) return VOF_ERR_ARG;
     if (!(solver->rtol > 0) || solver->max_iter < 1 || solver->nu_pre < 1 ||
         solver->nu_pre != solver->nu_post || !(solver->mg_omega >= 0.0) ||
         solver->mg_omega > 2.0 || solver->coarse_iters < 0 || !(solver->coarse_tol >= 0.0) ||

@@ -357,6 +357,16 @@ void launch_beta(vof_ctx* c, const double* alpha) {
                c->bz, c->rho32, (__half*)c->rho16, c->rho64, L.kchunk);
 }
 
+void launch_beta_apply_raw(const vof_grid* g, const vof_phys* ph, const double* alpha,
+                           const double* x, double* y, double* bx, double* by, double* bz,
+                           int sm_count, cudaStream_t s) {
+    const Dims d{g->nx, g->ny, g->nz};
+    const Launch L = launch_cells(d.nx, d.ny, d.nz, sm_count);
+    k_beta<<<L.grid, L.block, 0, s>>>(d, alpha, ph->rho_l, ph->rho_g, bx, by, bz, nullptr, nullptr,
+                                      nullptr, L.kchunk);
+    k_apply_A<<<L.grid, L.block, 0, s>>>(d, 1.0 / (g->h * g->h), bx, by, bz, x, y, L.kchunk);
+}
+
 void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y) {
     VOF_LAUNCH(c, k_apply_A, l.L.grid, l.L.block, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz, x, y,
                                                   l.L.kchunk);

@@ -346,6 +346,14 @@ void finalize_max(vof_ctx* c, int slot, int nparts, int dst);
 // ---------------------------------------------------------------------------
 // poisson (k_poisson.cu)
 void launch_beta(vof_ctx* c, const double* alpha);
+// the face coefficients from alpha into caller-given storage, then y = A x
+// with them: the kernels of launch_beta and launch_apply_A, without a context
+void launch_beta_apply_raw(const vof_grid* g, const vof_phys* ph, const double* alpha,
+                           const double* x, double* y, double* bx, double* by, double* bz,
+                           int sm_count, cudaStream_t s);
+// argument checks of vof_create for the grid and the physical properties
+bool grid_ok(const vof_grid* g, std::string& why);
+bool phys_ok(const vof_phys* p);
 void launch_apply_A(vof_ctx* c, const Level& l, const double* x, double* y);
 void launch_residual(vof_ctx* c, const Level& l, const double* x, const double* f, double* r,
                      int slot);
