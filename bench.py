@@ -93,7 +93,10 @@ def parse():
                     help="skip the static bubble (32^3, 20 steps) and the 64x64x128 swarm "
                          "(200 steps, FP64 against mixed)")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=32,
+    ap.add_argument("--cpu-full-steps", type=int, default=0,
+                    help="only time this many oracle steps on the whole 224x224x640 duct and "
+                         "print them (slow: minutes per step)")
+    ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests in the serving run (0 skips it)")
     ap.add_argument("--ensemble-cases", type=int, default=64,
                     help="cases in the ensemble run (0 skips it)")
@@ -209,63 +212,128 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def cpu_baseline(args, steps=1, label="bounded sample", nz_s=16, threads=0):
+FULL_CELLS = 224 * 224 * 640
+
+
+def sample_planes(steps: int, warmup: int) -> int:
+    """z-planes of the oracle's bounded sample (the full 224 x 224 cross
+    section): 16 while the reference arm's warmup + steps samples fit in
+    about 3 minutes on the host (25 samples of ~8 s), fewer (even, at least
+    8) for longer runs. Both CPU legs of a run use the same sample, so they
+    report the same thing."""
+    n = steps + warmup
+    if n <= 25:
+        return 16
+    return max(8, 2 * ((16 * 25) // (2 * n)))
+
+
+def cpu_baseline(args, steps=1, label="bounded sample", nz_s=16, threads=0, warmup=0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    the same generator with nz_s z-planes (224x224x16, ~0.8M cells, by
-    default). Its steps/s is scaled to the 32.1M-cell metric by the cell
-    ratio. threads > 0 caps the oracle's OpenMP threads."""
+    the same generator on 224 x 224 x nz_s (~0.8M cells for 16 planes).
+    Returns the measured seconds per sample step and the steps/s scaled to
+    the 32.1M-cell metric by the cell ratio. The oracle's Jacobi-CG needs
+    more iterations on the full grid than on a slab, so the scaled rate
+    overstates the oracle at full size; the full-size measurement is
+    recorded separately (profiles/oracle_full_duct.json). threads > 0 caps
+    the oracle's OpenMP threads."""
     import oracle
     from paper_2104_01636_b300 import inputs as I
-    full = 224 * 224 * 640
     if threads > 0:
         oracle.set_num_threads(threads)
-    case = I.paper_shaped(224, 224, nz_s, nbub=round(864 * nz_s / 640), seed=2106)
+    nb = round(864 * nz_s / 640)
+    case = I.paper_shaped(224, 224, nz_s, nbub=nb, seed=2106)
     g, ph = case.grid, case.phys
     state = case.state()
+    for s in range(warmup):
+        *state, rep, st = oracle.step(g, ph, *state, case.dt, s, rtol=args.rtol)
     t_tot, iters = 0.0, 0
-    for s in range(steps):
+    for s in range(warmup, warmup + steps):
         t0 = time.perf_counter()
         *state, rep, st = oracle.step(g, ph, *state, case.dt, s, rtol=args.rtol)
         t_tot += time.perf_counter() - t0
         iters += rep["iters"]
     sps_sample = steps / t_tot
     return {
-        "value": sps_sample * g.ncells / full,
+        "value": sps_sample * g.ncells / FULL_CELLS,
         "unit": UNIT,
         "cores": oracle.num_threads(),
         "cpu_model": cpu_model(),
         "host_cores": os.cpu_count(),
         "kind": "oracle",
-        "sample": (f"{steps} oracle step(s) of the same generator on 224x224x{nz_s} "
-                   f"({g.ncells} cells, {round(864 * nz_s / 640)} spheres), rtol {args.rtol:g}, "
-                   f"scaled to 32.1M cells by the cell ratio ({label})"),
+        "sample": (f"{steps} timed oracle step(s) (after {warmup} untimed) of the same generator "
+                   f"on 224x224x{nz_s} ({g.ncells} cells, {nb} spheres), rtol {args.rtol:g}; "
+                   f"value = measured sample steps/s x {g.ncells}/{FULL_CELLS} cells ({label})"),
+        "sample_cells": g.ncells,
         "sample_s_per_step": t_tot / steps,
         "poisson_cell_updates_per_s": g.ncells * iters / t_tot,
         "jacobi_cg_iters_per_step": iters / steps,
     }
 
 
+def oracle_full_record():
+    """The oracle timed once on the whole 224 x 224 x 640 duct (2 steps on
+    the GPU machine's host cores, bench.py --cpu-full-steps 2), as committed."""
+    p = os.path.join(ROOT, "profiles", "oracle_full_duct.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_full(args):
+    """--cpu-full-steps N: N oracle steps on the whole paper-shaped duct
+    (224 x 224 x 640, 864 spheres; about 10 GB of host memory), timed one by
+    one. Prints one JSON line; slow (minutes per step), never part of the
+    default run."""
+    import oracle
+    from paper_2104_01636_b300 import inputs as I
+    case = I.paper_shaped(seed=2106)
+    g, ph = case.grid, case.phys
+    state = case.state()
+    per, its = [], []
+    for s in range(args.cpu_full_steps):
+        t0 = time.perf_counter()
+        *state, rep, st = oracle.step(g, ph, *state, case.dt, s, rtol=args.rtol)
+        per.append(time.perf_counter() - t0)
+        its.append(rep["iters"])
+    rec = {"oracle_full": {
+        "workload": WORKLOAD, "cells": g.ncells, "steps": len(per), "rtol": args.rtol,
+        "s_per_step": per, "jacobi_cg_iters": its,
+        "value": len(per) / sum(per), "unit": UNIT,
+        "poisson_cell_updates_per_s": g.ncells * sum(its) / sum(per),
+        "cores": oracle.num_threads(), "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
+        "command": f"python bench.py --cpu-full-steps {args.cpu_full_steps} --rtol {args.rtol:g}"}}
+    print(json.dumps(rec), flush=True)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    # each step a bounded sample: 16 z-planes (about 8 s of oracle work on 16
-    # host cores) up to 13 steps in all, fewer planes for longer runs, so that
-    # the whole run stays within a few minutes
-    nz_s = max(4, min(16, (16 * 13) // max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_baseline(args, steps=1, nz_s=nz_s)
-    cb = cpu_baseline(args, steps=max(1, args.steps), label="reference arm", nz_s=nz_s)
+    # each step is one oracle step on the bounded sample of sample_planes();
+    # the same sample as the bench arm's cpu_baseline
+    nz_s = sample_planes(args.steps, args.warmup)
+    t0 = time.perf_counter()
+    cb = cpu_baseline(args, steps=max(1, args.steps), label="reference arm", nz_s=nz_s,
+                      warmup=args.warmup)
+    wall = time.perf_counter() - t0
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+        # the measured time of one sample step (value scales it to 32.1M cells)
+        "ms_per_step": 1e3 * cb["sample_s_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+        "config": {"workload": WORKLOAD, "sample": cb["sample"],
+                   "sample_cells": cb["sample_cells"]},
         "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "cpu_model", "kind",
                                             "sample")},
         "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "poisson_cell_updates_per_s": cb["poisson_cell_updates_per_s"],
+        "jacobi_cg_iters_per_step": cb["jacobi_cg_iters_per_step"],
+        "wall_s": wall,
+        "oracle_full_duct": oracle_full_record(),
     }
     print(json.dumps(line), flush=True)
 
@@ -349,24 +417,35 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
     sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500)
     out = {"cases": n_cases, "grid": "48x48x96", "cells_per_case": cases[0].grid.ncells,
            "precision": "mixed", "rtol": 1e-8, "steps": steps}
-    for label, ns in (("streams", streams), ("one_stream", 1)):
+    runs = (("batched", streams, vd.VofEnsemble.BATCHED),
+            ("streams", streams, vd.VofEnsemble.STREAMS),
+            ("one_stream", 1, vd.VofEnsemble.STREAMS))
+    for label, ns, mode in runs:
         fields = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in c.state()]
                   for c in cases]
         torch.cuda.synchronize()
-        with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], sv, n_streams=ns) as E:
+        with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], sv, n_streams=ns,
+                            mode=mode) as E:
             dts = [c.dt for c in cases]
             for s in range(warmup):
                 E.step(fields, dts, s)
             torch.cuda.synchronize()
+            n0 = E.launch_count()
             t0 = time.perf_counter()
             for s in range(warmup, warmup + steps):
-                E.step(fields, dts, s)
+                reps = E.step(fields, dts, s, reports=True)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3 / steps
+            launches = (E.launch_count() - n0) / steps
+            batched = E.batched
         del fields
-        out[label] = {"n_streams": ns, "ms_per_ensemble_step": ms,
+        out[label] = {"n_streams": ns, "batched_solves": batched,
+                      "ms_per_ensemble_step": ms,
                       "case_steps_per_s": n_cases / (ms / 1e3),
-                      "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3)}
+                      "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3),
+                      "kernel_launches_per_ensemble_step": launches,
+                      "max_inner_iters": max(r["iters"] for r in reps),
+                      "mean_inner_iters": sum(r["iters"] for r in reps) / len(reps)}
     return out
 
 
@@ -439,6 +518,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.cpu_full_steps > 0:
+        if rank == 0:
+            cpu_full(args)
         return
 
     import numpy as np
@@ -607,9 +690,11 @@ def main():
         return
     cb = None
     if world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(args, steps=1)
+        nz_s = sample_planes(args.steps, args.warmup)
+        cb = cpu_baseline(args, steps=2, nz_s=nz_s)
+        cb["oracle_full_duct"] = oracle_full_record()
         if args.cpu_one_thread:
-            one = cpu_baseline(args, steps=1, label="one host thread", threads=1)
+            one = cpu_baseline(args, steps=1, label="one host thread", nz_s=nz_s, threads=1)
             cb["one_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample",
                                                      "sample_s_per_step",
                                                      "poisson_cell_updates_per_s")}
@@ -619,7 +704,9 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.nz == 640 else WORKLOAD.replace("640", str(args.nz)),
+        "config": {"workload": WORKLOAD if args.nz == 640 else
+                   f"paper-shaped duct 224x224x{args.nz} ({N / 1e6:.1f}M cells), {nbub} spheres "
+                   "d=12h, Re_b=5300 1/7 profile + 8% noise",
                    "cells": N, "spheres": nbub, "rtol": args.rtol,
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "graph": args.graph,
@@ -631,8 +718,10 @@ def main():
         "roofline": roofline,
         "cpu_baseline": (None if cb is None else
                          {k: cb[k] for k in ("value", "unit", "cores", "cpu_model", "host_cores",
-                                             "kind", "sample", "sample_s_per_step",
-                                             "poisson_cell_updates_per_s", "one_thread")
+                                             "kind", "sample", "sample_cells",
+                                             "sample_s_per_step", "poisson_cell_updates_per_s",
+                                             "jacobi_cg_iters_per_step", "one_thread",
+                                             "oracle_full_duct")
                           if k in cb}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},

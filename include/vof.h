@@ -422,6 +422,37 @@ vof_status vof_ensemble_step(vof_ensemble* ensemble, double* const* fields, cons
                              long long step_index, vof_status* status, vof_report* reports);
 vof_status vof_ensemble_destroy(vof_ensemble* ensemble);
 
+/* How an ensemble runs its cases.
+ *  VOF_ENSEMBLE_BATCHED: the pressure solves of all cases run as one batched
+ *    solve (Eq. 7 for every case at once): the cases' workspaces are carved
+ *    from one device arena at a fixed stride, and every multigrid operation
+ *    of a level, every Krylov update and every reduction is one launch for
+ *    all cases, with per-case sums and per-case convergence (a case whose
+ *    loop has ended is switched off, its blocks return at once); the V-cycle
+ *    of all cases replays from one CUDA graph. The parts of the step before
+ *    and after the solve run per case on the worker streams. Each case's
+ *    kernels, block sums and decisions are those of its solo solve, so its
+ *    result is bitwise that of the case stepped alone. Needs the mixed
+ *    precision with the density-formed finest level (nx a multiple of 8),
+ *    constant prolongation, face-mean coarsening, a dense coarsest level, an
+ *    even number of finest-level sweeps, the single combined solve and no
+ *    cluster tail; otherwise VOF_ERR_UNSUPPORTED.
+ *  VOF_ENSEMBLE_STREAMS: every case steps through its own context on the
+ *    worker streams, overlapping on the GPU.
+ *  VOF_ENSEMBLE_AUTO: batched where the solver allows it, else streams
+ *    (vof_ensemble_create). */
+#define VOF_ENSEMBLE_AUTO 0
+#define VOF_ENSEMBLE_STREAMS 1
+#define VOF_ENSEMBLE_BATCHED 2
+vof_status vof_ensemble_create_mode(const vof_grid* grid, const vof_phys* phys, int n_phys,
+                                    const vof_solver* solver, int n_cases, int n_streams,
+                                    int mode, vof_ensemble** out);
+/* *batched = 1 when the ensemble runs its solves batched, else 0. */
+vof_status vof_ensemble_batched(const vof_ensemble* ensemble, int* batched);
+/* Kernels launched by the ensemble so far (every case, a batched launch
+ * counted once). */
+vof_status vof_ensemble_launch_count(const vof_ensemble* ensemble, long long* n);
+
 /* ---- duct statistics ------------------------------------------------------
  * Running sums for the profiles of Section 4 (averages over the streamwise
  * direction z and over time, mixture and liquid phase). For every column

@@ -135,6 +135,10 @@ def load() -> ctypes.CDLL:
                                 ctypes.c_int, P(_VP)],
         "vof_ensemble_step": [_VP, P(_VP), P(_D), ctypes.c_longlong, P(ctypes.c_int), P(CReport)],
         "vof_ensemble_destroy": [_VP],
+        "vof_ensemble_create_mode": [P(CGrid), P(CPhys), ctypes.c_int, P(CSolver), ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, P(_VP)],
+        "vof_ensemble_batched": [_VP, P(ctypes.c_int)],
+        "vof_ensemble_launch_count": [_VP, P(ctypes.c_longlong)],
         "vof_stats_create": [P(CGrid), P(_VP)],
         "vof_stats_accumulate": [_VP, _VP, _VP, _VP, _VP, _VP],
         "vof_stats_read": [_VP, P(_D), P(ctypes.c_longlong)],
@@ -454,7 +458,12 @@ class VofEnsemble:
     """n independent cases of one grid advanced together by one step per call
     (fields: per case the eight device tensors of `VofContext.step`)."""
 
-    def __init__(self, grid, phys_list, solver: CSolver | None = None, n_streams: int = 8):
+    AUTO, STREAMS, BATCHED = 0, 1, 2
+
+    def __init__(self, grid, phys_list, solver: CSolver | None = None, n_streams: int = 8,
+                 mode: int = 0):
+        """mode: AUTO (batched solves where the solver allows them, else
+        streams), STREAMS or BATCHED (vof_ensemble_create_mode)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -466,14 +475,22 @@ class VofEnsemble:
         self._g = c_grid(grid)
         self._s = solver or c_solver()
         self._e = _VP()
-        st = self.lib.vof_ensemble_create(ctypes.byref(self._g), self._phys, self.n,
-                                          ctypes.byref(self._s), self.n, int(n_streams),
-                                          ctypes.byref(self._e))
+        st = self.lib.vof_ensemble_create_mode(ctypes.byref(self._g), self._phys, self.n,
+                                               ctypes.byref(self._s), self.n, int(n_streams),
+                                               int(mode), ctypes.byref(self._e))
         if st:
-            raise VofError(st, "vof_ensemble_create")
+            raise VofError(st, "vof_ensemble_create_mode")
+        b = ctypes.c_int(0)
+        self.lib.vof_ensemble_batched(self._e, ctypes.byref(b))
+        self.batched = bool(b.value)
         cs = (grid.nz, grid.ny, grid.nx)
         self.shapes = (cs, cs, cs, cs, (grid.nz, grid.ny, grid.nx + 1),
                        (grid.nz, grid.ny + 1, grid.nx), cs, cs)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong(0)
+        self.lib.vof_ensemble_launch_count(self._e, ctypes.byref(n))
+        return int(n.value)
 
     def step(self, fields, dts, step_index: int, reports: bool = False):
         """fields: list (one per case) of the eight CUDA float64 tensors."""

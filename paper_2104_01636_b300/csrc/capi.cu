@@ -24,25 +24,6 @@ Sizes sizes_of(const vof_grid* g) {
     return s;
 }
 
-size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
-    const Sizes s = sizes_of(g);
-    const size_t faces = s.nu + s.nv + s.nw;
-    size_t b = 0;
-    b += 3 * faces * sizeof(double);                  // beta, surface force, fluxes
-    b += s.n * sizeof(double);                        // kappa
-    b += 3 * s.n;                                     // valid, cmask, has
-    b += s.n * sizeof(int) + 64;                      // interface list
-    b += 4 * s.n * sizeof(double);                    // planes
-    b += 3 * s.n * sizeof(double);                    // cell intermediate velocity
-    b += 3 * s.n * sizeof(double);                    // alpha scratch
-    b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
-    b += mg_workspace_bytes(g, sv, nullptr);
-    if (sv->precision == VOF_PREC_MIXED_FP32) b += 4 * s.n * sizeof(float);  // FP32 velocities, alpha
-    if (sv->ssf_solves == 2) b += 2 * s.n * sizeof(double);                  // p~ and p
-    b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
-    return b;
-}
-
 vof_status alloc(vof_ctx* c, void** p, size_t bytes) {
     *p = dev_alloc(c, bytes);
     if (!*p) return set_err(c, VOF_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes failed");
@@ -151,6 +132,25 @@ void report_timing_end(vof_ctx* c, const double snap[T_NCLASS], vof_report* r) {
 
 }  // namespace
 
+size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
+    const Sizes s = sizes_of(g);
+    const size_t faces = s.nu + s.nv + s.nw;
+    size_t b = 0;
+    b += 3 * faces * sizeof(double);                  // beta, surface force, fluxes
+    b += s.n * sizeof(double);                        // kappa
+    b += 3 * s.n;                                     // valid, cmask, has
+    b += s.n * sizeof(int) + 64;                      // interface list
+    b += 4 * s.n * sizeof(double);                    // planes
+    b += 3 * s.n * sizeof(double);                    // cell intermediate velocity
+    b += 3 * s.n * sizeof(double);                    // alpha scratch
+    b += 6 * s.n * sizeof(double);                    // b, r, z, p, q, rhs
+    b += mg_workspace_bytes(g, sv, nullptr);
+    if (sv->precision == VOF_PREC_MIXED_FP32) b += 4 * s.n * sizeof(float);  // FP32 velocities, alpha
+    if (sv->ssf_solves == 2) b += 2 * s.n * sizeof(double);                  // p~ and p
+    b += (size_t)NSLOTS * MAX_PARTIALS * sizeof(double) + S_NSCALARS * sizeof(double) + 64;
+    return b;
+}
+
 bool grid_ok(const vof_grid* g, std::string& why) {
     if (!g) { why = "grid is NULL"; return false; }
     if (g->nx < 2 || g->ny < 2 || g->nz < 4) { why = "need nx, ny >= 2 and nz >= 4"; return false; }
@@ -180,6 +180,12 @@ bool phys_ok(const vof_phys* p) {
 // freeing it does not synchronise the whole device, so contexts that come
 // and go on other streams (the request server) do not stall each other.
 void* dev_alloc(vof_ctx* c, size_t bytes) {
+    if (c->arena) {  // carved from an ensemble's arena, in allocation order
+        const size_t off = (c->arena_used + 255) & ~(size_t)255;
+        if (off + bytes > c->arena_size) return nullptr;
+        c->arena_used = off + bytes;
+        return c->arena + off;
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
         cudaGetLastError();
@@ -359,6 +365,59 @@ vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double*
     return step_run(c, alpha, uc, vc, wc, u, v, w, p, dt, step_index, report, nullptr);
 }
 
+// The ensemble's step around a batched pressure solve, for one case: step_pre
+// launches step_run's kernels up to the pressure solve and the solve's setup
+// (the guess P copied into the context's P workspace c->p); the batched solve
+// (solve_mixed_batch) runs the solve of every case; step_post launches the
+// rest. In sequence they launch the case's kernels of step_run, in its order,
+// on the same values (the mixed single-solve path).
+vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index) {
+    vof_status st = check_ctx(c);
+    if (st) return st;
+    for (int q = 0; q < 8; ++q)
+        if (!f[q]) return set_err(c, VOF_ERR_ARG, "a field is NULL");
+    if ((st = walls_only(c, "step"))) return st;
+    if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
+    double* const alpha = f[0];
+    const double *u = f[4], *v = f[5], *w = f[6];
+    if ((st = cfl_check(c, u, v, w, dt))) return st;
+    const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
+    cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    double* const flux[3] = {c->fx, c->fy, c->fz};
+    advect_impl(c, alpha, u, v, w, dt, step_index, flux);
+    launch_beta(c, alpha);
+    ssf_impl(c, alpha, c->kappa, c->sx, c->sy, c->sz);
+    const double* const U[3] = {f[1], f[2], f[3]};
+    launch_predict(c, c->an, alpha, U, u, v, w, c->fx, c->fy, c->fz, dt, c->uh);
+    launch_cell_to_face(c, c->uh[0], c->uh[1], c->uh[2], f[4], f[5], f[6]);
+    launch_rhs(c, u, v, w, c->sx, c->sy, c->sz, dt, c->rhs, 3);
+    launch_copy(c, c->p, f[7], (int)n);
+    solve_setup_mixed(c, c->rhs, c->p);
+    return launch_check(c, "step");
+}
+
+// solve: the status of the case's solve; its iteration counts are in *report
+vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve,
+                     vof_report* report) {
+    if (solve != VOF_OK && solve != VOF_ERR_NOT_CONVERGED) return solve;
+    const int n = c->d.nx * c->d.ny * c->d.nz;
+    launch_copy(c, f[7], c->p, n);
+    const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
+    double* const Uc[3] = {f[1], f[2], f[3]};
+    launch_correct(c, f[7], c->sx, c->sy, c->sz, dt, Uh, Uc, f[4], f[5], f[6], P_A, P_B);
+    readback(c);
+    vof_report r = report ? *report : vof_report{};
+    r.max_div = c->hbuf[S_MAXDIV];
+    r.max_u = c->hbuf[S_MAXU];
+    const vof_status st2 = launch_check(c, "project");
+    if (report) {
+        fill_vof_report(c, &r);
+        r.hf_fallbacks = (long long)llround(c->hbuf[S_FALLBACK]);
+        *report = r;
+    }
+    return st2 ? st2 : solve;
+}
+
 // vof_step_host: the device copies of the state and the copy streams, made
 // at the first call
 static vof_status host_step_setup(vof_ctx* c) {
@@ -403,8 +462,29 @@ vof_status vof_workspace_bytes(const vof_grid* grid, const vof_solver* solver, s
     return VOF_OK;
 }
 
+static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
+                              const vof_solver* solver, size_t budget_bytes, void* stream,
+                              char* arena, size_t arena_bytes, vof_ctx** out);
+
 vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solver* solver,
                       size_t budget_bytes, void* stream, vof_ctx** out) {
+    return create_impl(grid, phys, solver, budget_bytes, stream, nullptr, 0, out);
+}
+
+}  // extern "C"
+
+// a context whose workspace is carved from arena[0, arena_bytes) in a fixed
+// order, so contexts made alike in equal arenas hold every array at the same
+// offset (the ensemble's batched solve relies on it)
+vof_status create_in_arena(const vof_grid* grid, const vof_phys* phys, const vof_solver* solver,
+                           void* stream, void* arena, size_t arena_bytes, vof_ctx** out) {
+    if (!arena || !arena_bytes) return VOF_ERR_ARG;
+    return create_impl(grid, phys, solver, 0, stream, (char*)arena, arena_bytes, out);
+}
+
+static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
+                              const vof_solver* solver, size_t budget_bytes, void* stream,
+                              char* arena, size_t arena_bytes, vof_ctx** out) {
     if (!out) return VOF_ERR_ARG;
     *out = nullptr;
     std::string why;
@@ -427,6 +507,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     if (budget_bytes && need > budget_bytes) return VOF_ERR_ADMISSION;
 
     vof_ctx* c = new vof_ctx();
+    c->arena = arena;
+    c->arena_size = arena_bytes;
     c->g = *grid;
     c->ph = *phys;
     c->sv = *solver;
@@ -508,6 +590,8 @@ vof_status vof_create(const vof_grid* grid, const vof_phys* phys, const vof_solv
     *out = c;
     return VOF_OK;
 }
+
+extern "C" {
 
 vof_status vof_destroy(vof_ctx* c) {
     if (!c) return VOF_ERR_ARG;

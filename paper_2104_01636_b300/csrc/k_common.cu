@@ -20,7 +20,12 @@ Launch launch_cells(int nx, int ny, int nz, int sm_count) {
     return L;
 }
 
-__global__ void k_finalize_sum(const double* __restrict__ part, int n, double* out, double scale) {
+__global__ void k_finalize_sum(Bat t, const double* __restrict__ part, int n, double* out,
+                               double scale) {
+    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    if (bb.off) return;
+    part = bat_at(t, bb.cs, part);
+    out = bat_at(t, bb.cs, out);
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     s = block_sum(s);
@@ -34,8 +39,13 @@ __global__ void k_finalize_max(const double* __restrict__ part, int n, double* o
     if (threadIdx.x == 0) *out = s;
 }
 
-__global__ void k_finalize_dots_beta(const double* __restrict__ pa, const double* __restrict__ pb,
-                                     int n, double* scal) {
+__global__ void k_finalize_dots_beta(Bat t, const double* __restrict__ pa,
+                                     const double* __restrict__ pb, int n, double* scal) {
+    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    if (bb.off) return;
+    pa = bat_at(t, bb.cs, pa);
+    pb = bat_at(t, bb.cs, pb);
+    scal = bat_at(t, bb.cs, scal);
     const double rz = sum_partials(pa, n);
     const double zq = sum_partials(pb, n);
     if (threadIdx.x == 0) {
@@ -46,7 +56,11 @@ __global__ void k_finalize_dots_beta(const double* __restrict__ pa, const double
     }
 }
 
-__global__ void k_finalize_pq_alpha(const double* __restrict__ part, int n, double* scal) {
+__global__ void k_finalize_pq_alpha(Bat t, const double* __restrict__ part, int n, double* scal) {
+    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    if (bb.off) return;
+    part = bat_at(t, bb.cs, part);
+    scal = bat_at(t, bb.cs, scal);
     const double pq = sum_partials(part, n);
     if (threadIdx.x == 0) {
         scal[S_PQ] = pq * 1.0;
@@ -54,18 +68,52 @@ __global__ void k_finalize_pq_alpha(const double* __restrict__ part, int n, doub
     }
 }
 
+// x = 0 and dst = src on FP32 vectors of n4 float4s, batched along y (the
+// batched solve's memset of e and copy of p; one case: a plain launch)
+__global__ void k_zero32x4(Bat t, int n4, float4* __restrict__ x) {
+    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    x = bat_at(t, bb.cs, x);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x)
+        x[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_copy32x4(Bat t, int n4, float4* __restrict__ dst, const float4* __restrict__ src) {
+    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    dst = bat_at(t, bb.cs, dst);
+    src = bat_at(t, bb.cs, src);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x)
+        dst[c] = src[c];
+}
+
+// every case's scalars into the mapped host mirror, MIRROR_DOUBLES per case
+__global__ void k_to_mirror_bat(Bat t, const double* __restrict__ s, double* __restrict__ h,
+                                int n) {
+    const int cs = t.zb ? (int)blockIdx.x : 0;
+    s = bat_at(t, cs, s);
+    if ((int)threadIdx.x < n) h[(size_t)cs * MIRROR_DOUBLES + threadIdx.x] = s[threadIdx.x];
+    __threadfence_system();
+}
+
 void finalize_dots_beta(vof_ctx* c, int nparts) {
-    VOF_LAUNCH(c, k_finalize_dots_beta, 1, 1024, c->part + (size_t)S_RZ * MAX_PARTIALS,
+    dim3 g(1);
+    const Bat b = bat_of(c, g.x);
+    VOF_LAUNCH(c, k_finalize_dots_beta, g, 1024, b, c->part + (size_t)S_RZ * MAX_PARTIALS,
                c->part + (size_t)S_ZQ * MAX_PARTIALS, nparts, c->scal);
 }
 
 void finalize_pq_alpha(vof_ctx* c, int nparts) {
-    VOF_LAUNCH(c, k_finalize_pq_alpha, 1, 1024, c->part + (size_t)S_PQ * MAX_PARTIALS, nparts,
+    dim3 g(1);
+    const Bat b = bat_of(c, g.x);
+    VOF_LAUNCH(c, k_finalize_pq_alpha, g, 1024, b, c->part + (size_t)S_PQ * MAX_PARTIALS, nparts,
                c->scal);
 }
 
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale) {
-    VOF_LAUNCH(c, k_finalize_sum, 1, 1024, c->part + (size_t)slot * MAX_PARTIALS, nparts,
+    dim3 g(1);
+    const Bat b = bat_of(c, g.x);
+    VOF_LAUNCH(c, k_finalize_sum, g, 1024, b, c->part + (size_t)slot * MAX_PARTIALS, nparts,
                                           c->scal + dst, scale);
 }
 
@@ -121,5 +169,33 @@ void readback(vof_ctx* c) {
         cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost,
                         c->st);
     }
+    cudaStreamSynchronize(c->st);
+}
+
+static int flat_blocks4(int n4) {
+    int b = (n4 + 255) / 256;
+    return b < 1 ? 1 : (b > 1184 ? 1184 : b);
+}
+
+void launch_zero32_bat(vof_ctx* c, float* x, int n) {
+    dim3 g(flat_blocks4(n / 4));
+    const Bat b = bat_of(c, g.y);
+    VOF_LAUNCH(c, k_zero32x4, g, 256, b, n / 4, (float4*)x);
+}
+
+void launch_copy32_bat(vof_ctx* c, float* dst, const float* src, int n) {
+    dim3 g(flat_blocks4(n / 4));
+    const Bat b = bat_of(c, g.y);
+    VOF_LAUNCH(c, k_copy32x4, g, 256, b, n / 4, (float4*)dst, (const float4*)src);
+}
+
+// mirror_dev: the device address of a mapped page-locked buffer of
+// c->bat_n x MIRROR_DOUBLES doubles; every case's scalars, not only the
+// running ones, then a wait on the stream
+void readback_batch(vof_ctx* c, double* mirror_dev) {
+    dim3 g(1);
+    Bat b = bat_of(c, g.x);
+    b.act = nullptr;
+    VOF_LAUNCH(c, k_to_mirror_bat, g, MIRROR_DOUBLES, b, c->scal, mirror_dev, (int)S_NSCALARS);
     cudaStreamSynchronize(c->st);
 }

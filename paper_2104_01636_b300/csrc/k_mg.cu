@@ -84,14 +84,24 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
 // CT is the coefficients' storage type (T, or FP16 copies on a large coarse
 // level of the FP32 cycle).
 template <class T, int MODE, class CT>
-__global__ void k_rbgs_pair_t(Dims d, T h2, const CT* __restrict__ bx, const CT* __restrict__ by,
-                              const CT* __restrict__ bz, const T* __restrict__ xr,
-                              T* __restrict__ xw, const T* __restrict__ f, int color, int kchunk,
-                              Dims dc, const T* __restrict__ xc, T omega) {
+__global__ void k_rbgs_pair_t(Bat bt, Dims d, T h2, const CT* __restrict__ bx,
+                              const CT* __restrict__ by, const CT* __restrict__ bz,
+                              const T* __restrict__ xr, T* __restrict__ xw,
+                              const T* __restrict__ f, int color, int kchunk, Dims dc,
+                              const T* __restrict__ xc, T omega) {
     pdl_wait();
+    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    bx = bat_at(bt, bb.cs, bx);
+    by = bat_at(bt, bb.cs, by);
+    bz = bat_at(bt, bb.cs, bz);
+    xr = bat_at(bt, bb.cs, xr);
+    xw = bat_at(bt, bb.cs, xw);
+    f = bat_at(bt, bb.cs, f);
+    if (xc) xc = bat_at(bt, bb.cs, xc);
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (t >= (d.nx >> 1) || j >= d.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, d.nz);
 #pragma unroll 2
     for (int k = k0; k < k1; ++k)
         rbgs_cell<T, MODE>(d, h2, bx, by, bz, xr, xw, f, 2 * t + ((j + k + color) & 1), j, k, dc,
@@ -126,14 +136,22 @@ __device__ __forceinline__ float2 cpair(const __half* a, int c) {
 // CT: FP32 coefficients, or the level's FP16 copies (the colour passes of
 // the same level read the same copies, so the cycle keeps one operator).
 template <class CT>
-__global__ void k_restrict_pair_f(Dims df, float ih2f, const CT* __restrict__ bx,
+__global__ void k_restrict_pair_f(Bat bt, Dims df, float ih2f, const CT* __restrict__ bx,
                                   const CT* __restrict__ by, const CT* __restrict__ bz,
                                   const float* __restrict__ xf, const float* __restrict__ ff,
                                   Dims dc, float* __restrict__ fc, int kchunk) {
     pdl_wait();
+    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    bx = bat_at(bt, bb.cs, bx);
+    by = bat_at(bt, bb.cs, by);
+    bz = bat_at(bt, bb.cs, bz);
+    xf = bat_at(bt, bb.cs, xf);
+    ff = bat_at(bt, bb.cs, ff);
+    fc = bat_at(bt, bb.cs, fc);
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, dc.nz);
     const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
     auto cp2 = [](const CT* a, int c) { return cpair(a, c); };
@@ -180,12 +198,16 @@ __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __res
 
 // The same for a fine level with an even nx: a thread adds the correction
 // of parent I to the fine pair (2I, 2I+1) with one 8-byte load and store.
-__global__ void k_prolong_pair_f(Dims dc, const float* __restrict__ xc, Dims df,
+__global__ void k_prolong_pair_f(Bat bt, Dims dc, const float* __restrict__ xc, Dims df,
                                  float* __restrict__ xf, float omega, int kchunk) {
     pdl_wait();
+    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    xc = bat_at(bt, bb.cs, xc);
+    xf = bat_at(bt, bb.cs, xf);
     const int I = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (2 * I >= df.nx || j >= df.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, df.nz);
+    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, df.nz);
     for (int k = k0; k < k1; ++k) {
         const float cv = xc[cid(dc, I, j >> 1, k >> 1)];
         float2* p = reinterpret_cast<float2*>(xf + cid(df, 2 * I, j, k));
@@ -542,9 +564,14 @@ __global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const
 
 // x = Minv f: one warp per row (dense_row)
 template <class T>
-__global__ void k_dense_apply(int n, const T* __restrict__ Minv, const T* __restrict__ f,
+__global__ void k_dense_apply(Bat bt, int n, const T* __restrict__ Minv, const T* __restrict__ f,
                               T* __restrict__ x) {
     pdl_wait();
+    const BatBlk bb = bat_blk(bt, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    Minv = bat_at(bt, bb.cs, Minv);
+    f = bat_at(bt, bb.cs, f);
+    x = bat_at(bt, bb.cs, x);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const double s = dense_row(Minv + (long)warp * n, [&](int j) { return f[j]; }, n, lane);
@@ -634,8 +661,13 @@ __global__ void k_p_update32(int n, float* __restrict__ p, const float* __restri
 }
 
 // the same with 16-byte loads and stores (n4 = n / 4, 16-byte aligned arrays)
-__global__ void k_p_update32x4(int n4, float4* __restrict__ p, const float4* __restrict__ z,
-                               const double* __restrict__ scal) {
+__global__ void k_p_update32x4(Bat t, int n4, float4* __restrict__ p,
+                               const float4* __restrict__ z, const double* __restrict__ scal) {
+    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    p = bat_at(t, bb.cs, p);
+    z = bat_at(t, bb.cs, z);
+    scal = bat_at(t, bb.cs, scal);
     const float be = (float)scal[S_BETA];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
         const float4 zv = z[c];
@@ -650,9 +682,17 @@ __global__ void k_p_update32x4(int n4, float4* __restrict__ p, const float4* __r
 
 // k_cg_update32 with 16-byte loads and stores; each thread's (r, r) terms
 // are summed four at a time, in order
-__global__ void k_cg_update32x4(int n4, float4* __restrict__ e, float4* __restrict__ r,
+__global__ void k_cg_update32x4(Bat t, int n4, float4* __restrict__ e, float4* __restrict__ r,
                                 const float4* __restrict__ p, const float4* __restrict__ q,
                                 const double* __restrict__ scal, double* __restrict__ part) {
+    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    e = bat_at(t, bb.cs, e);
+    r = bat_at(t, bb.cs, r);
+    p = bat_at(t, bb.cs, p);
+    q = bat_at(t, bb.cs, q);
+    scal = bat_at(t, bb.cs, scal);
+    part = bat_at(t, bb.cs, part);
     const float al = (float)scal[S_ALPHA];
     Kahan ks;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
@@ -710,7 +750,12 @@ __global__ void k_to_f64(int n, const float* __restrict__ a, double* __restrict_
 
 // the same three with 16-byte accesses, four values per thread and pass
 // (n4 = n / 4; arrays 16-byte aligned)
-__global__ void k_add_f32_to_f64x4(int n4, const float4* __restrict__ e, double2* __restrict__ x) {
+__global__ void k_add_f32_to_f64x4(Bat t, int n4, const float4* __restrict__ e,
+                                   double2* __restrict__ x) {
+    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    e = bat_at(t, bb.cs, e);
+    x = bat_at(t, bb.cs, x);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
         const float4 ev = e[c];
         double2 lo = x[2 * c], hi = x[2 * c + 1];
@@ -765,8 +810,8 @@ LA<float> arrays<float>(const Level& L) {
 template <class T, class CT>
 void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, const CT* bz,
                const LA<T>& a, int color, int mode, const Level* C, int cls) {
-    using K = void (*)(Dims, T, const CT*, const CT*, const CT*, const T*, T*, const T*, int, int,
-                       Dims, const T*, T);
+    using K = void (*)(Bat, Dims, T, const CT*, const CT*, const CT*, const T*, T*, const T*, int,
+                       int, Dims, const T*, T);
     const K kern = mode == 1 ? k_rbgs_pair_t<T, 1, CT>
                              : (mode == 2 ? k_rbgs_pair_t<T, 2, CT> : k_rbgs_pair_t<T, 0, CT>);
     const Dims dc = C ? C->d : L.d;
@@ -776,9 +821,10 @@ void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, con
     // halve the z chunks to keep about as many blocks in flight
     const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
     const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
-    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
+    dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
+    const Bat bt = bat_of(c, grid.z);
     int m = timer_begin(c, cls);
-    launch_pdl(c, kern, grid, L.L.block, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f, color,
+    launch_pdl(c, kern, grid, L.L.block, bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f, color,
                kchunk, dc, xc, omega);
     timer_end(c, cls, m);
 }
@@ -819,16 +865,20 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
         VOF_LAUNCH(c, k_restrict_fw_t<T>, C.L.grid, C.L.block, F.d, (const T*)r, C.d, b.f,
                    C.L.kchunk);
     } else {
-        if (sizeof(T) == sizeof(float) && F.bxh)
-            launch_pdl(c, k_restrict_pair_f<__half>, C.L.grid, C.L.block, F.d,
+        dim3 g = C.L.grid;
+        if (sizeof(T) == sizeof(float) && F.bxh) {
+            const Bat bt = bat_of(c, g.z);
+            launch_pdl(c, k_restrict_pair_f<__half>, g, C.L.block, bt, F.d,
                        (float)(1.0 / (F.h * F.h)) * F.hscale, (const __half*)F.bxh, (const __half*)F.byh,
                        (const __half*)F.bzh, (const float*)a.x, (const float*)a.f, C.d,
                        (float*)b.f, C.L.kchunk);
-        else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0)
-            launch_pdl(c, k_restrict_pair_f<float>, C.L.grid, C.L.block, F.d,
+        } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
+            const Bat bt = bat_of(c, g.z);
+            launch_pdl(c, k_restrict_pair_f<float>, g, C.L.block, bt, F.d,
                        (float)(1.0 / (F.h * F.h)), (const float*)a.bx, (const float*)a.by,
                        (const float*)a.bz, (const float*)a.x, (const float*)a.f, C.d, (float*)b.f,
                        C.L.kchunk);
+        }
         else
             launch_pdl(c, k_restrict_t<T>, C.L.grid, C.L.block, F.d, (T)(1.0 / (F.h * F.h)),
                        a.bx, a.by, a.bz, a.x, a.f, C.d, b.f, C.L.kchunk);
@@ -847,9 +897,10 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
                    F.L.kchunk);
     else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
         const int kchunk = std::max(1, (F.L.kchunk + 1) / 2);  // half the blocks across
-        launch_pdl(c, k_prolong_pair_f,
-                   dim3((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, (F.d.nz + kchunk - 1) / kchunk),
-                   F.L.block, C.d, (const float*)a.x, F.d, (float*)b.x, (float)omega, kchunk);
+        dim3 g((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, (F.d.nz + kchunk - 1) / kchunk);
+        const Bat bt = bat_of(c, g.z);
+        launch_pdl(c, k_prolong_pair_f, g, F.L.block, bt, C.d, (const float*)a.x, F.d,
+                   (float*)b.x, (float)omega, kchunk);
     }
     else
         launch_pdl(c, k_prolong_t<T>, F.L.grid, F.L.block, C.d, a.x, F.d, b.x, omega, F.L.kchunk);
@@ -923,7 +974,9 @@ void mg_coarse(vof_ctx* c, const Level& L) {
     if (c->dense_n > 0) {
         const int n = L.ncells;
         const T* Minv = sizeof(T) == 4 ? (const T*)c->dense_inv_f : (const T*)c->dense_inv;
-        launch_pdl(c, k_dense_apply<T>, dim3((n * 32 + 255) / 256), dim3(256), n, Minv, a.f, a.x);
+        dim3 g((n * 32 + 255) / 256);
+        const Bat bt = bat_of(c, g.y);
+        launch_pdl(c, k_dense_apply<T>, g, dim3(256), bt, n, Minv, a.f, a.x);
         timer_end(c, T_COARSE, m);
         return;
     }
@@ -955,10 +1008,12 @@ int k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const f
     const bool v4 = vec4_ok(n, {e, r, p, q});
     const int nb = flat_blocks(v4 ? n / 4 : n);
     int m = timer_begin(c, T_KRYLOV);
-    if (v4)
-        VOF_LAUNCH(c, k_cg_update32x4, nb, 256, n / 4, (float4*)e, (float4*)r, (const float4*)p,
+    if (v4) {
+        dim3 g(nb);
+        const Bat b = bat_of(c, g.y);
+        VOF_LAUNCH(c, k_cg_update32x4, g, 256, b, n / 4, (float4*)e, (float4*)r, (const float4*)p,
                    (const float4*)q, c->scal, c->part + (size_t)slot * MAX_PARTIALS);
-    else
+    } else
         VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
                    c->part + (size_t)slot * MAX_PARTIALS);
     timer_end(c, T_KRYLOV, m);
@@ -977,20 +1032,22 @@ void k32_dot2(vof_ctx* c, int n, const float* z, const float* r, const float* q)
 
 void k32_p_update(vof_ctx* c, int n, float* p, const float* z) {
     int m = timer_begin(c, T_KRYLOV);
-    if (vec4_ok(n, {p, z}))
-        VOF_LAUNCH(c, k_p_update32x4, flat_blocks(n / 4), 256, n / 4, (float4*)p,
-                   (const float4*)z, c->scal);
-    else
+    if (vec4_ok(n, {p, z})) {
+        dim3 g(flat_blocks(n / 4));
+        const Bat b = bat_of(c, g.y);
+        VOF_LAUNCH(c, k_p_update32x4, g, 256, b, n / 4, (float4*)p, (const float4*)z, c->scal);
+    } else
         VOF_LAUNCH(c, k_p_update32, flat_blocks(n), 256, n, p, z, c->scal);
     timer_end(c, T_KRYLOV, m);
 }
 
 void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x) {
     int m = timer_begin(c, T_KRYLOV);
-    if (vec4_ok(n, {e, x}))
-        VOF_LAUNCH(c, k_add_f32_to_f64x4, flat_blocks(n / 4), 256, n / 4, (const float4*)e,
-                   (double2*)x);
-    else
+    if (vec4_ok(n, {e, x})) {
+        dim3 g(flat_blocks(n / 4));
+        const Bat b = bat_of(c, g.y);
+        VOF_LAUNCH(c, k_add_f32_to_f64x4, g, 256, b, n / 4, (const float4*)e, (double2*)x);
+    } else
         VOF_LAUNCH(c, k_add_f32_to_f64, flat_blocks(n), 256, n, e, x);
     timer_end(c, T_KRYLOV, m);
 }

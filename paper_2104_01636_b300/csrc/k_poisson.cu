@@ -146,11 +146,22 @@ __global__ void k_residual(Dims d, double ih2, const double* __restrict__ bx,
 
 // r = f - A x in FP64, stored as FP32 (the inner right side of the mixed
 // solve), with block partials of the FP64 r.r
-__global__ void k_residual_to32(Dims d, double ih2, const double* __restrict__ bx,
+__global__ void k_residual_to32(Bat t, Dims d, double ih2, const double* __restrict__ bx,
                                 const double* __restrict__ by, const double* __restrict__ bz,
                                 const double* __restrict__ x, const double* __restrict__ f,
                                 float* __restrict__ r32, double* __restrict__ part, int kchunk) {
+    const BatBlk bb = bat_blk(t, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    bx = bat_at(t, bb.cs, bx);
+    by = bat_at(t, bb.cs, by);
+    bz = bat_at(t, bb.cs, bz);
+    x = bat_at(t, bb.cs, x);
+    f = bat_at(t, bb.cs, f);
+    r32 = bat_at(t, bb.cs, r32);
+    part = bat_at(t, bb.cs, part);
     CellIdx r = cell_range(d, kchunk);
+    r.k0 = bb.b * kchunk;
+    r.k1 = min(r.k0 + kchunk, d.nz);
     double acc = 0.0;
     if (r.act)
         for (int k = r.k0; k < r.k1; ++k) {
@@ -160,7 +171,7 @@ __global__ void k_residual_to32(Dims d, double ih2, const double* __restrict__ b
             acc += v * v;
         }
     acc = block_sum(acc);
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear_z(bb)] = acc;
 }
 
 // ---- flat vector kernels (fixed grid => deterministic partials) ----------
@@ -394,7 +405,9 @@ void launch_residual(vof_ctx* c, const Level& l, const double* x, const double* 
 void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r32, int slot) {
     const Level& l = c->lv[0];
     int m = timer_begin(c, T_RESIDUAL);
-    VOF_LAUNCH(c, k_residual_to32, l.L.grid, l.L.block, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz,
+    dim3 g = l.L.grid;
+    const Bat b = bat_of(c, g.z);
+    VOF_LAUNCH(c, k_residual_to32, g, l.L.block, b, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz,
                x, f, r32, c->part + (size_t)slot * MAX_PARTIALS, l.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
     finalize_sum(c, slot, l.L.nblocks, slot, 1.0);

@@ -35,17 +35,22 @@ namespace {
 constexpr int STX = 32, STY = 32;            // tile of a sweep block
 constexpr int SBX = STX + 8, SBY = STY + 4;   // x box (FP32): x from i0-4 (16-byte aligned), y from j0-2
 constexpr int HBX = STX + 16;                 // density box (FP16): x from i0-8 (16-byte aligned)
-constexpr int RNX = STX + 2, RNY = STY + 2;   // first-colour values on the tile and its ring
+constexpr int RNX = STX + 2, RNY = STY + 2;   // the tile and its ring
+constexpr int NCX = RNX / 2;                  // first-colour cells per ring-region row (stored compactly)
+constexpr int NPL = NCX * RNY;                // floats per first-colour plane
 constexpr int NSLOT = 4;                      // staged planes: 3 in use, 1 in flight
 constexpr int XPLANE = SBX * SBY;             // floats per staged x plane
 constexpr int HPLANE = HBX * SBY;             // halves per staged density plane
 constexpr int WAIT_LIMIT = 1 << 20;           // bounded waits on the TMA barriers
+constexpr int SWEEP_BLOCKS_PER_SM = 5;        // resident sweep blocks per SM (registers <= 48)
 constexpr size_t SWEEP_SMEM = (size_t)NSLOT * XPLANE * sizeof(float) +
                               (size_t)NSLOT * HPLANE * sizeof(__half) +
-                              (size_t)3 * RNX * RNY * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
+                              (size_t)3 * NPL * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
 static_assert(sizeof(CUtensorMap) == 128, "tensor map storage in the context is 128 bytes");
 static_assert((SBX * sizeof(float)) % 16 == 0 && (HBX * sizeof(__half)) % 16 == 0,
               "TMA box rows must be a multiple of 16 bytes");
+static_assert(SWEEP_SMEM + 1024 <= 228 * 1024 / SWEEP_BLOCKS_PER_SM,
+              "shared memory of SWEEP_BLOCKS_PER_SM resident sweep blocks");
 static_assert((XPLANE * sizeof(float)) % 128 == 0 && (HPLANE * sizeof(__half)) % 128 == 0,
               "staged planes keep 128-byte alignment");
 
@@ -80,12 +85,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z) {
+// a box of plane z of case w (the fourth axis: the cases of a batched
+// launch, 0 for a single case)
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z, int w) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
         : "memory");
 }
 
@@ -100,6 +107,7 @@ struct SweepArgs {
     // DOT sweeps: block partials of (x_new, f) and (x_new, q) into pa, pb
     const float* q;
     double *pa, *pb;
+    Bat bt;  // the batch (Bat{} for a single case); the TMA maps carry the cases as a fourth axis
 };
 
 // 1 / (rho_L + rho_R), half the face coefficient: every finest-level kernel
@@ -123,22 +131,32 @@ __device__ __forceinline__ float hval(const __half* h, int o) { return __half2fl
 // (the preconditioner's last sweep forms the Krylov dots (z, r), (z, q)
 // from the z it writes, r being its right side).
 template <bool ZERO, bool DOT>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, SWEEP_BLOCKS_PER_SM)
     k_sweep_rho(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_rho,
-                SweepArgs a) {
+                SweepArgs a0) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     float* sX = reinterpret_cast<float*>(smem_raw + (((raw + 127u) & ~127u) - raw));
     __half* sH = reinterpret_cast<__half*>(sX + NSLOT * XPLANE);
     float* sN = reinterpret_cast<float*>(sH + NSLOT * HPLANE);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sN + 3 * RNX * RNY);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sN + 3 * NPL);
 
+    const BatBlk bb = bat_blk(a0.bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    SweepArgs a = a0;
+    a.f = bat_at(a0.bt, bb.cs, a0.f);
+    a.xout = bat_at(a0.bt, bb.cs, a0.xout);
+    a.err = bat_at(a0.bt, bb.cs, a0.err);
+    a.q = bat_at(a0.bt, bb.cs, a0.q);
+    a.pa = bat_at(a0.bt, bb.cs, a0.pa);
+    a.pb = bat_at(a0.bt, bb.cs, a0.pb);
+    const int blin = block_linear_z(bb);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 16 * ty;
     const int i0 = blockIdx.x * STX, j0 = blockIdx.y * STY;
-    const int k0 = blockIdx.z * a.kchunk;
+    const int k0 = bb.b * a.kchunk;
     const int k1 = min(k0 + a.kchunk, a.nz);
     if (k0 >= k1) {  // whole block
-        if (DOT && threadIdx.x == 0 && threadIdx.y == 0) a.pa[block_linear()] = a.pb[block_linear()] = 0.0;
+        if (DOT && threadIdx.x == 0 && threadIdx.y == 0) a.pa[blin] = a.pb[blin] = 0.0;
         return;
     }
     const int pbase = k0 - 2;  // first staged plane (unwrapped index)
@@ -156,8 +174,8 @@ __global__ void __launch_bounds__(256, 4)
         const int s = (p - pbase) % NSLOT;
         const int z = wrapk(p, a.nz);
         mbar_expect_tx(&bar[s], bytes);
-        if (!ZERO) tma_load_3d(sX + s * XPLANE, &tm_x, &bar[s], i0 - 4, j0 - 2, z);
-        tma_load_3d(sH + s * HPLANE, &tm_rho, &bar[s], i0 - 8, j0 - 2, z);
+        if (!ZERO) tma_load_4d(sX + s * XPLANE, &tm_x, &bar[s], i0 - 4, j0 - 2, z, bb.cs);
+        tma_load_4d(sH + s * HPLANE, &tm_rho, &bar[s], i0 - 8, j0 - 2, z, bb.cs);
         issued = p;
     };
     if (tid == 0)
@@ -179,7 +197,10 @@ __global__ void __launch_bounds__(256, 4)
     const bool ylA = jA > 0, yhA = jA < ny - 1, yhB = jB < ny - 1;  // jB > 0 always
     const int oA = (ty + 2) * SBX + 2 * tx + 4, oB = oA + 16 * SBX;  // x-box offsets of (ib, jA/jB)
     const int hA = (ty + 2) * HBX + 2 * tx + 8, hB = hA + 16 * HBX;  // density-box offsets
-    const int nA = (ty + 1) * RNX + 2 * tx + 1, nB = nA + 16 * RNX;  // first-colour offsets
+    // first-colour values are stored compactly, one per two cells of a region
+    // row: region column r (0..33) at r / 2. The thread's pair (2tx+1, 2tx+2)
+    // holds its first-colour cell at nA + P, P the cell's offset in the pair.
+    const int nA = (ty + 1) * NCX + tx, nB = nA + 16 * NCX;
     const size_t plane = (size_t)ny * nx;
     const float h2h = a.h2half;
     const float* __restrict__ fg = a.f;
@@ -223,9 +244,9 @@ __global__ void __launch_bounds__(256, 4)
     // slots of planes k, k+1, k+2 and first-colour planes k-1, k, k+1
     int S1 = 0, S2 = 1, S3 = 2;
     uint32_t par3 = 0;  // parity of slot S3's current fill
-    float* N0 = sN + 2 * (RNX * RNY);
+    float* N0 = sN + 2 * NPL;
     float* N1 = sN;
-    float* N2 = sN + (RNX * RNY);
+    float* N2 = sN + NPL;
     float2 bup1 = make_float2(0.f, 0.f), bup2 = make_float2(0.f, 0.f);  // z+ coefficients, 1 and 2 planes back
 
     for (int k = pbase; k < k1; ++k) {
@@ -302,7 +323,7 @@ __global__ void __launch_bounds__(256, 4)
                     b = half_beta(r0, hval(Hp, h)); if (!ZERO) rn = fmaf(b, Xp[o], rn); rd += b;
                     v = __fdividef(rn, rd);
                 }
-                N2[(rj - j0 + 1) * RNX + (ri - i0 + 1)] = v;
+                N2[(rj - j0 + 1) * NCX + ((ri - i0 + 1) >> 1)] = v;
             }
         }
         if (__syncthreads_or(bad)) {
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(256, 4)
                     for (int it = 0; !mbar_try_wait(&bar[s], par) && it < WAIT_LIMIT; ++it) {
                     }
                 }
-                if (DOT) a.pa[block_linear()] = a.pb[block_linear()] = 0.0;
+                if (DOT) a.pa[blin] = a.pb[blin] = 0.0;
             }
             return;
         }
@@ -336,19 +357,19 @@ __global__ void __launch_bounds__(256, 4)
             {
                 float2 b = half_beta2(rc, make_float2(hval(Hk, ha - 1), hval(Hk, hb - 1)));
                 if (i == 0) b = make_float2(0.f, 0.f);
-                acc(b, make_float2(N1[na - 1], N1[nb - 1]));
+                acc(b, make_float2(N1[nA], N1[nB]));  // first colour at ib + P - 1
                 b = half_beta2(rc, make_float2(hval(Hk, ha + 1), hval(Hk, hb + 1)));
                 if (i == nx - 1) b = make_float2(0.f, 0.f);
-                acc(b, make_float2(N1[na + 1], N1[nb + 1]));
+                acc(b, make_float2(N1[nA + 1], N1[nB + 1]));  // at ib + P + 1
             }
             {
                 float2 b = half_beta2(rc, make_float2(hval(Hk, ha - HBX), hval(Hk, hb - HBX)));
                 if (!ylA) b.x = 0.f;
-                acc(b, make_float2(N1[na - RNX], N1[nb - RNX]));
+                acc(b, make_float2(N1[na - NCX], N1[nb - NCX]));
                 b = half_beta2(rc, make_float2(hval(Hk, ha + HBX), hval(Hk, hb + HBX)));
                 if (!yhA) b.x = 0.f;
                 if (!yhB) b.y = 0.f;
-                acc(b, make_float2(N1[na + RNX], N1[nb + RNX]));
+                acc(b, make_float2(N1[na + NCX], N1[nb + NCX]));
             }
             acc(bup2, make_float2(N0[na], N0[nb]));   // face (k-1, k), from the first colour of plane k-1
             acc(bdown, make_float2(N2[na], N2[nb]));  // face (k, k+1), from the first colour of plane k+1
@@ -401,8 +422,8 @@ __global__ void __launch_bounds__(256, 4)
         const double sf = block_sum((double)dzf.x + (double)dzf.y);
         const double sq = block_sum((double)dzq.x + (double)dzq.y);
         if (tid == 0) {
-            a.pa[block_linear()] = sf;
-            a.pb[block_linear()] = sq;
+            a.pa[blin] = sf;
+            a.pb[blin] = sq;
         }
     }
 }
@@ -412,12 +433,18 @@ __global__ void __launch_bounds__(256, 4)
 // (each leaves one child and enters another), so only the 24 faces on the
 // block's boundary are formed:
 //   sum_c r_c = sum_c f_c - (1/h^2) sum_{boundary f} beta_f (x_in - x_out).
-__global__ void k_restrict_rho(Dims df, float ih2, const __half* __restrict__ rho,
+__global__ void k_restrict_rho(Bat bt, Dims df, float ih2, const __half* __restrict__ rho,
                                const float* __restrict__ xf, const float* __restrict__ ff, Dims dc,
                                float* __restrict__ fc, int kchunk) {
+    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    rho = bat_at(bt, bb.cs, rho);
+    xf = bat_at(bt, bb.cs, xf);
+    ff = bat_at(bt, bb.cs, ff);
+    fc = bat_at(bt, bb.cs, fc);
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, dc.nz);
     const int sy = df.nx;
     const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     // the two children of a row (a = 0, 1) are adjacent in x: their x, f and
@@ -551,13 +578,19 @@ __global__ void k_wait_probe(double* __restrict__ err, int limit) {
 // loads, the two outer x neighbours as scalars. Each cell's stencil is
 // summed in the order of k_apply_A_dot_rho32; the thread's partial of p.q
 // takes the pair's two cells in turn.
-__global__ void k_apply_A_dot_rho32_pair(Dims d, float ih2, const float* __restrict__ rho,
+__global__ void k_apply_A_dot_rho32_pair(Bat bt, Dims d, float ih2, const float* __restrict__ rho,
                                          const float* __restrict__ p, float* __restrict__ q,
                                          double* __restrict__ part, int kchunk) {
+    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    rho = bat_at(bt, bb.cs, rho);
+    p = bat_at(bt, bb.cs, p);
+    q = bat_at(bt, bb.cs, q);
+    part = bat_at(bt, bb.cs, part);
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     const int i = 2 * t;
     const bool act = i < d.nx && j < d.ny;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
+    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, d.nz);
     Kahan32 ks;
     if (act && k0 < k1) {
         auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
@@ -611,7 +644,7 @@ __global__ void k_apply_A_dot_rho32_pair(Dims d, float ih2, const float* __restr
         }
     }
     const double acc = block_sum(ks.value());
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear_z(bb)] = acc;
 }
 
 // ---- tensor maps -------------------------------------------------------------
@@ -635,18 +668,22 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// a (nx, ny, nz) array of 4- or 2-byte elements staged in box_x x SBY x 1
-// boxes, zero outside
-bool encode_plane_map(void* store, const Dims& d, const void* base, bool half, int box_x) {
+// ncase (nx, ny, nz) arrays of 4- or 2-byte elements, case_stride bytes
+// apart (0: a single array), staged in box_x x SBY x 1 boxes, zero outside
+bool encode_plane_map(void* store, const Dims& d, const void* base, bool half, int box_x,
+                      int ncase = 1, long long case_stride = 0) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
     const size_t e = half ? sizeof(__half) : sizeof(float);
-    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * e, (cuuint64_t)d.nx * d.ny * e};
-    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)SBY, 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const cuuint64_t vol = (cuuint64_t)d.nx * d.ny * d.nz * e;
+    const cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz,
+                                (cuuint64_t)ncase};
+    const cuuint64_t strides[3] = {(cuuint64_t)d.nx * e, (cuuint64_t)d.nx * d.ny * e,
+                                   ncase > 1 ? (cuuint64_t)case_stride : vol};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)SBY, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     return fn(reinterpret_cast<CUtensorMap*>(store),
-              half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
               const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -672,12 +709,28 @@ vof_status rho_path_setup(vof_ctx* c) {
         cudaFuncSetAttribute(k_sweep_rho<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SWEEP_SMEM) != cudaSuccess)
         return cuda_check(c, cudaGetLastError(), "smoother shared-memory attribute");
-    // z chunks: about four resident blocks per SM over the whole grid
+    // z chunks: one wave of resident blocks over the whole grid
     const int tiles = ((L0.d.nx + STX - 1) / STX) * ((L0.d.ny + STY - 1) / STY);
-    int zc = std::max(1, (4 * c->sm_count + tiles / 2) / tiles);
+    int zc = std::max(1, (SWEEP_BLOCKS_PER_SM * c->sm_count) / tiles);
     zc = std::min(zc, L0.d.nz);
-    c->sweep_kchunk = (L0.d.nz + zc - 1) / zc;
+    // at least four planes per block: a block also stages and recomputes
+    // two planes below its chunk, which for one plane would triple the work
+    // (small grids; the batched ensemble runs many such grids at once)
+    c->sweep_kchunk = std::max((L0.d.nz + zc - 1) / zc, std::min(4, L0.d.nz));
     c->sweep_dot = (long)tiles * ((L0.d.nz + c->sweep_kchunk - 1) / c->sweep_kchunk) <= MAX_PARTIALS;
+    return VOF_OK;
+}
+
+// the TMA maps of a batched solve through case 0's context: every map also
+// spans the nc cases, case_stride bytes apart (nc = 1: a single case)
+vof_status rho_path_batch_maps(vof_ctx* c, int nc, long long case_stride) {
+    const Level& L0 = c->lv[0];
+    if (nc > 1 && case_stride % 16 != 0)
+        return set_err(c, VOF_ERR_ARG, "batched TMA maps need a 16-byte case stride");
+    if (!encode_plane_map(c->tmap[0], L0.d, L0.xf, false, SBX, nc, case_stride) ||
+        !encode_plane_map(c->tmap[1], L0.d, c->x32b, false, SBX, nc, case_stride) ||
+        !encode_plane_map(c->tmap[2], L0.d, c->rho16, true, HBX, nc, case_stride))
+        return set_err(c, VOF_ERR_CUDA, "TMA tensor-map encoding is unavailable");
     return VOF_OK;
 }
 
@@ -701,8 +754,10 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
     const CUtensorMap* tx =
         reinterpret_cast<const CUtensorMap*>(src == c->x32b ? c->tmap[1] : c->tmap[0]);
     const CUtensorMap* tr = reinterpret_cast<const CUtensorMap*>(c->tmap[2]);
-    const dim3 grid((a.nx + STX - 1) / STX, (a.ny + STY - 1) / STY,
+    const dim3 solo((a.nx + STX - 1) / STX, (a.ny + STY - 1) / STY,
                     (a.nz + a.kchunk - 1) / a.kchunk);
+    dim3 grid = solo;
+    a.bt = bat_of(c, grid.z);
     int m = timer_begin(c, T_SMOOTH0);
     ++c->nlaunch;
     if (src == nullptr)
@@ -712,7 +767,7 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
     else
         k_sweep_rho<false, true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     timer_end(c, T_SMOOTH0, m);
-    if (dot) finalize_dots_beta(c, (int)(grid.x * grid.y * grid.z));
+    if (dot) finalize_dots_beta(c, (int)(solo.x * solo.y * solo.z));
 }
 
 void wait_probe(vof_ctx* c, int limit) {
@@ -723,7 +778,9 @@ void wait_probe(vof_ctx* c, int limit) {
 void rho_restrict(vof_ctx* c) {
     const Level &F = c->lv[0], &C = c->lv[1];
     int m = timer_begin(c, T_RESTRICT0);
-    VOF_LAUNCH(c, k_restrict_rho, C.L.grid, C.L.block, F.d, (float)(1.0 / (F.h * F.h)),
+    dim3 g = C.L.grid;
+    const Bat bt = bat_of(c, g.z);
+    VOF_LAUNCH(c, k_restrict_rho, g, C.L.block, bt, F.d, (float)(1.0 / (F.h * F.h)),
                (const __half*)c->rho16, F.xf, F.ff, C.d, C.ff, C.L.kchunk);
     timer_end(c, T_RESTRICT0, m);
 }
@@ -736,9 +793,11 @@ void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
     int kchunk = std::max(1, (L.L.kchunk + 1) / 2);
     if ((long)gx * L.L.grid.y * ((L.d.nz + kchunk - 1) / kchunk) > MAX_PARTIALS) kchunk = L.L.kchunk;
-    const dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
-    VOF_LAUNCH(c, k_apply_A_dot_rho32_pair, grid, L.L.block, L.d, (float)(1.0 / (L.h * L.h)),
+    const dim3 solo(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
+    dim3 grid = solo;
+    const Bat bt = bat_of(c, grid.z);
+    VOF_LAUNCH(c, k_apply_A_dot_rho32_pair, grid, L.L.block, bt, L.d, (float)(1.0 / (L.h * L.h)),
                c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, kchunk);
     timer_end(c, T_RESIDUAL, m);
-    finalize_pq_alpha(c, (int)(grid.x * grid.y * grid.z));
+    finalize_pq_alpha(c, (int)(solo.x * solo.y * solo.z));
 }

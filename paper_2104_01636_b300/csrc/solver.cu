@@ -930,3 +930,225 @@ vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report*
                            std::to_string(res) + ")");
     return VOF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// The ensemble's pressure solves as one batched solve. The cases' contexts
+// were carved from one arena, so every launch of case 0's context m runs for
+// all cases at once (bat_n cases, bat_stride bytes apart). The loop below is
+// solve_mixed's, taken for every case on the host after one readback of all
+// cases' scalars; a case whose loop has ended is switched off in the device
+// flags, and its blocks return at once in every batched kernel. Each case's
+// kernels, blocks, sums and decisions are those of its solo solve_mixed, so
+// its iterates are the same bits.
+// ---------------------------------------------------------------------------
+void solve_setup_mixed(vof_ctx* c, const double* b_in, double* P) {
+    const int n = c->lv[0].ncells;
+    mg_build_coefficients(c);
+    cudaMemsetAsync(c->scal + S_ERR, 0, sizeof(double), c->st);
+    launch_copy(c, c->b, b_in, n);
+    launch_sub_mean(c, c->b, n, S_MEAN);
+    launch_dot(c, c->b, c->b, n, S_BB);
+    launch_residual_to32(c, P, c->b, c->lv[0].ff, S_RR);
+}
+
+struct BatchSolveState {
+    int nc = 0;
+    int* act_h = nullptr;     // page-locked: the flags to push
+    int* act_d = nullptr;     // device flags the batched kernels read
+    double* mir_h = nullptr;  // mapped: nc x MIRROR_DOUBLES scalars
+    double* mir_d = nullptr;
+};
+
+bool batch_solve_eligible(const vof_ctx* c) {
+    if (c->sv.precision != VOF_PREC_MIXED_FP32 || !c->use_rho || !c->sweep_dot ||
+        c->sv.mg_interp != VOF_MG_CONSTANT || c->sv.mg_coarsen != VOF_COARSEN_FACE_MEAN ||
+        c->dense_n <= 0 || c->tail_level != 0 || c->sv.ssf_solves == 2 || c->timing)
+        return false;
+    const int nu = c->sv.nu_fine > 0 ? c->sv.nu_fine : c->sv.nu_pre;
+    if (nu % 2 != 0 || c->lv[0].ncells % 4 != 0) return false;  // the finest sweeps end in xf
+    for (size_t l = 1; l + 1 < c->lv.size(); ++l)
+        if (c->lv[l].d.nx % 2 != 0) return false;  // the pair kernels on every smoothed level
+    return true;
+}
+
+BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride) {
+    BatchSolveState* b = new BatchSolveState();
+    b->nc = nc;
+    bool ok = cudaHostAlloc((void**)&b->act_h, sizeof(int) * nc, cudaHostAllocPortable) ==
+                  cudaSuccess &&
+              cudaMalloc((void**)&b->act_d, sizeof(int) * nc) == cudaSuccess &&
+              cudaHostAlloc((void**)&b->mir_h, sizeof(double) * MIRROR_DOUBLES * nc,
+                            cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&b->mir_d, b->mir_h, 0) == cudaSuccess;
+    ok = ok && rho_path_batch_maps(m, nc, stride) == VOF_OK;
+    if (!ok) {
+        cudaGetLastError();
+        batch_solve_destroy(b);
+        return nullptr;
+    }
+    return b;
+}
+
+void batch_solve_destroy(BatchSolveState* b) {
+    if (!b) return;
+    if (b->act_h) cudaFreeHost(b->act_h);
+    if (b->act_d) cudaFree(b->act_d);
+    if (b->mir_h) cudaFreeHost(b->mir_h);
+    delete b;
+}
+
+namespace {
+struct CaseSolve {
+    bool outer = false, inner = false, conv = false, err = false, zero = false;
+    double bnorm = 1.0, res = 0.0, res0 = 0.0, rr0 = 0.0, tol_in = 0.0;
+    int inner_total = 0, outer_n = 0, cap = 0;
+};
+}  // namespace
+
+vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* run,
+                             BatchSolveState* bs, vof_status* status, vof_report* reps,
+                             vof_ctx* const* cases) {
+    Level& L0 = m->lv[0];
+    const int n = L0.ncells;
+    float* r32 = L0.ff;
+    float* z32 = L0.xf;
+    const double rtol = m->sv.rtol;
+    const int max_iter = m->sv.max_iter;
+    std::vector<CaseSolve> cs(nc);
+    m->bat_n = nc;
+    m->bat_stride = stride;
+    m->bat_act = bs->act_d;
+    auto S = [&](int i, int slot) { return bs->mir_h[(size_t)i * MIRROR_DOUBLES + slot]; };
+    auto push = [&](bool CaseSolve::*flag) {
+        int any = 0;
+        for (int i = 0; i < nc; ++i) any |= (bs->act_h[i] = (cs[i].*flag && !cs[i].err) ? 1 : 0);
+        cudaMemcpyAsync(bs->act_d, bs->act_h, sizeof(int) * nc, cudaMemcpyHostToDevice, m->st);
+        return any != 0;
+    };
+    auto fail = [&](int i, vof_status st, const char* msg) {
+        cs[i].err = true;
+        cs[i].outer = cs[i].inner = false;
+        status[i] = set_err(cases[i], st, msg);
+    };
+    readback_batch(m, bs->mir_d);
+    for (int i = 0; i < nc; ++i) {
+        status[i] = VOF_OK;
+        if (!run[i]) {
+            cs[i].err = true;
+            continue;
+        }
+        reps[i].iters = 0;
+        reps[i].refinements = 0;
+        reps[i].b_mean = S(i, S_MEAN);
+        const double bb = S(i, S_BB);
+        if (bb == 0.0) {  // P = 0, as zero_solution
+            cs[i].zero = true;
+            reps[i].res0 = reps[i].res = 0.0;
+            continue;
+        }
+        double bnorm = std::sqrt(bb);
+        if (!(bnorm >= 1e-300)) bnorm = 1e-300;
+        cs[i].bnorm = bnorm;
+        cs[i].res0 = cs[i].res = std::sqrt(S(i, S_RR)) / bnorm;
+        if (!std::isfinite(cs[i].res0)) {
+            fail(i, VOF_ERR_NONFINITE, "non-finite initial residual");
+            continue;
+        }
+        cs[i].conv = cs[i].res <= rtol;
+        cs[i].outer = !cs[i].conv;
+    }
+    for (;;) {
+        for (auto& q : cs)
+            if (q.outer && !(q.inner_total < max_iter && q.outer_n < 50)) q.outer = false;
+        for (auto& q : cs)
+            if (q.outer) {
+                q.rr0 = q.res * q.bnorm * q.res * q.bnorm;
+                q.tol_in = std::max(1e-5, 0.2 * rtol / q.res);
+                q.cap = q.inner_total + std::max(20, max_iter / 4);
+                q.inner = true;
+            }
+        if (!push(&CaseSolve::outer)) break;
+        launch_zero32_bat(m, m->e32, n);
+        run_vcycle<float>(m);
+        krylov_dots(m, n, z32, r32, r32);
+        launch_copy32_bat(m, m->p32, z32, n);
+        for (;;) {
+            for (auto& q : cs)
+                if (q.inner && !(q.inner_total < max_iter && q.inner_total < q.cap)) q.inner = false;
+            for (auto& q : cs)
+                if (q.inner) ++q.inner_total;
+            if (!push(&CaseSolve::inner)) break;
+            rho_apply_A_dot(m, m->p32, m->q32, S_PQ);
+            k32_cg_update(m, n, m->e32, r32, m->p32, m->q32, S_RR);
+            readback_batch(m, bs->mir_d);
+            for (int i = 0; i < nc; ++i) {
+                CaseSolve& q = cs[i];
+                if (!q.inner || q.err) continue;
+                if (S(i, S_ERR) != 0.0) {
+                    fail(i, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+                    continue;
+                }
+                const double rr = S(i, S_RR);
+                if (!std::isfinite(rr)) {
+                    fail(i, VOF_ERR_NONFINITE, "non-finite inner residual");
+                    continue;
+                }
+                if (rr <= q.tol_in * q.tol_in * q.rr0) q.inner = false;
+            }
+            if (!push(&CaseSolve::inner)) break;
+            run_vcycle<float>(m);
+            krylov_dots(m, n, z32, r32, m->q32);
+            k32_p_update(m, n, m->p32, z32);
+        }
+        if (!push(&CaseSolve::outer)) break;
+        // FP64 update and true residual
+        k32_add_to_f64(m, n, m->e32, m->p);
+        launch_residual_to32(m, m->p, m->b, r32, S_RR);
+        readback_batch(m, bs->mir_d);
+        for (int i = 0; i < nc; ++i) {
+            CaseSolve& q = cs[i];
+            if (!q.outer || q.err) continue;
+            q.res = std::sqrt(S(i, S_RR)) / q.bnorm;
+            if (S(i, S_ERR) != 0.0) {
+                fail(i, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+                continue;
+            }
+            if (!std::isfinite(q.res)) {
+                fail(i, VOF_ERR_NONFINITE, "non-finite residual");
+                continue;
+            }
+            ++q.outer_n;
+            q.conv = q.res <= rtol;
+            if (q.conv) q.outer = false;
+        }
+    }
+    const vof_status cst = cuda_check(m, cudaGetLastError(), "batched pressure solve");
+    m->bat_n = 1;
+    m->bat_stride = 0;
+    m->bat_act = nullptr;
+    // the rest of each case's solve on its own stream: P = 0 for a zero right
+    // side, else P made mean-free
+    for (int i = 0; i < nc; ++i) {
+        if (!run[i]) continue;
+        vof_ctx* c = cases[i];
+        if (cst != VOF_OK) {
+            status[i] = cst;
+            continue;
+        }
+        if (cs[i].err) continue;
+        if (cs[i].zero) {
+            launch_zero(c, c->p, n);
+            continue;
+        }
+        launch_sub_mean(c, c->p, n, S_SUM);
+        reps[i].iters = cs[i].inner_total;
+        reps[i].refinements = cs[i].outer_n;
+        reps[i].res0 = cs[i].res0;
+        reps[i].res = cs[i].res;
+        if (!cs[i].conv)
+            status[i] = set_err(c, VOF_ERR_NOT_CONVERGED,
+                                "pressure solve did not reach rtol within max_iter (res=" +
+                                    std::to_string(cs[i].res) + ")");
+    }
+    return cst;
+}

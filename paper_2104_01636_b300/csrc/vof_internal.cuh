@@ -103,6 +103,51 @@ __device__ __forceinline__ int block_linear() {
 }
 
 // ---------------------------------------------------------------------------
+// Batched launches: one launch runs a kernel of the pressure solve for every
+// case of an ensemble. The cases' workspaces are carved from one arena at a
+// fixed stride, so case c's arrays are case 0's moved by c * stride bytes. A
+// batched launch repeats the solo grid once per case along one axis (z for
+// the cell kernels, y for the flat vector kernels, x for the one-block
+// finalisers); each block finds its case, its block index in the solo grid
+// and its arrays from the Bat argument, so every case runs the blocks, and
+// sums in the order, of its solo launch. A solo launch passes Bat{}.
+// ---------------------------------------------------------------------------
+struct Bat {
+    int zb = 0;                // solo grid extent along the batched axis (0: a solo launch)
+    long long stride = 0;      // bytes between consecutive cases' workspaces
+    const int* act = nullptr;  // per case: 0 once its solve has finished (its blocks return)
+};
+struct BatBlk {
+    int cs;    // the block's case
+    int b;     // its index along the batched axis in the solo grid
+    int g;     // the solo grid's extent along that axis
+    bool off;  // its case has finished
+};
+__device__ __forceinline__ BatBlk bat_blk(const Bat& t, unsigned idx, unsigned dim) {
+    BatBlk r;
+    if (t.zb) {
+        r.cs = (int)(idx / (unsigned)t.zb);
+        r.b = (int)idx - r.cs * t.zb;
+        r.g = t.zb;
+    } else {
+        r.cs = 0;
+        r.b = (int)idx;
+        r.g = (int)dim;
+    }
+    r.off = t.act != nullptr && t.act[r.cs] == 0;
+    return r;
+}
+// the case's copy of a workspace array
+template <class T>
+__device__ __forceinline__ T* bat_at(const Bat& t, int cs, T* p) {
+    return t.zb ? (T*)((const char*)p + (long long)cs * t.stride) : p;
+}
+// block_linear() of the solo grid, for a grid batched along z
+__device__ __forceinline__ int block_linear_z(const BatBlk& bb) {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * bb.b);
+}
+
+// ---------------------------------------------------------------------------
 // timing classes (CUDA events on the context stream, when enabled)
 // ---------------------------------------------------------------------------
 enum TimerClass {
@@ -268,7 +313,28 @@ struct vof_ctx {
 
     long long nlaunch = 0;  // kernels launched by this context
     std::string err;
+
+    // workspace carved from an arena owned by an ensemble (nullptr: the
+    // stream-ordered allocator); the ensemble's batched solve launches
+    // through case 0's context with bat_n cases at bat_stride bytes apart
+    char* arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
+    int bat_n = 1;
+    long long bat_stride = 0;
+    const int* bat_act = nullptr;
 };
+
+// The batch of the context's launches: Bat{} for a single case; otherwise
+// the grid extent axis_blocks is multiplied by the number of cases.
+inline Bat bat_of(const vof_ctx* c, unsigned& axis_blocks) {
+    Bat b;
+    if (c->bat_n <= 1) return b;
+    b.zb = (int)axis_blocks;
+    b.stride = c->bat_stride;
+    b.act = c->bat_act;
+    axis_blocks *= (unsigned)c->bat_n;
+    return b;
+}
 
 // ---------------------------------------------------------------------------
 // programmatic dependent launch: a kernel launched by launch_pdl is set up
@@ -403,6 +469,7 @@ void mg_to_f64(vof_ctx* c, const float* a, double* b, int n);
 // finest level of the mixed V-cycle from the cell density (k_smooth_tma.cu)
 bool rho_path_eligible(const vof_grid* g, const vof_solver* sv, int nlevels);
 vof_status rho_path_setup(vof_ctx* c);
+vof_status rho_path_batch_maps(vof_ctx* c, int nc, long long case_stride);
 void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot = false);
 // one block waiting out a bounded wait on a barrier nothing completes
 void wait_probe(vof_ctx* c, int limit);
@@ -450,11 +517,36 @@ void launch_correct(vof_ctx* c, const double* P, const double* sx, const double*
 
 // solver driver (solver.cu)
 vof_status solve_pressure(vof_ctx* c, const double* b_in, double* P, vof_report* rep);
+// the mixed solve's setup (coefficients, mean-free b, its norm, the first
+// FP64 residual into the scalars), as solve_pressure launches it
+void solve_setup_mixed(vof_ctx* c, const double* b_in, double* P);
+// the mixed solves of nc cases whose contexts were carved from one arena at
+// stride bytes apart, launched through case 0's context m after every case's
+// solve_setup_mixed (P: the contexts' c->p); run[i] = 0 leaves case i out.
+// Per case: its status and its report's iters, refinements, res0, res, b_mean.
+struct BatchSolveState;
+vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* run,
+                             BatchSolveState* bs, vof_status* status, vof_report* reps,
+                             vof_ctx* const* cases);
+BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride);
+void batch_solve_destroy(BatchSolveState* bs);
+// whether the batched solve supports contexts made with this solver
+bool batch_solve_eligible(const vof_ctx* c);
+vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index);
+vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve,
+                     vof_report* report);
+void launch_zero32_bat(vof_ctx* c, float* x, int n);                 // x = 0 (batched, masked)
+void launch_copy32_bat(vof_ctx* c, float* dst, const float* src, int n);  // dst = src
+void readback_batch(vof_ctx* c, double* mirror_dev);  // every case's scalars, then a wait
 // the whole time step (the body of the exported step/vof_step); the
 // library's own callers use this name, which no system library exports
 vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double* wc, double* u,
                       double* v, double* w, double* p, double dt, long long step_index,
                       vof_report* report);
 size_t mg_workspace_bytes(const vof_grid* g, const vof_solver* sv, int* nlevels);
+// a context whose workspace comes from [arena, arena + arena_bytes) (capi.cu)
+vof_status create_in_arena(const vof_grid* grid, const vof_phys* phys, const vof_solver* solver,
+                           void* stream, void* arena, size_t arena_bytes, vof_ctx** out);
+size_t workspace_bytes(const vof_grid* g, const vof_solver* sv);
 vof_status mg_allocate(vof_ctx* c);
 void mg_build_coefficients(vof_ctx* c);

@@ -1,5 +1,6 @@
 """The ensemble: every case's result is bitwise that of the same case stepped
-alone; a case that fails reports its own status."""
+alone, with the cases' pressure solves batched into shared launches or with
+the cases overlapped on streams; a case that fails reports its own status."""
 import numpy as np
 import pytest
 
@@ -10,13 +11,16 @@ from gpu_util import ctx, dev, host
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,streams", [(1, 2), (0, 3), (1, 1)])
-def test_ensemble_equals_solo(prec, streams):
+@pytest.mark.parametrize("prec,streams,mode,batched", [
+    (1, 2, vd.VofEnsemble.AUTO, True), (0, 3, vd.VofEnsemble.AUTO, False),
+    (1, 1, vd.VofEnsemble.STREAMS, False), (1, 3, vd.VofEnsemble.BATCHED, True)])
+def test_ensemble_equals_solo(prec, streams, mode, batched):
     cases = I.ensemble_cases(3, dims=(32, 32, 48), seed=77)
     kw = dict(precision=prec, rtol=1e-9, max_iter=300)
     fields = [[dev(a) for a in c.state()] for c in cases]
     with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], vd.c_solver(**kw),
-                        n_streams=streams) as E:
+                        n_streams=streams, mode=mode) as E:
+        assert E.batched == batched
         for s in range(3):
             reps = E.step(fields, [c.dt for c in cases], s, reports=True)
             assert all(r["res"] <= 1e-9 for r in reps)
@@ -27,6 +31,33 @@ def test_ensemble_equals_solo(prec, streams):
                 C.step(*solo, c.dt, s)
         for a, b in zip(fs, solo):
             assert np.array_equal(host(a), host(b))
+
+
+def test_batched_ensemble_of_many_cases_equals_solo():
+    """Eight cases with different bubbles (so their solves take different
+    numbers of iterations and the batch switches finished cases off) and
+    reports; each case bitwise equal to its solo run, iteration counts
+    equal to the solo solve's."""
+    cases = I.ensemble_cases(8, dims=(48, 48, 96), seed=2109)
+    kw = dict(precision=1, rtol=1e-8, max_iter=500)
+    fields = [[dev(a) for a in c.state()] for c in cases]
+    with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], vd.c_solver(**kw),
+                        n_streams=4, mode=vd.VofEnsemble.BATCHED) as E:
+        assert E.batched
+        reps = [E.step(fields, [c.dt for c in cases], s, reports=True) for s in range(2)]
+    iters = set()
+    for k, (c, fs) in enumerate(zip(cases, fields)):
+        solo = [dev(a) for a in c.state()]
+        with ctx(c, **kw) as C:
+            solo_reps = [C.step(*solo, c.dt, s) for s in range(2)]
+        for a, b in zip(fs, solo):
+            assert np.array_equal(host(a), host(b))
+        for s in range(2):
+            assert reps[s][k]["iters"] == solo_reps[s]["iters"]
+            assert reps[s][k]["res"] == solo_reps[s]["res"]
+            assert reps[s][k]["max_div"] == solo_reps[s]["max_div"]
+            iters.add(reps[s][k]["iters"])
+    assert len(iters) > 1  # the cases did not all take the same number of iterations
 
 
 def test_ensemble_reports_failing_case():

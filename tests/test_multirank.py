@@ -48,3 +48,13 @@ def test_single_process_needs_no_group():
     assert bench.max_over_ranks(42.0, None, "cpu") == 42.0
     assert bench.whole_job_rate(1, 10, 500.0) == pytest.approx(20.0)
     assert bench.replica_seed(0) == 2106
+
+
+def test_cpu_legs_share_one_bounded_sample():
+    # the bench arm's cpu_baseline and the reference arm take the same sample
+    assert bench.sample_planes(20, 5) == 16
+    assert bench.sample_planes(1, 3) == 16
+    for k, w in [(50, 5), (200, 10), (26, 0)]:
+        n = bench.sample_planes(k, w)
+        assert n % 2 == 0 and 8 <= n < 16
+        assert n * (k + w) <= 16 * 25 or n == 8
