@@ -431,12 +431,14 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
                 E.step(fields, dts, s)
             torch.cuda.synchronize()
             n0 = E.launch_count()
+            ph0 = E.phase_ms()
             t0 = time.perf_counter()
             for s in range(warmup, warmup + steps):
                 reps = E.step(fields, dts, s, reports=True)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3 / steps
             launches = (E.launch_count() - n0) / steps
+            phases = [(b - a) / steps for a, b in zip(ph0, E.phase_ms())]
             batched = E.batched
         del fields
         out[label] = {"n_streams": ns, "batched_solves": batched,
@@ -444,6 +446,7 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
                       "case_steps_per_s": n_cases / (ms / 1e3),
                       "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3),
                       "kernel_launches_per_ensemble_step": launches,
+                      "ms_before_solve_solve_after": phases,
                       "max_inner_iters": max(r["iters"] for r in reps),
                       "mean_inner_iters": sum(r["iters"] for r in reps) / len(reps)}
     return out

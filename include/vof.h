@@ -452,6 +452,10 @@ vof_status vof_ensemble_batched(const vof_ensemble* ensemble, int* batched);
 /* Kernels launched by the ensemble so far (every case, a batched launch
  * counted once). */
 vof_status vof_ensemble_launch_count(const vof_ensemble* ensemble, long long* n);
+/* Host wall time (ms) the steps so far spent in their three parts: ms[0]
+ * the parts before the solves (the whole step for a streams ensemble),
+ * ms[1] the batched solve, ms[2] the parts after it. */
+vof_status vof_ensemble_phase_ms(const vof_ensemble* ensemble, double* ms);
 
 /* ---- duct statistics ------------------------------------------------------
  * Running sums for the profiles of Section 4 (averages over the streamwise

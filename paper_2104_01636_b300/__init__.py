@@ -139,6 +139,7 @@ def load() -> ctypes.CDLL:
                                      ctypes.c_int, ctypes.c_int, P(_VP)],
         "vof_ensemble_batched": [_VP, P(ctypes.c_int)],
         "vof_ensemble_launch_count": [_VP, P(ctypes.c_longlong)],
+        "vof_ensemble_phase_ms": [_VP, P(_D)],
         "vof_stats_create": [P(CGrid), P(_VP)],
         "vof_stats_accumulate": [_VP, _VP, _VP, _VP, _VP, _VP],
         "vof_stats_read": [_VP, P(_D), P(ctypes.c_longlong)],
@@ -486,6 +487,12 @@ class VofEnsemble:
         cs = (grid.nz, grid.ny, grid.nx)
         self.shapes = (cs, cs, cs, cs, (grid.nz, grid.ny, grid.nx + 1),
                        (grid.nz, grid.ny + 1, grid.nx), cs, cs)
+
+    def phase_ms(self):
+        """Host ms so far: (before the solves, the batched solve, after it)."""
+        ms = (_D * 3)()
+        self.lib.vof_ensemble_phase_ms(self._e, ms)
+        return tuple(ms)
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong(0)

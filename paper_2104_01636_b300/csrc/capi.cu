@@ -371,16 +371,28 @@ vof_status step_entry(vof_ctx* c, double* alpha, double* uc, double* vc, double*
 // (solve_mixed_batch) runs the solve of every case; step_post launches the
 // rest. In sequence they launch the case's kernels of step_run, in its order,
 // on the same values (the mixed single-solve path).
-vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index) {
+vof_status step_pre_cfl(vof_ctx* c, double* const f[8], double dt) {
     vof_status st = check_ctx(c);
     if (st) return st;
     for (int q = 0; q < 8; ++q)
         if (!f[q]) return set_err(c, VOF_ERR_ARG, "a field is NULL");
     if ((st = walls_only(c, "step"))) return st;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(c, VOF_ERR_ARG, "dt must be positive");
+    launch_cfl(c, f[4], f[5], f[6], dt, P_A);
+    readback_async(c);
+    return VOF_OK;
+}
+
+// after step_pre_cfl and a wait on the stream: cfl_check's test, then the
+// rest of the step up to the solve
+vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index) {
     if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
     double* const alpha = f[0];
     const double *u = f[4], *v = f[5], *w = f[6];
-    if ((st = cfl_check(c, u, v, w, dt))) return st;
+    const double cfl = c->hbuf[S_CFL] * dt / c->g.h;
+    if (!std::isfinite(cfl)) return set_err(c, VOF_ERR_NONFINITE, "non-finite velocity");
+    if (cfl > 1.0)
+        return set_err(c, VOF_ERR_CFL, "Courant number " + std::to_string(cfl) + " exceeds 1");
     const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
     cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     double* const flux[3] = {c->fx, c->fy, c->fz};
@@ -396,16 +408,23 @@ vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_in
     return launch_check(c, "step");
 }
 
-// solve: the status of the case's solve; its iteration counts are in *report
-vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve,
-                     vof_report* report) {
+// solve: the status of the case's solve; its iteration counts are in
+// *report. step_post launches the correction and the readback of its maxima
+// without a wait; step_post_report, after a wait on the stream, fills the
+// report and returns the step's status.
+vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve) {
     if (solve != VOF_OK && solve != VOF_ERR_NOT_CONVERGED) return solve;
     const int n = c->d.nx * c->d.ny * c->d.nz;
     launch_copy(c, f[7], c->p, n);
     const double* const Uh[3] = {c->uh[0], c->uh[1], c->uh[2]};
     double* const Uc[3] = {f[1], f[2], f[3]};
     launch_correct(c, f[7], c->sx, c->sy, c->sz, dt, Uh, Uc, f[4], f[5], f[6], P_A, P_B);
-    readback(c);
+    readback_async(c);
+    return solve;
+}
+
+vof_status step_post_report(vof_ctx* c, vof_status solve, vof_report* report) {
+    if (solve != VOF_OK && solve != VOF_ERR_NOT_CONVERGED) return solve;
     vof_report r = report ? *report : vof_report{};
     r.max_div = c->hbuf[S_MAXDIV];
     r.max_u = c->hbuf[S_MAXU];

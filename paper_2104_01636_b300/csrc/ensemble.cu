@@ -12,6 +12,7 @@
 //    worker threads launch on their own streams;
 //  * streams: cases are dealt round-robin to worker threads, each driving its
 //    own CUDA stream, so the cases' kernels overlap on the GPU.
+#include <chrono>
 #include <condition_variable>
 #include <mutex>
 #include <thread>
@@ -44,6 +45,7 @@ struct vof_ensemble {
     std::vector<int> run;
     std::vector<vof_status> solve_st;
     std::vector<vof_report> rep;
+    double phase_ms[3] = {0.0, 0.0, 0.0};  // host time: before the solve, the solve, after it
 };
 
 namespace {
@@ -65,12 +67,25 @@ void ensemble_worker(vof_ensemble* e, int w) {
                 e->status[c] = step_entry(e->ctx[c], f[0], f[1], f[2], f[3], f[4], f[5], f[6],
                                           f[7], e->dt[c], e->step_index, rep);
             } else if (e->phase == 1) {
-                e->status[c] = step_pre(e->ctx[c], f, e->dt[c], e->step_index);
+                e->status[c] = step_pre_cfl(e->ctx[c], f, e->dt[c]);
             } else if (e->run[c]) {
-                e->status[c] = step_post(e->ctx[c], f, e->dt[c], e->solve_st[c], &e->rep[c]);
+                e->status[c] = step_post(e->ctx[c], f, e->dt[c], e->solve_st[c]);
             }
         }
         cudaStreamSynchronize(e->streams[w]);
+        if (e->phase == 1) {
+            // the CFL tests of the worker's cases, read back together; then the
+            // rest of each case's step up to the solve, launched without a wait
+            for (int c = w; c < e->n; c += e->nworkers)
+                if (e->status[c] == VOF_OK)
+                    e->status[c] = step_pre(e->ctx[c], e->fields + 8 * (size_t)c, e->dt[c],
+                                            e->step_index);
+            cudaStreamSynchronize(e->streams[w]);
+        } else if (e->phase == 2) {
+            for (int c = w; c < e->n; c += e->nworkers)
+                if (e->run[c])
+                    e->status[c] = step_post_report(e->ctx[c], e->solve_st[c], &e->rep[c]);
+        }
         {
             std::lock_guard<std::mutex> lk(e->mu);
             if (--e->pending == 0) e->cv_done.notify_all();
@@ -234,10 +249,19 @@ vof_status vof_ensemble_step(vof_ensemble* e, double* const* fields, const doubl
         e->step_index = step_index;
         e->reports = reports;
     }
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t0) {
+        return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    };
     if (!e->batched) {
+        const auto t0 = clk::now();
         run_phase(e, 0);
+        e->phase_ms[0] += ms_since(t0);
     } else {
+        auto t0 = clk::now();
         run_phase(e, 1);
+        e->phase_ms[0] += ms_since(t0);
+        t0 = clk::now();
         for (int c = 0; c < e->n; ++c) {
             e->run[c] = e->status[c] == VOF_OK ? 1 : 0;
             e->rep[c] = vof_report{};
@@ -248,7 +272,10 @@ vof_status vof_ensemble_step(vof_ensemble* e, double* const* fields, const doubl
         if (st != VOF_OK)
             for (int c = 0; c < e->n; ++c)
                 if (e->run[c]) e->status[c] = st;
+        e->phase_ms[1] += ms_since(t0);
+        t0 = clk::now();
         run_phase(e, 2);
+        e->phase_ms[2] += ms_since(t0);
         if (reports)
             for (int c = 0; c < e->n; ++c)
                 if (e->run[c]) reports[c] = e->rep[c];
@@ -259,6 +286,12 @@ vof_status vof_ensemble_step(vof_ensemble* e, double* const* fields, const doubl
         if (first == VOF_OK) first = e->status[c];
     }
     return first;
+}
+
+vof_status vof_ensemble_phase_ms(const vof_ensemble* e, double* ms) {
+    if (!e || !ms) return VOF_ERR_ARG;
+    for (int q = 0; q < 3; ++q) ms[q] = e->phase_ms[q];
+    return VOF_OK;
 }
 
 vof_status vof_ensemble_launch_count(const vof_ensemble* e, long long* n) {

@@ -20,12 +20,13 @@ Launch launch_cells(int nx, int ny, int nz, int sm_count) {
     return L;
 }
 
+template <bool B>
 __global__ void k_finalize_sum(Bat t, const double* __restrict__ part, int n, double* out,
                                double scale) {
-    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.x, gridDim.x);
     if (bb.off) return;
-    part = bat_at(t, bb.cs, part);
-    out = bat_at(t, bb.cs, out);
+    part = bat_at<B>(t, bb.cs, part);
+    out = bat_at<B>(t, bb.cs, out);
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     s = block_sum(s);
@@ -39,13 +40,14 @@ __global__ void k_finalize_max(const double* __restrict__ part, int n, double* o
     if (threadIdx.x == 0) *out = s;
 }
 
+template <bool B>
 __global__ void k_finalize_dots_beta(Bat t, const double* __restrict__ pa,
                                      const double* __restrict__ pb, int n, double* scal) {
-    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.x, gridDim.x);
     if (bb.off) return;
-    pa = bat_at(t, bb.cs, pa);
-    pb = bat_at(t, bb.cs, pb);
-    scal = bat_at(t, bb.cs, scal);
+    pa = bat_at<B>(t, bb.cs, pa);
+    pb = bat_at<B>(t, bb.cs, pb);
+    scal = bat_at<B>(t, bb.cs, scal);
     const double rz = sum_partials(pa, n);
     const double zq = sum_partials(pb, n);
     if (threadIdx.x == 0) {
@@ -56,11 +58,12 @@ __global__ void k_finalize_dots_beta(Bat t, const double* __restrict__ pa,
     }
 }
 
+template <bool B>
 __global__ void k_finalize_pq_alpha(Bat t, const double* __restrict__ part, int n, double* scal) {
-    const BatBlk bb = bat_blk(t, blockIdx.x, gridDim.x);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.x, gridDim.x);
     if (bb.off) return;
-    part = bat_at(t, bb.cs, part);
-    scal = bat_at(t, bb.cs, scal);
+    part = bat_at<B>(t, bb.cs, part);
+    scal = bat_at<B>(t, bb.cs, scal);
     const double pq = sum_partials(part, n);
     if (threadIdx.x == 0) {
         scal[S_PQ] = pq * 1.0;
@@ -70,19 +73,21 @@ __global__ void k_finalize_pq_alpha(Bat t, const double* __restrict__ part, int 
 
 // x = 0 and dst = src on FP32 vectors of n4 float4s, batched along y (the
 // batched solve's memset of e and copy of p; one case: a plain launch)
+template <bool B>
 __global__ void k_zero32x4(Bat t, int n4, float4* __restrict__ x) {
-    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    x = bat_at(t, bb.cs, x);
+    x = bat_at<B>(t, bb.cs, x);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x)
         x[c] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+template <bool B>
 __global__ void k_copy32x4(Bat t, int n4, float4* __restrict__ dst, const float4* __restrict__ src) {
-    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    dst = bat_at(t, bb.cs, dst);
-    src = bat_at(t, bb.cs, src);
+    dst = bat_at<B>(t, bb.cs, dst);
+    src = bat_at<B>(t, bb.cs, src);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x)
         dst[c] = src[c];
 }
@@ -91,7 +96,7 @@ __global__ void k_copy32x4(Bat t, int n4, float4* __restrict__ dst, const float4
 __global__ void k_to_mirror_bat(Bat t, const double* __restrict__ s, double* __restrict__ h,
                                 int n) {
     const int cs = t.zb ? (int)blockIdx.x : 0;
-    s = bat_at(t, cs, s);
+    s = bat_at<true>(t, cs, s);
     if ((int)threadIdx.x < n) h[(size_t)cs * MIRROR_DOUBLES + threadIdx.x] = s[threadIdx.x];
     __threadfence_system();
 }
@@ -99,21 +104,24 @@ __global__ void k_to_mirror_bat(Bat t, const double* __restrict__ s, double* __r
 void finalize_dots_beta(vof_ctx* c, int nparts) {
     dim3 g(1);
     const Bat b = bat_of(c, g.x);
-    VOF_LAUNCH(c, k_finalize_dots_beta, g, 1024, b, c->part + (size_t)S_RZ * MAX_PARTIALS,
+    auto kern = b.zb ? k_finalize_dots_beta<true> : k_finalize_dots_beta<false>;
+    VOF_LAUNCH(c, kern, g, 1024, b, c->part + (size_t)S_RZ * MAX_PARTIALS,
                c->part + (size_t)S_ZQ * MAX_PARTIALS, nparts, c->scal);
 }
 
 void finalize_pq_alpha(vof_ctx* c, int nparts) {
     dim3 g(1);
     const Bat b = bat_of(c, g.x);
-    VOF_LAUNCH(c, k_finalize_pq_alpha, g, 1024, b, c->part + (size_t)S_PQ * MAX_PARTIALS, nparts,
+    auto kern = b.zb ? k_finalize_pq_alpha<true> : k_finalize_pq_alpha<false>;
+    VOF_LAUNCH(c, kern, g, 1024, b, c->part + (size_t)S_PQ * MAX_PARTIALS, nparts,
                c->scal);
 }
 
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale) {
     dim3 g(1);
     const Bat b = bat_of(c, g.x);
-    VOF_LAUNCH(c, k_finalize_sum, g, 1024, b, c->part + (size_t)slot * MAX_PARTIALS, nparts,
+    auto kern = b.zb ? k_finalize_sum<true> : k_finalize_sum<false>;
+    VOF_LAUNCH(c, kern, g, 1024, b, c->part + (size_t)slot * MAX_PARTIALS, nparts,
                                           c->scal + dst, scale);
 }
 
@@ -161,7 +169,7 @@ void mirror_release(double* p) {
     g_mirror_free.push_back(p);
 }
 
-void readback(vof_ctx* c) {
+void readback_async(vof_ctx* c) {
     if (c->hmirror_dev) {
         ++c->nlaunch;
         k_to_mirror<<<1, MIRROR_DOUBLES, 0, c->st>>>(c->scal, c->hmirror_dev, S_NSCALARS);
@@ -169,6 +177,10 @@ void readback(vof_ctx* c) {
         cudaMemcpyAsync(c->hbuf, c->scal, sizeof(double) * S_NSCALARS, cudaMemcpyDeviceToHost,
                         c->st);
     }
+}
+
+void readback(vof_ctx* c) {
+    readback_async(c);
     cudaStreamSynchronize(c->st);
 }
 
@@ -180,13 +192,15 @@ static int flat_blocks4(int n4) {
 void launch_zero32_bat(vof_ctx* c, float* x, int n) {
     dim3 g(flat_blocks4(n / 4));
     const Bat b = bat_of(c, g.y);
-    VOF_LAUNCH(c, k_zero32x4, g, 256, b, n / 4, (float4*)x);
+    auto kern = b.zb ? k_zero32x4<true> : k_zero32x4<false>;
+    VOF_LAUNCH(c, kern, g, 256, b, n / 4, (float4*)x);
 }
 
 void launch_copy32_bat(vof_ctx* c, float* dst, const float* src, int n) {
     dim3 g(flat_blocks4(n / 4));
     const Bat b = bat_of(c, g.y);
-    VOF_LAUNCH(c, k_copy32x4, g, 256, b, n / 4, (float4*)dst, (const float4*)src);
+    auto kern = b.zb ? k_copy32x4<true> : k_copy32x4<false>;
+    VOF_LAUNCH(c, kern, g, 256, b, n / 4, (float4*)dst, (const float4*)src);
 }
 
 // mirror_dev: the device address of a mapped page-locked buffer of

@@ -83,22 +83,22 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
 // is needed.
 // CT is the coefficients' storage type (T, or FP16 copies on a large coarse
 // level of the FP32 cycle).
-template <class T, int MODE, class CT>
+template <class T, int MODE, class CT, bool B>
 __global__ void k_rbgs_pair_t(Bat bt, Dims d, T h2, const CT* __restrict__ bx,
                               const CT* __restrict__ by, const CT* __restrict__ bz,
                               const T* __restrict__ xr, T* __restrict__ xw,
                               const T* __restrict__ f, int color, int kchunk, Dims dc,
                               const T* __restrict__ xc, T omega) {
     pdl_wait();
-    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    bx = bat_at(bt, bb.cs, bx);
-    by = bat_at(bt, bb.cs, by);
-    bz = bat_at(bt, bb.cs, bz);
-    xr = bat_at(bt, bb.cs, xr);
-    xw = bat_at(bt, bb.cs, xw);
-    f = bat_at(bt, bb.cs, f);
-    if (xc) xc = bat_at(bt, bb.cs, xc);
+    bx = bat_at<B>(bt, bb.cs, bx);
+    by = bat_at<B>(bt, bb.cs, by);
+    bz = bat_at<B>(bt, bb.cs, bz);
+    xr = bat_at<B>(bt, bb.cs, xr);
+    xw = bat_at<B>(bt, bb.cs, xw);
+    f = bat_at<B>(bt, bb.cs, f);
+    if (xc) xc = bat_at<B>(bt, bb.cs, xc);
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (t >= (d.nx >> 1) || j >= d.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -135,20 +135,20 @@ __device__ __forceinline__ float2 cpair(const __half* a, int c) {
 // (8-byte loads; 2I and nx are even). Same terms in the same order.
 // CT: FP32 coefficients, or the level's FP16 copies (the colour passes of
 // the same level read the same copies, so the cycle keeps one operator).
-template <class CT>
+template <class CT, bool B>
 __global__ void k_restrict_pair_f(Bat bt, Dims df, float ih2f, const CT* __restrict__ bx,
                                   const CT* __restrict__ by, const CT* __restrict__ bz,
                                   const float* __restrict__ xf, const float* __restrict__ ff,
                                   Dims dc, float* __restrict__ fc, int kchunk) {
     pdl_wait();
-    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    bx = bat_at(bt, bb.cs, bx);
-    by = bat_at(bt, bb.cs, by);
-    bz = bat_at(bt, bb.cs, bz);
-    xf = bat_at(bt, bb.cs, xf);
-    ff = bat_at(bt, bb.cs, ff);
-    fc = bat_at(bt, bb.cs, fc);
+    bx = bat_at<B>(bt, bb.cs, bx);
+    by = bat_at<B>(bt, bb.cs, by);
+    bz = bat_at<B>(bt, bb.cs, bz);
+    xf = bat_at<B>(bt, bb.cs, xf);
+    ff = bat_at<B>(bt, bb.cs, ff);
+    fc = bat_at<B>(bt, bb.cs, fc);
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, dc.nz);
@@ -198,13 +198,14 @@ __global__ void k_prolong_t(Dims dc, const T* __restrict__ xc, Dims df, T* __res
 
 // The same for a fine level with an even nx: a thread adds the correction
 // of parent I to the fine pair (2I, 2I+1) with one 8-byte load and store.
+template <bool B>
 __global__ void k_prolong_pair_f(Bat bt, Dims dc, const float* __restrict__ xc, Dims df,
                                  float* __restrict__ xf, float omega, int kchunk) {
     pdl_wait();
-    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    xc = bat_at(bt, bb.cs, xc);
-    xf = bat_at(bt, bb.cs, xf);
+    xc = bat_at<B>(bt, bb.cs, xc);
+    xf = bat_at<B>(bt, bb.cs, xf);
     const int I = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (2 * I >= df.nx || j >= df.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, df.nz);
@@ -563,15 +564,15 @@ __global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const
 }
 
 // x = Minv f: one warp per row (dense_row)
-template <class T>
+template <class T, bool B>
 __global__ void k_dense_apply(Bat bt, int n, const T* __restrict__ Minv, const T* __restrict__ f,
                               T* __restrict__ x) {
     pdl_wait();
-    const BatBlk bb = bat_blk(bt, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    Minv = bat_at(bt, bb.cs, Minv);
-    f = bat_at(bt, bb.cs, f);
-    x = bat_at(bt, bb.cs, x);
+    Minv = bat_at<B>(bt, bb.cs, Minv);
+    f = bat_at<B>(bt, bb.cs, f);
+    x = bat_at<B>(bt, bb.cs, x);
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const double s = dense_row(Minv + (long)warp * n, [&](int j) { return f[j]; }, n, lane);
@@ -661,13 +662,14 @@ __global__ void k_p_update32(int n, float* __restrict__ p, const float* __restri
 }
 
 // the same with 16-byte loads and stores (n4 = n / 4, 16-byte aligned arrays)
+template <bool B>
 __global__ void k_p_update32x4(Bat t, int n4, float4* __restrict__ p,
                                const float4* __restrict__ z, const double* __restrict__ scal) {
-    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    p = bat_at(t, bb.cs, p);
-    z = bat_at(t, bb.cs, z);
-    scal = bat_at(t, bb.cs, scal);
+    p = bat_at<B>(t, bb.cs, p);
+    z = bat_at<B>(t, bb.cs, z);
+    scal = bat_at<B>(t, bb.cs, scal);
     const float be = (float)scal[S_BETA];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
         const float4 zv = z[c];
@@ -682,17 +684,18 @@ __global__ void k_p_update32x4(Bat t, int n4, float4* __restrict__ p,
 
 // k_cg_update32 with 16-byte loads and stores; each thread's (r, r) terms
 // are summed four at a time, in order
+template <bool B>
 __global__ void k_cg_update32x4(Bat t, int n4, float4* __restrict__ e, float4* __restrict__ r,
                                 const float4* __restrict__ p, const float4* __restrict__ q,
                                 const double* __restrict__ scal, double* __restrict__ part) {
-    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    e = bat_at(t, bb.cs, e);
-    r = bat_at(t, bb.cs, r);
-    p = bat_at(t, bb.cs, p);
-    q = bat_at(t, bb.cs, q);
-    scal = bat_at(t, bb.cs, scal);
-    part = bat_at(t, bb.cs, part);
+    e = bat_at<B>(t, bb.cs, e);
+    r = bat_at<B>(t, bb.cs, r);
+    p = bat_at<B>(t, bb.cs, p);
+    q = bat_at<B>(t, bb.cs, q);
+    scal = bat_at<B>(t, bb.cs, scal);
+    part = bat_at<B>(t, bb.cs, part);
     const float al = (float)scal[S_ALPHA];
     Kahan ks;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
@@ -750,12 +753,13 @@ __global__ void k_to_f64(int n, const float* __restrict__ a, double* __restrict_
 
 // the same three with 16-byte accesses, four values per thread and pass
 // (n4 = n / 4; arrays 16-byte aligned)
+template <bool B>
 __global__ void k_add_f32_to_f64x4(Bat t, int n4, const float4* __restrict__ e,
                                    double2* __restrict__ x) {
-    const BatBlk bb = bat_blk(t, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.y, gridDim.y);
     if (bb.off) return;
-    e = bat_at(t, bb.cs, e);
-    x = bat_at(t, bb.cs, x);
+    e = bat_at<B>(t, bb.cs, e);
+    x = bat_at<B>(t, bb.cs, x);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n4; c += gridDim.x * blockDim.x) {
         const float4 ev = e[c];
         double2 lo = x[2 * c], hi = x[2 * c + 1];
@@ -812,8 +816,13 @@ void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, con
                const LA<T>& a, int color, int mode, const Level* C, int cls) {
     using K = void (*)(Bat, Dims, T, const CT*, const CT*, const CT*, const T*, T*, const T*, int,
                        int, Dims, const T*, T);
-    const K kern = mode == 1 ? k_rbgs_pair_t<T, 1, CT>
-                             : (mode == 2 ? k_rbgs_pair_t<T, 2, CT> : k_rbgs_pair_t<T, 0, CT>);
+    const bool bat = c->bat_n > 1;
+    const K kern =
+        bat ? (mode == 1 ? k_rbgs_pair_t<T, 1, CT, true>
+                         : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, true> : k_rbgs_pair_t<T, 0, CT, true>))
+            : (mode == 1 ? k_rbgs_pair_t<T, 1, CT, false>
+                         : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, false>
+                                      : k_rbgs_pair_t<T, 0, CT, false>));
     const Dims dc = C ? C->d : L.d;
     const T* xc = C ? arrays<T>(*C).x : nullptr;
     const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
@@ -868,13 +877,15 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
         dim3 g = C.L.grid;
         if (sizeof(T) == sizeof(float) && F.bxh) {
             const Bat bt = bat_of(c, g.z);
-            launch_pdl(c, k_restrict_pair_f<__half>, g, C.L.block, bt, F.d,
+            launch_pdl(c, bt.zb ? k_restrict_pair_f<__half, true> : k_restrict_pair_f<__half, false>,
+                       g, C.L.block, bt, F.d,
                        (float)(1.0 / (F.h * F.h)) * F.hscale, (const __half*)F.bxh, (const __half*)F.byh,
                        (const __half*)F.bzh, (const float*)a.x, (const float*)a.f, C.d,
                        (float*)b.f, C.L.kchunk);
         } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
             const Bat bt = bat_of(c, g.z);
-            launch_pdl(c, k_restrict_pair_f<float>, g, C.L.block, bt, F.d,
+            launch_pdl(c, bt.zb ? k_restrict_pair_f<float, true> : k_restrict_pair_f<float, false>,
+                       g, C.L.block, bt, F.d,
                        (float)(1.0 / (F.h * F.h)), (const float*)a.bx, (const float*)a.by,
                        (const float*)a.bz, (const float*)a.x, (const float*)a.f, C.d, (float*)b.f,
                        C.L.kchunk);
@@ -899,7 +910,8 @@ void mg_prolong(vof_ctx* c, const Level& C, const Level& F) {
         const int kchunk = std::max(1, (F.L.kchunk + 1) / 2);  // half the blocks across
         dim3 g((F.d.nx / 2 + TBX - 1) / TBX, F.L.grid.y, (F.d.nz + kchunk - 1) / kchunk);
         const Bat bt = bat_of(c, g.z);
-        launch_pdl(c, k_prolong_pair_f, g, F.L.block, bt, C.d, (const float*)a.x, F.d,
+        launch_pdl(c, bt.zb ? k_prolong_pair_f<true> : k_prolong_pair_f<false>, g, F.L.block, bt,
+                   C.d, (const float*)a.x, F.d,
                    (float*)b.x, (float)omega, kchunk);
     }
     else
@@ -976,7 +988,8 @@ void mg_coarse(vof_ctx* c, const Level& L) {
         const T* Minv = sizeof(T) == 4 ? (const T*)c->dense_inv_f : (const T*)c->dense_inv;
         dim3 g((n * 32 + 255) / 256);
         const Bat bt = bat_of(c, g.y);
-        launch_pdl(c, k_dense_apply<T>, g, dim3(256), bt, n, Minv, a.f, a.x);
+        launch_pdl(c, bt.zb ? k_dense_apply<T, true> : k_dense_apply<T, false>, g, dim3(256), bt, n,
+                   Minv, a.f, a.x);
         timer_end(c, T_COARSE, m);
         return;
     }
@@ -1011,7 +1024,8 @@ int k32_cg_update(vof_ctx* c, int n, float* e, float* r, const float* p, const f
     if (v4) {
         dim3 g(nb);
         const Bat b = bat_of(c, g.y);
-        VOF_LAUNCH(c, k_cg_update32x4, g, 256, b, n / 4, (float4*)e, (float4*)r, (const float4*)p,
+        auto kern = b.zb ? k_cg_update32x4<true> : k_cg_update32x4<false>;
+        VOF_LAUNCH(c, kern, g, 256, b, n / 4, (float4*)e, (float4*)r, (const float4*)p,
                    (const float4*)q, c->scal, c->part + (size_t)slot * MAX_PARTIALS);
     } else
         VOF_LAUNCH(c, k_cg_update32, nb, 256, n, e, r, p, q, c->scal,
@@ -1035,7 +1049,8 @@ void k32_p_update(vof_ctx* c, int n, float* p, const float* z) {
     if (vec4_ok(n, {p, z})) {
         dim3 g(flat_blocks(n / 4));
         const Bat b = bat_of(c, g.y);
-        VOF_LAUNCH(c, k_p_update32x4, g, 256, b, n / 4, (float4*)p, (const float4*)z, c->scal);
+        auto kern = b.zb ? k_p_update32x4<true> : k_p_update32x4<false>;
+        VOF_LAUNCH(c, kern, g, 256, b, n / 4, (float4*)p, (const float4*)z, c->scal);
     } else
         VOF_LAUNCH(c, k_p_update32, flat_blocks(n), 256, n, p, z, c->scal);
     timer_end(c, T_KRYLOV, m);
@@ -1046,7 +1061,8 @@ void k32_add_to_f64(vof_ctx* c, int n, const float* e, double* x) {
     if (vec4_ok(n, {e, x})) {
         dim3 g(flat_blocks(n / 4));
         const Bat b = bat_of(c, g.y);
-        VOF_LAUNCH(c, k_add_f32_to_f64x4, g, 256, b, n / 4, (const float4*)e, (double2*)x);
+        auto kern = b.zb ? k_add_f32_to_f64x4<true> : k_add_f32_to_f64x4<false>;
+        VOF_LAUNCH(c, kern, g, 256, b, n / 4, (const float4*)e, (double2*)x);
     } else
         VOF_LAUNCH(c, k_add_f32_to_f64, flat_blocks(n), 256, n, e, x);
     timer_end(c, T_KRYLOV, m);

@@ -146,19 +146,20 @@ __global__ void k_residual(Dims d, double ih2, const double* __restrict__ bx,
 
 // r = f - A x in FP64, stored as FP32 (the inner right side of the mixed
 // solve), with block partials of the FP64 r.r
+template <bool B>
 __global__ void k_residual_to32(Bat t, Dims d, double ih2, const double* __restrict__ bx,
                                 const double* __restrict__ by, const double* __restrict__ bz,
                                 const double* __restrict__ x, const double* __restrict__ f,
                                 float* __restrict__ r32, double* __restrict__ part, int kchunk) {
-    const BatBlk bb = bat_blk(t, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(t, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    bx = bat_at(t, bb.cs, bx);
-    by = bat_at(t, bb.cs, by);
-    bz = bat_at(t, bb.cs, bz);
-    x = bat_at(t, bb.cs, x);
-    f = bat_at(t, bb.cs, f);
-    r32 = bat_at(t, bb.cs, r32);
-    part = bat_at(t, bb.cs, part);
+    bx = bat_at<B>(t, bb.cs, bx);
+    by = bat_at<B>(t, bb.cs, by);
+    bz = bat_at<B>(t, bb.cs, bz);
+    x = bat_at<B>(t, bb.cs, x);
+    f = bat_at<B>(t, bb.cs, f);
+    r32 = bat_at<B>(t, bb.cs, r32);
+    part = bat_at<B>(t, bb.cs, part);
     CellIdx r = cell_range(d, kchunk);
     r.k0 = bb.b * kchunk;
     r.k1 = min(r.k0 + kchunk, d.nz);
@@ -407,7 +408,8 @@ void launch_residual_to32(vof_ctx* c, const double* x, const double* f, float* r
     int m = timer_begin(c, T_RESIDUAL);
     dim3 g = l.L.grid;
     const Bat b = bat_of(c, g.z);
-    VOF_LAUNCH(c, k_residual_to32, g, l.L.block, b, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz,
+    auto kern = b.zb ? k_residual_to32<true> : k_residual_to32<false>;
+    VOF_LAUNCH(c, kern, g, l.L.block, b, l.d, 1.0 / (l.h * l.h), l.bx, l.by, l.bz,
                x, f, r32, c->part + (size_t)slot * MAX_PARTIALS, l.L.kchunk);
     timer_end(c, T_RESIDUAL, m);
     finalize_sum(c, slot, l.L.nblocks, slot, 1.0);

@@ -42,7 +42,7 @@ constexpr int NSLOT = 4;                      // staged planes: 3 in use, 1 in f
 constexpr int XPLANE = SBX * SBY;             // floats per staged x plane
 constexpr int HPLANE = HBX * SBY;             // halves per staged density plane
 constexpr int WAIT_LIMIT = 1 << 20;           // bounded waits on the TMA barriers
-constexpr int SWEEP_BLOCKS_PER_SM = 5;        // resident sweep blocks per SM (registers <= 48)
+constexpr int SWEEP_BLOCKS_PER_SM = 4;        // resident sweep blocks per SM (registers <= 64)
 constexpr size_t SWEEP_SMEM = (size_t)NSLOT * XPLANE * sizeof(float) +
                               (size_t)NSLOT * HPLANE * sizeof(__half) +
                               (size_t)3 * NPL * sizeof(float) + NSLOT * sizeof(uint64_t) + 128;
@@ -130,7 +130,7 @@ __device__ __forceinline__ float hval(const __half* h, int o) { return __half2fl
 // DOT: as the pair is written, its products with f and with q are summed
 // (the preconditioner's last sweep forms the Krylov dots (z, r), (z, q)
 // from the z it writes, r being its right side).
-template <bool ZERO, bool DOT>
+template <bool ZERO, bool DOT, bool B>
 __global__ void __launch_bounds__(256, SWEEP_BLOCKS_PER_SM)
     k_sweep_rho(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_rho,
                 SweepArgs a0) {
@@ -141,15 +141,15 @@ __global__ void __launch_bounds__(256, SWEEP_BLOCKS_PER_SM)
     float* sN = reinterpret_cast<float*>(sH + NSLOT * HPLANE);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sN + 3 * NPL);
 
-    const BatBlk bb = bat_blk(a0.bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(a0.bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
     SweepArgs a = a0;
-    a.f = bat_at(a0.bt, bb.cs, a0.f);
-    a.xout = bat_at(a0.bt, bb.cs, a0.xout);
-    a.err = bat_at(a0.bt, bb.cs, a0.err);
-    a.q = bat_at(a0.bt, bb.cs, a0.q);
-    a.pa = bat_at(a0.bt, bb.cs, a0.pa);
-    a.pb = bat_at(a0.bt, bb.cs, a0.pb);
+    a.f = bat_at<B>(a0.bt, bb.cs, a0.f);
+    a.xout = bat_at<B>(a0.bt, bb.cs, a0.xout);
+    a.err = bat_at<B>(a0.bt, bb.cs, a0.err);
+    a.q = bat_at<B>(a0.bt, bb.cs, a0.q);
+    a.pa = bat_at<B>(a0.bt, bb.cs, a0.pa);
+    a.pb = bat_at<B>(a0.bt, bb.cs, a0.pb);
     const int blin = block_linear_z(bb);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 16 * ty;
     const int i0 = blockIdx.x * STX, j0 = blockIdx.y * STY;
@@ -433,15 +433,16 @@ __global__ void __launch_bounds__(256, SWEEP_BLOCKS_PER_SM)
 // (each leaves one child and enters another), so only the 24 faces on the
 // block's boundary are formed:
 //   sum_c r_c = sum_c f_c - (1/h^2) sum_{boundary f} beta_f (x_in - x_out).
+template <bool B>
 __global__ void k_restrict_rho(Bat bt, Dims df, float ih2, const __half* __restrict__ rho,
                                const float* __restrict__ xf, const float* __restrict__ ff, Dims dc,
                                float* __restrict__ fc, int kchunk) {
-    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    rho = bat_at(bt, bb.cs, rho);
-    xf = bat_at(bt, bb.cs, xf);
-    ff = bat_at(bt, bb.cs, ff);
-    fc = bat_at(bt, bb.cs, fc);
+    rho = bat_at<B>(bt, bb.cs, rho);
+    xf = bat_at<B>(bt, bb.cs, xf);
+    ff = bat_at<B>(bt, bb.cs, ff);
+    fc = bat_at<B>(bt, bb.cs, fc);
     const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
     if (I >= dc.nx || J >= dc.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, dc.nz);
@@ -578,15 +579,16 @@ __global__ void k_wait_probe(double* __restrict__ err, int limit) {
 // loads, the two outer x neighbours as scalars. Each cell's stencil is
 // summed in the order of k_apply_A_dot_rho32; the thread's partial of p.q
 // takes the pair's two cells in turn.
+template <bool B>
 __global__ void k_apply_A_dot_rho32_pair(Bat bt, Dims d, float ih2, const float* __restrict__ rho,
                                          const float* __restrict__ p, float* __restrict__ q,
                                          double* __restrict__ part, int kchunk) {
-    const BatBlk bb = bat_blk(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
-    rho = bat_at(bt, bb.cs, rho);
-    p = bat_at(bt, bb.cs, p);
-    q = bat_at(bt, bb.cs, q);
-    part = bat_at(bt, bb.cs, part);
+    rho = bat_at<B>(bt, bb.cs, rho);
+    p = bat_at<B>(bt, bb.cs, p);
+    q = bat_at<B>(bt, bb.cs, q);
+    part = bat_at<B>(bt, bb.cs, part);
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     const int i = 2 * t;
     const bool act = i < d.nx && j < d.ny;
@@ -702,12 +704,15 @@ vof_status rho_path_setup(vof_ctx* c) {
         !encode_plane_map(c->tmap[1], L0.d, c->x32b, false, SBX) ||
         !encode_plane_map(c->tmap[2], L0.d, c->rho16, true, HBX))
         return set_err(c, VOF_ERR_CUDA, "TMA tensor-map encoding is unavailable");
-    if (cudaFuncSetAttribute(k_sweep_rho<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SWEEP_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sweep_rho<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SWEEP_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sweep_rho<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SWEEP_SMEM) != cudaSuccess)
+    void (*const sweeps[6])(const CUtensorMap, const CUtensorMap, SweepArgs) = {
+        k_sweep_rho<true, false, false>, k_sweep_rho<false, false, false>,
+        k_sweep_rho<false, true, false>, k_sweep_rho<true, false, true>,
+        k_sweep_rho<false, false, true>, k_sweep_rho<false, true, true>};
+    bool attr_ok = true;
+    for (auto k : sweeps)
+        attr_ok = attr_ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)SWEEP_SMEM) == cudaSuccess;
+    if (!attr_ok)
         return cuda_check(c, cudaGetLastError(), "smoother shared-memory attribute");
     // z chunks: one wave of resident blocks over the whole grid
     const int tiles = ((L0.d.nx + STX - 1) / STX) * ((L0.d.ny + STY - 1) / STY);
@@ -760,12 +765,11 @@ void rho_sweep(vof_ctx* c, const float* src, float* dst, int c0, bool dot) {
     a.bt = bat_of(c, grid.z);
     int m = timer_begin(c, T_SMOOTH0);
     ++c->nlaunch;
-    if (src == nullptr)
-        k_sweep_rho<true, false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
-    else if (!dot)
-        k_sweep_rho<false, false><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
-    else
-        k_sweep_rho<false, true><<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
+    const bool bat = a.bt.zb != 0;
+    auto kern = src == nullptr ? (bat ? k_sweep_rho<true, false, true> : k_sweep_rho<true, false, false>)
+                : !dot         ? (bat ? k_sweep_rho<false, false, true> : k_sweep_rho<false, false, false>)
+                               : (bat ? k_sweep_rho<false, true, true> : k_sweep_rho<false, true, false>);
+    kern<<<grid, dim3(16, 16), SWEEP_SMEM, c->st>>>(*tx, *tr, a);
     timer_end(c, T_SMOOTH0, m);
     if (dot) finalize_dots_beta(c, (int)(solo.x * solo.y * solo.z));
 }
@@ -780,7 +784,8 @@ void rho_restrict(vof_ctx* c) {
     int m = timer_begin(c, T_RESTRICT0);
     dim3 g = C.L.grid;
     const Bat bt = bat_of(c, g.z);
-    VOF_LAUNCH(c, k_restrict_rho, g, C.L.block, bt, F.d, (float)(1.0 / (F.h * F.h)),
+    auto kern = bt.zb ? k_restrict_rho<true> : k_restrict_rho<false>;
+    VOF_LAUNCH(c, kern, g, C.L.block, bt, F.d, (float)(1.0 / (F.h * F.h)),
                (const __half*)c->rho16, F.xf, F.ff, C.d, C.ff, C.L.kchunk);
     timer_end(c, T_RESTRICT0, m);
 }
@@ -796,7 +801,8 @@ void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot) {
     const dim3 solo(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
     dim3 grid = solo;
     const Bat bt = bat_of(c, grid.z);
-    VOF_LAUNCH(c, k_apply_A_dot_rho32_pair, grid, L.L.block, bt, L.d, (float)(1.0 / (L.h * L.h)),
+    auto kern = bt.zb ? k_apply_A_dot_rho32_pair<true> : k_apply_A_dot_rho32_pair<false>;
+    VOF_LAUNCH(c, kern, grid, L.L.block, bt, L.d, (float)(1.0 / (L.h * L.h)),
                c->rho32, p, q, c->part + (size_t)slot * MAX_PARTIALS, kchunk);
     timer_end(c, T_RESIDUAL, m);
     finalize_pq_alpha(c, (int)(solo.x * solo.y * solo.z));

@@ -123,8 +123,18 @@ struct BatBlk {
     int g;     // the solo grid's extent along that axis
     bool off;  // its case has finished
 };
+// B: the kernel was instantiated for batched launches; the solo instantiation
+// (B = false) compiles to the unbatched code
+template <bool B>
 __device__ __forceinline__ BatBlk bat_blk(const Bat& t, unsigned idx, unsigned dim) {
     BatBlk r;
+    if (!B) {
+        r.cs = 0;
+        r.b = (int)idx;
+        r.g = (int)dim;
+        r.off = false;
+        return r;
+    }
     if (t.zb) {
         r.cs = (int)(idx / (unsigned)t.zb);
         r.b = (int)idx - r.cs * t.zb;
@@ -138,8 +148,9 @@ __device__ __forceinline__ BatBlk bat_blk(const Bat& t, unsigned idx, unsigned d
     return r;
 }
 // the case's copy of a workspace array
-template <class T>
+template <bool B, class T>
 __device__ __forceinline__ T* bat_at(const Bat& t, int cs, T* p) {
+    if (!B) return p;
     return t.zb ? (T*)((const char*)p + (long long)cs * t.stride) : p;
 }
 // block_linear() of the solo grid, for a grid batched along z
@@ -397,6 +408,8 @@ void timer_end(vof_ctx* c, int cls, int mark);
 // reductions (k_common.cu): sum / max of the block partials of slot into scal[dst]
 // the device scalars into c->hbuf, then a wait on the context stream
 void readback(vof_ctx* c);
+// the same without the wait: c->hbuf is valid once the stream has reached it
+void readback_async(vof_ctx* c);
 double* mirror_acquire();
 void mirror_release(double* p);
 void finalize_sum(vof_ctx* c, int slot, int nparts, int dst, double scale);
@@ -532,9 +545,12 @@ BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride);
 void batch_solve_destroy(BatchSolveState* bs);
 // whether the batched solve supports contexts made with this solver
 bool batch_solve_eligible(const vof_ctx* c);
+// step_pre in two parts: the CFL reduction and its readback, launched without
+// a wait, then (once the stream has finished them) its test and the rest
+vof_status step_pre_cfl(vof_ctx* c, double* const f[8], double dt);
 vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index);
-vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve,
-                     vof_report* report);
+vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve);
+vof_status step_post_report(vof_ctx* c, vof_status solve, vof_report* report);
 void launch_zero32_bat(vof_ctx* c, float* x, int n);                 // x = 0 (batched, masked)
 void launch_copy32_bat(vof_ctx* c, float* dst, const float* src, int n);  // dst = src
 void readback_batch(vof_ctx* c, double* mirror_dev);  // every case's scalars, then a wait
