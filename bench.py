@@ -84,6 +84,10 @@ def parse():
                          "loops on the host: the same kernels in the same order, and the mode "
                          "ncu can profile (it cannot profile kernel nodes of graphs with "
                          "conditional nodes)")
+    ap.add_argument("--mg-tail", type=int, default=0,
+                    help="coarse levels: 0 one launch per operation (replayed from the cycle's "
+                         "graph), 1 one cluster launch per visit, 2 one grid-wide cooperative "
+                         "launch per visit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-one-thread", action="store_true",
                     help="also time the oracle's sample on one host thread (slow)")
@@ -553,7 +557,8 @@ def main():
     with torch.cuda.stream(stream):
         gmode = {"auto": vd.GRAPH_AUTO, "cycle": vd.GRAPH_CYCLE, "off": vd.GRAPH_OFF}[args.graph]
         ctx = vd.VofContext(g, case.phys,
-                            vd.c_solver(prec, rtol=args.rtol, max_iter=500, graph=gmode),
+                            vd.c_solver(prec, rtol=args.rtol, max_iter=500, graph=gmode,
+                                        mg_tail=args.mg_tail),
                             stream=stream)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         T = [dev(x) for x in case.state()]

@@ -134,13 +134,18 @@ typedef struct {
                              at most 8192 cells down, each visit of the cycle
                              runs as one launch on one thread-block cluster,
                              its operations separated by cluster barriers,
-                             with the same arithmetic (equal iterates)      */
+                             with the same arithmetic (equal iterates);
+                             VOF_TAIL_GRID: the same from the first level of
+                             at most 131072 cells down, each visit one
+                             cooperative launch over every SM with its
+                             operations separated by grid-wide barriers
+                             (bounded waits: VOF_ERR_TIMEOUT if one gives up) */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
 enum { VOF_CYCLE_W = 0, VOF_CYCLE_V = 1 };
 enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1, VOF_GRAPH_CYCLE = 2 };
-enum { VOF_TAIL_LAUNCHES = 0, VOF_TAIL_CLUSTER = 1 };
+enum { VOF_TAIL_LAUNCHES = 0, VOF_TAIL_CLUSTER = 1, VOF_TAIL_GRID = 2 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 

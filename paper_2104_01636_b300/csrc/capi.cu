@@ -517,7 +517,8 @@ static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
         (solver->mg_cycle != VOF_CYCLE_V && solver->mg_cycle != VOF_CYCLE_W) ||
         (solver->graph != VOF_GRAPH_AUTO && solver->graph != VOF_GRAPH_OFF &&
          solver->graph != VOF_GRAPH_CYCLE) ||
-        (solver->mg_tail != VOF_TAIL_LAUNCHES && solver->mg_tail != VOF_TAIL_CLUSTER) ||
+        (solver->mg_tail != VOF_TAIL_LAUNCHES && solver->mg_tail != VOF_TAIL_CLUSTER &&
+         solver->mg_tail != VOF_TAIL_GRID) ||
         solver->mg_w_depth < 0 || solver->ssf_solves < 0 || solver->ssf_solves > 2 ||
         solver->nu_fine < 0 ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))

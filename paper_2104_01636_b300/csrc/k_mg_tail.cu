@@ -13,6 +13,15 @@
 // boundaries. The level arrays stay in global memory (a few MB, resident in
 // L2); values written inside the launch are read back with L2 loads.
 //
+// The grid-wide variant (VOF_TAIL_GRID) runs the same program as one
+// cooperative launch with one block on every SM, the operations separated
+// by a grid-wide barrier: a counter in global memory that each block's
+// first thread raises after a fence and then waits on with acquire loads.
+// The counter only grows within a launch (operation o completes at
+// (o + 1) x blocks) and is cleared before each launch. Every wait is
+// bounded: a block that gives up sets the error flag and returns, so the
+// others give up at their next barrier and the launch ends.
+//
 // The operations and their order come from the host (the same recursion as
 // the launch-per-operation cycle, solver.cu) as a short program in device
 // memory; the cell arithmetic is that of k_mg.cu (mg_cell.cuh), so the tail
@@ -30,14 +39,42 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+constexpr int GRID_WAIT_LIMIT = 1 << 21;  // acquire loads before a barrier wait gives up
+
+// false once the wait gave up (the error flag is then set)
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* count, unsigned target, double* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        ok = 1;
+        for (int it = 0;; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (it >= GRID_WAIT_LIMIT) {
+                *err = 1.0;
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned cluster_ctarank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
 
+template <bool GRID>
 __global__ void __launch_bounds__(TAIL_THREADS, 1)
-    k_mg_tail(const TailProg* __restrict__ prog, const float* __restrict__ minv) {
+    k_mg_tail(const TailProg* __restrict__ prog, const float* __restrict__ minv,
+              unsigned* __restrict__ bar, double* __restrict__ err) {
     __shared__ float fs[DENSE_MAX];
     __shared__ TailProg sp;  // the program, read once
     {
@@ -47,8 +84,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1)
             dst[e] = src[e];
         __syncthreads();
     }
-    const int nthr = gridDim.x * blockDim.x;  // the grid is one cluster
-    const int gt = (int)cluster_ctarank() * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;  // the grid: one cluster, or one block per SM
+    const int gt = (int)(GRID ? blockIdx.x : cluster_ctarank()) * blockDim.x + threadIdx.x;
     const int nops = sp.nops;
     const float omega = sp.omega;
     const LdL2 ld;
@@ -97,7 +134,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1)
                 if (lane == 0) L.x[row] = (float)s;
             }
         }
-        cluster_sync_all();
+        if (GRID) {
+            if (!grid_sync_bounded(bar, (unsigned)(o + 1) * gridDim.x, err)) return;
+        } else {
+            cluster_sync_all();
+        }
     }
 }
 
@@ -107,15 +148,28 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1)
 // 8) and uploads the two programs (first visit from zero, later visits from
 // the level's current x). Leaves c->tail_level at 0 when the tail cannot run.
 vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero,
-                         const TailProg* from_x) {
+                         const TailProg* from_x, bool grid) {
     c->tail_level = 0;
-    if (cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-        cudaSuccess) {
+    int cs = 0, gb = 0;
+    if (grid) {
+        // one resident block per SM, which a cooperative launch guarantees
+        int coop = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev) != cudaSuccess ||
+            !coop ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_tail<true>, TAIL_THREADS,
+                                                          0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            return VOF_OK;
+        }
+        gb = c->sm_count;
+    } else if (cudaFuncSetAttribute(k_mg_tail<false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                    1) != cudaSuccess) {
         cudaGetLastError();
         return VOF_OK;
     }
-    int cs = 0;
     for (int want : {16, 8}) {
+        if (grid) break;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -127,16 +181,17 @@ vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero,
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail, &cfg) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail<false>, &cfg) == cudaSuccess &&
             nclusters >= 1) {
             cs = want;
             break;
         }
         cudaGetLastError();
     }
-    if (cs == 0) return VOF_OK;
-    TailProg* d = (TailProg*)dev_alloc(c, 2 * sizeof(TailProg));
+    if (cs == 0 && gb == 0) return VOF_OK;
+    TailProg* d = (TailProg*)dev_alloc(c, 2 * sizeof(TailProg) + 256);
     if (!d) return set_err(c, VOF_ERR_OOM, "allocation of the coarse-tail program failed");
+    c->tail_bar = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(d) + 2 * sizeof(TailProg));
     c->tail_host[0] = *from_zero;
     c->tail_host[1] = *from_x;
     if (cudaMemcpyAsync(d, c->tail_host, 2 * sizeof(TailProg), cudaMemcpyHostToDevice, c->st) !=
@@ -144,6 +199,7 @@ vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero,
         return cuda_check(c, cudaGetLastError(), "coarse-tail program upload");
     c->tail_prog = d;
     c->tail_cluster = cs;
+    c->tail_grid = gb;
     c->tail_level = level;
     return VOF_OK;
 }
@@ -151,11 +207,17 @@ vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero,
 void mg_tail_run(vof_ctx* c, bool zero_start) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = c->tail_cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(c->tail_cluster);
+    if (c->tail_grid) {
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.gridDim = dim3(c->tail_grid);
+    } else {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = c->tail_cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(c->tail_cluster);
+    }
     cfg.blockDim = dim3(TAIL_THREADS);
     cfg.stream = c->st;
     cfg.attrs = at;
@@ -163,6 +225,13 @@ void mg_tail_run(vof_ctx* c, bool zero_start) {
     const TailProg* p = c->tail_prog + (zero_start ? 0 : 1);
     int m = timer_begin(c, T_COARSE);
     ++c->nlaunch;
-    cudaLaunchKernelEx(&cfg, k_mg_tail, p, (const float*)c->dense_inv_f);
+    if (c->tail_grid) {
+        cudaMemsetAsync(c->tail_bar, 0, sizeof(unsigned), c->st);
+        cudaLaunchKernelEx(&cfg, k_mg_tail<true>, p, (const float*)c->dense_inv_f, c->tail_bar,
+                           c->scal + S_ERR);
+    } else {
+        cudaLaunchKernelEx(&cfg, k_mg_tail<false>, p, (const float*)c->dense_inv_f, c->tail_bar,
+                           c->scal + S_ERR);
+    }
     timer_end(c, T_COARSE, m);
 }

@@ -146,10 +146,16 @@ bool tail_emit(const vof_ctx* c, int l, int t0, bool zero_start, TailProg& p) {
 vof_status tail_setup(vof_ctx* c) {
     const int nl = (int)c->lv.size();
     if (c->sv.precision != VOF_PREC_MIXED_FP32 || c->sv.mg_interp != VOF_MG_CONSTANT ||
-        c->dense_n <= 0 || c->sv.mg_tail != VOF_TAIL_CLUSTER)
+        c->dense_n <= 0 ||
+        (c->sv.mg_tail != VOF_TAIL_CLUSTER && c->sv.mg_tail != VOF_TAIL_GRID))
         return VOF_OK;
+    const bool grid = c->sv.mg_tail == VOF_TAIL_GRID;
     for (int t0 = 1; t0 + 1 < nl; ++t0) {
-        if (c->lv[t0].ncells > TAIL_MAX_CELLS || nl - t0 > TAIL_MAX_LEVELS) continue;
+        if (c->lv[t0].ncells > (grid ? TAIL_GRID_MAX_CELLS : TAIL_MAX_CELLS) ||
+            nl - t0 > TAIL_MAX_LEVELS)
+            continue;
+        // the FP16 coefficient copies of a large level are not the tail's
+        if (c->lv[t0].bxh) continue;
         TailProg p[2];
         for (int z = 0; z < 2; ++z) {
             p[z] = TailProg{};
@@ -161,7 +167,7 @@ vof_status tail_setup(vof_ctx* c) {
             }
         }
         if (tail_emit(c, t0, t0, true, p[0]) && tail_emit(c, t0, t0, false, p[1]))
-            return mg_tail_setup(c, t0, &p[0], &p[1]);
+            return mg_tail_setup(c, t0, &p[0], &p[1], grid);
     }
     return VOF_OK;
 }
@@ -491,7 +497,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
             k32_cg_update(c, n, c->e32, r32, c->p32, c->q32, S_RR);
             readback(c);
             if (c->hbuf[S_ERR] != 0.0)
-                return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+                return set_err(c, VOF_ERR_TIMEOUT, "a bounded device wait (TMA loads or a grid barrier) gave up");
             const double rr = c->hbuf[S_RR];
             if (!std::isfinite(rr)) return set_err(c, VOF_ERR_NONFINITE, "non-finite inner residual");
             if (rr <= tol_in * tol_in * rr0) break;
@@ -505,7 +511,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
         readback(c);
         res = std::sqrt(c->hbuf[S_RR]) / bnorm;
         if (c->hbuf[S_ERR] != 0.0)
-            return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+            return set_err(c, VOF_ERR_TIMEOUT, "a bounded device wait (TMA loads or a grid barrier) gave up");
         if (!std::isfinite(res)) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
         ++outer;
         converged = res <= c->sv.rtol;
@@ -796,7 +802,7 @@ vof_status solve_mixed_graph(vof_ctx* c, const vof_ctx::SolveGraph& sg, vof_repo
     if (st != VOF_OK) return st;
     const int status = (int)c->hbuf[S_STATUS];
     if (status == ST_TIMEOUT)
-        return set_err(c, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+        return set_err(c, VOF_ERR_TIMEOUT, "a bounded device wait (TMA loads or a grid barrier) gave up");
     if (status == ST_NONFINITE) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
     if (c->hbuf[S_CONV] == 0.0)
         return set_err(c, VOF_ERR_NOT_CONVERGED,
@@ -1085,7 +1091,7 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
                 CaseSolve& q = cs[i];
                 if (!q.inner || q.err) continue;
                 if (S(i, S_ERR) != 0.0) {
-                    fail(i, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+                    fail(i, VOF_ERR_TIMEOUT, "a bounded device wait (TMA loads or a grid barrier) gave up");
                     continue;
                 }
                 const double rr = S(i, S_RR);
@@ -1110,7 +1116,7 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
             if (!q.outer || q.err) continue;
             q.res = std::sqrt(S(i, S_RR)) / q.bnorm;
             if (S(i, S_ERR) != 0.0) {
-                fail(i, VOF_ERR_TIMEOUT, "a smoother wait on its TMA loads gave up");
+                fail(i, VOF_ERR_TIMEOUT, "a bounded device wait (TMA loads or a grid barrier) gave up");
                 continue;
             }
             if (!std::isfinite(q.res)) {

@@ -200,7 +200,8 @@ struct Level {
 constexpr int HALF_COEF_MIN_CELLS = 1 << 18;
 constexpr int TAIL_MAX_LEVELS = 16;
 constexpr int TAIL_MAX_OPS = 256;
-constexpr int TAIL_MAX_CELLS = 8192;  // largest level the tail starts from
+constexpr int TAIL_MAX_CELLS = 8192;  // largest level the cluster tail starts from
+constexpr int TAIL_GRID_MAX_CELLS = 1 << 17;  // largest level the grid-wide tail starts from
 enum TailKind { TAIL_SMOOTH = 0, TAIL_RESTRICT = 1, TAIL_DENSE = 2 };
 struct TailLevel {
     Dims d;
@@ -309,7 +310,9 @@ struct vof_ctx {
 
     // coarse tail (0: not used); programs from zero / from the current x
     int tail_level = 0;
-    int tail_cluster = 0;
+    int tail_cluster = 0;  // CTAs of the cluster tail, or 0
+    int tail_grid = 0;     // blocks of the grid-wide tail (one per SM), or 0
+    unsigned* tail_bar = nullptr;  // its barrier counter
     TailProg* tail_prog = nullptr;  // device copies of tail_host
     TailProg tail_host[2];
 
@@ -493,7 +496,8 @@ void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
 void mg_half_coefficients(vof_ctx* c);
 
 // coarse tail (k_mg_tail.cu)
-vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero, const TailProg* from_x);
+vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero, const TailProg* from_x,
+                         bool grid);
 void mg_tail_run(vof_ctx* c, bool zero_start);
 
 // vof (k_vof.cu)

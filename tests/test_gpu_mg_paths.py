@@ -84,18 +84,22 @@ def _solve_counted(g, ph, a, b, **kw):
         return host(p), rep, C.launch_count() - n0
 
 
-@pytest.mark.parametrize("dims,kw", [((64, 48, 64), {}),                 # tail from level 2
-                                     ((128, 96, 64), {}),                # tail from level 3
+@pytest.mark.parametrize("tail", [1, 2])
+@pytest.mark.parametrize("dims,kw", [((64, 48, 64), {}),                 # cluster tail from level 2
+                                     ((128, 96, 64), {}),                # cluster tail from level 3
                                      ((64, 32, 32), {"mg_w_depth": 8}),  # W visits inside the tail
                                      ((64, 32, 32), {"mg_cycle": 1}),    # V-cycle
                                      ((88, 40, 32), {"nu_pre": 3, "nu_post": 3})])
-def test_coarse_tail_equals_launch_per_operation(dims, kw):
+def test_coarse_tail_equals_launch_per_operation(dims, kw, tail):
     """The coarse levels run as one launch per smoothing pass, restriction
-    and coarsest solve (default) or, from a level of at most 8192 cells down,
-    as one thread-block-cluster launch per visit: same cell arithmetic in the
-    same order, so the same iterates bit for bit, with fewer launches."""
+    and coarsest solve (default) or, from a small level down, as one launch
+    per visit: on one thread-block cluster from a level of at most 8192
+    cells (tail 1), or cooperatively on every SM with grid-wide barriers
+    from a level of at most 131072 cells (tail 2). Same cell arithmetic in
+    the same order, so the same iterates bit for bit, with fewer launches."""
     g, ph, a, b, _ = _problem(dims, 4, 53)
-    Pt, rt, nt = _solve_counted(g, ph, a, b, rtol=1e-10, precision=1, graph=1, mg_tail=1, **kw)
+    Pt, rt, nt = _solve_counted(g, ph, a, b, rtol=1e-10, precision=1, graph=1, mg_tail=tail,
+                                **kw)
     Po, ro, no = _solve_counted(g, ph, a, b, rtol=1e-10, precision=1, graph=1, **kw)
     assert rt["res"] <= 1e-10 and ro["res"] <= 1e-10
     assert rt["iters"] == ro["iters"]
