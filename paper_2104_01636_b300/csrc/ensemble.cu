@@ -145,6 +145,7 @@ bool create_batched(vof_ensemble* e, const vof_grid* grid, const vof_phys* phys,
             create_in_arena(grid, phys + (n_phys == 1 ? 0 : c), sv, e->streams[c % e->nworkers],
                             e->arena + (size_t)c * S, (size_t)S, &e->ctx[c]);
         ok = st == VOF_OK && e->ctx[c]->arena_used == e->ctx[0]->arena_used;
+        if (ok) e->ctx[c]->defer_dense = true;
         if (c == 0 && ok) ok = batch_solve_eligible(e->ctx[0]);
     }
     if (ok) {
@@ -154,6 +155,7 @@ bool create_batched(vof_ensemble* e, const vof_grid* grid, const vof_phys* phys,
     if (!ok) {
         for (vof_ctx*& c : e->ctx)
             if (c) {
+                c->defer_dense = false;
                 vof_destroy(c);
                 c = nullptr;
             }

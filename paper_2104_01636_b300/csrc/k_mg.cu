@@ -464,10 +464,16 @@ __global__ void k_coarse_cg_t(Dims d, T ih2, const T* __restrict__ bx, const T* 
 // M = A_c + s 1 1^T (SPD; on mean-free right sides M^{-1} f is the mean-free
 // solution of A_c x = f, since the constants are an eigenvector of M with
 // eigenvalue s n and the range of A_c is orthogonal to them).
-template <class T>
-__global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
+template <class T, bool B>
+__global__ void k_dense_assemble(Bat bt, Dims d, double ih2, const T* __restrict__ bx,
                                  const T* __restrict__ by, const T* __restrict__ bz, double s,
                                  T* __restrict__ M) {
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    bx = bat_at<B>(bt, bb.cs, bx);
+    by = bat_at<B>(bt, bb.cs, by);
+    bz = bat_at<B>(bt, bb.cs, bz);
+    M = bat_at<B>(bt, bb.cs, M);
     const int n = d.nx * d.ny * d.nz;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n;
          e += (long)gridDim.x * blockDim.x) {
@@ -505,9 +511,15 @@ __global__ void k_dense_assemble(Dims d, double ih2, const T* __restrict__ bx,
 // identity, then -C A^-1 and A^-1 B) and the rank-32 update of the rest.
 constexpr int GJB = 32;
 
-template <class S>
-__global__ void k_gj_panel(int n, int k, int bs, const S* __restrict__ M, S* __restrict__ P,
-                           S* __restrict__ Cp, S* __restrict__ Bp) {
+template <class S, bool B>
+__global__ void k_gj_panel(Bat bt, int n, int k, int bs, const S* __restrict__ M,
+                           S* __restrict__ P, S* __restrict__ Cp, S* __restrict__ Bp) {
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.y, gridDim.y);
+    if (bb.off) return;
+    M = bat_at<B>(bt, bb.cs, M);
+    P = bat_at<B>(bt, bb.cs, P);
+    Cp = bat_at<B>(bt, bb.cs, Cp);
+    Bp = bat_at<B>(bt, bb.cs, Bp);
     __shared__ S a[GJB][GJB + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     a[ty][tx] = (ty < bs && tx < bs) ? M[(long)(k + ty) * n + k + tx] : S(ty == tx ? 1 : 0);
@@ -541,9 +553,17 @@ __global__ void k_gj_panel(int n, int k, int bs, const S* __restrict__ M, S* __r
     }
 }
 
-template <class S>
-__global__ void k_gj_update(int n, int k, int bs, const S* __restrict__ M, const S* __restrict__ P,
-                            const S* __restrict__ Cp, const S* __restrict__ Bp, S* __restrict__ out) {
+template <class S, bool B>
+__global__ void k_gj_update(Bat bt, int n, int k, int bs, const S* __restrict__ M,
+                            const S* __restrict__ P, const S* __restrict__ Cp,
+                            const S* __restrict__ Bp, S* __restrict__ out) {
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
+    if (bb.off) return;
+    M = bat_at<B>(bt, bb.cs, M);
+    P = bat_at<B>(bt, bb.cs, P);
+    Cp = bat_at<B>(bt, bb.cs, Cp);
+    Bp = bat_at<B>(bt, bb.cs, Bp);
+    out = bat_at<B>(bt, bb.cs, out);
     __shared__ S cps[GJB][GJB + 1], mk[GJB][GJB + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = blockIdx.y * GJB + ty, j = blockIdx.x * GJB + tx;
@@ -962,16 +982,24 @@ void mg_dense_setup(vof_ctx* c, const Level& L) {
     int m = timer_begin(c, T_COARSE);
     T* A = (T*)c->dense_a;
     T* B = (T*)c->dense_b;
-    VOF_LAUNCH(c, k_dense_assemble<T>, nb, 256, L.d, ih2, a.bx, a.by, a.bz, s, A);
+    const bool bat = c->bat_n > 1;
+    dim3 ga(nb);
+    const Bat bta = bat_of(c, ga.y);
+    auto kas = bat ? k_dense_assemble<T, true> : k_dense_assemble<T, false>;
+    VOF_LAUNCH(c, kas, ga, 256, bta, L.d, ih2, a.bx, a.by, a.bz, s, A);
     T* Pw = (T*)c->dense_w;
     T* Cp = Pw + GJB * GJB;
     T* Bp = Cp + (size_t)GJB * n;
     const int nt = (n + GJB - 1) / GJB;
     for (int k = 0; k < n; k += GJB) {
         const int bs = std::min(GJB, n - k);
-        VOF_LAUNCH(c, k_gj_panel<T>, nt, dim3(GJB, GJB), n, k, bs, (const T*)A, Pw, Cp, Bp);
-        VOF_LAUNCH(c, k_gj_update<T>, dim3(nt, nt), dim3(GJB, GJB), n, k, bs, (const T*)A,
-                   (const T*)Pw, (const T*)Cp, (const T*)Bp, B);
+        dim3 gp(nt), gu(nt, nt);
+        const Bat btp = bat_of(c, gp.y), btu = bat_of(c, gu.z);
+        auto kp = bat ? k_gj_panel<T, true> : k_gj_panel<T, false>;
+        auto ku = bat ? k_gj_update<T, true> : k_gj_update<T, false>;
+        VOF_LAUNCH(c, kp, gp, dim3(GJB, GJB), btp, n, k, bs, (const T*)A, Pw, Cp, Bp);
+        VOF_LAUNCH(c, ku, gu, dim3(GJB, GJB), btu, n, k, bs, (const T*)A, (const T*)Pw,
+                   (const T*)Cp, (const T*)Bp, B);
         std::swap(A, B);
     }
     if (sizeof(T) == 4) c->dense_inv_f = (float*)A;

@@ -439,7 +439,7 @@ static void build_level_coefficients(vof_ctx* c) {
         mg_coarsen_density<float>(c, c->rho32, L0, c->lv[1]);
         for (size_t l = 2; l < c->lv.size(); ++l)
             mg_coarsen_density<float>(c, (const float*)c->lv[l - 1].rho, c->lv[l - 1], c->lv[l]);
-        if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
+        if (c->dense_n > 0 && !c->defer_dense) mg_dense_setup<float>(c, c->lv.back());
         return;
     }
     if (c->sv.precision == VOF_PREC_FP64) {
@@ -453,7 +453,7 @@ static void build_level_coefficients(vof_ctx* c) {
         // the FP64 ones); level 1 averages the FP64 faces
         mg_coarsen_beta_from64(c, L0, c->lv[1]);
         for (size_t l = 2; l < c->lv.size(); ++l) mg_coarsen_beta<float>(c, c->lv[l - 1], c->lv[l]);
-        if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
+        if (c->dense_n > 0 && !c->defer_dense) mg_dense_setup<float>(c, c->lv.back());
         return;
     }
     const int nu = (L0.d.nx + 1) * L0.d.ny * L0.d.nz, nv = L0.d.nx * (L0.d.ny + 1) * L0.d.nz;
@@ -461,7 +461,7 @@ static void build_level_coefficients(vof_ctx* c) {
     mg_to_f32(c, c->by, L0.byf, nv);
     mg_to_f32(c, c->bz, L0.bzf, L0.ncells);
     for (size_t l = 1; l < c->lv.size(); ++l) mg_coarsen_beta<float>(c, c->lv[l - 1], c->lv[l]);
-    if (c->dense_n > 0) mg_dense_setup<float>(c, c->lv.back());
+    if (c->dense_n > 0 && !c->defer_dense) mg_dense_setup<float>(c, c->lv.back());
 }
 
 // Mixed precision: FP64 defect correction around an inner FP32 solve.
@@ -1036,6 +1036,11 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
         cs[i].outer = cs[i].inner = false;
         status[i] = set_err(cases[i], st, msg);
     };
+    // the dense coarsest inverses of all cases (their coefficients were built
+    // by each case's setup), one launch per Gauss-Jordan block step
+    for (int i = 0; i < nc; ++i) bs->act_h[i] = run[i] ? 1 : 0;
+    cudaMemcpyAsync(bs->act_d, bs->act_h, sizeof(int) * nc, cudaMemcpyHostToDevice, m->st);
+    if (m->defer_dense) mg_dense_setup<float>(m, m->lv.back());
     readback_batch(m, bs->mir_d);
     for (int i = 0; i < nc; ++i) {
         status[i] = VOF_OK;

@@ -336,6 +336,7 @@ struct vof_ctx {
     int bat_n = 1;
     long long bat_stride = 0;
     const int* bat_act = nullptr;
+    bool defer_dense = false;  // the batched solve forms the dense coarsest inverse
 };
 
 // The batch of the context's launches: Bat{} for a single case; otherwise
