@@ -609,7 +609,10 @@ def main():
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic_for(cls, args.precision), "algorithmic_bytes": algo,
                     "avg_launch_ms": avg_ms, "launches_per_step": kn / k_steps,
-                    "share_of_step": kms / k_steps / step_ms_timed if step_ms_timed else None,
+                    # the kernel's time per step over the timed step (ms_per_step)
+                    "share_of_step": kms / k_steps / ms_per_step,
+                    "share_of_timed_classes": (kms / k_steps / step_ms_timed
+                                               if step_ms_timed else None),
                     "classes_ms_per_step": {k: round(v[0] / k_steps, 4) for k, v in kt.items()}}
         poisson = N * it2 / (solve_ms / 1e3) if solve_ms > 0 else None
         solves = k_steps / (solve_ms / 1e3) if solve_ms > 0 else None
