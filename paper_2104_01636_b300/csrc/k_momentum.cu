@@ -71,8 +71,11 @@ template <> __device__ __forceinline__ float mu_cell<float>(const Pred& P, int c
 
 // VT: arithmetic of the viscous term (double on the FP64 path; float on the
 // mixed path, where it changes the velocity by ~1e-4 of itself per step).
-// Convection, densities and the update are FP64 on both paths; the face
-// viscosities are formed in VT. Central
+// The mass fluxes, densities and the update are FP64 on both paths; the face
+// viscosities are formed in VT. On the mixed path the transport sum
+// sum_f M_f q*_f is also taken in FP32 (fluxes rounded once, FP32 copies of the
+// cell velocities): it is rounded to 6e-8 of the convective change, which is a
+// fraction of the velocity, so u_hat moves by ~1e-8 of itself. Central
 // convection uses sum_f (+-) M_f (q_c + q_nb)/2 = (q_c net + sum_f (+-) M_f
 // q_nb)/2 with the net outward mass flux formed once per cell; each
 // tangential derivative at the cell is formed once and shared by its two
@@ -141,13 +144,39 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
             left_donor[f] = __double_as_longlong(uf) > 0LL;
         }
         const double r_rn1 = rcp_cubic(rn1);
+        float Msf[6];
+        float netf = 0.f;
+        if constexpr (sizeof(VT) == sizeof(float)) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) Msf[f] = (float)Ms[f];
+            netf = (float)net;
+        }
         double out[3];
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
             const double qc = P.U[comp][c];
             // convection: outward mass flux times the transported velocity
             double C = 0.0;
-            if (P.upwind) {
+            if constexpr (sizeof(VT) == sizeof(float)) {
+                // mixed path: the transport sum in FP32 from the FP32 copies
+                const float* Q = P.U32[comp];
+                const float qcf = Q[c];
+                float Cf = 0.f;
+                if (P.upwind) {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        const bool own = (f & 1) ? left_donor[f] : !left_donor[f];
+                        Cf = fmaf(Msf[f], own ? qcf : Q[nbc[f]], Cf);
+                    }
+                    Cf = 2.f * Cf;
+                } else {
+                    float sf = 0.f;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) sf = fmaf(Msf[f], Q[nbc[f]], sf);
+                    Cf = fmaf(netf, qcf, sf);
+                }
+                C = (double)Cf;
+            } else if (P.upwind) {
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
                     const double qn = P.U[comp][nbc[f]];

@@ -129,8 +129,9 @@ def test_ssf_force_parity(kappa_mode):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_predict_parity(conv, prec):
     """FP64 path: 1e-12 of the field. The mixed path forms the viscous term
-    in FP32: its error is FP32 rounding of a part of the step's increment,
-    so it is bounded by 1e-6 of the largest increment u_hat - u^n."""
+    and the transport sum in FP32: its error is FP32 rounding of parts of the
+    step's increment, so it is bounded by 1e-6 of the largest increment
+    u_hat - u^n."""
     case = I.rising_swarm(36, 28, 40, nbub=3, seed=8, steps=1)
     g = case.grid
     ph = I.Phys(**{**case.phys.__dict__, "conv_scheme": conv})
