@@ -97,11 +97,14 @@ def test_face_force_full_size(duct, bench_ctx):
 
 
 def test_predictor_full_size(duct, advected, bench_ctx):
-    """Mixed path: the viscous term is FP32. Its rounding of the velocities
-    (about 1e-8 m/s here) is multiplied by dt mu_f / (h^2 rho) of up to ~0.1
-    in interface cells, where a liquid face viscosity meets a gas-dominated
-    density, so the bound is stated on the velocity scale: 1e-8 of the
-    largest velocity, the mixed path's bar on velocity."""
+    """Mixed path: the viscous term and the transport sum are FP32. The
+    viscous term's rounding of the velocities is multiplied by
+    dt mu_f / (h^2 rho) of up to ~0.1 in interface cells, where a liquid face
+    viscosity meets a gas-dominated density; the transport sum is rounded to
+    FP32 (6e-8 of itself) and divided by the cell's new density, which in such
+    cells makes it of the order of the velocity itself. So the bound is FP32
+    rounding on the velocity scale: 6e-8 of the largest velocity (measured
+    1.2e-8)."""
     C, stream = bench_ctx
     g = duct.grid
     a1, fl, _ = advected
@@ -115,7 +118,7 @@ def test_predictor_full_size(duct, advected, bench_ctx):
         _sync(stream)
         got = [host(t) for t in T]
     for x, y in zip(got, list(ref_c) + list(ref_f)):
-        assert np.max(np.abs(x - y)) < 1e-8 * np.max(np.abs(y))
+        assert np.max(np.abs(x - y)) < 6e-8 * np.max(np.abs(y))
 
 
 def test_pressure_solve_full_size_meets_rtol(duct, advected, bench_ctx):
