@@ -414,17 +414,22 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
     """n independent 48x48x96 ducts (4-16 spheres each, seeded) advanced
     together, fields resident on the device; mixed precision, rtol 1e-8.
     Timed on the host clock around whole ensemble steps (each call returns
-    when every case has finished), against the same cases on one stream."""
+    when every case has finished): batched solves with the whole step one
+    graph launch and with the loops on the host, the cases overlapped on
+    streams, and on one stream."""
     import numpy as np
     import torch
     cases = I.ensemble_cases(n_cases, dims=(48, 48, 96), seed=2109)
-    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500)
     out = {"cases": n_cases, "grid": "48x48x96", "cells_per_case": cases[0].grid.ncells,
            "precision": "mixed", "rtol": 1e-8, "steps": steps}
-    runs = (("batched", streams, vd.VofEnsemble.BATCHED),
-            ("streams", streams, vd.VofEnsemble.STREAMS),
-            ("one_stream", 1, vd.VofEnsemble.STREAMS))
-    for label, ns, mode in runs:
+    # batched: the whole ensemble step one CUDA graph launch; batched_host_loops:
+    # the same batched solve with its loops on the host
+    runs = (("batched", streams, vd.VofEnsemble.BATCHED, vd.GRAPH_AUTO),
+            ("batched_host_loops", streams, vd.VofEnsemble.BATCHED, vd.GRAPH_CYCLE),
+            ("streams", streams, vd.VofEnsemble.STREAMS, vd.GRAPH_AUTO),
+            ("one_stream", 1, vd.VofEnsemble.STREAMS, vd.GRAPH_AUTO))
+    for label, ns, mode, graph in runs:
+        sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500, graph=graph)
         fields = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in c.state()]
                   for c in cases]
         torch.cuda.synchronize()
@@ -436,12 +441,14 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
             torch.cuda.synchronize()
             n0 = E.launch_count()
             ph0 = E.phase_ms()
+            g0 = E.graph_steps()
             t0 = time.perf_counter()
             for s in range(warmup, warmup + steps):
                 reps = E.step(fields, dts, s, reports=True)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3 / steps
             launches = (E.launch_count() - n0) / steps
+            graph_steps = (E.graph_steps() - g0) / steps
             phases = [(b - a) / steps for a, b in zip(ph0, E.phase_ms())]
             batched = E.batched
         del fields
@@ -450,7 +457,8 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
                       "case_steps_per_s": n_cases / (ms / 1e3),
                       "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3),
                       "kernel_launches_per_ensemble_step": launches,
-                      "ms_before_solve_solve_after": phases,
+                      "graph_launches_per_ensemble_step": graph_steps,
+                      "ms_before_solve_solve_after": phases if graph_steps == 0 else None,
                       "max_inner_iters": max(r["iters"] for r in reps),
                       "mean_inner_iters": sum(r["iters"] for r in reps) / len(reps)}
     return out

@@ -442,6 +442,19 @@ vof_status vof_ensemble_destroy(vof_ensemble* ensemble);
  *    constant prolongation, face-mean coarsening, a dense coarsest level, an
  *    even number of finest-level sweeps, the single combined solve and no
  *    cluster tail; otherwise VOF_ERR_UNSUPPORTED.
+ *    With solver->graph VOF_GRAPH_AUTO the whole batched step is one CUDA
+ *    graph launch: the CFL test of every case (one kernel and a device-side
+ *    test), then, under a conditional IF node the test opens, every case's
+ *    step up to its solve (the cases' branches side by side), the batched
+ *    solve with its two loops as conditional WHILE nodes whose per-case
+ *    decisions are taken on the device, and every case's correction. The
+ *    graph is captured at the first step and again whenever the field
+ *    pointers, the time steps or the parity of step_index change. A step
+ *    whose CFL test fails in any case runs again the host-driven way
+ *    (nothing of it was launched), which reports each case's status. In the
+ *    graph, a case whose solve fails (non-finite, or a bounded wait gave up)
+ *    still has its correction applied from the failed pressure; its status
+ *    reports the failure. VOF_GRAPH_CYCLE keeps the loops on the host.
  *  VOF_ENSEMBLE_STREAMS: every case steps through its own context on the
  *    worker streams, overlapping on the GPU.
  *  VOF_ENSEMBLE_AUTO: batched where the solver allows it, else streams
@@ -457,10 +470,13 @@ vof_status vof_ensemble_batched(const vof_ensemble* ensemble, int* batched);
 /* Kernels launched by the ensemble so far (every case, a batched launch
  * counted once). */
 vof_status vof_ensemble_launch_count(const vof_ensemble* ensemble, long long* n);
-/* Host wall time (ms) the steps so far spent in their three parts: ms[0]
- * the parts before the solves (the whole step for a streams ensemble),
- * ms[1] the batched solve, ms[2] the parts after it. */
+/* Host wall time (ms) the host-driven steps so far spent in their three
+ * parts: ms[0] the parts before the solves (the whole step for a streams
+ * ensemble), ms[1] the batched solve, ms[2] the parts after it. Steps run as
+ * one graph launch are not split and not counted here. */
 vof_status vof_ensemble_phase_ms(const vof_ensemble* ensemble, double* ms);
+/* Steps so far that ran as one graph launch. */
+vof_status vof_ensemble_graph_steps(const vof_ensemble* ensemble, long long* n);
 
 /* ---- duct statistics ------------------------------------------------------
  * Running sums for the profiles of Section 4 (averages over the streamwise

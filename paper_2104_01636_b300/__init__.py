@@ -140,6 +140,7 @@ def load() -> ctypes.CDLL:
         "vof_ensemble_batched": [_VP, P(ctypes.c_int)],
         "vof_ensemble_launch_count": [_VP, P(ctypes.c_longlong)],
         "vof_ensemble_phase_ms": [_VP, P(_D)],
+        "vof_ensemble_graph_steps": [_VP, P(ctypes.c_longlong)],
         "vof_stats_create": [P(CGrid), P(_VP)],
         "vof_stats_accumulate": [_VP, _VP, _VP, _VP, _VP, _VP],
         "vof_stats_read": [_VP, P(_D), P(ctypes.c_longlong)],
@@ -497,6 +498,12 @@ class VofEnsemble:
     def launch_count(self) -> int:
         n = ctypes.c_longlong(0)
         self.lib.vof_ensemble_launch_count(self._e, ctypes.byref(n))
+        return int(n.value)
+
+    def graph_steps(self) -> int:
+        """Steps so far that ran as one CUDA graph launch."""
+        n = ctypes.c_longlong(0)
+        self.lib.vof_ensemble_graph_steps(self._e, ctypes.byref(n))
         return int(n.value)
 
     def step(self, fields, dts, step_index: int, reports: bool = False):

@@ -387,12 +387,16 @@ vof_status step_pre_cfl(vof_ctx* c, double* const f[8], double dt) {
 // rest of the step up to the solve
 vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index) {
     if (step_index < 0) return set_err(c, VOF_ERR_ARG, "step_index must be >= 0");
-    double* const alpha = f[0];
-    const double *u = f[4], *v = f[5], *w = f[6];
     const double cfl = c->hbuf[S_CFL] * dt / c->g.h;
     if (!std::isfinite(cfl)) return set_err(c, VOF_ERR_NONFINITE, "non-finite velocity");
     if (cfl > 1.0)
         return set_err(c, VOF_ERR_CFL, "Courant number " + std::to_string(cfl) + " exceeds 1");
+    return step_pre_launch(c, f, dt, step_index);
+}
+
+vof_status step_pre_launch(vof_ctx* c, double* const f[8], double dt, long long step_index) {
+    double* const alpha = f[0];
+    const double *u = f[4], *v = f[5], *w = f[6];
     const size_t n = (size_t)c->d.nx * c->d.ny * c->d.nz;
     cudaMemcpyAsync(c->an, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     double* const flux[3] = {c->fx, c->fy, c->fz};

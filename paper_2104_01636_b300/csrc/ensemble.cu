@@ -12,6 +12,19 @@
 //    worker threads launch on their own streams;
 //  * streams: cases are dealt round-robin to worker threads, each driving its
 //    own CUDA stream, so the cases' kernels overlap on the GPU.
+//
+// In the batched mode with the solver's graph option left at AUTO, the whole
+// ensemble step is one CUDA graph launch: the CFL test of every case (one
+// launch and a device-side test), then, under a conditional IF node that the
+// test opens, every case's step up to its solve (the cases' branches run
+// side by side), the batched solve with its loops as conditional WHILE
+// nodes steered on the device, and every case's correction. A step whose
+// CFL test fails in any case is run again the host-driven way, which reports
+// each case's status; nothing of the step has been launched by then. The
+// graph is captured for the step's field pointers and time steps and the
+// parity of the step index (the sweep order), and captured again when they
+// change.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <mutex>
@@ -19,6 +32,16 @@
 #include <vector>
 
 #include "vof_internal.cuh"
+
+// one captured ensemble step and what it was captured for
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double*> f;  // the 8 n field pointers
+    std::vector<double> dt;
+    double* dt_d = nullptr;        // device copies the CFL test reads
+    const double** uvw_d = nullptr;
+    long long k_top = 0, k_body = 0, k_outer = 0, k_inner = 0;  // kernels per replay
+};
 
 struct vof_ensemble {
     int n = 0, nworkers = 0, dev = 0;
@@ -46,9 +69,60 @@ struct vof_ensemble {
     std::vector<vof_status> solve_st;
     std::vector<vof_report> rep;
     double phase_ms[3] = {0.0, 0.0, 0.0};  // host time: before the solve, the solve, after it
+    // the whole step as one graph: 1 in use, 0 host-driven, -1 capture failed
+    int step_graph = 0;
+    StepGraph sg[2];                           // by the parity of the step index
+    cudaStream_t gst[2] = {nullptr, nullptr};  // capture origin, IF body
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    unsigned long long* vmax_d = nullptr;  // per case: largest face-velocity magnitude (bits)
+    int* abort_h = nullptr;                // mapped: the CFL test failed in some case
+    int* abort_d = nullptr;
+    long long graph_steps = 0, graph_kernels = 0;
 };
 
 namespace {
+
+// The CFL test of every case in one launch (blockIdx.y: the case): the
+// largest face-velocity magnitude, over the faces k_cfl reads, with the bit
+// patterns of the magnitudes compared as integers (their order is that of the
+// values, and a NaN sorts above every number).
+__global__ void k_ens_vmax(Dims d, int per_x, int per_y, const double* const* __restrict__ uvw,
+                           unsigned long long* __restrict__ vmax) {
+    const int cs = blockIdx.y;
+    const double* __restrict__ u = uvw[3 * cs];
+    const double* __restrict__ v = uvw[3 * cs + 1];
+    const double* __restrict__ w = uvw[3 * cs + 2];
+    const int n = d.nx * d.ny * d.nz;
+    constexpr unsigned long long MAG = 0x7FFFFFFFFFFFFFFFULL;
+    auto mag = [](double x) { return (unsigned long long)__double_as_longlong(x) & MAG; };
+    unsigned long long mb = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / (d.nx * d.ny);
+        if (i > 0 || per_x) mb = max(mb, mag(u[uid(d, i, j, k)]));
+        if (j > 0 || per_y) mb = max(mb, mag(v[vid(d, i, j, k)]));
+        mb = max(mb, mag(w[wid(d, i, j, k)]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(vmax + cs, mb);
+}
+
+// the test step_pre takes per case (a Courant number above 1 or not finite);
+// the IF node opens only when every case passes
+__global__ void k_ens_cfl_ctl(const unsigned long long* __restrict__ vmax,
+                              const double* __restrict__ dt, int nc, double h, int* abort_flag,
+                              cudaGraphConditionalHandle h_go) {
+    int bad = 0;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const double cfl = __longlong_as_double((long long)vmax[i]) * dt[i] / h;
+        if (!isfinite(cfl) || cfl > 1.0) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        *abort_flag = bad;
+        cudaGraphSetConditional(h_go, bad ? 0u : 1u);
+    }
+}
 
 void ensemble_worker(vof_ensemble* e, int w) {
     cudaSetDevice(e->dev);
@@ -106,6 +180,218 @@ void run_phase(vof_ensemble* e, int phase) {
     e->cv_done.wait(lk, [&] { return e->pending == 0; });
 }
 
+// ---- the whole step as one graph ---------------------------------------------
+void free_step_graph(StepGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.dt_d) cudaFree(g.dt_d);
+    if (g.uvw_d) cudaFree((void*)g.uvw_d);
+    g = StepGraph{};
+}
+
+// the streams, events and flags the captured step uses; false (the
+// ensemble stays host-driven) when any is unavailable
+bool step_graph_resources(vof_ensemble* e) {
+    bool ok = true;
+    for (cudaStream_t& s : e->gst)
+        ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    e->ev_join.assign(e->nworkers, nullptr);
+    for (cudaEvent_t& ev : e->ev_join)
+        ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&e->vmax_d, sizeof(unsigned long long) * e->n) == cudaSuccess;
+    ok = ok && cudaHostAlloc((void**)&e->abort_h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer((void**)&e->abort_d, e->abort_h, 0) == cudaSuccess;
+    cudaGetLastError();
+    return ok;
+}
+
+void free_step_graph_resources(vof_ensemble* e) {
+    for (StepGraph& g : e->sg) free_step_graph(g);
+    for (cudaStream_t& s : e->gst)
+        if (s) cudaStreamDestroy(s);
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    for (cudaEvent_t ev : e->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (e->vmax_d) cudaFree(e->vmax_d);
+    if (e->abort_h) cudaFreeHost(e->abort_h);
+}
+
+// the worker streams join the capture on s, and later join it again
+void fork_to_workers(vof_ensemble* e, cudaStream_t s) {
+    cudaEventRecord(e->ev_fork, s);
+    for (cudaStream_t w : e->streams) cudaStreamWaitEvent(w, e->ev_fork, 0);
+}
+void join_workers(vof_ensemble* e, cudaStream_t s) {
+    for (int w = 0; w < e->nworkers; ++w) {
+        cudaEventRecord(e->ev_join[w], e->streams[w]);
+        cudaStreamWaitEvent(s, e->ev_join[w], 0);
+    }
+}
+
+// Captures the ensemble step for these fields, time steps and step parity
+// into g. Each case's launches go to its own stream (its context's), which
+// joins the capture, so the cases' branches of the graph are those streams'
+// orders; the batched solve is captured on the IF body's origin. False when
+// capture is unavailable (nothing stays captured).
+bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const double* dt,
+                  long long step_index) {
+    const int n = e->n;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    if (!g.dt_d && cudaMalloc((void**)&g.dt_d, sizeof(double) * n) != cudaSuccess) return false;
+    if (!g.uvw_d && cudaMalloc((void**)&g.uvw_d, sizeof(double*) * 3 * n) != cudaSuccess)
+        return false;
+    std::vector<const double*> uvw(3 * (size_t)n);
+    for (int c = 0; c < n; ++c)
+        for (int q = 0; q < 3; ++q) uvw[3 * (size_t)c + q] = fields[8 * (size_t)c + 4 + q];
+    if (cudaMemcpy(g.dt_d, dt, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy((void*)g.uvw_d, uvw.data(), sizeof(double*) * 3 * n,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return false;
+    vof_ctx* m = e->ctx[0];
+    for (cudaStream_t& s : m->cap_st)  // the solve's loop bodies are captured on these
+        if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    std::vector<long long> n0(n);
+    for (int c = 0; c < n; ++c) n0[c] = e->ctx[c]->nlaunch;
+    cudaStream_t s0 = e->gst[0], sb = e->gst[1];
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t gt = capture_graph_of(s0);
+    cudaGraphConditionalHandle h_go = 0;
+    bool ok = gt && cudaGraphConditionalHandleCreate(&h_go, gt, 0, cudaGraphCondAssignDefault) ==
+                        cudaSuccess;
+    const int ncell = m->d.nx * m->d.ny * m->d.nz;
+    const int bpc = std::max(1, std::min((ncell + 2047) / 2048, 1024));
+    const int nthr = n < 1024 ? ((n + 31) / 32) * 32 : 1024;
+    cudaMemsetAsync(e->vmax_d, 0, sizeof(unsigned long long) * n, s0);
+    k_ens_vmax<<<dim3(bpc, n), 256, 0, s0>>>(m->d, m->g.periodic_x, m->g.periodic_y, g.uvw_d,
+                                             e->vmax_d);
+    k_ens_cfl_ctl<<<1, nthr, 0, s0>>>(e->vmax_d, g.dt_d, n, m->g.h, e->abort_d, h_go);
+    cudaGraph_t gif = ok ? capture_if(s0, h_go) : nullptr;
+    ok = ok && gif &&
+         cudaStreamBeginCaptureToGraph(sb, gif, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    long long kk[3] = {0, 0, 0};
+    if (ok) {
+        fork_to_workers(e, sb);
+        for (int c = 0; c < n; ++c)
+            ok = step_pre_launch(e->ctx[c], fields + 8 * (size_t)c, dt[c], step_index) == VOF_OK &&
+                 ok;
+        join_workers(e, sb);
+        cudaStream_t st_m = m->st;
+        m->st = sb;
+        ok = capture_solve_mixed_batch(m, n, e->stride, e->bs, kk) && ok;
+        m->st = st_m;
+        fork_to_workers(e, sb);
+        for (int c = 0; c < n; ++c) {
+            solve_tail_captured(e->ctx[c]);
+            ok = step_post(e->ctx[c], fields + 8 * (size_t)c, dt[c], VOF_OK) == VOF_OK && ok;
+        }
+        join_workers(e, sb);
+        cudaGraph_t gb = nullptr;
+        ok = cudaStreamEndCapture(sb, &gb) == cudaSuccess && ok;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s0, &graph);
+    ok = ok && ee == cudaSuccess && graph &&
+         cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    long long body = 0;
+    for (int c = 0; c < n; ++c) {
+        body += e->ctx[c]->nlaunch - n0[c];
+        e->ctx[c]->nlaunch = n0[c];
+    }
+    if (!ok) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        return false;
+    }
+    g.k_top = 2;
+    g.k_body = body + kk[0];
+    g.k_outer = kk[1];
+    g.k_inner = kk[2];
+    g.f.assign(fields, fields + 8 * (size_t)n);
+    g.dt.assign(dt, dt + n);
+    return true;
+}
+
+// One ensemble step as one graph launch. *done is false when the step has to
+// run the host-driven way (a failed CFL test, or no graph).
+void run_step_graph(vof_ensemble* e, double* const* fields, const double* dt,
+                    long long step_index, vof_report* reports, bool* done) {
+    *done = false;
+    const int n = e->n;
+    StepGraph& g = e->sg[step_index & 1];
+    const bool same = g.exec && std::equal(g.f.begin(), g.f.end(), fields) &&
+                      std::equal(g.dt.begin(), g.dt.end(), dt);
+    if (!same && !capture_step(e, g, fields, dt, step_index)) {
+        e->step_graph = -1;
+        return;
+    }
+    for (vof_ctx* c : e->ctx) c->err.clear();
+    cudaGraphLaunch(g.exec, e->gst[0]);
+    const cudaError_t ce = cudaStreamSynchronize(e->gst[0]);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        for (int c = 0; c < n; ++c)
+            e->status[c] = cuda_check(e->ctx[c], ce, "ensemble step graph");
+        *done = true;
+        return;
+    }
+    if (*e->abort_h) {
+        e->graph_kernels += g.k_top;
+        return;
+    }
+    long long to = 0, ti = 0;
+    batch_solve_trips(e->bs, &to, &ti);
+    e->graph_kernels += g.k_top + g.k_body + to * g.k_outer + ti * g.k_inner;
+    ++e->graph_steps;
+    for (int c = 0; c < n; ++c) {
+        vof_report r{};
+        const vof_status solve = captured_case_result(e->ctx[c], &r);
+        e->status[c] = step_post_report(e->ctx[c], solve, &r);
+        if (reports) reports[c] = r;
+    }
+    *done = true;
+}
+
+// the batched step driven from the host: the cases' parts before the solve
+// on the worker streams, the batched solve with its loops on the host, the
+// parts after it on the worker streams
+void batched_host_step(vof_ensemble* e, vof_report* reports) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t0) {
+        return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    };
+    auto t0 = clk::now();
+    run_phase(e, 1);
+    e->phase_ms[0] += ms_since(t0);
+    t0 = clk::now();
+    for (int c = 0; c < e->n; ++c) {
+        e->run[c] = e->status[c] == VOF_OK ? 1 : 0;
+        e->rep[c] = vof_report{};
+        e->solve_st[c] = VOF_OK;
+    }
+    const vof_status st = solve_mixed_batch(e->ctx[0], e->n, e->stride, e->run.data(), e->bs,
+                                            e->solve_st.data(), e->rep.data(), e->ctx.data());
+    if (st != VOF_OK)
+        for (int c = 0; c < e->n; ++c)
+            if (e->run[c]) e->status[c] = st;
+    e->phase_ms[1] += ms_since(t0);
+    t0 = clk::now();
+    run_phase(e, 2);
+    e->phase_ms[2] += ms_since(t0);
+    if (reports)
+        for (int c = 0; c < e->n; ++c)
+            if (e->run[c]) reports[c] = e->rep[c];
+}
+
 void destroy_all(vof_ensemble* e) {
     {
         std::lock_guard<std::mutex> lk(e->mu);
@@ -113,6 +399,7 @@ void destroy_all(vof_ensemble* e) {
     }
     e->cv_go.notify_all();
     for (auto& t : e->workers) t.join();
+    free_step_graph_resources(e);
     for (vof_ctx* c : e->ctx)
         if (c) vof_destroy(c);
     batch_solve_destroy(e->bs);
@@ -211,6 +498,10 @@ vof_status vof_ensemble_create_mode(const vof_grid* grid, const vof_phys* phys, 
             destroy_all(e);
             return err != VOF_OK ? err : VOF_ERR_UNSUPPORTED;
         }
+        // the batched step as one graph unless the solver asks for the
+        // host-driven loops (VOF_GRAPH_CYCLE) or direct launches
+        if (e->batched && solver->graph == VOF_GRAPH_AUTO)
+            e->step_graph = step_graph_resources(e) ? 1 : -1;
     }
     if (!e->batched)
         for (int c = 0; c < n_cases; ++c) {
@@ -260,27 +551,9 @@ vof_status vof_ensemble_step(vof_ensemble* e, double* const* fields, const doubl
         run_phase(e, 0);
         e->phase_ms[0] += ms_since(t0);
     } else {
-        auto t0 = clk::now();
-        run_phase(e, 1);
-        e->phase_ms[0] += ms_since(t0);
-        t0 = clk::now();
-        for (int c = 0; c < e->n; ++c) {
-            e->run[c] = e->status[c] == VOF_OK ? 1 : 0;
-            e->rep[c] = vof_report{};
-            e->solve_st[c] = VOF_OK;
-        }
-        const vof_status st = solve_mixed_batch(e->ctx[0], e->n, e->stride, e->run.data(), e->bs,
-                                                e->solve_st.data(), e->rep.data(), e->ctx.data());
-        if (st != VOF_OK)
-            for (int c = 0; c < e->n; ++c)
-                if (e->run[c]) e->status[c] = st;
-        e->phase_ms[1] += ms_since(t0);
-        t0 = clk::now();
-        run_phase(e, 2);
-        e->phase_ms[2] += ms_since(t0);
-        if (reports)
-            for (int c = 0; c < e->n; ++c)
-                if (e->run[c]) reports[c] = e->rep[c];
+        bool done = false;
+        if (e->step_graph > 0) run_step_graph(e, fields, dt, step_index, reports, &done);
+        if (!done) batched_host_step(e, reports);
     }
     vof_status first = VOF_OK;
     for (int c = 0; c < e->n; ++c) {
@@ -296,9 +569,15 @@ vof_status vof_ensemble_phase_ms(const vof_ensemble* e, double* ms) {
     return VOF_OK;
 }
 
+vof_status vof_ensemble_graph_steps(const vof_ensemble* e, long long* n) {
+    if (!e || !n) return VOF_ERR_ARG;
+    *n = e->graph_steps;
+    return VOF_OK;
+}
+
 vof_status vof_ensemble_launch_count(const vof_ensemble* e, long long* n) {
     if (!e || !n) return VOF_ERR_ARG;
-    long long t = 0;
+    long long t = e->graph_kernels;
     for (const vof_ctx* c : e->ctx)
         if (c) t += c->nlaunch;
     *n = t;

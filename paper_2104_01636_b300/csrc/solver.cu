@@ -635,9 +635,10 @@ cudaGraph_t capture_graph(cudaStream_t s) {
     return g;
 }
 
-// appends a conditional WHILE node on handle h after the work captured so
-// far on s; later captures on s follow the node; returns its body graph
-cudaGraph_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+// appends a conditional node (WHILE or IF) on handle h after the work
+// captured so far on s; later captures on s follow the node; returns its body
+// graph
+cudaGraph_t capture_cond(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -649,7 +650,7 @@ cudaGraph_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h) {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.type = type;
     np.conditional.size = 1;
     cudaGraphNode_t node;
     if (cudaGraphAddNode(&node, g, deps, edges, nd, &np) != cudaSuccess) return nullptr;
@@ -657,6 +658,10 @@ cudaGraph_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h) {
                                             cudaStreamSetCaptureDependencies) != cudaSuccess)
         return nullptr;
     return np.conditional.phGraph_out[0];
+}
+
+cudaGraph_t capture_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    return capture_cond(s, h, cudaGraphCondTypeWhile);
 }
 
 // the first CG step of a refinement or the later ones: z = M r, the
@@ -832,6 +837,19 @@ const vof_ctx::SolveGraph* solve_graph_for(vof_ctx* c, const double* b_in, doubl
 
 }  // namespace
 
+cudaGraph_t capture_if(cudaStream_t s, cudaGraphConditionalHandle h) {
+    return capture_cond(s, h, cudaGraphCondTypeIf);
+}
+
+cudaGraph_t capture_graph_of(cudaStream_t s) { return capture_graph(s); }
+
+void solve_tail_captured(vof_ctx* c) {
+    const int n = c->lv[0].ncells;
+    ++c->nlaunch;
+    k_zero_if<<<4 * c->sm_count, 256, 0, c->st>>>(c->p, c->scal, n);
+    launch_sub_mean(c, c->p, n, S_SUM);
+}
+
 // A right side that is exactly zero after its mean is removed has the
 // mean-free solution P = 0.
 static vof_status zero_solution(vof_ctx* c, double* P, vof_report* rep, double b_mean) {
@@ -963,6 +981,8 @@ struct BatchSolveState {
     int* act_d = nullptr;     // device flags the batched kernels read
     double* mir_h = nullptr;  // mapped: nc x MIRROR_DOUBLES scalars
     double* mir_d = nullptr;
+    long long* trips_h = nullptr;  // mapped: passes of the captured loop bodies (outer, inner)
+    long long* trips_d = nullptr;
 };
 
 bool batch_solve_eligible(const vof_ctx* c) {
@@ -985,7 +1005,10 @@ BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride) {
               cudaMalloc((void**)&b->act_d, sizeof(int) * nc) == cudaSuccess &&
               cudaHostAlloc((void**)&b->mir_h, sizeof(double) * MIRROR_DOUBLES * nc,
                             cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
-              cudaHostGetDevicePointer((void**)&b->mir_d, b->mir_h, 0) == cudaSuccess;
+              cudaHostGetDevicePointer((void**)&b->mir_d, b->mir_h, 0) == cudaSuccess &&
+              cudaHostAlloc((void**)&b->trips_h, 2 * sizeof(long long),
+                            cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&b->trips_d, b->trips_h, 0) == cudaSuccess;
     ok = ok && rho_path_batch_maps(m, nc, stride) == VOF_OK;
     if (!ok) {
         cudaGetLastError();
@@ -1000,6 +1023,7 @@ void batch_solve_destroy(BatchSolveState* b) {
     if (b->act_h) cudaFreeHost(b->act_h);
     if (b->act_d) cudaFree(b->act_d);
     if (b->mir_h) cudaFreeHost(b->mir_h);
+    if (b->trips_h) cudaFreeHost(b->trips_h);
     delete b;
 }
 
@@ -1162,4 +1186,267 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
                                     std::to_string(cs[i].res) + ")");
     }
     return cst;
+}
+
+// ---------------------------------------------------------------------------
+// The batched solve captured whole. The host loop of solve_mixed_batch takes
+// its per-case decisions after readbacks; here one thread per case takes the
+// same decisions on the device (those of the single duct's captured solve,
+// k_ctl_*), keeps each case's loop flags in its scalars (S_OUTACT, S_INACT),
+// writes the flags the batched kernels read (act) and sets the WHILE handles
+// while any case goes on. The kernels and their order per case are those of
+// the host loop, so the iterates are the same bits.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchCtl {
+    double* scal0;      // case 0's scalars; case i's are stride bytes further
+    long long stride;
+    int* act;
+    int nc;
+    SolveCtl p;
+    long long* trips;   // passes of the outer and inner loop bodies
+};
+
+__device__ __forceinline__ double* case_scal(const BatchCtl& b, int i) {
+    return (double*)((char*)b.scal0 + (long long)i * b.stride);
+}
+
+// every case takes part in the dense setup; the loop counters start at zero
+__global__ void k_bctl_begin(BatchCtl b) {
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x) b.act[i] = 1;
+    if (threadIdx.x == 0) b.trips[0] = b.trips[1] = 0;
+}
+
+__global__ void k_bctl_setup(BatchCtl b, cudaGraphConditionalHandle h_out) {
+    int any = 0;
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x) {
+        double* s = case_scal(b, i);
+        const double bb = s[S_BB];
+        double bnorm = sqrt(bb);
+        if (!(bnorm >= 1e-300)) bnorm = 1e-300;
+        const bool zero = bb == 0.0;
+        const double res0 = zero ? 0.0 : sqrt(s[S_RR]) / bnorm;
+        s[S_BNORM] = bnorm;
+        s[S_RES0] = res0;
+        s[S_RES] = res0;
+        s[S_INNER] = 0.0;
+        s[S_OUTER] = 0.0;
+        s[S_GUARD] = 0.0;
+        s[S_ZERO] = zero ? 1.0 : 0.0;
+        const int status = (!zero && !isfinite(res0)) ? ST_NONFINITE : ST_OK;
+        s[S_STATUS] = status;
+        const bool conv = zero || res0 <= b.p.rtol;
+        s[S_CONV] = conv ? 1.0 : 0.0;
+        const int go = (!conv && status == ST_OK) ? 1 : 0;
+        s[S_OUTACT] = go;
+        s[S_INACT] = 0.0;
+        b.act[i] = go;
+        any |= go;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_out, any ? 1u : 0u);
+}
+
+__global__ void k_bctl_outer_begin(BatchCtl b) {
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x) {
+        double* s = case_scal(b, i);
+        if (s[S_OUTACT] == 0.0) continue;
+        const double res = s[S_RES], bnorm = s[S_BNORM];
+        const double rr0 = res * bnorm * res * bnorm;
+        const double tol_in = fmax(1e-5, 0.2 * b.p.rtol / res);
+        s[S_THR] = tol_in * tol_in * rr0;
+        s[S_CAP] = s[S_INNER] + b.p.cap_add;
+        s[S_INACT] = 1.0;
+    }
+    if (threadIdx.x == 0) ++b.trips[0];
+}
+
+// after a batched CG update (S_RR of every running case formed): count the
+// iteration, check the wait flag and the residual, continue while the inner
+// tolerance, max_iter and the cap allow
+__global__ void k_bctl_inner(BatchCtl b, cudaGraphConditionalHandle h_in, int count_pass) {
+    int any = 0;
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x) {
+        double* s = case_scal(b, i);
+        int go = 0;
+        if (s[S_INACT] != 0.0) {
+            const double inner = s[S_INNER] + 1.0, guard = s[S_GUARD] + 1.0;
+            s[S_INNER] = inner;
+            s[S_GUARD] = guard;
+            int status = (int)s[S_STATUS];
+            if (s[S_ERR] != 0.0) status = ST_TIMEOUT;
+            const double rr = s[S_RR];
+            if (status == ST_OK && !isfinite(rr)) status = ST_NONFINITE;
+            s[S_STATUS] = status;
+            go = (status == ST_OK && !(rr <= s[S_THR]) && inner < b.p.max_iter &&
+                  inner < s[S_CAP] && guard < b.p.max_iter + 8)
+                     ? 1
+                     : 0;
+            s[S_INACT] = go;
+        }
+        b.act[i] = go;
+        any |= go;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        if (count_pass) ++b.trips[1];
+        cudaGraphSetConditional(h_in, any ? 1u : 0u);
+    }
+}
+
+// the inner loop has ended: the FP64 update and residual run for the cases
+// of this refinement
+__global__ void k_bctl_inner_exit(BatchCtl b) {
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x)
+        b.act[i] = case_scal(b, i)[S_OUTACT] != 0.0 ? 1 : 0;
+}
+
+__global__ void k_bctl_outer_end(BatchCtl b, cudaGraphConditionalHandle h_out) {
+    int any = 0;
+    for (int i = threadIdx.x; i < b.nc; i += blockDim.x) {
+        double* s = case_scal(b, i);
+        int go = 0;
+        if (s[S_OUTACT] != 0.0) {
+            const double res = sqrt(s[S_RR]) / s[S_BNORM];
+            s[S_RES] = res;
+            int status = (int)s[S_STATUS];
+            if (s[S_ERR] != 0.0) status = ST_TIMEOUT;
+            if (status == ST_OK && !isfinite(res)) status = ST_NONFINITE;
+            s[S_STATUS] = status;
+            const double outer = s[S_OUTER] + 1.0;
+            s[S_OUTER] = outer;
+            const bool conv = res <= b.p.rtol;
+            s[S_CONV] = conv ? 1.0 : 0.0;
+            go = (!conv && status == ST_OK && s[S_INNER] < b.p.max_iter && outer < 50.0 &&
+                  s[S_GUARD] < b.p.max_iter + 8)
+                     ? 1
+                     : 0;
+            s[S_OUTACT] = go;
+        }
+        b.act[i] = go;
+        any |= go;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_out, any ? 1u : 0u);
+}
+
+}  // namespace
+
+vof_status captured_case_result(vof_ctx* c, vof_report* rep) {
+    const double* h = c->hbuf;
+    rep->iters = (int)h[S_INNER];
+    rep->refinements = (int)h[S_OUTER];
+    rep->res0 = h[S_RES0];
+    rep->res = h[S_RES];
+    rep->b_mean = h[S_MEAN];
+    const int status = (int)h[S_STATUS];
+    if (status == ST_TIMEOUT)
+        return set_err(c, VOF_ERR_TIMEOUT,
+                       "a bounded device wait (TMA loads or a grid barrier) gave up");
+    if (status == ST_NONFINITE) return set_err(c, VOF_ERR_NONFINITE, "non-finite residual");
+    if (h[S_CONV] == 0.0)
+        return set_err(c, VOF_ERR_NOT_CONVERGED,
+                       "pressure solve did not reach rtol within max_iter (res=" +
+                           std::to_string(h[S_RES]) + ")");
+    return VOF_OK;
+}
+
+void batch_solve_trips(const BatchSolveState* bs, long long* outer, long long* inner) {
+    *outer = bs->trips_h[0];
+    *inner = bs->trips_h[1];
+}
+
+bool capture_solve_mixed_batch(vof_ctx* m, int nc, long long stride, BatchSolveState* bs,
+                               long long k[3]) {
+    Level& L0 = m->lv[0];
+    const int n = L0.ncells;
+    float* r32 = L0.ff;
+    float* z32 = L0.xf;
+    for (cudaStream_t& s : m->cap_st)
+        if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    cudaStream_t st0 = m->st;
+    cudaGraph_t g_top = capture_graph(st0);
+    if (!g_top) return false;
+    m->bat_n = nc;
+    m->bat_stride = stride;
+    m->bat_act = bs->act_d;
+    m->in_solve_capture = true;
+    const int nthr = nc < 1024 ? ((nc + 31) / 32) * 32 : 1024;
+    const BatchCtl b{m->scal, stride, bs->act_d, nc,
+                     SolveCtl{m->sv.rtol, m->sv.max_iter, std::max(20, m->sv.max_iter / 4)},
+                     bs->trips_d};
+    const long long n0 = m->nlaunch;
+    long long k_outer = 0, k_inner = 0;
+    cudaGraphConditionalHandle h_out = 0, h_in = 0;
+    bool ok = cudaGraphConditionalHandleCreate(&h_out, g_top, 0, cudaGraphCondAssignDefault) ==
+              cudaSuccess;
+    m->nlaunch += 2;
+    k_bctl_begin<<<1, nthr, 0, st0>>>(b);
+    if (m->defer_dense) mg_dense_setup<float>(m, m->lv.back());
+    k_bctl_setup<<<1, nthr, 0, st0>>>(b, h_out);
+    cudaGraph_t g_out = ok ? capture_while(st0, h_out) : nullptr;
+    ok = ok && g_out;
+    if (ok) {
+        const long long m0 = m->nlaunch;
+        m->st = m->cap_st[0];
+        ok = cudaStreamBeginCaptureToGraph(m->st, g_out, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess &&
+             cudaGraphConditionalHandleCreate(&h_in, g_out, 0, cudaGraphCondAssignDefault) ==
+                 cudaSuccess;
+        if (ok) {
+            ++m->nlaunch;
+            k_bctl_outer_begin<<<1, nthr, 0, m->st>>>(b);
+            launch_zero32_bat(m, m->e32, n);
+            vcycle<float>(m, 0);
+            krylov_dots(m, n, z32, r32, r32);
+            launch_copy32_bat(m, m->p32, z32, n);
+            rho_apply_A_dot(m, m->p32, m->q32, S_PQ);
+            k32_cg_update(m, n, m->e32, r32, m->p32, m->q32, S_RR);
+            ++m->nlaunch;
+            k_bctl_inner<<<1, nthr, 0, m->st>>>(b, h_in, 0);
+            cudaGraph_t g_in = capture_while(m->st, h_in);
+            ok = g_in != nullptr;
+            if (ok) {
+                const long long i0 = m->nlaunch;
+                m->st = m->cap_st[1];
+                ok = cudaStreamBeginCaptureToGraph(m->st, g_in, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    vcycle<float>(m, 0);
+                    krylov_dots(m, n, z32, r32, m->q32);
+                    k32_p_update(m, n, m->p32, z32);
+                    rho_apply_A_dot(m, m->p32, m->q32, S_PQ);
+                    k32_cg_update(m, n, m->e32, r32, m->p32, m->q32, S_RR);
+                    ++m->nlaunch;
+                    k_bctl_inner<<<1, nthr, 0, m->st>>>(b, h_in, 1);
+                    cudaGraph_t gb = nullptr;
+                    ok = cudaStreamEndCapture(m->st, &gb) == cudaSuccess;
+                }
+                m->st = m->cap_st[0];
+                k_inner = m->nlaunch - i0;
+            }
+            m->nlaunch += 2;
+            k_bctl_inner_exit<<<1, nthr, 0, m->st>>>(b);
+            k32_add_to_f64(m, n, m->e32, m->p);
+            launch_residual_to32(m, m->p, m->b, r32, S_RR);
+            k_bctl_outer_end<<<1, nthr, 0, m->st>>>(b, h_out);
+            cudaGraph_t gb = nullptr;
+            ok = (cudaStreamEndCapture(m->st, &gb) == cudaSuccess) && ok;
+        }
+        m->st = st0;
+        k_outer = m->nlaunch - m0 - k_inner;
+    }
+    m->in_solve_capture = false;
+    m->bat_n = 1;
+    m->bat_stride = 0;
+    m->bat_act = nullptr;
+    k[0] = m->nlaunch - n0 - k_outer - k_inner;
+    k[1] = k_outer;
+    k[2] = k_inner;
+    m->nlaunch = n0;
+    return ok;
 }

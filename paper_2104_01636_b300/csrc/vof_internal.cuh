@@ -395,6 +395,9 @@ enum ScalarSlot {
     S_ERR,        // a kernel gave up a bounded wait (set to 1)
     // device-side control of the captured mixed solve (solver.cu)
     S_INNER, S_OUTER, S_RES, S_RES0, S_BNORM, S_THR, S_CAP, S_CONV, S_STATUS, S_ZERO, S_GUARD,
+    // the same for each case of a batched solve captured whole: whether the
+    // case takes part in the current refinement and in the inner loop
+    S_OUTACT, S_INACT,
     S_NSCALARS
 };
 static_assert(S_NSCALARS <= MIRROR_DOUBLES, "the host mirror holds every device scalar");
@@ -556,6 +559,32 @@ vof_status step_pre_cfl(vof_ctx* c, double* const f[8], double dt);
 vof_status step_pre(vof_ctx* c, double* const f[8], double dt, long long step_index);
 vof_status step_post(vof_ctx* c, double* const f[8], double dt, vof_status solve);
 vof_status step_post_report(vof_ctx* c, vof_status solve, vof_report* report);
+// step_pre's launches after its CFL test (the test taken elsewhere)
+vof_status step_pre_launch(vof_ctx* c, double* const f[8], double dt, long long step_index);
+// Captures, on m->st (which must be capturing), the batched mixed solve of
+// nc cases whose setups have been captured before it: the dense coarsest
+// inverses, then the loops of solve_mixed_batch as two nested conditional
+// WHILE nodes whose per-case decisions are taken on the device. Each case's
+// outcome is left in its scalars (S_INNER, S_OUTER, S_RES0, S_RES, S_CONV,
+// S_STATUS, S_ZERO); the kernels launched per pass of the outer and inner
+// loop bodies and the rest are counted into k[0..2] (rest, outer, inner).
+// False when capture or conditional nodes are unavailable.
+bool capture_solve_mixed_batch(vof_ctx* m, int nc, long long stride, BatchSolveState* bs,
+                               long long k[3]);
+// the outcome of case c's captured batched solve, from its scalars as the
+// host mirror holds them after the step: report fields and status
+vof_status captured_case_result(vof_ctx* c, vof_report* rep);
+// passes of the two loop bodies in the last replay of that capture
+void batch_solve_trips(const BatchSolveState* bs, long long* outer, long long* inner);
+// after a captured batched solve, on case c's stream: P = 0 for a zero
+// right side, then P made mean-free (the end of solve_mixed's graph)
+void solve_tail_captured(vof_ctx* c);
+// a conditional IF node on handle h after the work captured so far on s;
+// later captures on s follow the node; returns its body graph (nullptr on
+// failure)
+cudaGraph_t capture_if(cudaStream_t s, cudaGraphConditionalHandle h);
+// the graph being captured on s (nullptr when s is not capturing)
+cudaGraph_t capture_graph_of(cudaStream_t s);
 void launch_zero32_bat(vof_ctx* c, float* x, int n);                 // x = 0 (batched, masked)
 void launch_copy32_bat(vof_ctx* c, float* dst, const float* src, int n);  // dst = src
 void readback_batch(vof_ctx* c, double* mirror_dev);  // every case's scalars, then a wait

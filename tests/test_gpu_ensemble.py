@@ -1,5 +1,6 @@
 """The ensemble: every case's result is bitwise that of the same case stepped
-alone, with the cases' pressure solves batched into shared launches or with
+alone, with the cases' pressure solves batched into shared launches (the
+whole step one CUDA graph launch, or its loops driven from the host) or with
 the cases overlapped on streams; a case that fails reports its own status."""
 import numpy as np
 import pytest
@@ -11,12 +12,16 @@ from gpu_util import ctx, dev, host
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,streams,mode,batched", [
-    (1, 2, vd.VofEnsemble.AUTO, True), (0, 3, vd.VofEnsemble.AUTO, False),
-    (1, 1, vd.VofEnsemble.STREAMS, False), (1, 3, vd.VofEnsemble.BATCHED, True)])
-def test_ensemble_equals_solo(prec, streams, mode, batched):
+@pytest.mark.parametrize("prec,streams,mode,batched,graph", [
+    (1, 2, vd.VofEnsemble.AUTO, True, vd.GRAPH_AUTO),
+    (0, 3, vd.VofEnsemble.AUTO, False, vd.GRAPH_AUTO),
+    (1, 1, vd.VofEnsemble.STREAMS, False, vd.GRAPH_AUTO),
+    (1, 3, vd.VofEnsemble.BATCHED, True, vd.GRAPH_AUTO),
+    (1, 3, vd.VofEnsemble.BATCHED, True, vd.GRAPH_CYCLE)])
+def test_ensemble_equals_solo(prec, streams, mode, batched, graph):
+    """Three steps (both sweep orders, so both captured step graphs)."""
     cases = I.ensemble_cases(3, dims=(32, 32, 48), seed=77)
-    kw = dict(precision=prec, rtol=1e-9, max_iter=300)
+    kw = dict(precision=prec, rtol=1e-9, max_iter=300, graph=graph)
     fields = [[dev(a) for a in c.state()] for c in cases]
     with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], vd.c_solver(**kw),
                         n_streams=streams, mode=mode) as E:
@@ -24,6 +29,7 @@ def test_ensemble_equals_solo(prec, streams, mode, batched):
         for s in range(3):
             reps = E.step(fields, [c.dt for c in cases], s, reports=True)
             assert all(r["res"] <= 1e-9 for r in reps)
+        assert E.graph_steps() == (3 if batched and graph == vd.GRAPH_AUTO else 0)
     for c, fs in zip(cases, fields):
         solo = [dev(a) for a in c.state()]
         with ctx(c, **kw) as C:
@@ -45,6 +51,7 @@ def test_batched_ensemble_of_many_cases_equals_solo():
                         n_streams=4, mode=vd.VofEnsemble.BATCHED) as E:
         assert E.batched
         reps = [E.step(fields, [c.dt for c in cases], s, reports=True) for s in range(2)]
+        assert E.graph_steps() == 2
     iters = set()
     for k, (c, fs) in enumerate(zip(cases, fields)):
         solo = [dev(a) for a in c.state()]
@@ -60,6 +67,31 @@ def test_batched_ensemble_of_many_cases_equals_solo():
     assert len(iters) > 1  # the cases did not all take the same number of iterations
 
 
+def test_step_graph_recaptured_for_new_time_steps_and_fields():
+    """The step graph is captured for the field pointers, the time steps and
+    the sweep order: a new dt and new field tensors are captured again, and
+    each case stays bitwise equal to its solo run with the same dt."""
+    cases = I.ensemble_cases(3, dims=(32, 32, 48), seed=79)
+    kw = dict(precision=1, rtol=1e-9, max_iter=300)
+    fields = [[dev(a) for a in c.state()] for c in cases]
+    dts = [[c.dt for c in cases], [c.dt for c in cases], [0.8 * c.dt for c in cases],
+           [0.8 * c.dt for c in cases]]
+    with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], vd.c_solver(**kw),
+                        n_streams=2, mode=vd.VofEnsemble.BATCHED) as E:
+        for s in range(4):
+            if s == 3:
+                fields = [[t.clone() for t in f] for f in fields]
+            E.step(fields, dts[s], s)
+        assert E.graph_steps() == 4
+    for k, (c, fs) in enumerate(zip(cases, fields)):
+        solo = [dev(a) for a in c.state()]
+        with ctx(c, **kw) as C:
+            for s in range(4):
+                C.step(*solo, dts[s][k], s)
+        for a, b in zip(fs, solo):
+            assert np.array_equal(host(a), host(b))
+
+
 def test_ensemble_reports_failing_case():
     cases = I.ensemble_cases(2, dims=(32, 32, 48), seed=78)
     fields = [[dev(a) for a in c.state()] for c in cases]
@@ -69,3 +101,5 @@ def test_ensemble_reports_failing_case():
             E.step(fields, [cases[0].dt, cases[1].dt * 1e4], 0)
         assert e.value.name == "VOF_ERR_CFL"
         assert "[0, 6]" in str(e.value)
+        # the step graph's CFL test failed, so the step ran host-driven
+        assert E.graph_steps() == 0
