@@ -83,14 +83,17 @@ __global__ void k_rbgs_t(Dims d, T h2, const T* __restrict__ bx, const T* __rest
 // is needed.
 // CT is the coefficients' storage type (T, or FP16 copies on a large coarse
 // level of the FP32 cycle).
-template <class T, int MODE, class CT, bool B>
+// FLAT: a thread per (x-pair, y, z) in 1-D blocks, the case along grid y
+// (the levels with small planes, where the 32 x 8 tiles leave most lanes
+// idle); the cells and their arithmetic are the same either way
+template <class T, int MODE, class CT, bool B, bool FLAT = false>
 __global__ void k_rbgs_pair_t(Bat bt, Dims d, T h2, const CT* __restrict__ bx,
                               const CT* __restrict__ by, const CT* __restrict__ bz,
                               const T* __restrict__ xr, T* __restrict__ xw,
                               const T* __restrict__ f, int color, int kchunk, Dims dc,
                               const T* __restrict__ xc, T omega) {
     pdl_wait();
-    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, FLAT ? blockIdx.y : blockIdx.z, FLAT ? gridDim.y : gridDim.z);
     if (bb.off) return;
     bx = bat_at<B>(bt, bb.cs, bx);
     by = bat_at<B>(bt, bb.cs, by);
@@ -99,6 +102,15 @@ __global__ void k_rbgs_pair_t(Bat bt, Dims d, T h2, const CT* __restrict__ bx,
     xw = bat_at<B>(bt, bb.cs, xw);
     f = bat_at<B>(bt, bb.cs, f);
     if (xc) xc = bat_at<B>(bt, bb.cs, xc);
+    if (FLAT) {  // a thread per (x-pair, y, z) of the level
+        const int hp = d.nx >> 1;
+        const int q = blockIdx.x * blockDim.x + threadIdx.x;
+        if (q >= hp * d.ny * d.nz) return;
+        const int t = q % hp, r = q / hp, j = r % d.ny, k = r / d.ny;
+        rbgs_cell<T, MODE>(d, h2, bx, by, bz, xr, xw, f, 2 * t + ((j + k + color) & 1), j, k, dc,
+                           xc, omega, LdPlain());
+        return;
+    }
     const int t = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (t >= (d.nx >> 1) || j >= d.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, d.nz);
@@ -135,13 +147,14 @@ __device__ __forceinline__ float2 cpair(const __half* a, int c) {
 // (8-byte loads; 2I and nx are even). Same terms in the same order.
 // CT: FP32 coefficients, or the level's FP16 copies (the colour passes of
 // the same level read the same copies, so the cycle keeps one operator).
-template <class CT, bool B>
+// FLAT: a thread per coarse cell in 1-D blocks, the case along grid y
+template <class CT, bool B, bool FLAT = false>
 __global__ void k_restrict_pair_f(Bat bt, Dims df, float ih2f, const CT* __restrict__ bx,
                                   const CT* __restrict__ by, const CT* __restrict__ bz,
                                   const float* __restrict__ xf, const float* __restrict__ ff,
                                   Dims dc, float* __restrict__ fc, int kchunk) {
     pdl_wait();
-    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
+    const BatBlk bb = bat_blk<B>(bt, FLAT ? blockIdx.y : blockIdx.z, FLAT ? gridDim.y : gridDim.z);
     if (bb.off) return;
     bx = bat_at<B>(bt, bb.cs, bx);
     by = bat_at<B>(bt, bb.cs, by);
@@ -149,9 +162,21 @@ __global__ void k_restrict_pair_f(Bat bt, Dims df, float ih2f, const CT* __restr
     xf = bat_at<B>(bt, bb.cs, xf);
     ff = bat_at<B>(bt, bb.cs, ff);
     fc = bat_at<B>(bt, bb.cs, fc);
-    const int I = blockIdx.x * TBX + threadIdx.x, J = blockIdx.y * TBY + threadIdx.y;
-    if (I >= dc.nx || J >= dc.ny) return;
-    const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, dc.nz);
+    int I, J, k0, k1;
+    if (FLAT) {
+        const int q = blockIdx.x * blockDim.x + threadIdx.x;
+        if (q >= dc.nx * dc.ny * dc.nz) return;
+        I = q % dc.nx;
+        J = (q / dc.nx) % dc.ny;
+        k0 = q / (dc.nx * dc.ny);
+        k1 = k0 + 1;
+    } else {
+        I = blockIdx.x * TBX + threadIdx.x;
+        J = blockIdx.y * TBY + threadIdx.y;
+        if (I >= dc.nx || J >= dc.ny) return;
+        k0 = bb.b * kchunk;
+        k1 = min(k0 + kchunk, dc.nz);
+    }
     const bool xl = I > 0, xh = 2 * I + 2 < df.nx, yl = J > 0, yh = 2 * J + 2 < df.ny;
     auto ld2 = [](const float* a, int c) { return *reinterpret_cast<const float2*>(a + c); };
     auto cp2 = [](const CT* a, int c) { return cpair(a, c); };
@@ -829,6 +854,13 @@ LA<float> arrays<float>(const Level& L) {
 
 }  // namespace
 
+// Levels narrower than FLAT_NX cells in x run their colour passes and the
+// restriction from them a thread per (x-pair, y, z) or coarse cell in 1-D
+// blocks of FLAT_BLOCK threads, instead of 32 x 8 tiles of which a 24- or
+// 12-cell-wide plane fills a third or less.
+constexpr int FLAT_NX = 64;
+constexpr int FLAT_BLOCK = 256;
+
 // one colour pass on a level with an even nx, a thread per x-pair; CT is
 // the coefficients' storage type
 template <class T, class CT>
@@ -837,24 +869,39 @@ void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, con
     using K = void (*)(Bat, Dims, T, const CT*, const CT*, const CT*, const T*, T*, const T*, int,
                        int, Dims, const T*, T);
     const bool bat = c->bat_n > 1;
+    const bool flat = L.d.nx < FLAT_NX;
     const K kern =
-        bat ? (mode == 1 ? k_rbgs_pair_t<T, 1, CT, true>
-                         : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, true> : k_rbgs_pair_t<T, 0, CT, true>))
-            : (mode == 1 ? k_rbgs_pair_t<T, 1, CT, false>
-                         : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, false>
-                                      : k_rbgs_pair_t<T, 0, CT, false>));
+        flat ? (bat ? (mode == 1 ? k_rbgs_pair_t<T, 1, CT, true, true>
+                                 : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, true, true>
+                                              : k_rbgs_pair_t<T, 0, CT, true, true>))
+                    : (mode == 1 ? k_rbgs_pair_t<T, 1, CT, false, true>
+                                 : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, false, true>
+                                              : k_rbgs_pair_t<T, 0, CT, false, true>)))
+             : (bat ? (mode == 1 ? k_rbgs_pair_t<T, 1, CT, true>
+                                 : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, true>
+                                              : k_rbgs_pair_t<T, 0, CT, true>))
+                    : (mode == 1 ? k_rbgs_pair_t<T, 1, CT, false>
+                                 : (mode == 2 ? k_rbgs_pair_t<T, 2, CT, false>
+                                              : k_rbgs_pair_t<T, 0, CT, false>)));
     const Dims dc = C ? C->d : L.d;
     const T* xc = C ? arrays<T>(*C).x : nullptr;
     const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
-    // a thread per x-pair halves the blocks of the level's cell geometry:
-    // halve the z chunks to keep about as many blocks in flight
-    const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
-    const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
-    dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
-    const Bat bt = bat_of(c, grid.z);
     int m = timer_begin(c, cls);
-    launch_pdl(c, kern, grid, L.L.block, bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f, color,
-               kchunk, dc, xc, omega);
+    if (flat) {
+        dim3 grid((L.ncells / 2 + FLAT_BLOCK - 1) / FLAT_BLOCK);
+        const Bat bt = bat_of(c, grid.y);
+        launch_pdl(c, kern, grid, dim3(FLAT_BLOCK), bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x,
+                   a.f, color, 1, dc, xc, omega);
+    } else {
+        // a thread per x-pair halves the blocks of the level's cell geometry:
+        // halve the z chunks to keep about as many blocks in flight
+        const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
+        const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
+        dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
+        const Bat bt = bat_of(c, grid.z);
+        launch_pdl(c, kern, grid, L.L.block, bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f,
+                   color, kchunk, dc, xc, omega);
+    }
     timer_end(c, cls, m);
 }
 
@@ -902,6 +949,14 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
                        (float)(1.0 / (F.h * F.h)) * F.hscale, (const __half*)F.bxh, (const __half*)F.byh,
                        (const __half*)F.bzh, (const float*)a.x, (const float*)a.f, C.d,
                        (float*)b.f, C.L.kchunk);
+        } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0 && F.d.nx < FLAT_NX) {
+            dim3 gf((C.ncells + FLAT_BLOCK - 1) / FLAT_BLOCK);
+            const Bat bt = bat_of(c, gf.y);
+            launch_pdl(c, bt.zb ? k_restrict_pair_f<float, true, true>
+                                : k_restrict_pair_f<float, false, true>,
+                       gf, dim3(FLAT_BLOCK), bt, F.d, (float)(1.0 / (F.h * F.h)),
+                       (const float*)a.bx, (const float*)a.by, (const float*)a.bz,
+                       (const float*)a.x, (const float*)a.f, C.d, (float*)b.f, 1);
         } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
             const Bat bt = bat_of(c, g.z);
             launch_pdl(c, bt.zb ? k_restrict_pair_f<float, true> : k_restrict_pair_f<float, false>,

@@ -24,8 +24,19 @@ __device__ __forceinline__ float cval(float v) { return v; }
 __device__ __forceinline__ double cval(double v) { return v; }
 __device__ __forceinline__ float cval(__half v) { return __half2float(v); }
 
+// Multiply and fused multiply-add rounded as written: the compiler may not
+// contract or split them, so every kernel that evaluates a cell through
+// these functions (whatever its thread mapping and unrolling) produces the
+// same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Red-black Gauss-Seidel update of cell (i, j, k) on one level:
-//   x_c = (h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f.
+//   x_c = (h^2 f_c + sum_f beta_f x_nb) / sum_f beta_f,
+// the sum formed as h^2 f_c followed by one fused multiply-add per face in
+// the order west, east, south, north, below, above.
 // Across a wall (beta = 0) the neighbour counts as 0 and is not read.
 // MODE 1: x is zero (first pass from a zero guess), neighbours are not read.
 // MODE 2: each neighbour is read as x + omega x_coarse(parent): the first
@@ -48,20 +59,24 @@ __device__ __forceinline__ void rbgs_cell(const Dims& d, T h2, const CT* __restr
     const T b2 = cval(by[vid(d, i, j, k)]), b3 = cval(by[vid(d, i, j + 1, k)]);
     const T b4 = cval(bz[wid(d, i, j, k)]), b5 = cval(bz[wid(d, i, j, kp)]);
     const bool hw = i > 0, he = i < d.nx - 1, hs = j > 0, hn = j < d.ny - 1;
-    T num;
-    if (MODE == 1) {
-        num = h2 * ld(f + c);
-    } else if (MODE == 2) {
+    T num = mul_rn(h2, ld(f + c));
+    if (MODE == 2) {
         auto xv = [&](int cc, int ii, int jj, int kk) {
-            return ld(xr + cc) + omega * ld(xc + cid(dc, ii >> 1, jj >> 1, kk >> 1));
+            return fma_rn(omega, ld(xc + cid(dc, ii >> 1, jj >> 1, kk >> 1)), ld(xr + cc));
         };
-        num = h2 * ld(f + c) + b0 * (hw ? xv(cw, iw, j, k) : T(0)) +
-              b1 * (he ? xv(ce, ie, j, k) : T(0)) + b2 * (hs ? xv(cs, i, js, k) : T(0)) +
-              b3 * (hn ? xv(cn, i, jn, k) : T(0)) + b4 * xv(cb, i, j, km) + b5 * xv(ct, i, j, kp);
-    } else {
-        num = h2 * ld(f + c) + b0 * (hw ? ld(xr + cw) : T(0)) + b1 * (he ? ld(xr + ce) : T(0)) +
-              b2 * (hs ? ld(xr + cs) : T(0)) + b3 * (hn ? ld(xr + cn) : T(0)) + b4 * ld(xr + cb) +
-              b5 * ld(xr + ct);
+        num = fma_rn(b0, hw ? xv(cw, iw, j, k) : T(0), num);
+        num = fma_rn(b1, he ? xv(ce, ie, j, k) : T(0), num);
+        num = fma_rn(b2, hs ? xv(cs, i, js, k) : T(0), num);
+        num = fma_rn(b3, hn ? xv(cn, i, jn, k) : T(0), num);
+        num = fma_rn(b4, xv(cb, i, j, km), num);
+        num = fma_rn(b5, xv(ct, i, j, kp), num);
+    } else if (MODE == 0) {
+        num = fma_rn(b0, hw ? ld(xr + cw) : T(0), num);
+        num = fma_rn(b1, he ? ld(xr + ce) : T(0), num);
+        num = fma_rn(b2, hs ? ld(xr + cs) : T(0), num);
+        num = fma_rn(b3, hn ? ld(xr + cn) : T(0), num);
+        num = fma_rn(b4, ld(xr + cb), num);
+        num = fma_rn(b5, ld(xr + ct), num);
     }
     const T den = b0 + b1 + b2 + b3 + b4 + b5;
     xw[c] = den > T(0) ? num / den : T(0);
