@@ -458,7 +458,7 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
                       "cell_steps_per_s": n_cases * cases[0].grid.ncells / (ms / 1e3),
                       "kernel_launches_per_ensemble_step": launches,
                       "graph_launches_per_ensemble_step": graph_steps,
-                      "ms_before_solve_solve_after": phases if graph_steps == 0 else None,
+                      "ms_before_solve_solve_after": phases,
                       "max_inner_iters": max(r["iters"] for r in reps),
                       "mean_inner_iters": sum(r["iters"] for r in reps) / len(reps)}
     return out

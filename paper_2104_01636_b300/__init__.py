@@ -490,7 +490,8 @@ class VofEnsemble:
                        (grid.nz, grid.ny + 1, grid.nx), cs, cs)
 
     def phase_ms(self):
-        """Host ms so far: (before the solves, the batched solve, after it)."""
+        """ms so far (before the solves, the batched solve, after it): host
+        time for host-driven steps, the device timer for graph steps."""
         ms = (_D * 3)()
         self.lib.vof_ensemble_phase_ms(self._e, ms)
         return tuple(ms)

@@ -18,12 +18,14 @@
 // launch and a device-side test), then, under a conditional IF node that the
 // test opens, every case's step up to its solve (the cases' branches run
 // side by side), the batched solve with its loops as conditional WHILE
-// nodes steered on the device, and every case's correction. A step whose
-// CFL test fails in any case is run again the host-driven way, which reports
-// each case's status; nothing of the step has been launched by then. The
-// graph is captured for the step's field pointers and time steps and the
-// parity of the step index (the sweep order), and captured again when they
-// change.
+// nodes steered on the device, and every case's correction. From 8 cases
+// up the cases run in two groups with a batched solve each: the second
+// group's part before its solve starts when the first group's has ended, so
+// it runs beside the first group's solve. A step whose CFL test fails in
+// any case is run again the host-driven way, which reports each case's
+// status; nothing of the step has been launched by then. The graph is
+// captured for the step's field pointers and time steps and the parity of
+// the step index (the sweep order), and captured again when they change.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -40,7 +42,8 @@ struct StepGraph {
     std::vector<double> dt;
     double* dt_d = nullptr;        // device copies the CFL test reads
     const double** uvw_d = nullptr;
-    long long k_top = 0, k_body = 0, k_outer = 0, k_inner = 0;  // kernels per replay
+    long long k_top = 0, k_body = 0;        // kernels per replay outside the solves' loops
+    std::vector<long long> k_outer, k_inner;  // per case group: kernels per pass of its loops
 };
 
 struct vof_ensemble {
@@ -75,9 +78,23 @@ struct vof_ensemble {
     cudaStream_t gst[2] = {nullptr, nullptr};  // capture origin, IF body
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
+    // The cases in groups of consecutive cases, each with its own batched
+    // solve, so that one group's solve runs beside the next group's part
+    // before the solve (which starts when the group before has finished
+    // its own). Per group: its solve's state, the origin of its branch, an
+    // event at the end of its part before the solve; per group and worker:
+    // the stream its cases launch on while the step is captured.
+    int ngroups = 1;
+    std::vector<BatchSolveState*> gbs;
+    std::vector<cudaStream_t> gorig, gwork;
+    std::vector<cudaEvent_t> ev_grp;
     unsigned long long* vmax_d = nullptr;  // per case: largest face-velocity magnitude (bits)
     int* abort_h = nullptr;                // mapped: the CFL test failed in some case
     int* abort_d = nullptr;
+    // mapped: device clock (ns) at the step's start, after the parts before
+    // the solves, after the solve, at the end
+    unsigned long long* stamp_h = nullptr;
+    unsigned long long* stamp_d = nullptr;
     long long graph_steps = 0, graph_kernels = 0;
 };
 
@@ -122,6 +139,13 @@ __global__ void k_ens_cfl_ctl(const unsigned long long* __restrict__ vmax,
         *abort_flag = bad;
         cudaGraphSetConditional(h_go, bad ? 0u : 1u);
     }
+}
+
+// the device's global clock (ns) into slot q, once the work before it is done
+__global__ void k_stamp(unsigned long long* t, int q) {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    t[q] = v;
 }
 
 void ensemble_worker(vof_ensemble* e, int w) {
@@ -181,6 +205,12 @@ void run_phase(vof_ensemble* e, int phase) {
 }
 
 // ---- the whole step as one graph ---------------------------------------------
+// ensembles of at least this many cases run the captured step in two groups
+constexpr int ENSEMBLE_GROUP_MIN_CASES = 8;
+
+// the first case of group g (g = ngroups: one past the last case)
+int group_first(const vof_ensemble* e, int g) { return (int)((long long)g * e->n / e->ngroups); }
+
 void free_step_graph(StepGraph& g) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.dt_d) cudaFree(g.dt_d);
@@ -194,6 +224,26 @@ bool step_graph_resources(vof_ensemble* e) {
     bool ok = true;
     for (cudaStream_t& s : e->gst)
         ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    e->ngroups = e->n >= ENSEMBLE_GROUP_MIN_CASES ? 2 : 1;
+    const int G = e->ngroups;
+    e->gbs.assign(G, nullptr);
+    e->gorig.assign(G, nullptr);
+    e->ev_grp.assign(G, nullptr);
+    e->gwork.assign((size_t)G * e->nworkers, nullptr);
+    for (int g = 0; g < G && ok; ++g) {
+        e->gbs[g] = batch_solve_create(e->ctx[group_first(e, g)], group_first(e, g + 1) -
+                                                                      group_first(e, g),
+                                       e->stride);
+        ok = e->gbs[g] != nullptr &&
+             cudaStreamCreateWithFlags(&e->gorig[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->ev_grp[g], cudaEventDisableTiming) == cudaSuccess;
+    }
+    for (cudaStream_t& s : e->gwork)
+        ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    // the groups' states encoded their TMA maps into the groups' first
+    // contexts; case 0's context keeps those of the whole batch (the
+    // host-driven solve)
+    ok = ok && rho_path_batch_maps(e->ctx[0], e->n, e->stride) == VOF_OK;
     ok = ok && cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     e->ev_join.assign(e->nworkers, nullptr);
     for (cudaEvent_t& ev : e->ev_join)
@@ -201,6 +251,10 @@ bool step_graph_resources(vof_ensemble* e) {
     ok = ok && cudaMalloc((void**)&e->vmax_d, sizeof(unsigned long long) * e->n) == cudaSuccess;
     ok = ok && cudaHostAlloc((void**)&e->abort_h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
          cudaHostGetDevicePointer((void**)&e->abort_d, e->abort_h, 0) == cudaSuccess;
+    ok = ok &&
+         cudaHostAlloc((void**)&e->stamp_h, 4 * sizeof(unsigned long long), cudaHostAllocMapped) ==
+             cudaSuccess &&
+         cudaHostGetDevicePointer((void**)&e->stamp_d, e->stamp_h, 0) == cudaSuccess;
     cudaGetLastError();
     return ok;
 }
@@ -209,33 +263,43 @@ void free_step_graph_resources(vof_ensemble* e) {
     for (StepGraph& g : e->sg) free_step_graph(g);
     for (cudaStream_t& s : e->gst)
         if (s) cudaStreamDestroy(s);
+    for (BatchSolveState* b : e->gbs) batch_solve_destroy(b);
+    for (cudaStream_t s : e->gorig)
+        if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : e->gwork)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : e->ev_grp)
+        if (ev) cudaEventDestroy(ev);
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
     for (cudaEvent_t ev : e->ev_join)
         if (ev) cudaEventDestroy(ev);
     if (e->vmax_d) cudaFree(e->vmax_d);
     if (e->abort_h) cudaFreeHost(e->abort_h);
+    if (e->stamp_h) cudaFreeHost(e->stamp_h);
 }
 
-// the worker streams join the capture on s, and later join it again
-void fork_to_workers(vof_ensemble* e, cudaStream_t s) {
+// group g's capture streams join the capture on s, and later join it again
+void fork_to_group(vof_ensemble* e, int g, cudaStream_t s) {
     cudaEventRecord(e->ev_fork, s);
-    for (cudaStream_t w : e->streams) cudaStreamWaitEvent(w, e->ev_fork, 0);
+    for (int w = 0; w < e->nworkers; ++w)
+        cudaStreamWaitEvent(e->gwork[(size_t)g * e->nworkers + w], e->ev_fork, 0);
 }
-void join_workers(vof_ensemble* e, cudaStream_t s) {
+void join_group(vof_ensemble* e, int g, cudaStream_t s) {
     for (int w = 0; w < e->nworkers; ++w) {
-        cudaEventRecord(e->ev_join[w], e->streams[w]);
+        cudaEventRecord(e->ev_join[w], e->gwork[(size_t)g * e->nworkers + w]);
         cudaStreamWaitEvent(s, e->ev_join[w], 0);
     }
 }
 
 // Captures the ensemble step for these fields, time steps and step parity
-// into g. Each case's launches go to its own stream (its context's), which
-// joins the capture, so the cases' branches of the graph are those streams'
-// orders; the batched solve is captured on the IF body's origin. False when
-// capture is unavailable (nothing stays captured).
+// into g. While the step is captured, each case's context launches on its
+// group's stream for its worker, which joins the capture, so a group's cases
+// are side-by-side branches of the graph; each group's batched solve is
+// captured on the group's origin. False when capture is unavailable
+// (nothing stays captured).
 bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const double* dt,
                   long long step_index) {
-    const int n = e->n;
+    const int n = e->n, G = e->ngroups, nw = e->nworkers;
     if (g.exec) cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
     if (!g.dt_d && cudaMalloc((void**)&g.dt_d, sizeof(double) * n) != cudaSuccess) return false;
@@ -248,17 +312,28 @@ bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const do
         cudaMemcpy((void*)g.uvw_d, uvw.data(), sizeof(double*) * 3 * n,
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return false;
-    vof_ctx* m = e->ctx[0];
-    for (cudaStream_t& s : m->cap_st)  // the solve's loop bodies are captured on these
-        if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
+    for (int q = 0; q < G; ++q)  // the solves' loop bodies are captured on these
+        for (cudaStream_t& s : e->ctx[group_first(e, q)]->cap_st)
+            if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+    const vof_ctx* m = e->ctx[0];
     std::vector<long long> n0(n);
-    for (int c = 0; c < n; ++c) n0[c] = e->ctx[c]->nlaunch;
+    std::vector<cudaStream_t> st0(n);
+    for (int c = 0; c < n; ++c) {
+        n0[c] = e->ctx[c]->nlaunch;
+        st0[c] = e->ctx[c]->st;
+    }
+    int grp = 0;
+    for (int c = 0; c < n; ++c) {
+        while (c >= group_first(e, grp + 1)) ++grp;
+        e->ctx[c]->st = e->gwork[(size_t)grp * nw + c % nw];
+    }
     cudaStream_t s0 = e->gst[0], sb = e->gst[1];
     if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
+        for (int c = 0; c < n; ++c) e->ctx[c]->st = st0[c];
         return false;
     }
     cudaGraph_t gt = capture_graph_of(s0);
@@ -268,6 +343,7 @@ bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const do
     const int ncell = m->d.nx * m->d.ny * m->d.nz;
     const int bpc = std::max(1, std::min((ncell + 2047) / 2048, 1024));
     const int nthr = n < 1024 ? ((n + 31) / 32) * 32 : 1024;
+    k_stamp<<<1, 1, 0, s0>>>(e->stamp_d, 0);
     cudaMemsetAsync(e->vmax_d, 0, sizeof(unsigned long long) * n, s0);
     k_ens_vmax<<<dim3(bpc, n), 256, 0, s0>>>(m->d, m->g.periodic_x, m->g.periodic_y, g.uvw_d,
                                              e->vmax_d);
@@ -276,23 +352,42 @@ bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const do
     ok = ok && gif &&
          cudaStreamBeginCaptureToGraph(sb, gif, nullptr, nullptr, 0,
                                        cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    long long kk[3] = {0, 0, 0};
+    std::vector<long long> kk(3 * (size_t)G, 0);
     if (ok) {
-        fork_to_workers(e, sb);
-        for (int c = 0; c < n; ++c)
-            ok = step_pre_launch(e->ctx[c], fields + 8 * (size_t)c, dt[c], step_index) == VOF_OK &&
+        cudaEventRecord(e->ev_fork, sb);
+        for (int q = 0; q < G; ++q) {
+            cudaStream_t o = e->gorig[q];
+            // group q's part before the solve after group q - 1's
+            cudaStreamWaitEvent(o, q == 0 ? e->ev_fork : e->ev_grp[q - 1], 0);
+            const int c0 = group_first(e, q), c1 = group_first(e, q + 1);
+            fork_to_group(e, q, o);
+            for (int c = c0; c < c1; ++c)
+                ok = step_pre_launch(e->ctx[c], fields + 8 * (size_t)c, dt[c], step_index) ==
+                         VOF_OK &&
+                     ok;
+            join_group(e, q, o);
+            cudaEventRecord(e->ev_grp[q], o);
+            if (q == 0) k_stamp<<<1, 1, 0, o>>>(e->stamp_d, 1);
+            vof_ctx* mq = e->ctx[c0];
+            cudaStream_t sq = mq->st;
+            mq->st = o;
+            ok = ok && rho_path_batch_maps(mq, c1 - c0, e->stride) == VOF_OK;
+            ok = capture_solve_mixed_batch(mq, c1 - c0, e->stride, e->gbs[q], &kk[3 * (size_t)q]) &&
                  ok;
-        join_workers(e, sb);
-        cudaStream_t st_m = m->st;
-        m->st = sb;
-        ok = capture_solve_mixed_batch(m, n, e->stride, e->bs, kk) && ok;
-        m->st = st_m;
-        fork_to_workers(e, sb);
-        for (int c = 0; c < n; ++c) {
-            solve_tail_captured(e->ctx[c]);
-            ok = step_post(e->ctx[c], fields + 8 * (size_t)c, dt[c], VOF_OK) == VOF_OK && ok;
+            mq->st = sq;
+            if (q == G - 1) k_stamp<<<1, 1, 0, o>>>(e->stamp_d, 2);
+            fork_to_group(e, q, o);
+            for (int c = c0; c < c1; ++c) {
+                solve_tail_captured(e->ctx[c]);
+                ok = step_post(e->ctx[c], fields + 8 * (size_t)c, dt[c], VOF_OK) == VOF_OK && ok;
+            }
+            join_group(e, q, o);
         }
-        join_workers(e, sb);
+        for (int q = 0; q < G; ++q) {
+            cudaEventRecord(e->ev_grp[q], e->gorig[q]);
+            cudaStreamWaitEvent(sb, e->ev_grp[q], 0);
+        }
+        k_stamp<<<1, 1, 0, sb>>>(e->stamp_d, 3);
         cudaGraph_t gb = nullptr;
         ok = cudaStreamEndCapture(sb, &gb) == cudaSuccess && ok;
     }
@@ -306,16 +401,24 @@ bool capture_step(vof_ensemble* e, StepGraph& g, double* const* fields, const do
     for (int c = 0; c < n; ++c) {
         body += e->ctx[c]->nlaunch - n0[c];
         e->ctx[c]->nlaunch = n0[c];
+        e->ctx[c]->st = st0[c];
     }
+    // case 0's context keeps the TMA maps of the whole batch (host-driven steps)
+    ok = rho_path_batch_maps(e->ctx[0], n, e->stride) == VOF_OK && ok;
     if (!ok) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
         return false;
     }
-    g.k_top = 2;
-    g.k_body = body + kk[0];
-    g.k_outer = kk[1];
-    g.k_inner = kk[2];
+    g.k_top = 3;
+    g.k_body = body + 3;
+    g.k_outer.assign(G, 0);
+    g.k_inner.assign(G, 0);
+    for (int q = 0; q < G; ++q) {
+        g.k_body += kk[3 * (size_t)q];
+        g.k_outer[q] = kk[3 * (size_t)q + 1];
+        g.k_inner[q] = kk[3 * (size_t)q + 2];
+    }
     g.f.assign(fields, fields + 8 * (size_t)n);
     g.dt.assign(dt, dt + n);
     return true;
@@ -348,10 +451,15 @@ void run_step_graph(vof_ensemble* e, double* const* fields, const double* dt,
         e->graph_kernels += g.k_top;
         return;
     }
-    long long to = 0, ti = 0;
-    batch_solve_trips(e->bs, &to, &ti);
-    e->graph_kernels += g.k_top + g.k_body + to * g.k_outer + ti * g.k_inner;
+    e->graph_kernels += g.k_top + g.k_body;
+    for (int q = 0; q < e->ngroups; ++q) {
+        long long to = 0, ti = 0;
+        batch_solve_trips(e->gbs[q], &to, &ti);
+        e->graph_kernels += to * g.k_outer[q] + ti * g.k_inner[q];
+    }
     ++e->graph_steps;
+    const unsigned long long* t = e->stamp_h;
+    for (int q = 0; q < 3; ++q) e->phase_ms[q] += (double)(t[q + 1] - t[q]) * 1e-6;
     for (int c = 0; c < n; ++c) {
         vof_report r{};
         const vof_status solve = captured_case_result(e->ctx[c], &r);

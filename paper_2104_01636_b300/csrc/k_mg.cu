@@ -489,21 +489,22 @@ __global__ void k_coarse_cg_t(Dims d, T ih2, const T* __restrict__ bx, const T* 
 // M = A_c + s 1 1^T (SPD; on mean-free right sides M^{-1} f is the mean-free
 // solution of A_c x = f, since the constants are an eigenvector of M with
 // eigenvalue s n and the range of A_c is orthogonal to them).
+// Row r = blockIdx.y, columns across x (the case along z).
 template <class T, bool B>
 __global__ void k_dense_assemble(Bat bt, Dims d, double ih2, const T* __restrict__ bx,
                                  const T* __restrict__ by, const T* __restrict__ bz, double s,
                                  T* __restrict__ M) {
-    const BatBlk bb = bat_blk<B>(bt, blockIdx.y, gridDim.y);
+    const BatBlk bb = bat_blk<B>(bt, blockIdx.z, gridDim.z);
     if (bb.off) return;
     bx = bat_at<B>(bt, bb.cs, bx);
     by = bat_at<B>(bt, bb.cs, by);
     bz = bat_at<B>(bt, bb.cs, bz);
     M = bat_at<B>(bt, bb.cs, M);
     const int n = d.nx * d.ny * d.nz;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)n * n;
-         e += (long)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n), col = (int)(e % n);
-        const int i = r % d.nx, j = (r / d.nx) % d.ny, k = r / (d.nx * d.ny);
+    const int r = blockIdx.y;
+    const int i = r % d.nx, j = (r / d.nx) % d.ny, k = r / (d.nx * d.ny);
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n; col += gridDim.x * blockDim.x) {
+        const long e = (long)r * n + col;
         double v = s;
         if (col == r) {
             v += ((double)bx[uid(d, i, j, k)] + bx[uid(d, i + 1, j, k)] + by[vid(d, i, j, k)] +
@@ -1028,18 +1029,16 @@ template <class T>
 void mg_dense_setup(vof_ctx* c, const Level& L) {
     const LA<T> a = arrays<T>(L);
     const int n = L.ncells;
-    const long n2 = (long)n * n;
     const double ih2 = 1.0 / (L.h * L.h);
     // s n: the liquid-coefficient scale of the diagonal, so the constants'
     // eigenvalue of the shifted matrix sits among the operator's own
     const double s = c->dense_shift * ih2 / n;
-    const int nb = (int)std::min<long>((n2 + 255) / 256, 65535L * 8);
     int m = timer_begin(c, T_COARSE);
     T* A = (T*)c->dense_a;
     T* B = (T*)c->dense_b;
     const bool bat = c->bat_n > 1;
-    dim3 ga(nb);
-    const Bat bta = bat_of(c, ga.y);
+    dim3 ga((n + 255) / 256, n);
+    const Bat bta = bat_of(c, ga.z);
     auto kas = bat ? k_dense_assemble<T, true> : k_dense_assemble<T, false>;
     VOF_LAUNCH(c, kas, ga, 256, bta, L.d, ih2, a.bx, a.by, a.bz, s, A);
     T* Pw = (T*)c->dense_w;
