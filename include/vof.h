@@ -448,10 +448,10 @@ vof_status vof_ensemble_destroy(vof_ensemble* ensemble);
  *    step up to its solve (the cases' branches side by side), the batched
  *    solve with its two loops as conditional WHILE nodes whose per-case
  *    decisions are taken on the device, and every case's correction. From
- *    8 cases up the cases run in two groups (the first and the second half),
- *    each with its own batched solve; the second group's step up to its
- *    solve starts when the first group's has finished, and so runs beside
- *    the first group's solve. The
+ *    8 cases up the cases run in min(4, n_cases / 4) groups of consecutive
+ *    cases, each with its own batched solve; a group's step up to its solve
+ *    starts when the group before has finished its own, and so runs beside
+ *    that group's solve. The
  *    graph is captured at the first step and again whenever the field
  *    pointers, the time steps or the parity of step_index change. A step
  *    whose CFL test fails in any case runs again the host-driven way
@@ -477,11 +477,10 @@ vof_status vof_ensemble_launch_count(const vof_ensemble* ensemble, long long* n)
 /* Time (ms) the steps so far spent in their three parts. Host-driven steps
  * (host wall time): ms[0] the parts before the solves (the whole step for a
  * streams ensemble), ms[1] the batched solve, ms[2] the parts after it.
- * Steps run as one graph launch (the device's global timer): the cases run
- * in groups of consecutive cases (two from 8 cases up), each group's solve
- * beside the next group's part before it; ms[0] from the CFL test to the end
- * of the first group's part before its solve, ms[1] from there to the end
- * of the last group's solve, ms[2] the rest. */
+ * Steps run as one graph launch (the device's global timer; the groups'
+ * parts overlap): ms[0] from the CFL test to the end of the first group's
+ * part before its solve, ms[1] from there to the end of the last group's
+ * solve, ms[2] the rest. */
 vof_status vof_ensemble_phase_ms(const vof_ensemble* ensemble, double* ms);
 /* Steps so far that ran as one graph launch. */
 vof_status vof_ensemble_graph_steps(const vof_ensemble* ensemble, long long* n);
