@@ -71,8 +71,11 @@ template <> __device__ __forceinline__ float mu_cell<float>(const Pred& P, int c
 
 // VT: arithmetic of the viscous term (double on the FP64 path; float on the
 // mixed path, where it changes the velocity by ~1e-4 of itself per step).
-// The mass fluxes, densities and the update are FP64 on both paths; the face
-// viscosities are formed in VT. On the mixed path the transport sum
+// The mass fluxes, densities, body force and the update are FP64 on both
+// paths; the face viscosities are formed in VT. On the mixed path the
+// convective and viscous increments are combined in FP32 before the FP64
+// update, and the net outward flux is summed in FP32 from the rounded
+// fluxes. On the mixed path the transport sum
 // sum_f M_f q*_f is also taken in FP32 (fluxes rounded once, FP32 copies of the
 // cell velocities): it is rounded to 6e-8 of the convective change, which is a
 // fraction of the velocity, so u_hat moves by ~1e-8 of itself. Central
@@ -98,6 +101,16 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
     // dt B on z: dt ((rho^n - rho0) g_z + dpdz) = rho^n (dt g_z) + dt (dpdz - rho0 g_z)
     const double dt_gz = P.dt * P.gz, dt_b0 = P.dt * (P.dpdz - P.rho0 * P.gz);
     const VT* const* UV = visc_src<VT>(P);
+    constexpr bool MIXED = sizeof(VT) == sizeof(float);
+    // the -z face of plane k is the +z face of plane k - 1: its half flux and
+    // face velocity carry over along the march (the same expression, formed
+    // once); planes k0's -z face is formed at the start
+    double M_up = 0.0, uf_up = 0.0;
+    {
+        const int fk = wrapk(k0, d.nz);
+        uf_up = P.w[wid(d, i, j, fk)];
+        M_up = fma(drho_h, P.fz[wid(d, i, j, fk)], rg_dth_h * uf_up);
+    }
     for (int k = k0; k < k1; ++k) {
         const int c = cid(d, i, j, k);
         const double an = P.an[c];
@@ -130,26 +143,37 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
                 if (!wall) { uf = P.v[vid(d, i, fj, k)]; F = P.fy[vid(d, i, fj, k)]; }
             } else {
                 nk = side ? k + 1 : k - 1;
-                const int fk = wrapk(k + side, d.nz);
-                uf = P.w[wid(d, i, j, fk)];
-                F = P.fz[wid(d, i, j, fk)];
+                if (side) {
+                    const int fk = wrapk(k + 1, d.nz);
+                    uf = P.w[wid(d, i, j, fk)];
+                    F = P.fz[wid(d, i, j, fk)];
+                } else {
+                    uf = uf_up;
+                }
             }
             const int ci = min(max(ni, 0), d.nx - 1), cj = min(max(nj, 0), d.ny - 1);
             nbc[f] = cid(d, ci, cj, wrapk(nk, d.nz));
             muf[f] = VT(0.5) * (muc + mu_cell<VT>(P, nbc[f]));
-            const double M = wall ? 0.0 : fma(drho_h, F, rg_dth_h * uf);
+            const double M = f == 4 ? M_up : (wall ? 0.0 : fma(drho_h, F, rg_dth_h * uf));
+            if (f == 5) {
+                M_up = M;
+                uf_up = uf;
+            }
             Ms[f] = side ? M : -M;
-            net += Ms[f];
+            if constexpr (!MIXED) net += Ms[f];
             // u_f > 0 as a sign test of the bits (no FP64 compare; +-0 is not > 0)
             left_donor[f] = __double_as_longlong(uf) > 0LL;
         }
         const double r_rn1 = rcp_cubic(rn1);
         float Msf[6];
         float netf = 0.f;
-        if constexpr (sizeof(VT) == sizeof(float)) {
+        if constexpr (MIXED) {
+            // the net outward flux summed in FP32 from the rounded fluxes
 #pragma unroll
-            for (int f = 0; f < 6; ++f) Msf[f] = (float)Ms[f];
-            netf = (float)net;
+            for (int f = 0; f < 6; ++f) {
+                Msf[f] = (float)Ms[f];
+                netf += Msf[f];
+            }
         }
         double out[3];
 #pragma unroll
@@ -157,6 +181,7 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
             const double qc = P.U[comp][c];
             // convection: outward mass flux times the transported velocity
             double C = 0.0;
+            float Cm = 0.f;  // the mixed path's FP32 sum
             if constexpr (sizeof(VT) == sizeof(float)) {
                 // mixed path: the transport sum in FP32 from the FP32 copies
                 const float* Q = P.U32[comp];
@@ -175,7 +200,7 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
                     for (int f = 0; f < 6; ++f) sf = fmaf(Msf[f], Q[nbc[f]], sf);
                     Cf = fmaf(netf, qcf, sf);
                 }
-                C = (double)Cf;
+                Cm = Cf;
             } else if (P.upwind) {
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
@@ -223,9 +248,18 @@ __global__ void __launch_bounds__(TBX * TBY, sizeof(VT) == sizeof(float) ? 2 : 1
                 V = fma(muf[f], t, V);
             }
             // rho^n q - C + dt (V / h^2 + B), B on z only
-            double num = fma(rn, qc, -C) + (double)(V * dt_ih2);
-            if (comp == 2) num += fma(rn, dt_gz, dt_b0);
-            out[comp] = num * r_rn1;
+            if constexpr (MIXED) {
+                // convection and viscous term combined in FP32 (each a fraction
+                // of the momentum); the body force stays FP64: in the liquid
+                // rho^n dt g_z and dt (dpdz - rho0 g_z) nearly cancel
+                double num = fma(rn, qc, (double)fmaf(V, dt_ih2, -Cm));
+                if (comp == 2) num += fma(rn, dt_gz, dt_b0);
+                out[comp] = num * r_rn1;
+            } else {
+                double num = fma(rn, qc, -C) + (double)(V * dt_ih2);
+                if (comp == 2) num += fma(rn, dt_gz, dt_b0);
+                out[comp] = num * r_rn1;
+            }
         }
         o0[c] = out[0];
         o1[c] = out[1];
