@@ -104,6 +104,10 @@ def parse():
                     help="requests in the serving run (0 skips it)")
     ap.add_argument("--ensemble-cases", type=int, default=64,
                     help="cases in the ensemble run (0 skips it)")
+    ap.add_argument("--ensemble-profile-step", default=None, choices=["auto", "cycle"],
+                    help="only build the ensemble of --ensemble-cases cases (graph option auto "
+                         "or cycle), take three steps and bracket a fourth with "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -410,6 +414,31 @@ def serving(vd, I, n_req: int, do_fp64: bool):
     return out
 
 
+def ensemble_profile_step(vd, I, n_cases: int, graph: str, streams: int = 16):
+    """The bench's ensemble, three steps, then one step between
+    cudaProfilerStart and cudaProfilerStop; prints that step's host time."""
+    import numpy as np
+    import torch
+    cases = I.ensemble_cases(n_cases, dims=(48, 48, 96), seed=2109)
+    gm = {"auto": vd.GRAPH_AUTO, "cycle": vd.GRAPH_CYCLE}[graph]
+    sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500, graph=gm)
+    fields = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in c.state()] for c in cases]
+    torch.cuda.synchronize()
+    with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], sv, n_streams=streams,
+                        mode=vd.VofEnsemble.BATCHED) as E:
+        dts = [c.dt for c in cases]
+        for s in range(3):
+            E.step(fields, dts, s)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        t0 = time.perf_counter()
+        E.step(fields, dts, 3)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"ensemble_profile_step": {"cases": n_cases, "graph": graph, "ms": ms}}))
+
+
 def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int = 2):
     """n independent 48x48x96 ducts (4-16 spheres each, seeded) advanced
     together, fields resident on the device; mixed precision, rtol 1e-8.
@@ -546,6 +575,10 @@ def main():
     from paper_2104_01636_b300 import inputs as I
 
     torch.cuda.set_device(local)
+    if args.ensemble_profile_step:
+        if rank == 0:
+            ensemble_profile_step(vd, I, args.ensemble_cases, args.ensemble_profile_step)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
