@@ -234,14 +234,37 @@ __global__ void k_prolong_pair_f(Bat bt, Dims dc, const float* __restrict__ xc, 
     const int I = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
     if (2 * I >= df.nx || j >= df.ny) return;
     const int k0 = bb.b * kchunk, k1 = min(k0 + kchunk, df.nz);
-    for (int k = k0; k < k1; ++k) {
+    auto one = [&](int k) {
         const float cv = xc[cid(dc, I, j >> 1, k >> 1)];
         float2* p = reinterpret_cast<float2*>(xf + cid(df, 2 * I, j, k));
         float2 v = *p;
         v.x += omega * cv;
         v.y += omega * cv;
         *p = v;
+    };
+    int k = k0;
+    if (k < k1 && (k & 1)) one(k++);
+    // four planes (two parents) per pass: every load issued before the
+    // stores, so a thread has four planes in flight instead of one
+    for (; k + 3 < k1; k += 4) {
+        const float c0 = xc[cid(dc, I, j >> 1, k >> 1)], c1 = xc[cid(dc, I, j >> 1, (k >> 1) + 1)];
+        float2* p = reinterpret_cast<float2*>(xf + cid(df, 2 * I, j, k));
+        const size_t pl = (size_t)df.nx * df.ny / 2;  // plane stride in pairs
+        float2 v0 = p[0], v1 = p[pl], v2 = p[2 * pl], v3 = p[3 * pl];
+        v0.x += omega * c0;
+        v0.y += omega * c0;
+        v1.x += omega * c0;
+        v1.y += omega * c0;
+        v2.x += omega * c1;
+        v2.y += omega * c1;
+        v3.x += omega * c1;
+        v3.y += omega * c1;
+        p[0] = v0;
+        p[pl] = v1;
+        p[2 * pl] = v2;
+        p[3 * pl] = v3;
     }
+    for (; k < k1; ++k) one(k);
 }
 
 // Cell-centred trilinear prolongation along one axis: the fine cell 2I
