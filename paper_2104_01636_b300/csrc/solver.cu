@@ -481,7 +481,7 @@ static vof_status solve_mixed(vof_ctx* c, double* P, double bnorm, double res0, 
     while (!converged && inner_total < c->sv.max_iter && outer < 50) {
         // r32 holds the current FP64 residual rounded to FP32
         const double rr0 = res * bnorm * res * bnorm;
-        const double tol_in = std::max(1e-5, 0.2 * c->sv.rtol / res);
+        const double tol_in = std::max(INNER_TOL_FLOOR, 0.2 * c->sv.rtol / res);
         // a stagnating FP32 inner solve must not use up the whole budget
         const int inner_cap = inner_total + std::max(20, c->sv.max_iter / 4);
         cudaMemsetAsync(c->e32, 0, sizeof(float) * (size_t)n, c->st);
@@ -577,7 +577,7 @@ __global__ void k_ctl_setup(double* s, SolveCtl p, cudaGraphConditionalHandle h_
 __global__ void k_ctl_outer_begin(double* s, SolveCtl p) {
     const double res = s[S_RES], bnorm = s[S_BNORM];
     const double rr0 = res * bnorm * res * bnorm;
-    const double tol_in = fmax(1e-5, 0.2 * p.rtol / res);
+    const double tol_in = fmax(INNER_TOL_FLOOR, 0.2 * p.rtol / res);
     s[S_THR] = tol_in * tol_in * rr0;
     s[S_CAP] = s[S_INNER] + p.cap_add;
 }
@@ -1098,7 +1098,7 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
         for (auto& q : cs)
             if (q.outer) {
                 q.rr0 = q.res * q.bnorm * q.res * q.bnorm;
-                q.tol_in = std::max(1e-5, 0.2 * rtol / q.res);
+                q.tol_in = std::max(INNER_TOL_FLOOR, 0.2 * rtol / q.res);
                 q.cap = q.inner_total + std::max(20, max_iter / 4);
                 q.inner = true;
             }
@@ -1254,7 +1254,7 @@ __global__ void k_bctl_outer_begin(BatchCtl b) {
         if (s[S_OUTACT] == 0.0) continue;
         const double res = s[S_RES], bnorm = s[S_BNORM];
         const double rr0 = res * bnorm * res * bnorm;
-        const double tol_in = fmax(1e-5, 0.2 * b.p.rtol / res);
+        const double tol_in = fmax(INNER_TOL_FLOOR, 0.2 * b.p.rtol / res);
         s[S_THR] = tol_in * tol_in * rr0;
         s[S_CAP] = s[S_INNER] + b.p.cap_add;
         s[S_INACT] = 1.0;

@@ -472,6 +472,10 @@ template <class T> void mg_dense_setup(vof_ctx* c, const Level& L);
 template <class T> void mg_coarsen_density(vof_ctx* c, const T* rho_fine, const Level& fine,
                                            const Level& coarse);
 constexpr int DENSE_MAX = 1536;  // largest coarsest level solved by the dense inverse
+// The mixed solve's inner FP32 tolerance for a refinement that starts from
+// relative residual res: max(INNER_TOL_FLOOR, 0.2 rtol / res) of its initial
+// residual (the floor keeps the FP32 iteration above its rounding level)
+constexpr double INNER_TOL_FLOOR = 1e-5;
 void mg_to_f32(vof_ctx* c, const double* a, float* b, int n);
 // inner FP32 Krylov of the mixed solve (k_mg.cu) and its FP64 residual (k_poisson.cu)
 void k32_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
