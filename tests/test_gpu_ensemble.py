@@ -67,6 +67,27 @@ def test_batched_ensemble_of_many_cases_equals_solo():
     assert len(iters) > 1  # the cases did not all take the same number of iterations
 
 
+def test_step_graph_in_four_case_groups_equals_solo():
+    """Sixteen cases run as four groups of four, each group with its own
+    batched solve and the groups' parts before their solves pipelined; every
+    case bitwise equal to its solo run over both sweep orders."""
+    cases = I.ensemble_cases(16, dims=(32, 32, 48), seed=81)
+    kw = dict(precision=1, rtol=1e-9, max_iter=300)
+    fields = [[dev(a) for a in c.state()] for c in cases]
+    with vd.VofEnsemble(cases[0].grid, [c.phys for c in cases], vd.c_solver(**kw),
+                        n_streams=3, mode=vd.VofEnsemble.BATCHED) as E:
+        reps = [E.step(fields, [c.dt for c in cases], s, reports=True) for s in range(2)]
+        assert E.graph_steps() == 2
+    for k, (c, fs) in enumerate(zip(cases, fields)):
+        solo = [dev(a) for a in c.state()]
+        with ctx(c, **kw) as C:
+            solo_reps = [C.step(*solo, c.dt, s) for s in range(2)]
+        for a, b in zip(fs, solo):
+            assert np.array_equal(host(a), host(b))
+        for s in range(2):
+            assert reps[s][k]["iters"] == solo_reps[s]["iters"]
+
+
 def test_step_graph_recaptured_for_new_time_steps_and_fields():
     """The step graph is captured for the field pointers, the time steps and
     the sweep order: a new dt and new field tensors are captured again, and
