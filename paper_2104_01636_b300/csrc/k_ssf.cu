@@ -33,25 +33,38 @@ __global__ void k_curv_list(Dims d, const double* __restrict__ a, double* __rest
     const bool act = i < d.nx && j < d.ny;
     const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
     const unsigned lane = (threadIdx.x + TBX * threadIdx.y) & 31;
-    for (int k = k0; k < k1; ++k) {
-        int c = 0;
-        bool itf = false;
-        if (act) {
-            c = cid(d, i, j, k);
-            // eps < alpha < 1 - eps on the integer pipe (bit-pattern order of
-            // doubles >= +0; a negative alpha compares below eps)
-            const long long ab = __double_as_longlong(a[c]);
-            itf = ab > __double_as_longlong(EPS_IF) && ab < __double_as_longlong(1.0 - EPS_IF);
-            kappa[c] = 0.0;
-            valid[c] = 0;
+    const unsigned below = (1u << lane) - 1u;
+    // a warp (one row of 32 cells) takes eight planes at a time: their
+    // loads in flight together, one atomic for all their interface cells
+    constexpr int G = 8;
+    for (int kb = k0; kb < k1; kb += G) {
+        unsigned m[G];
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int k = kb + q;
+            bool itf = false;
+            if (act && k < k1) {
+                const int c = cid(d, i, j, k);
+                // eps < alpha < 1 - eps on the integer pipe (bit-pattern order of
+                // doubles >= +0; a negative alpha compares below eps)
+                const long long ab = __double_as_longlong(a[c]);
+                itf = ab > __double_as_longlong(EPS_IF) && ab < __double_as_longlong(1.0 - EPS_IF);
+                kappa[c] = 0.0;
+                valid[c] = 0;
+            }
+            m[q] = __ballot_sync(0xffffffffu, itf);
+            tot += __popc(m[q]);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, itf);
-        if (m) {
+        if (tot) {
             int base = 0;
-            const int leader = __ffs(m) - 1;
-            if ((int)lane == leader) base = atomicAdd(count, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (itf) list[base + __popc(m & ((1u << lane) - 1u))] = c;
+            if (lane == 0) base = atomicAdd(count, tot);
+            base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                if ((m[q] >> lane) & 1u) list[base + __popc(m[q] & below)] = cid(d, i, j, kb + q);
+                base += __popc(m[q]);
+            }
         }
     }
 }
