@@ -218,3 +218,37 @@ def test_step_rising_swarm_parity(prec):
     assert rel_l2(got[1:7], ref[1:7]) <= 1e-8
     assert np.max(np.abs(got[0] - ref[0])) < 1e-10
     assert rel_l2(got[7], ref[7]) < 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_single_phase_duct_parity(prec):
+    """No bubble: alpha is 1 everywhere, so the interface lists are empty and
+    the surface force is zero; the step is the single-phase projection of the
+    laminar duct flow with noise. alpha stays 1 to rounding (each sweep's
+    flux difference and divergence term cancel to an ulp), as in the oracle.
+    Mixed path: both solves reach 1e-13, and P differs from the oracle's by
+    what the predictor's FP32 increments (about 1e-8 of u_hat) put into the
+    right side, about 1.5e-6 Pa on a pressure that falls to 2.5 Pa when only
+    the noise drives it: 3e-7 relative, hence the bar of 1e-6."""
+    case = I.rising_swarm(32, 32, 48, nbub=0, seed=5, steps=3)
+    got, ref, reps, oreps = _run_both(case, case.steps, rtol=1e-12, precision=prec)
+    assert np.max(np.abs(got[0] - 1.0)) < 1e-13
+    assert np.max(np.abs(got[0] - ref[0])) < 1e-13
+    assert rel_l2(got[1:7], ref[1:7]) <= (1e-11 if prec == 0 else 1e-8)
+    assert rel_l2(got[7], ref[7]) < (1e-9 if prec == 0 else 1e-6)
+    for r in reps:
+        assert r["max_div"] * case.dt < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_ragged_grid_parity(prec):
+    """A grid that fills no tile evenly (40 x 24 x 50: 32 x 32 sweep tiles,
+    32 x 8 cell tiles and z chunks all ragged; an odd-width level, 5 x 3 x
+    ..., in the hierarchy) with two small bubbles: whole steps against the
+    oracle."""
+    case = I.rising_swarm(40, 24, 50, nbub=2, d_cells=8, seed=13, steps=3)
+    got, ref, reps, oreps = _run_both(case, case.steps, rtol=1e-12, precision=prec)
+    for r, o in zip(reps, oreps):
+        assert r["vol_after"] == pytest.approx(o["vol_after"], rel=1e-13)
+    assert rel_l2(got[1:7], ref[1:7]) <= (1e-10 if prec == 0 else 1e-8)
+    assert np.max(np.abs(got[0] - ref[0])) < (1e-12 if prec == 0 else 1e-10)
