@@ -114,6 +114,15 @@ def parse():
 # ----------------------------------------------------------------------------
 # Multi-GPU: every rank advances an independent replica (its own seeded duct);
 # the job's time is the slowest rank's, and the value counts every rank's steps.
+_T0 = time.perf_counter()
+
+
+def progress(what: str) -> None:
+    """One line per finished part of the run on stderr (the JSON line stays
+    the only output on stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f} s] {what}", file=sys.stderr, flush=True)
+
+
 def replica_seed(rank: int) -> int:
     return 2106 + rank
 
@@ -409,7 +418,9 @@ def serving(vd, I, n_req: int, do_fp64: bool):
         if name == "fp64" and not do_fp64:
             continue
         sat = serving_run(vd, reqs, prec, None)
+        progress(f"serving {name} saturated run done")
         loaded = serving_run(vd, reqs, prec, 0.7 * sat["requests_per_s"])
+        progress(f"serving {name} loaded run done")
         out[name] = {"saturation": sat, "loaded": loaded}
     return out
 
@@ -481,6 +492,7 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
             phases = [(b - a) / steps for a, b in zip(ph0, E.phase_ms())]
             batched = E.batched
         del fields
+        progress(f"ensemble {label} timed")
         out[label] = {"n_streams": ns, "batched_solves": batched,
                       "ms_per_ensemble_step": ms,
                       "case_steps_per_s": n_cases / (ms / 1e3),
@@ -658,6 +670,7 @@ def main():
         poisson = N * it2 / (solve_ms / 1e3) if solve_ms > 0 else None
         solves = k_steps / (solve_ms / 1e3) if solve_ms > 0 else None
 
+        progress("device-resident steps timed")
         # ---- end to end: the state in pinned host memory, copied in and out
         # every step by the host-buffer step of the C ABI (vof_step_host) --
         H = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in T]
@@ -680,6 +693,7 @@ def main():
         e2e_value = whole_job_rate(world, args.steps, max_over_ranks(ms_e2e, dist, "cuda"))
         ctx.close()
 
+        progress("host-buffer steps timed")
         # ---- the FP64 path on the same workload, for comparison ------------
         fp64 = None
         if args.precision == "mixed" and not args.no_fp64_compare:
@@ -702,6 +716,7 @@ def main():
             ctx64.close()
             del T64
 
+        progress("FP64 path timed")
         # ---- the paper's regular 6 x 6 x 24 bubble array (same grid) -------
         regular = None
         if not args.no_regular_array:
@@ -726,15 +741,19 @@ def main():
             ctxr.close()
             del TR
 
+    progress("paper-shaped duct done")
     serve = None
     if world == 1 and args.serve_requests > 0:
         serve = serving(vd, I, args.serve_requests, not args.no_fp64_compare)
+        progress("serving done")
     ens = None
     if world == 1 and args.ensemble_cases > 0:
         ens = ensemble(vd, I, args.ensemble_cases)
+        progress("ensemble done")
     small = None
     if world == 1 and not args.no_small_configs:
         small = small_configs(vd, I)
+        progress("small configurations done")
 
     if rank != 0:
         if dist is not None:
@@ -745,6 +764,7 @@ def main():
         nz_s = sample_planes(args.steps, args.warmup)
         cb = cpu_baseline(args, steps=2, nz_s=nz_s)
         cb["oracle_full_duct"] = oracle_full_record()
+        progress("CPU baseline done")
         if args.cpu_one_thread:
             one = cpu_baseline(args, steps=1, label="one host thread", nz_s=nz_s, threads=1)
             cb["one_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample",
