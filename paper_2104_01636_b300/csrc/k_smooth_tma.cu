@@ -19,7 +19,7 @@
 //    With the sweep it forms the V-cycle's finest-level operator from the
 //    FP16 density (a preconditioner: the 11-bit density changes no
 //    convergence test), so the V-cycle stays symmetric.
-//  * k_apply_A_dot_rho32: q = A p with the partials of p.q, from the FP32
+//  * k_apply_A_dot_rho32_pair: q = A p with the partials of p.q, from the FP32
 //    density: the inner CG's operator, which the FP64 defect correction
 //    must see to within FP32 rounding.
 #include <cuda.h>
@@ -497,65 +497,6 @@ struct Kahan32 {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// q = A p on the FP32 density with the block partials of p.q. Each thread
-// marches up its z chunk and carries the coefficient of the face below;
-// the coefficient of the face to the +x neighbour is the neighbour lane's
-// -x coefficient (a warp spans 32 consecutive x).
-__global__ void k_apply_A_dot_rho32(Dims d, float ih2, const float* __restrict__ rho,
-                                    const float* __restrict__ p, float* __restrict__ q,
-                                    double* __restrict__ part, int kchunk) {
-    const int i = blockIdx.x * TBX + threadIdx.x, j = blockIdx.y * TBY + threadIdx.y;
-    const bool act = i < d.nx && j < d.ny;
-    const int ic = min(i, d.nx - 1), jc = min(j, d.ny - 1);  // inactive lanes mirror a valid cell
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nz);
-    const int lane = threadIdx.x & 31;
-    Kahan32 ks;
-    if (k0 < k1) {
-        int c = cid(d, ic, jc, k0);
-        const int cb0 = cid(d, ic, jc, wrapk(k0 - 1, d.nz));
-        float rc = rho[c], pc = p[c];
-        float bzm = beta_rho(rc, rho[cb0]);
-        float pm = p[cb0];
-        for (int k = k0; k < k1; ++k) {
-            const int ct = cid(d, ic, jc, wrapk(k + 1, d.nz));
-            const float rt = rho[ct], pt = p[ct];
-            // x faces: own -x face, +x face from the next lane
-            const float rw = ic > 0 ? rho[c - 1] : rc;
-            const float pw = ic > 0 ? p[c - 1] : pc;
-            const float bxm = ic > 0 ? beta_rho(rc, rw) : 0.f;
-            float bxp = __shfl_down_sync(0xffffffffu, bxm, 1);
-            float pe = __shfl_down_sync(0xffffffffu, pc, 1);
-            if (lane == 31 || ic + 1 >= d.nx) {
-                bxp = ic + 1 < d.nx ? beta_rho(rc, rho[c + 1]) : 0.f;
-                pe = ic + 1 < d.nx ? p[c + 1] : pc;
-            }
-            const float bym = jc > 0 ? beta_rho(rc, rho[c - d.nx]) : 0.f;
-            const float byp = jc + 1 < d.ny ? beta_rho(rc, rho[c + d.nx]) : 0.f;
-            const float ps = jc > 0 ? p[c - d.nx] : pc, pn = jc + 1 < d.ny ? p[c + d.nx] : pc;
-            const float bzp = beta_rho(rc, rt);
-            float s = bxm * (pc - pw);
-            s = fmaf(bxp, pc - pe, s);
-            s = fmaf(bym, pc - ps, s);
-            s = fmaf(byp, pc - pn, s);
-            s = fmaf(bzm, pc - pm, s);
-            s = fmaf(bzp, pc - pt, s);
-            const float v = s * ih2;
-            if (act) {
-                q[c] = v;
-                ks.add(pc * v);
-            }
-            // move up one plane
-            bzm = bzp;
-            pm = pc;
-            rc = rt;
-            pc = pt;
-            c = ct;
-        }
-    }
-    const double acc = block_sum(ks.value());
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = acc;
-}
-
 // One block waits, with the sweep's bounded wait, on a shared-memory barrier
 // that nothing completes (no copy is issued): the limit runs out and the
 // block sets the error flag, as the sweep does when a staged plane never
@@ -573,12 +514,13 @@ __global__ void k_wait_probe(double* __restrict__ err, int limit) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) *err = 1.0;
 }
 
-// The same operator on x-pairs: a thread owns cells (2t, 2t+1) of its row
-// and walks up its z chunk carrying the pair's plane below; p and the density
-// of the pair, of the pairs across in y and of the pair above come as 8-byte
-// loads, the two outer x neighbours as scalars. Each cell's stencil is
-// summed in the order of k_apply_A_dot_rho32; the thread's partial of p.q
-// takes the pair's two cells in turn.
+// q = A p on the FP32 density with the block partials of p.q, on x-pairs:
+// a thread owns cells (2t, 2t+1) of its row and walks up its z chunk
+// carrying the pair's plane below and the coefficient of the face below; p
+// and the density of the pair, of the pairs across in y and of the pair
+// above come as 8-byte loads, the two outer x neighbours as scalars. Each
+// cell's stencil is summed over its faces -x, +x, -y, +y, -z, +z; the
+// thread's partial of p.q takes the pair's two cells in turn.
 template <bool B>
 __global__ void k_apply_A_dot_rho32_pair(Bat bt, Dims d, float ih2, const float* __restrict__ rho,
                                          const float* __restrict__ p, float* __restrict__ q,
