@@ -140,6 +140,7 @@ size_t workspace_bytes(const vof_grid* g, const vof_solver* sv) {
     b += s.n * sizeof(double);                        // kappa
     b += 3 * s.n;                                     // valid, cmask, has
     b += s.n * sizeof(int) + 64;                      // interface list
+    b += s.n * (sizeof(int) + 1) + 512;               // its piece order and pieces
     b += 4 * s.n * sizeof(double);                    // planes
     b += 3 * s.n * sizeof(double);                    // cell intermediate velocity
     b += 3 * s.n * sizeof(double);                    // alpha scratch
@@ -569,6 +570,8 @@ static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
     A((void**)&c->has, s.n);
     A((void**)&c->if_list, s.n * sizeof(int));
     A((void**)&c->if_count, 64);
+    A((void**)&c->if_perm, s.n * sizeof(int));
+    A((void**)&c->if_piece, s.n);
     A((void**)&c->plane, 4 * s.n * D);
     A((void**)&c->a1, s.n * D);
     A((void**)&c->a2, s.n * D);

@@ -21,11 +21,12 @@
 // nodes steered on the device, and every case's correction. From 8 cases
 // up the cases run in groups of consecutive cases (up to four) with a
 // batched solve each: a group's part before its solve starts when the group
-// before has ended its own, so it runs beside that group's solve. A step whose CFL test fails in
-// any case is run again the host-driven way, which reports each case's
-// status; nothing of the step has been launched by then. The graph is
-// captured for the step's field pointers and time steps and the parity of
-// the step index (the sweep order), and captured again when they change.
+// before has ended its own, so it runs beside that group's solve. A step
+// whose CFL test fails in any case is run again the host-driven way, which
+// reports each case's status; nothing of the step has been launched by then.
+// The graph is captured for the step's field pointers and time steps and the
+// parity of the step index (the sweep order), and captured again when they
+// change.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>

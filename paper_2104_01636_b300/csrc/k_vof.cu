@@ -66,21 +66,90 @@ __global__ void k_if_list(Dims d, const double* __restrict__ a, unsigned char* _
     }
 }
 
-// Pass 2: normal and FP64 plane constant of every listed interface cell.
-__global__ void k_reconstruct_list(Geo g, const double* __restrict__ a,
-                                   const int* __restrict__ list, const int* __restrict__ count,
-                                   unsigned char* __restrict__ has, Plane* __restrict__ plane) {
-    const int n = *count;
+// Pass 2: normal and FP64 plane constant of every listed interface cell, in
+// three launches so that the plane constants run in warps of one branch:
+//  (a) the normal (stored in the plane) and the estimated branch of every
+//      listed cell, counted per branch;
+//  (b) (one block) the start of each branch's range in if_perm;
+//  (c) every cell with a plane placed in its branch's range;
+//  (d) the plane constant of every cell in that order.
+// Each cell's normal and plane constant are the same expressions as in one
+// pass, so the planes do not depend on the order.
+constexpr int NPIECE = 6;
+// slots of if_count (16 ints): 0 the list's length, 1-6 the counts per
+// branch, 8-13 the branches' cursors in if_perm, 14 the cells with a plane
+constexpr int PIECE_CNT = 1, PIECE_CUR = 8;
+static_assert(PIECE_CUR + NPIECE < 16, "if_count holds 16 ints");
+
+__global__ void k_reconstruct_normals(Geo g, const double* __restrict__ a,
+                                      const int* __restrict__ list, int* __restrict__ cnt,
+                                      unsigned char* __restrict__ piece, Plane* __restrict__ plane) {
+    __shared__ int bc[NPIECE];
+    if (threadIdx.x < NPIECE) bc[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = cnt[0];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const int c = list[t];
         const int i = c % g.d.nx, j = (c / g.d.nx) % g.d.ny, k = c / (g.d.nx * g.d.ny);
         double nrm[3];
         smoothed_normal(g, a, i, j, k, nrm);
+        unsigned char pc = 255;
         if (nrm[0] != 0.0 || nrm[1] != 0.0 || nrm[2] != 0.0) {
-            plane[c] = Plane{nrm[0], nrm[1], nrm[2],
-                             plic::plane_constant(nrm[0], nrm[1], nrm[2], a[c])};
-            has[c] = 1;
+            Plane& pl = plane[c];
+            pl.n0 = nrm[0];
+            pl.n1 = nrm[1];
+            pl.n2 = nrm[2];
+            pc = (unsigned char)plic::plane_piece_estimate(nrm[0], nrm[1], nrm[2], a[c]);
+            atomicAdd(&bc[pc], 1);
         }
+        piece[t] = pc;
+    }
+    __syncthreads();
+    if (threadIdx.x < NPIECE && bc[threadIdx.x]) atomicAdd(&cnt[PIECE_CNT + threadIdx.x], bc[threadIdx.x]);
+}
+
+__global__ void k_piece_offsets(int* __restrict__ cnt) {
+    if (threadIdx.x != 0) return;
+    int o = 0;
+    for (int p = 0; p < NPIECE; ++p) {
+        cnt[PIECE_CUR + p] = o;
+        o += cnt[PIECE_CNT + p];
+    }
+    cnt[PIECE_CUR + NPIECE] = o;  // cells with a plane
+}
+
+__global__ void k_piece_scatter(const int* __restrict__ list, int* __restrict__ cnt,
+                                const unsigned char* __restrict__ piece, int* __restrict__ perm) {
+    const int n = cnt[0];
+    const unsigned lane = threadIdx.x & 31, below = (1u << lane) - 1u;
+    // every lane of a warp runs the same number of passes, so the ballots
+    // below always have the whole warp
+    const int stride = gridDim.x * blockDim.x;
+    const int base0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (int w = base0; w < n; w += stride) {
+        const int t = w + (int)lane;
+        const int p = t < n ? (int)piece[t] : 255;
+#pragma unroll
+        for (int q = 0; q < NPIECE; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, p == q);
+            if (!m) continue;
+            int b = 0;
+            if (lane == (unsigned)(__ffs(m) - 1)) b = atomicAdd(&cnt[PIECE_CUR + q], __popc(m));
+            b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
+            if (p == q) perm[b + __popc(m & below)] = list[t];
+        }
+    }
+}
+
+__global__ void k_reconstruct_planes(const double* __restrict__ a, const int* __restrict__ cnt,
+                                     const int* __restrict__ perm, unsigned char* __restrict__ has,
+                                     Plane* __restrict__ plane) {
+    const int n = cnt[PIECE_CUR + NPIECE];  // cells with a plane
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int c = perm[u];
+        Plane& pl = plane[c];
+        pl.d = plic::plane_constant(pl.n0, pl.n1, pl.n2, a[c]);
+        has[c] = 1;
     }
 }
 
@@ -280,11 +349,16 @@ void launch_volume(vof_ctx* c, const double* alpha, int slot) {
 void launch_reconstruct(vof_ctx* c, const double* alpha) {
     const Launch& L = c->Lc;
     int m = timer_begin(c, T_ADVECT);
-    cudaMemsetAsync(c->if_count, 0, sizeof(int), c->st);
+    cudaMemsetAsync(c->if_count, 0, 64, c->st);
     VOF_LAUNCH(c, k_if_list, L.grid, L.block, c->d, alpha, c->has, c->if_list, c->if_count,
                L.kchunk);
-    VOF_LAUNCH(c, k_reconstruct_list, c->sm_count * 16, 128, geo(c), alpha, c->if_list,
-               c->if_count, c->has, (Plane*)c->plane);
+    VOF_LAUNCH(c, k_reconstruct_normals, c->sm_count * 16, 128, geo(c), alpha, c->if_list,
+               c->if_count, c->if_piece, (Plane*)c->plane);
+    VOF_LAUNCH(c, k_piece_offsets, 1, 32, c->if_count);
+    VOF_LAUNCH(c, k_piece_scatter, c->sm_count * 8, 256, c->if_list, c->if_count, c->if_piece,
+               c->if_perm);
+    VOF_LAUNCH(c, k_reconstruct_planes, c->sm_count * 16, 128, alpha, c->if_count, c->if_perm,
+               c->has, (Plane*)c->plane);
     timer_end(c, T_ADVECT, m);
 }
 

@@ -142,6 +142,37 @@ __device__ __forceinline__ double plane_constant(double m0, double m1, double m2
     return a * S + off;
 }
 
+// Which branch of plane_constant a cell takes, estimated in FP32 (0: a
+// closed form with no piece search, 1: cube-corner piece (cube root), 2:
+// the quadratic piece (square root), 3: the linear piece, 4 and 5: the two
+// cubic pieces (Newton)). The estimate only orders the cells so that the
+// lanes of a warp take the same branch; plane_constant decides each cell's
+// branch itself, so a wrong estimate near a piece boundary changes nothing.
+__device__ __forceinline__ int plane_piece_estimate(double n0, double n1, double n2, double alpha) {
+    float m0 = fabsf((float)n0), m1 = fabsf((float)n1), m2 = fabsf((float)n2);
+    const float S = m0 + m1 + m2;
+    if (!(S > 0.f)) return 0;
+    const float iS = 1.f / S;
+    float b1 = m0 * iS, b2 = m1 * iS, b3 = m2 * iS, t;
+    if (b1 > b2) { t = b1; b1 = b2; b2 = t; }
+    if (b2 > b3) { t = b2; b2 = b3; b3 = t; }
+    if (b1 > b2) { t = b1; b1 = b2; b2 = t; }
+    b3 = 1.f - b1 - b2;
+    const float a = (float)alpha, V = a <= 0.5f ? a : 1.f - a;
+    if (V <= 0.f || b2 <= 0.f) return 0;
+    const float i6 = 1.f / (6.f * b2 * b3);
+    if (V < b1 * b1 * i6) return 1;
+    if (V < (3.f * b2 * (b2 - b1) + b1 * b1) * i6) return 2;
+    const float b12 = b1 + b2;
+    if (b12 <= b3) return (V < b12 / (2.f * b3) && b1 > 0.f) ? 4 : 3;
+    float V3 = (3.f * b2 * (b2 - b1) + b1 * b1) * i6;
+    if (b1 > 0.f) {
+        const float p = b3 - b1, q = b3 - b2;
+        V3 = (b3 * b3 + b3 * p + p * p - q * q * q / b1) * i6;
+    }
+    return V < V3 ? 4 : 5;
+}
+
 // Liquid fraction (of the whole cell) inside the donor slab of relative
 // width c next to the face: the plus face when plus_side, else the minus
 // face. The slab is rescaled to a unit cube along dir.

@@ -237,7 +237,9 @@ struct vof_ctx {
     double *kappa = nullptr;                               // curvature (step)
     unsigned char *valid = nullptr, *cmask = nullptr, *has = nullptr;
     int* if_list = nullptr;   // interface cells of the current sweep
-    int* if_count = nullptr;  // their number (device)
+    int* if_count = nullptr;  // their number (device), then per plane-constant piece: counts, cursors
+    int* if_perm = nullptr;   // the listed cells with a plane, ordered by piece
+    unsigned char* if_piece = nullptr;  // per list entry: its piece (255: no plane)
     double *plane = nullptr;  // 4 per cell: n[3], d
     double *fx = nullptr, *fy = nullptr, *fz = nullptr;  // liquid fluxes / face accelerations
     double *uh[3] = {nullptr, nullptr, nullptr};          // cell intermediate velocity
