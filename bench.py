@@ -88,6 +88,9 @@ def parse():
                     help="coarse levels: 0 one launch per operation (replayed from the cycle's "
                          "graph), 1 one cluster launch per visit, 2 one grid-wide cooperative "
                          "launch per visit")
+    ap.add_argument("--mg-tune", default="auto", choices=["auto", "off"],
+                    help="launch shapes of the coarse levels' colour passes: timed when a "
+                         "context is created (auto) or built in (off); the same bits either way")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-one-thread", action="store_true",
                     help="also time the oracle's sample on one host thread (slow)")
@@ -450,7 +453,8 @@ def ensemble_profile_step(vd, I, n_cases: int, graph: str, streams: int = 16):
     print(json.dumps({"ensemble_profile_step": {"cases": n_cases, "graph": graph, "ms": ms}}))
 
 
-def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int = 2):
+def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int = 2,
+             tune: int = 0):
     """n independent 48x48x96 ducts (4-16 spheres each, seeded) advanced
     together, fields resident on the device; mixed precision, rtol 1e-8.
     Timed on the host clock around whole ensemble steps (each call returns
@@ -469,7 +473,8 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
             ("streams", streams, vd.VofEnsemble.STREAMS, vd.GRAPH_AUTO),
             ("one_stream", 1, vd.VofEnsemble.STREAMS, vd.GRAPH_AUTO))
     for label, ns, mode, graph in runs:
-        sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500, graph=graph)
+        sv = vd.c_solver(vd.PREC_MIXED_FP32, rtol=1e-8, max_iter=500, graph=graph,
+                         mg_tune=tune)
         fields = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in c.state()]
                   for c in cases]
         torch.cuda.synchronize()
@@ -491,6 +496,7 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
             graph_steps = (E.graph_steps() - g0) / steps
             phases = [(b - a) / steps for a, b in zip(ph0, E.phase_ms())]
             batched = E.batched
+            shapes = mg_shapes(vd, E) if batched else None
         del fields
         progress(f"ensemble {label} timed")
         out[label] = {"n_streams": ns, "batched_solves": batched,
@@ -502,6 +508,25 @@ def ensemble(vd, I, n_cases: int, streams: int = 16, steps: int = 5, warmup: int
                       "ms_before_solve_solve_after": phases,
                       "max_inner_iters": max(r["iters"] for r in reps),
                       "mean_inner_iters": sum(r["iters"] for r in reps) / len(reps)}
+        if shapes is not None:
+            out[label]["mg_shapes"] = shapes
+    return out
+
+
+TUNE = {"auto": 0, "off": 1}
+
+
+def mg_shapes(vd, obj):
+    """The coarse levels' launch shapes of a context or of an ensemble's
+    batched solve, by level."""
+    out = {}
+    for level in range(1, 16):
+        try:
+            sh = obj.mg_shape(level)
+        except vd.VofError:
+            continue
+        out[str(level)] = {"planes_per_thread": sh[0], "block": sh[1], "restrict_block": sh[2],
+                           "timed": sh[3]}
     return out
 
 
@@ -611,8 +636,9 @@ def main():
         gmode = {"auto": vd.GRAPH_AUTO, "cycle": vd.GRAPH_CYCLE, "off": vd.GRAPH_OFF}[args.graph]
         ctx = vd.VofContext(g, case.phys,
                             vd.c_solver(prec, rtol=args.rtol, max_iter=500, graph=gmode,
-                                        mg_tail=args.mg_tail),
+                                        mg_tail=args.mg_tail, mg_tune=TUNE[args.mg_tune]),
                             stream=stream)
+        shapes = mg_shapes(vd, ctx)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         T = [dev(x) for x in case.state()]
         torch.cuda.synchronize()
@@ -748,7 +774,7 @@ def main():
         progress("serving done")
     ens = None
     if world == 1 and args.ensemble_cases > 0:
-        ens = ensemble(vd, I, args.ensemble_cases)
+        ens = ensemble(vd, I, args.ensemble_cases, tune=TUNE[args.mg_tune])
         progress("ensemble done")
     small = None
     if world == 1 and not args.no_small_configs:
@@ -798,6 +824,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
         "gpu_launches": launches,
+        "mg_shapes": shapes,
         "clocks": ck,
         "fp64_path": fp64,
         "regular_array": regular,

@@ -140,12 +140,25 @@ typedef struct {
                              cooperative launch over every SM with its
                              operations separated by grid-wide barriers
                              (bounded waits: VOF_ERR_TIMEOUT if one gives up) */
+    int mg_tune;          /* VOF_TUNE_AUTO (default): when the context is
+                             created (and when an ensemble sets up its
+                             batched solve), the launch shapes of the coarse
+                             levels' colour passes (z chunk of a tiled pass,
+                             threads of a 1-D block) and of the 1-D
+                             restriction from a narrow level are timed on
+                             the level's own arrays and the fastest kept;
+                             the result is cached per level shape and batch
+                             for the process. VOF_TUNE_OFF: the built-in
+                             shapes. The passes are pointwise, so every
+                             shape gives the same bits (vof_mg_shape reports
+                             the choice). */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };
 enum { VOF_CYCLE_W = 0, VOF_CYCLE_V = 1 };
 enum { VOF_GRAPH_AUTO = 0, VOF_GRAPH_OFF = 1, VOF_GRAPH_CYCLE = 2 };
 enum { VOF_TAIL_LAUNCHES = 0, VOF_TAIL_CLUSTER = 1, VOF_TAIL_GRID = 2 };
+enum { VOF_TUNE_AUTO = 0, VOF_TUNE_OFF = 1 };
 
 enum { VOF_MG_CONSTANT = 0, VOF_MG_TRILINEAR = 1 };
 
@@ -334,6 +347,23 @@ vof_status vof_diag_wait_timeout(vof_ctx* ctx);
 /* Number of CUDA kernels this context has launched since creation. */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
 
+/* Launch shape of multigrid level `level`'s colour passes (solver->mg_tune):
+ * shape[0] the z planes per thread of a tiled pass (0 when the level runs
+ * 1-D blocks), shape[1] the threads of a 1-D block of the passes (0 when
+ * tiled), shape[2] the threads of a 1-D block of the restriction from this
+ * level (0 when that restriction is tiled), shape[3] 1 when the shape was
+ * chosen by timing, 0 when built in. VOF_ERR_ARG for a null argument or a
+ * level that runs no colour passes through these kernels (the finest level,
+ * the coarsest, a level with an odd nx). */
+vof_status vof_mg_shape(const vof_ctx* ctx, int level, int shape[4]);
+/* Sets that shape: shape[0..2] as vof_mg_shape reports them, nonzero
+ * exactly where the level uses a value (z planes per thread in [1, nz];
+ * block threads a multiple of 32 in [32, 1024]); the shape then counts as
+ * built in. It applies to the launches made, and the graphs captured, after
+ * the call: set it before the first solve. Any valid shape gives the same
+ * bits. VOF_ERR_ARG for a bad level or value, nothing changed. */
+vof_status vof_mg_set_shape(vof_ctx* ctx, int level, const int shape[3]);
+
 /* Per-phase CUDA-event timing inside the calls (off by default). When on,
  * kernel classes are bracketed by events on the context stream and the
  * accumulated device time and launch counts are returned by
@@ -484,6 +514,10 @@ vof_status vof_ensemble_launch_count(const vof_ensemble* ensemble, long long* n)
 vof_status vof_ensemble_phase_ms(const vof_ensemble* ensemble, double* ms);
 /* Steps so far that ran as one graph launch. */
 vof_status vof_ensemble_graph_steps(const vof_ensemble* ensemble, long long* n);
+/* vof_mg_shape of the batched solve's levels (the launches that cover the
+ * first group of cases, or every case when the steps are host-driven);
+ * VOF_ERR_UNSUPPORTED for an ensemble without batched solves. */
+vof_status vof_ensemble_mg_shape(const vof_ensemble* ensemble, int level, int shape[4]);
 
 /* ---- duct statistics ------------------------------------------------------
  * Running sums for the profiles of Section 4 (averages over the streamwise

@@ -54,7 +54,7 @@ class CSolver(ctypes.Structure):
                 ("mg_coarsen", ctypes.c_int), ("mg_cycle", ctypes.c_int),
                 ("mg_w_depth", ctypes.c_int), ("graph", ctypes.c_int),
                 ("nu_fine", ctypes.c_int), ("ssf_solves", ctypes.c_int),
-                ("mg_tail", ctypes.c_int)]
+                ("mg_tail", ctypes.c_int), ("mg_tune", ctypes.c_int)]
 
 
 class CReport(ctypes.Structure):
@@ -124,6 +124,8 @@ def load() -> ctypes.CDLL:
         "vof_diag_wait_timeout": [_VP],
         "vof_set_timing": [_VP, ctypes.c_int],
         "vof_launch_count": [_VP, ctypes.POINTER(ctypes.c_longlong)],
+        "vof_mg_shape": [_VP, ctypes.c_int, P(ctypes.c_int)],
+        "vof_mg_set_shape": [_VP, ctypes.c_int, P(ctypes.c_int)],
         "vof_kernel_times": [_VP, P(ctypes.c_char_p), P(_D), P(ctypes.c_longlong), ctypes.c_int,
                              P(ctypes.c_int)],
         "vof_server_create": [ctypes.c_size_t, ctypes.c_int, P(_VP)],
@@ -141,6 +143,7 @@ def load() -> ctypes.CDLL:
         "vof_ensemble_launch_count": [_VP, P(ctypes.c_longlong)],
         "vof_ensemble_phase_ms": [_VP, P(_D)],
         "vof_ensemble_graph_steps": [_VP, P(ctypes.c_longlong)],
+        "vof_ensemble_mg_shape": [_VP, ctypes.c_int, P(ctypes.c_int)],
         "vof_stats_create": [P(CGrid), P(_VP)],
         "vof_stats_accumulate": [_VP, _VP, _VP, _VP, _VP, _VP],
         "vof_stats_read": [_VP, P(_D), P(ctypes.c_longlong)],
@@ -171,16 +174,17 @@ COARSEN_FACE_MEAN, COARSEN_DENSITY_MEAN = 0, 1
 CYCLE_W, CYCLE_V = 0, 1
 GRAPH_AUTO, GRAPH_OFF, GRAPH_CYCLE = 0, 1, 2
 TAIL_LAUNCHES, TAIL_CLUSTER = 0, 1
+TUNE_AUTO, TUNE_OFF = 0, 1
 
 
 def c_solver(precision=PREC_FP64, rtol=1e-10, max_iter=200, nu_pre=2, nu_post=2, mg_omega=0.0,
              coarse_iters=0, coarse_tol=0.0, mg_interp=0, mg_coarsen=COARSEN_FACE_MEAN,
              mg_cycle=CYCLE_W, mg_w_depth=0, graph=GRAPH_AUTO, nu_fine=0,
-             ssf_solves=1, mg_tail=0) -> CSolver:
+             ssf_solves=1, mg_tail=0, mg_tune=TUNE_AUTO) -> CSolver:
     return CSolver(int(precision), float(rtol), int(max_iter), int(nu_pre), int(nu_post),
                    float(mg_omega), int(coarse_iters), float(coarse_tol), int(mg_interp),
                    int(mg_coarsen), int(mg_cycle), int(mg_w_depth), int(graph), int(nu_fine),
-                   int(ssf_solves), int(mg_tail))
+                   int(ssf_solves), int(mg_tail), int(mg_tune))
 
 
 def workspace_bytes(grid, solver: CSolver | None = None) -> int:
@@ -347,6 +351,20 @@ class VofContext:
         self._chk(self.lib.vof_launch_count(self._ctx, ctypes.byref(n)), "vof_launch_count")
         return int(n.value)
 
+    def mg_shape(self, level: int):
+        """Launch shape of a coarse level's colour passes: (z planes per
+        thread of a tiled pass or 0, threads of a 1-D block or 0, threads of
+        a 1-D block of the restriction from it or 0, timed)."""
+        sh = (ctypes.c_int * 4)()
+        self._chk(self.lib.vof_mg_shape(self._ctx, int(level), sh), "vof_mg_shape")
+        return (sh[0], sh[1], sh[2], bool(sh[3]))
+
+    def set_mg_shape(self, level: int, planes: int, block: int, restrict_block: int):
+        """Sets a coarse level's launch shape (the first three values of
+        mg_shape); before the first solve."""
+        sh = (ctypes.c_int * 3)(int(planes), int(block), int(restrict_block))
+        self._chk(self.lib.vof_mg_set_shape(self._ctx, int(level), sh), "vof_mg_set_shape")
+
     def set_timing(self, on: bool):
         self._chk(self.lib.vof_set_timing(self._ctx, int(bool(on))), "vof_set_timing")
 
@@ -506,6 +524,14 @@ class VofEnsemble:
         n = ctypes.c_longlong(0)
         self.lib.vof_ensemble_graph_steps(self._e, ctypes.byref(n))
         return int(n.value)
+
+    def mg_shape(self, level: int):
+        """Ctx.mg_shape of the batched solve's launches."""
+        sh = (ctypes.c_int * 4)()
+        st = self.lib.vof_ensemble_mg_shape(self._e, int(level), sh)
+        if st != 0:
+            raise VofError(st, "vof_ensemble_mg_shape")
+        return (sh[0], sh[1], sh[2], bool(sh[3]))
 
     def step(self, fields, dts, step_index: int, reports: bool = False):
         """fields: list (one per case) of the eight CUDA float64 tensors."""

@@ -524,6 +524,7 @@ static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
          solver->graph != VOF_GRAPH_CYCLE) ||
         (solver->mg_tail != VOF_TAIL_LAUNCHES && solver->mg_tail != VOF_TAIL_CLUSTER &&
          solver->mg_tail != VOF_TAIL_GRID) ||
+        (solver->mg_tune != VOF_TUNE_AUTO && solver->mg_tune != VOF_TUNE_OFF) ||
         solver->mg_w_depth < 0 || solver->ssf_solves < 0 || solver->ssf_solves > 2 ||
         solver->nu_fine < 0 ||
         (solver->precision != VOF_PREC_FP64 && solver->precision != VOF_PREC_MIXED_FP32))
@@ -592,6 +593,10 @@ static vof_status create_impl(const vof_grid* grid, const vof_phys* phys,
         A((void**)&c->pflow, s.n * D);
     }
     if (st == VOF_OK) st = mg_allocate(c);
+    if (st == VOF_OK && mg_tune_shapes(c, 1, 0, nullptr) != VOF_OK) {
+        st = launch_check(c, "timing the multigrid launch shapes");
+        if (st == VOF_OK) st = set_err(c, VOF_ERR_CUDA, "timing the multigrid launch shapes failed");
+    }
     if (st == VOF_OK) {
         // the scalar mirror: a mapped page-locked slot, else pageable memory
         c->hbuf = mirror_acquire();
@@ -878,6 +883,15 @@ vof_status vof_launch_count(const vof_ctx* c, long long* n) {
     if (!c || !n) return VOF_ERR_ARG;
     *n = c->nlaunch;
     return VOF_OK;
+}
+
+vof_status vof_mg_shape(const vof_ctx* c, int level, int shape[4]) {
+    return mg_shape_of(c, level, shape);
+}
+
+vof_status vof_mg_set_shape(vof_ctx* c, int level, const int shape[3]) {
+    if (!c || !shape) return VOF_ERR_ARG;
+    return mg_set_shape(c, level, shape);
 }
 
 vof_status vof_set_timing(vof_ctx* c, int on) {

@@ -569,6 +569,20 @@ bool create_batched(vof_ensemble* e, const vof_grid* grid, const vof_phys* phys,
     return true;
 }
 
+// the batched solve's launch shapes, timed as the steps launch them: for
+// each group through its first context (the step graph), or for every case
+// through case 0's (host-driven steps)
+vof_status tune_batched(vof_ensemble* e) {
+    if (e->step_graph == 1) {
+        for (int g = 0; g < e->ngroups; ++g) {
+            const vof_status st = batch_solve_tune(e->ctx[group_first(e, g)], e->gbs[g], e->stride);
+            if (st != VOF_OK) return st;
+        }
+        return VOF_OK;
+    }
+    return batch_solve_tune(e->ctx[0], e->bs, e->stride);
+}
+
 }  // namespace
 
 extern "C" {
@@ -614,6 +628,13 @@ vof_status vof_ensemble_create_mode(const vof_grid* grid, const vof_phys* phys, 
         // host-driven loops (VOF_GRAPH_CYCLE) or direct launches
         if (e->batched && solver->graph == VOF_GRAPH_AUTO)
             e->step_graph = step_graph_resources(e) ? 1 : -1;
+        if (e->batched) {
+            const vof_status st = tune_batched(e);
+            if (st != VOF_OK) {
+                destroy_all(e);
+                return st;
+            }
+        }
     }
     if (!e->batched)
         for (int c = 0; c < n_cases; ++c) {
@@ -685,6 +706,12 @@ vof_status vof_ensemble_graph_steps(const vof_ensemble* e, long long* n) {
     if (!e || !n) return VOF_ERR_ARG;
     *n = e->graph_steps;
     return VOF_OK;
+}
+
+vof_status vof_ensemble_mg_shape(const vof_ensemble* e, int level, int shape[4]) {
+    if (!e || !shape) return VOF_ERR_ARG;
+    if (!e->batched) return VOF_ERR_UNSUPPORTED;
+    return mg_shape_of(e->ctx[0], level, shape);
 }
 
 vof_status vof_ensemble_launch_count(const vof_ensemble* e, long long* n) {

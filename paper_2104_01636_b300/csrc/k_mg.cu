@@ -13,8 +13,9 @@
 // inverse formed once per solve by FP64 Gauss-Jordan elimination; larger
 // coarsest levels fall back to Jacobi-preconditioned CG in one thread block.
 #include <algorithm>
-
 #include <initializer_list>
+#include <mutex>
+#include <vector>
 
 #include "mg_cell.cuh"
 #include "vof_internal.cuh"
@@ -880,10 +881,9 @@ LA<float> arrays<float>(const Level& L) {
 
 // Levels narrower than FLAT_NX cells in x run their colour passes and the
 // restriction from them a thread per (x-pair, y, z) or coarse cell in 1-D
-// blocks of FLAT_BLOCK threads, instead of 32 x 8 tiles of which a 24- or
-// 12-cell-wide plane fills a third or less.
+// blocks (Level::pass_block, restrict_block threads), instead of 32 x 8
+// tiles of which a 24- or 12-cell-wide plane fills a third or less.
 constexpr int FLAT_NX = 64;
-constexpr int FLAT_BLOCK = 256;
 
 // one colour pass on a level with an even nx, a thread per x-pair; CT is
 // the coefficients' storage type
@@ -912,15 +912,17 @@ void rbgs_pair(vof_ctx* c, const Level& L, T h2, const CT* bx, const CT* by, con
     const T omega = (T)(c->sv.mg_omega > 0.0 ? c->sv.mg_omega : 1.0);
     int m = timer_begin(c, cls);
     if (flat) {
-        dim3 grid((L.ncells / 2 + FLAT_BLOCK - 1) / FLAT_BLOCK);
+        const int nb = L.pass_block;
+        dim3 grid((L.ncells / 2 + nb - 1) / nb);
         const Bat bt = bat_of(c, grid.y);
-        launch_pdl(c, kern, grid, dim3(FLAT_BLOCK), bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x,
+        launch_pdl(c, kern, grid, dim3(nb), bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x,
                    a.f, color, 1, dc, xc, omega);
     } else {
-        // a thread per x-pair halves the blocks of the level's cell geometry:
-        // halve the z chunks to keep about as many blocks in flight
+        // a thread per x-pair halves the blocks of the level's cell geometry;
+        // the z chunks are divided (by 4 unless timed or set otherwise) to
+        // keep enough blocks in flight
         const int gx = (L.d.nx / 2 + TBX - 1) / TBX;
-        const int kchunk = std::max(1, (L.L.kchunk + 3) / 4);
+        const int kchunk = pass_kchunk_of(L);
         dim3 grid(gx, L.L.grid.y, (L.d.nz + kchunk - 1) / kchunk);
         const Bat bt = bat_of(c, grid.z);
         launch_pdl(c, kern, grid, L.L.block, bt, L.d, h2, bx, by, bz, (const T*)a.x, a.x, a.f,
@@ -974,11 +976,12 @@ void mg_restrict(vof_ctx* c, const Level& F, const Level& C) {
                        (const __half*)F.bzh, (const float*)a.x, (const float*)a.f, C.d,
                        (float*)b.f, C.L.kchunk);
         } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0 && F.d.nx < FLAT_NX) {
-            dim3 gf((C.ncells + FLAT_BLOCK - 1) / FLAT_BLOCK);
+            const int nb = F.restrict_block;
+            dim3 gf((C.ncells + nb - 1) / nb);
             const Bat bt = bat_of(c, gf.y);
             launch_pdl(c, bt.zb ? k_restrict_pair_f<float, true, true>
                                 : k_restrict_pair_f<float, false, true>,
-                       gf, dim3(FLAT_BLOCK), bt, F.d, (float)(1.0 / (F.h * F.h)),
+                       gf, dim3(nb), bt, F.d, (float)(1.0 / (F.h * F.h)),
                        (const float*)a.bx, (const float*)a.by, (const float*)a.bz,
                        (const float*)a.x, (const float*)a.f, C.d, (float*)b.f, 1);
         } else if (sizeof(T) == sizeof(float) && F.d.nx % 2 == 0) {
@@ -1212,3 +1215,242 @@ template void mg_zero<double>(vof_ctx*, const Level&);
 template void mg_dense_setup<double>(vof_ctx*, const Level&);
 template void mg_dense_setup<float>(vof_ctx*, const Level&);
 template void mg_zero<float>(vof_ctx*, const Level&);
+
+// ---------------------------------------------------------------------------
+// Launch shapes of the coarse levels' colour passes, chosen by timing. A
+// colour pass and the 1-D restriction are pointwise: each thread writes its
+// own cells from loads, with the same rounded operations whatever the
+// mapping, so the shape changes the time and never a bit. The choices are
+// cached for the process per device, level dimensions, number of cases and
+// storage types, so contexts of one shape (a server's requests, an
+// ensemble's cases) time a level once.
+namespace {
+
+struct ShapeKey {
+    int dev, nx, ny, nz, nb, tsize, half, kind;  // kind 0: colour passes, 1: restriction
+    bool operator==(const ShapeKey& o) const {
+        return dev == o.dev && nx == o.nx && ny == o.ny && nz == o.nz && nb == o.nb &&
+               tsize == o.tsize && half == o.half && kind == o.kind;
+    }
+};
+std::mutex g_shape_mu;
+std::vector<std::pair<ShapeKey, int>> g_shapes;
+
+bool cached_shape(const ShapeKey& k, int* v) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    for (const auto& e : g_shapes)
+        if (e.first == k) {
+            *v = e.second;
+            return true;
+        }
+    return false;
+}
+
+void cache_shape(const ShapeKey& k, int v) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    for (auto& e : g_shapes)
+        if (e.first == k) {
+            e.second = v;
+            return;
+        }
+    g_shapes.push_back({k, v});
+}
+
+// finite, normal values in a level's arrays for the timed passes: every
+// coefficient byte 0x3C (1.06 in FP16, 0.0115 in FP32, 1.6e-18 in FP64),
+// x and f zero (so the passes keep x at zero)
+template <class T>
+void fill_for_timing(vof_ctx* c, const Level& L) {
+    const LA<T> a = arrays<T>(L);
+    const size_t nu = (size_t)(L.d.nx + 1) * L.d.ny * L.d.nz;
+    const size_t nv = (size_t)L.d.nx * (L.d.ny + 1) * L.d.nz;
+    const size_t n = L.ncells;
+    cudaMemsetAsync(a.bx, 0x3C, sizeof(T) * nu, c->st);
+    cudaMemsetAsync(a.by, 0x3C, sizeof(T) * nv, c->st);
+    cudaMemsetAsync(a.bz, 0x3C, sizeof(T) * n, c->st);
+    cudaMemsetAsync(a.x, 0, sizeof(T) * n, c->st);
+    cudaMemsetAsync(a.f, 0, sizeof(T) * n, c->st);
+    if (sizeof(T) == sizeof(float) && L.bxh) {
+        cudaMemsetAsync(L.bxh, 0x3C, sizeof(__half) * nu, c->st);
+        cudaMemsetAsync(L.byh, 0x3C, sizeof(__half) * nv, c->st);
+        cudaMemsetAsync(L.bzh, 0x3C, sizeof(__half) * n, c->st);
+    }
+}
+
+// milliseconds of `reps` runs of op after one untimed run; negative on a
+// CUDA error
+template <class F>
+float time_op(vof_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int reps, F op) {
+    op();
+    cudaEventRecord(e0, c->st);
+    for (int r = 0; r < reps; ++r) op();
+    cudaEventRecord(e1, c->st);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        return -1.f;
+    return ms;
+}
+
+// the fastest of the candidate values set by `set` (two interleaved rounds,
+// the minimum of each candidate's times), or the built-in value `dflt`
+// unless a candidate beats it by 3%; dflt on any error
+template <class S, class F>
+int pick(vof_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int reps, const int* cand, int ncand,
+         int dflt, S set, F op, bool* err) {
+    float best[8];
+    for (int i = 0; i < ncand; ++i) best[i] = 1e30f;
+    for (int round = 0; round < 2; ++round)
+        for (int i = 0; i < ncand; ++i) {
+            set(cand[i]);
+            const float ms = time_op(c, e0, e1, reps, op);
+            if (ms < 0.f) {
+                *err = true;
+                set(dflt);
+                return dflt;
+            }
+            best[i] = std::min(best[i], ms);
+        }
+    int bi = -1, di = -1;
+    for (int i = 0; i < ncand; ++i) {
+        if (cand[i] == dflt) di = i;
+        if (bi < 0 || best[i] < best[bi]) bi = i;
+    }
+    const int v = (di < 0 || best[bi] < 0.97f * best[di]) ? cand[bi] : dflt;
+    set(v);
+    return v;
+}
+
+template <class T>
+vof_status tune_levels(vof_ctx* c, int nb) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VOF_ERR_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return VOF_ERR_CUDA;
+    }
+    static const int kFlat[4] = {64, 128, 256, 512};
+    static const int kRestrict[3] = {64, 128, 256};
+    bool err = false;
+    const int nl = (int)c->lv.size();
+    for (int l = 1; l + 1 < nl && !err; ++l) {
+        if (c->tail_level > 0 && l >= c->tail_level) break;  // visited by one tail launch
+        Level& L = c->lv[l];
+        if (L.d.nx % 2 != 0) continue;
+        const bool flat = L.d.nx < FLAT_NX;
+        const bool half = sizeof(T) == sizeof(float) && L.bxh;
+        // about 2M cell updates per timing, at least 3 and at most 20 pass pairs
+        const long long cells = std::max(1LL, (long long)L.ncells * nb);
+        const int reps = (int)std::min(20LL, std::max(3LL, (2LL << 20) / cells));
+        ShapeKey k{dev, L.d.nx, L.d.ny, L.d.nz, nb, (int)sizeof(T), half ? 1 : 0, 0};
+        int v = 0;
+        if (cached_shape(k, &v)) {
+            (flat ? L.pass_block : L.pass_kchunk) = v;
+        } else {
+            auto pair = [&] {
+                mg_rbgs<T>(c, L, 0, 0);
+                mg_rbgs<T>(c, L, 1, 0);
+            };
+            if (flat) {
+                v = pick(c, e0, e1, reps, kFlat, 4, 256, [&](int b) { L.pass_block = b; }, pair, &err);
+            } else {
+                // the level's z chunk divided by 1, 2, 4 (built in) or 8
+                int kz[4];
+                for (int i = 0; i < 4; ++i) {
+                    kz[i] = std::max(1, (L.L.kchunk + (1 << i) - 1) >> i);
+                    // grid z extent (chunks x cases) within the launch limit
+                    if ((long long)((L.d.nz + kz[i] - 1) / kz[i]) * nb > 65535) kz[i] = L.L.kchunk;
+                }
+                v = pick(c, e0, e1, reps, kz, 4, kz[2], [&](int q) { L.pass_kchunk = q; }, pair,
+                         &err);
+            }
+            if (!err) cache_shape(k, v);
+        }
+        L.tuned = !err;
+        // the 1-D restriction from this level (FP32 coefficients, constant prolongation)
+        if (sizeof(T) == sizeof(float) && flat && !L.bxh && c->sv.mg_interp != VOF_MG_TRILINEAR &&
+            !err) {
+            k.kind = 1;
+            if (cached_shape(k, &v)) {
+                L.restrict_block = v;
+            } else {
+                const Level& C = c->lv[l + 1];
+                v = pick(c, e0, e1, 2 * reps, kRestrict, 3, 256,
+                         [&](int b) { L.restrict_block = b; },
+                         [&] { mg_restrict<T>(c, L, C); }, &err);
+                if (!err) cache_shape(k, v);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err ? VOF_ERR_CUDA : VOF_OK;
+}
+
+}  // namespace
+
+vof_status mg_tune_shapes(vof_ctx* c, int nb, long long stride, int* act_d) {
+    if (c->sv.mg_tune == VOF_TUNE_OFF || c->lv.size() < 3) return VOF_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->st, &cs) != cudaSuccess) return VOF_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return VOF_OK;  // no timing inside a capture
+    const bool mixed = c->sv.precision == VOF_PREC_MIXED_FP32;
+    if (nb <= 1) {
+        // every case's arrays are filled by its own context before a batched
+        // launch through case 0's reads them
+        for (size_t l = 1; l < c->lv.size(); ++l) {
+            if (mixed) fill_for_timing<float>(c, c->lv[l]);
+            else fill_for_timing<double>(c, c->lv[l]);
+        }
+    } else {
+        std::vector<int> on(nb, 1);
+        if (cudaMemcpyAsync(act_d, on.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess)
+            return VOF_ERR_CUDA;
+        c->bat_n = nb;
+        c->bat_stride = stride;
+        c->bat_act = act_d;
+    }
+    const vof_status st = mixed ? tune_levels<float>(c, nb) : tune_levels<double>(c, nb);
+    c->bat_n = 1;
+    c->bat_stride = 0;
+    c->bat_act = nullptr;
+    return st;
+}
+
+vof_status mg_shape_of(const vof_ctx* c, int level, int shape[4]) {
+    if (!c || !shape || level < 1 || level + 1 >= (int)c->lv.size()) return VOF_ERR_ARG;
+    const Level& L = c->lv[level];
+    if (L.d.nx % 2 != 0) return VOF_ERR_ARG;
+    const bool flat = L.d.nx < FLAT_NX;
+    const bool mixed = c->sv.precision == VOF_PREC_MIXED_FP32;
+    shape[0] = flat ? 0 : pass_kchunk_of(L);
+    shape[1] = flat ? L.pass_block : 0;
+    shape[2] = (mixed && flat && !L.bxh && c->sv.mg_interp != VOF_MG_TRILINEAR) ? L.restrict_block : 0;
+    shape[3] = L.tuned ? 1 : 0;
+    return VOF_OK;
+}
+
+vof_status mg_set_shape(vof_ctx* c, int level, const int shape[3]) {
+    int cur[4];
+    const vof_status st = mg_shape_of(c, level, cur);
+    if (st != VOF_OK) return st;
+    Level& L = c->lv[level];
+    auto block_ok = [](int b) { return b >= 32 && b <= 1024 && b % 32 == 0; };
+    // a value must be given exactly where the level uses one
+    if ((cur[0] == 0) != (shape[0] == 0) || (cur[1] == 0) != (shape[1] == 0) ||
+        (cur[2] == 0) != (shape[2] == 0))
+        return VOF_ERR_ARG;
+    if (shape[0] && (shape[0] < 1 || shape[0] > L.d.nz || (L.d.nz + shape[0] - 1) / shape[0] > 65535))
+        return VOF_ERR_ARG;
+    if ((shape[1] && !block_ok(shape[1])) || (shape[2] && !block_ok(shape[2]))) return VOF_ERR_ARG;
+    if (shape[0]) L.pass_kchunk = shape[0];
+    if (shape[1]) L.pass_block = shape[1];
+    if (shape[2]) L.restrict_block = shape[2];
+    L.tuned = false;
+    return VOF_OK;
+}
+
+int pass_kchunk_of(const Level& L) {
+    return L.pass_kchunk > 0 ? L.pass_kchunk : std::max(1, (L.L.kchunk + 3) / 4);
+}

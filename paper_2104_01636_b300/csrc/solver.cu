@@ -1018,6 +1018,10 @@ BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride) {
     return b;
 }
 
+vof_status batch_solve_tune(vof_ctx* m, BatchSolveState* b, long long stride) {
+    return mg_tune_shapes(m, b->nc, stride, b->act_d);
+}
+
 void batch_solve_destroy(BatchSolveState* b) {
     if (!b) return;
     if (b->act_h) cudaFreeHost(b->act_h);

@@ -185,6 +185,15 @@ struct Level {
     void* rs = nullptr;  // residual scratch for full-weighting restriction (T per cell)
     void* rho = nullptr; // cell density (T per cell), levels >= 1 with density coarsening
     Launch L;
+    // launch shape of the colour passes: a tiled pass takes pass_kchunk z
+    // planes per thread (0: a quarter of L.kchunk), a narrow level's 1-D
+    // blocks pass_block threads, and the 1-D restriction from it
+    // restrict_block threads (mg_tune_shapes, vof_mg_set_shape; every shape
+    // computes the same cells the same way)
+    int pass_kchunk = 0;
+    int pass_block = 256;
+    int restrict_block = 256;
+    bool tuned = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -504,6 +513,17 @@ void rho_apply_A_dot(vof_ctx* c, const float* p, float* q, int slot);
 void mg_coarsen_beta_from64(vof_ctx* c, const Level& fine, const Level& coarse);
 // FP16 copies of the FP32 coefficients of the levels that carry them
 void mg_half_coefficients(vof_ctx* c);
+// times the candidate launch shapes of the coarse levels' colour passes and
+// narrow restrictions as launched for nb cases (nb > 1: the batched solve
+// through this context, cases `stride` bytes apart, act_d their flags) and
+// keeps the fastest in the levels; fills the levels' arrays with finite
+// values first (the solve writes them before it reads them)
+vof_status mg_tune_shapes(vof_ctx* c, int nb, long long stride, int* act_d);
+// vof_mg_shape / vof_mg_set_shape for a context
+vof_status mg_shape_of(const vof_ctx* c, int level, int shape[4]);
+vof_status mg_set_shape(vof_ctx* c, int level, const int shape[3]);
+// z planes per thread of a tiled colour pass of level L
+int pass_kchunk_of(const Level& L);
 
 // coarse tail (k_mg_tail.cu)
 vof_status mg_tail_setup(vof_ctx* c, int level, const TailProg* from_zero, const TailProg* from_x,
@@ -557,6 +577,8 @@ vof_status solve_mixed_batch(vof_ctx* m, int nc, long long stride, const int* ru
                              vof_ctx* const* cases);
 BatchSolveState* batch_solve_create(vof_ctx* m, int nc, long long stride);
 void batch_solve_destroy(BatchSolveState* bs);
+// mg_tune_shapes for the batched launches of bs's cases through m
+vof_status batch_solve_tune(vof_ctx* m, BatchSolveState* bs, long long stride);
 // whether the batched solve supports contexts made with this solver
 bool batch_solve_eligible(const vof_ctx* c);
 // step_pre in two parts: the CFL reduction and its readback, launched without
