@@ -344,7 +344,8 @@ vof_status vof_host_join(vof_ctx* ctx);
  * flag is cleared again, so the context stays usable. Synchronous. */
 vof_status vof_diag_wait_timeout(vof_ctx* ctx);
 
-/* Number of CUDA kernels this context has launched since creation. */
+/* Number of CUDA kernels this context has launched since creation (the
+ * launch-shape timing of solver->mg_tune included). */
 vof_status vof_launch_count(const vof_ctx* ctx, long long* n);
 
 /* Launch shape of multigrid level `level`'s colour passes (solver->mg_tune):
