@@ -149,9 +149,11 @@ typedef struct {
                              the level's own arrays and the fastest kept;
                              the result is cached per level shape and batch
                              for the process. VOF_TUNE_OFF: the built-in
-                             shapes. The passes are pointwise, so every
-                             shape gives the same bits (vof_mg_shape reports
-                             the choice). */
+                             shapes (the request server's contexts always
+                             use these: shapes timed for a context alone
+                             lose when several share the GPU). The passes
+                             are pointwise, so every shape gives the same
+                             bits (vof_mg_shape reports the choice). */
 } vof_solver;
 
 enum { VOF_COARSEN_FACE_MEAN = 0, VOF_COARSEN_DENSITY_MEAN = 1 };

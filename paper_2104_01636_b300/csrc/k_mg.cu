@@ -1291,15 +1291,15 @@ float time_op(vof_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int reps, F op) {
     return ms;
 }
 
-// the fastest of the candidate values set by `set` (two interleaved rounds,
-// the minimum of each candidate's times), or the built-in value `dflt`
-// unless a candidate beats it by 3%; dflt on any error
+// the fastest of the candidate values set by `set` (three interleaved
+// rounds, the minimum of each candidate's times), or the built-in value
+// `dflt` unless a candidate beats it by 5%; dflt on any error
 template <class S, class F>
 int pick(vof_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int reps, const int* cand, int ncand,
          int dflt, S set, F op, bool* err) {
     float best[8];
     for (int i = 0; i < ncand; ++i) best[i] = 1e30f;
-    for (int round = 0; round < 2; ++round)
+    for (int round = 0; round < 3; ++round)
         for (int i = 0; i < ncand; ++i) {
             set(cand[i]);
             const float ms = time_op(c, e0, e1, reps, op);
@@ -1315,7 +1315,7 @@ int pick(vof_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int reps, const int* cand, 
         if (cand[i] == dflt) di = i;
         if (bi < 0 || best[i] < best[bi]) bi = i;
     }
-    const int v = (di < 0 || best[bi] < 0.97f * best[di]) ? cand[bi] : dflt;
+    const int v = (di < 0 || best[bi] < 0.95f * best[di]) ? cand[bi] : dflt;
     set(v);
     return v;
 }
