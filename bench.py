@@ -788,7 +788,8 @@ def main():
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         nz_s = sample_planes(args.steps, args.warmup)
-        cb = cpu_baseline(args, steps=2, nz_s=nz_s)
+        # three sample steps: 10-30 s of host work for the samples sample_planes() picks
+        cb = cpu_baseline(args, steps=3, nz_s=nz_s)
         cb["oracle_full_duct"] = oracle_full_record()
         progress("CPU baseline done")
         if args.cpu_one_thread:
