@@ -67,7 +67,7 @@ __global__ void k_if_list(Dims d, const double* __restrict__ a, unsigned char* _
 }
 
 // Pass 2: normal and FP64 plane constant of every listed interface cell, in
-// three launches so that the plane constants run in warps of one branch:
+// four launches so that the plane constants run in warps of one branch:
 //  (a) the normal (stored in the plane) and the estimated branch of every
 //      listed cell, counted per branch;
 //  (b) (one block) the start of each branch's range in if_perm;
