@@ -65,7 +65,7 @@ def test_binding_struct_layouts_match_header(tmp_path):
         "vof_phys": (vd.CPhys, ["rho_l", "conv_scheme", "kappa_exact"]),
         "vof_solver": (vd.CSolver, ["precision", "rtol", "mg_omega", "coarse_tol", "mg_interp",
                                     "mg_coarsen", "mg_cycle", "mg_w_depth", "graph",
-                                    "nu_fine", "ssf_solves"]),
+                                    "nu_fine", "ssf_solves", "mg_tail", "mg_tune"]),
         "vof_report": (vd.CReport, ["iters", "res0", "hf_fallbacks", "ms"]),
         "vof_request": (vd.CRequest, ["kind", "grid", "phys", "solver", "n_steps", "dt", "step0",
                                       "alpha", "p", "b"]),
@@ -91,6 +91,39 @@ def test_binding_struct_layouts_match_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f in fields:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_constants_match_header(tmp_path):
+    """The binding's enum and status constants have the header's values."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    consts = {
+        "VOF_PREC_FP64": vd.PREC_FP64, "VOF_PREC_MIXED_FP32": vd.PREC_MIXED_FP32,
+        "VOF_COARSEN_FACE_MEAN": vd.COARSEN_FACE_MEAN,
+        "VOF_COARSEN_DENSITY_MEAN": vd.COARSEN_DENSITY_MEAN,
+        "VOF_CYCLE_W": vd.CYCLE_W, "VOF_CYCLE_V": vd.CYCLE_V,
+        "VOF_GRAPH_AUTO": vd.GRAPH_AUTO, "VOF_GRAPH_OFF": vd.GRAPH_OFF,
+        "VOF_GRAPH_CYCLE": vd.GRAPH_CYCLE,
+        "VOF_TAIL_LAUNCHES": vd.TAIL_LAUNCHES, "VOF_TAIL_CLUSTER": vd.TAIL_CLUSTER,
+        "VOF_TUNE_AUTO": vd.TUNE_AUTO, "VOF_TUNE_OFF": vd.TUNE_OFF,
+        "VOF_REQ_STEP": vd.REQ_STEP, "VOF_REQ_SOLVE": vd.REQ_SOLVE,
+        "VOF_ENSEMBLE_AUTO": vd.VofEnsemble.AUTO, "VOF_ENSEMBLE_STREAMS": vd.VofEnsemble.STREAMS,
+        "VOF_ENSEMBLE_BATCHED": vd.VofEnsemble.BATCHED,
+    }
+    consts.update({name: code for code, name in vd.STATUS.items()})
+    lines = ['#include <stdio.h>', '#include "vof.h"', "int main(void){"]
+    lines += [f'printf("{n} %d\\n", (int)({n}));' for n in consts]
+    lines.append("return 0;}")
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = dict((n, int(v)) for n, v in (line.split() for line in out.splitlines()))
+    assert got == consts
 
 
 def test_library_binds_its_own_symbols():
